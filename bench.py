@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: ms per spin-2 synthesis + analysis pair at lmax 4095.
+
+Workload (the configuration the headline metric is quoted on): Gauss-Legendre
+grid nlat = 4096, nlon = 8191 (prime ring length), lmax = mmax = 4095, spin 2,
+one (E, B) pair with C_l = 1/(l+1)^2 and zero monopole/dipole, seed 2.  One
+step = one synthesis (E, B -> Q, U) followed by one analysis (Q, U -> E, B)
+through the C ABI, inputs resident in HBM.  Inputs (268 MB of a_lm, 537 MB
+of maps) are larger than L2 (129 MB), so no flush is needed between steps.
+
+Reported:
+  value / ms_per_step  device time per pair (CUDA events, max over ranks)
+  forms                both the mixed form and the plain FP64 form
+  roofline             dominant Legendre kernel: algorithmic flops / its
+                       event-timed duration against the pipe it runs on
+  e2e                  same pair through the public API from pinned host a_lm,
+                       host<->device copies inside the timed region
+  cpu_baseline         the FP64 CPU oracle on a bounded sample, host cores
+  accuracy             GPU results against the oracle on that sample
+
+--impl reference runs the oracle (the reference for this build) instead.
+Multi-GPU: replicas only (one independent transform pair per rank).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LMAX, NLAT, NLON, SPIN, SEED = 4095, 4096, 8191, 2, 2
+METRIC = "ms per synth+analysis at lmax 4095 (spin 2, GL 4096x8191)"
+CONFIG = {"workload": "spin-2 synthesis+analysis, Gauss-Legendre nlat=4096 nlon=8191, lmax=mmax=4095, "
+                      "E/B a_lm C_l=1/(l+1)^2 seed 2",
+          "lmax": LMAX, "nlat": NLAT, "nlon": NLON, "spin": SPIN, "ncomp": 1,
+          "l2_policy": "inputs larger than L2 (268 MB a_lm, 537 MB maps)", "parallelism": "replicas"}
+SMS = 152
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def flops_per_triple(spin, ncomp):
+    """Algorithmic flops per (m, l, ring-pair) step: recursion + accumulation."""
+    return (10 + 16 * ncomp) if spin else (3 + 4 * ncomp)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) > 8 for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if os.environ.get("SHT_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle ---
+def oracle_sample(target_s=15.0, gpu_out=None):
+    """Time the FP64 CPU oracle on a bounded sample of the workload and
+    extrapolate to one full synthesis + analysis pair (ms).
+
+    Synthesis: every ring costs the same (all m, all l, one DFT), so the
+    sample is a set of rings spread over latitude, scaled by nrings / sample.
+    Analysis: per-m cost varies with lmax - m; the sample is m values evenly
+    spaced over 0..mmax, scaled by (mmax + 1) / sample.  The sample size is
+    grown from a probe so the whole leg takes about target_s seconds.
+    If gpu_out is given, the sampled outputs are compared with it.
+    """
+    import numpy as np
+
+    import oracle
+    from paper_1303_4945_gb300 import inputs
+
+    th, w = oracle.gauss_nodes(NLAT)
+    rings = oracle.Rings(th, np.full(NLAT, NLON), np.zeros(NLAT), w * 2 * np.pi / NLON)
+    alm = inputs.spin2_eb(SEED, LMAX)
+    cores = os.cpu_count() or 1
+
+    if gpu_out is not None:
+        ana_in = gpu_out["maps"]  # the GPU's own synthesis output: compares the analyses on equal input
+    else:
+        rng = np.random.default_rng(7)
+        ana_in = [rng.standard_normal(rings.npix) for _ in range(2)]
+
+    def run(nr, nmv):
+        rsel = np.unique(np.linspace(0, NLAT - 1, nr).round().astype(int))
+        msel = np.unique(np.linspace(0, LMAX, nmv).round().astype(int))
+        t0 = time.perf_counter()
+        maps = oracle.synthesis(SPIN, LMAX, LMAX, alm, rings, rings_sel=rsel)
+        t1 = time.perf_counter()
+        back = oracle.analysis(SPIN, LMAX, LMAX, ana_in, rings, m_sel=msel)
+        t2 = time.perf_counter()
+        return rsel, msel, maps, back, t1 - t0, t2 - t1
+
+    # probe with a tiny sample, then size the real one
+    rsel, msel, _, _, ts, ta = run(max(2, cores // 4), 2)
+    per_ring = ts / len(rsel)
+    per_m = ta / len(msel)
+    nr = int(max(len(rsel), min(NLAT, 0.5 * target_s / max(per_ring, 1e-6))))
+    nm = int(max(2, min(LMAX + 1, 0.5 * target_s / max(per_m, 1e-6))))
+    rsel, msel, maps, back, ts, ta = run(nr, nm)
+    full_ms = 1e3 * (ts * NLAT / len(rsel) + ta * (LMAX + 1) / len(msel))
+    res = {"value": full_ms, "unit": "ms", "cores": cores, "kind": "oracle",
+           "sample": f"synthesis of {len(rsel)} of {NLAT} rings ({ts:.1f} s) and analysis of {len(msel)} of "
+                     f"{LMAX + 1} m values ({ta:.1f} s), evenly spaced, extrapolated to one full pair"}
+    acc = None
+    if gpu_out is not None:
+        acc = {}
+        o = rings.ofs
+        for name, g_maps, o_maps in (("Q", gpu_out["maps"][0], maps[0]), ("U", gpu_out["maps"][1], maps[1])):
+            idx = np.concatenate([np.arange(o[y], o[y] + NLON) for y in rsel])
+            d = g_maps[idx] - o_maps[idx]
+            acc[f"synthesis_{name}_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(o_maps[idx]))
+        l, m = inputs.lm_arrays(LMAX, LMAX)
+        sel = np.isin(m, msel)
+        for name, g_a, o_a in (("E", gpu_out["alm"][0], back[0]), ("B", gpu_out["alm"][1], back[1])):
+            d = g_a[sel] - o_a[sel]
+            acc[f"analysis_{name}_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(o_a[sel]))
+        acc["sample"] = f"{len(rsel)} rings, {len(msel)} m values"
+    return res, acc
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the oracle itself, timed on host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    per_step = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        res, _ = oracle_sample(target_s=max(5.0, 60.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            per_step.append(res["value"])
+            base = res
+    ms = statistics.median(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU ---
+def time_form(sht, torch, plan, alm_d, maps_d, out_d, steps, warmup, world, stream):
+    for _ in range(warmup):
+        sht.sht_execute(plan, sht.SHT_SYNTHESIS, alm_d, maps_d, 0, stream)
+        sht.sht_execute(plan, sht.SHT_ANALYSIS, out_d, maps_d, 0, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    plan.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        sht.sht_execute(plan, sht.SHT_SYNTHESIS, alm_d, maps_d, 0, stream)
+        sht.sht_execute(plan, sht.SHT_ANALYSIS, out_d, maps_d, 0, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1) / steps
+    stages = plan.profile_read()
+    plan.profile(False)
+    return max_over_ranks(ms, world), stages
+
+
+def roofline_for(stages, plan, spin, precision, peaks, steps):
+    """Dominant Legendre kernel vs the pipe it runs on."""
+    import numpy as np  # noqa: F401
+
+    syn_ms, syn_n = stages["legendre_synthesis"]
+    ana_ms, ana_n = stages["legendre_analysis"]
+    name, t_ms, n = ("legendre_synthesis", syn_ms, syn_n) if syn_ms >= ana_ms else ("legendre_analysis", ana_ms, ana_n)
+    per_launch_ms = t_ms / max(n, 1)
+    flops = plan.triples(0) * flops_per_triple(spin, 1)
+    clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    if precision == "fp64":
+        peak = SMS * 4 * clock / 1e12  # 2 FP64 FMA lanes per SM per clock (measured DFMA rate)
+        how = "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x sm_max clock"
+    else:
+        peak = SMS * 256 * clock / 1e12  # 128 FP32 FMA lanes per SM per clock
+        how = "FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x sm_max clock"
+    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": how,
+            "algorithmic_flops_per_launch": flops, "ms_per_launch": per_launch_ms}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1303_4945_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1303_4945_gb300 import inputs, sht
+
+    peaks = _peaks()
+    geom = sht.sht_geom_gauss(NLAT, NLON)
+    lay = sht.sht_alm_create(LMAX, LMAX)
+    forms = {"fp64": sht.SHT_FP64}
+    try:
+        sht.sht_plan_create(sht.sht_geom_gauss(8, 15), sht.sht_alm_create(7, 7), 2, 1, sht.SHT_MIXED)
+        forms["mixed"] = sht.SHT_MIXED
+    except sht.ShtError:
+        pass
+    alm_h = inputs.spin2_eb(SEED, LMAX)
+    stream = torch.cuda.current_stream()
+    alm_d = [torch.from_numpy(a).cuda() for a in alm_h]
+    maps_d = [torch.empty(geom.npix, dtype=torch.float64, device="cuda") for _ in range(2)]
+    out_d = [torch.empty_like(a) for a in alm_d]
+
+    results = {}
+    outputs = {}
+    sampler = ClockSampler(local)
+    for name, prec in forms.items():
+        plan = sht.sht_plan_create(geom, lay, SPIN, 1, prec)
+        if name == list(forms)[-1]:
+            sampler.start()
+        ms, stages = time_form(sht, torch, plan, alm_d, maps_d, out_d, args.steps, args.warmup, world, stream)
+        if name == list(forms)[-1]:
+            clocks = sampler.stop()
+        results[name] = {"ms_per_step": ms, "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+                         "roofline": roofline_for(stages, plan, SPIN, name, peaks, args.steps),
+                         "triples": plan.triples(0), "workspace_bytes": plan.workspace()}
+        outputs[name] = {"maps": [m.cpu().numpy() for m in maps_d], "alm": [a.cpu().numpy() for a in out_d]}
+        del plan
+    head = "mixed" if "mixed" in forms else "fp64"
+    # mixed vs FP64 on the full output
+    if "mixed" in forms:
+        def rl2(a, b):
+            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        results["mixed"]["vs_fp64_rel_l2"] = {
+            "Q": rl2(outputs["mixed"]["maps"][0], outputs["fp64"]["maps"][0]),
+            "U": rl2(outputs["mixed"]["maps"][1], outputs["fp64"]["maps"][1]),
+            "E": rl2(outputs["mixed"]["alm"][0], outputs["fp64"]["alm"][0]),
+            "B": rl2(outputs["mixed"]["alm"][1], outputs["fp64"]["alm"][1])}
+
+    # end to end through the public API from pinned host memory
+    plan = sht.sht_plan_create(geom, lay, SPIN, 1, forms[head])
+    host_in = [torch.from_numpy(a).pin_memory() for a in alm_h]
+    host_out = [torch.empty(a.shape, dtype=torch.complex128).pin_memory() for a in alm_h]
+    for it in range(args.warmup + args.steps):
+        if it == args.warmup:
+            torch.cuda.synchronize()
+            barrier(world)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        for d, h in zip(alm_d, host_in):
+            d.copy_(h, non_blocking=True)
+        sht.sht_execute(plan, sht.SHT_SYNTHESIS, alm_d, maps_d, 0, stream)
+        sht.sht_execute(plan, sht.SHT_ANALYSIS, out_d, maps_d, 0, stream)
+        for d, h in zip(out_d, host_out):
+            h.copy_(d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    nbytes = sum(a.nbytes for a in alm_h)
+    del plan
+
+    line = {"metric": METRIC, "value": results[head]["ms_per_step"] / world, "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": results[head]["ms_per_step"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2" if head == "mixed" else "f64", "data": "synthetic", "config": CONFIG,
+            "form": head, "roofline": results[head]["roofline"], "clocks": clocks,
+            "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": 5 * args.steps, "forms": results}
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        cb, acc = oracle_sample(args.cpu_seconds, gpu_out=outputs[head])
+        line["cpu_baseline"] = cb
+        line["accuracy_vs_oracle_sample"] = acc
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

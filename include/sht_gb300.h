@@ -1,0 +1,211 @@
+/*
+ * sht_gb300.h -- C ABI of the GB300 (sm_103a) spherical harmonic transform library.
+ *
+ * The problem statement follows Reinecke & Seljebotn 2013, "Libsharp --
+ * spherical harmonic transforms revisited", Sect. 2:
+ *
+ *   synthesis (Eq. syn_used)
+ *     p_xy = sum_{m=-lmax}^{lmax} sum_{l>=|m|} sa_lm  sLambda_lm(theta_y)
+ *            exp(i m phi0_y + 2 pi i m x / Nphi_y)
+ *   analysis (Eq. ana_used)
+ *     sa_lm = sum_y sum_x p_xy w_y sLambda_lm(theta_y) exp(-i m phi0_y - 2 pi i m x / Nphi_y)
+ *
+ * with sLambda_lm(theta) = sY_lm(theta, 0) = (-1)^m sqrt((2l+1)/(4 pi)) d^l_{-m,s}(theta)
+ * (Sect. 4.1), on any iso-latitude grid (Sect. 2 and 4.4): ring y has
+ * colatitude theta_y, Nphi_y equidistant pixels starting at azimuth phi0_y,
+ * a quadrature weight w_y, and its pixels live at map[ofs_y + x * stride_y].
+ *
+ * Conventions (no C99 complex type appears in this interface, Sect. 3.1):
+ *  - a_lm are complex numbers stored as interleaved (re, im) doubles, only for
+ *    m >= 0; for a listed m the coefficient a_lm sits at complex index
+ *    mstart[m_index] + l * stride (l = m..lmax).  The default layout is the
+ *    triangular m-major one, index m (2 lmax + 1 - m) / 2 + l.
+ *  - Maps are real doubles.  The imaginary part of a_l0 is ignored on input
+ *    and written as 0 on output (real fields).
+ *  - spin s != 0: ncomp counts (E, B) pairs.  alm[2k], alm[2k+1] are E and B,
+ *    map[2k], map[2k+1] are Q and U, with
+ *        sa = -(E + iB),  (-s)a = -(-1)^s (E - iB),  Q + iU = sum sa_lm sY_lm.
+ *    spin 0: alm[k] and map[k], k < ncomp.
+ *  - All a_lm and map pointers passed to sht_execute are DEVICE pointers on
+ *    the device that was current when the plan was made; the arrays of
+ *    pointers themselves are host memory.  The caller owns these buffers.
+ *  - Geometry, a_lm descriptor and plan handles are owned by the library
+ *    until the matching *_destroy call.  A plan copies what it needs from the
+ *    geometry and a_lm descriptors, which may be destroyed right after.
+ *  - Every function returns SHT_OK (0) or a negative error code; no
+ *    exceptions cross this boundary.  sht_strerror() names the code and
+ *    sht_last_error() gives a message for the last failure on this thread.
+ *
+ * This header is shared by the C/C++ caller and the Python binding; it names
+ * no CUDA or torch type (streams are passed as void*).
+ */
+#ifndef SHT_GB300_H
+#define SHT_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SHT_API __attribute__((visibility("default")))
+#else
+#define SHT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SHT_OK 0
+#define SHT_ERR_INVALID_ARG -1  /* a size, index, pointer or enum is out of range */
+#define SHT_ERR_UNSUPPORTED -2  /* valid request the library does not implement (e.g. spin > lmax, an FFT length it cannot factor) */
+#define SHT_ERR_OOM -3          /* device or host allocation failed */
+#define SHT_ERR_CUDA -4         /* a CUDA runtime call or kernel launch failed */
+#define SHT_ERR_TIMEOUT -5      /* a bounded device-side wait gave up */
+
+/* ---- enums ------------------------------------------------------------- */
+#define SHT_ECP_FEJER1 0 /* theta_n = (n + 1/2) pi / nlat, n = 0..nlat-1 (Sect. 4.4.1) */
+#define SHT_ECP_FEJER2 1 /* theta_n = n pi / (nlat + 1),  n = 1..nlat */
+#define SHT_ECP_CC 2     /* theta_n = n pi / (nlat - 1),  n = 0..nlat-1 (Clenshaw-Curtis) */
+
+#define SHT_FP64 0  /* recursion and accumulation in IEEE double */
+#define SHT_MIXED 1 /* recursion and accumulation in compensated FP32 pairs; FP64 kept for tables, start values and FFT */
+
+#define SHT_SYNTHESIS 0         /* a_lm -> map, Eq. syn_used */
+#define SHT_ANALYSIS 1          /* map -> a_lm, Eq. ana_used (with the ring weights) */
+#define SHT_ADJOINT_SYNTHESIS 2 /* map -> a_lm, Y^T p: analysis with all weights 1 (Sect. 4.5) */
+#define SHT_ADJOINT_ANALYSIS 3  /* a_lm -> map, W Y a: synthesis times the ring weights (Sect. 4.5) */
+
+#define SHT_ADD_OUTPUT 1   /* add the result to the output arrays instead of overwriting them */
+#define SHT_NO_POLAR_OPT 2 /* evaluate every (m, ring) term, skipping none (Sect. 3.3) */
+
+typedef struct sht_geom_s *sht_geom_t;
+typedef struct sht_alm_s *sht_alm_t;
+typedef struct sht_plan_s *sht_plan_t;
+
+/* ---- geometry (Sect. 2, Sect. 4.4) -------------------------------------- */
+
+/*
+ * General iso-latitude grid; partial coverage is allowed (any subset of rings).
+ * theta[nrings] in (0, pi) or [0, pi]; nphi[nrings] >= 1; phi0[nrings] radians;
+ * ofs[nrings] index of pixel 0 of the ring in each map; stride[nrings] pixel
+ * stride (may be NULL: all 1); weight[nrings] quadrature weight per pixel
+ * (may be NULL: all 1; the user is responsible for correct weights, Sect. 4.4).
+ * Rings whose colatitudes mirror each other (theta' = pi - theta within 1e-12
+ * rad) and have equal nphi are processed as north/south pairs.
+ * Host arrays, copied.  Errors: SHT_ERR_INVALID_ARG.
+ */
+SHT_API int sht_geom_general(int nrings, const double *theta, const int *nphi, const double *phi0,
+                     const int64_t *ofs, const int *stride, const double *weight, sht_geom_t *out);
+
+/*
+ * Gauss-Legendre grid (Sect. 4.4, used throughout Sect. 5): nlat rings at the
+ * roots of P_nlat, north to south, nlon pixels each, phi0 = 0, contiguous
+ * ring-major map (ofs = y * nlon), weight = Gauss weight * 2 pi / nlon.
+ */
+SHT_API int sht_geom_gauss(int nlat, int nlon, sht_geom_t *out);
+
+/*
+ * ECP grid (Sect. 4.4.1): kind SHT_ECP_FEJER1 / FEJER2 / CC, nlat rings,
+ * nlon pixels each, phi0 = 0, contiguous ring-major map, weights of
+ * Fejer's first / second rule or Clenshaw-Curtis times 2 pi / nlon.
+ */
+SHT_API int sht_geom_ecp(int kind, int nlat, int nlon, sht_geom_t *out);
+
+/*
+ * HEALPix grid (named in Sect. 1 and 4.4; ring layout of Gorski et al. 2005):
+ * 4 nside - 1 rings, RING pixel order, polar rings Nphi = 4i with
+ * phi0 = pi/(4i), equatorial rings Nphi = 4 nside with phi0 = pi/(4 nside) for
+ * even (i - nside) and 0 for odd, weight 4 pi / (12 nside^2) per pixel.
+ */
+SHT_API int sht_geom_healpix(int nside, sht_geom_t *out);
+
+/* Partial coverage: a new geometry holding rings[0..nsel-1] of g (pixel offsets kept). */
+SHT_API int sht_geom_subset(sht_geom_t g, int nsel, const int *rings, sht_geom_t *out);
+
+/* Ring count, total pixel span (max over rings of ofs + (nphi-1)*stride + 1) and number of ring pairs. */
+SHT_API int sht_geom_info(sht_geom_t g, int *nrings, int64_t *npix, int *npairs);
+
+/* Copy out the per-ring description (any pointer may be NULL). */
+SHT_API int sht_geom_rings(sht_geom_t g, double *theta, int *nphi, double *phi0, int64_t *ofs,
+                   int *stride, double *weight);
+
+SHT_API void sht_geom_destroy(sht_geom_t g);
+
+/* ---- a_lm layout (any subset of m may be listed, e.g. a round-robin share, Sect. 4.2) */
+
+/*
+ * lmax >= 0, 0 <= mmax <= lmax.  nm = number of listed m (mval == NULL: all
+ * m = 0..mmax, nm ignored).  mval[nm] distinct values in [0, mmax];
+ * mstart[nm] (NULL: triangular layout over the listed m, see above);
+ * stride = complex stride in l (>= 1).
+ */
+SHT_API int sht_alm_create(int lmax, int mmax, int nm, const int *mval, const int64_t *mstart, int stride,
+                   sht_alm_t *out);
+
+/* Number of complex entries an array must hold for this layout. */
+SHT_API int sht_alm_size(sht_alm_t a, int64_t *ncomplex);
+
+SHT_API void sht_alm_destroy(sht_alm_t a);
+
+/* ---- plan and execution -------------------------------------------------- */
+
+/*
+ * Plan a transform on the current CUDA device: spin s (|s| <= lmax,
+ * |s| <= 64), ncomp simultaneous transforms of identical type (1..16; Sect. 3.2),
+ * precision SHT_FP64 or SHT_MIXED.  Builds, on the device, the recursion
+ * coefficient tables for every listed m and l (Sect. 4.1), the ring-pair
+ * list, the polar-optimisation ranges (Sect. 3.3) and the ring FFT plans.
+ * Errors: SHT_ERR_INVALID_ARG, SHT_ERR_UNSUPPORTED (e.g. a ring length the FFT
+ * cannot handle), SHT_ERR_OOM, SHT_ERR_CUDA.
+ */
+SHT_API int sht_plan_create(sht_geom_t geom, sht_alm_t alm, int spin, int ncomp, int precision,
+                    sht_plan_t *out);
+
+/*
+ * Run one transform of the planned kind on stream cuda_stream (a cudaStream_t,
+ * NULL = legacy default stream).  type is one of SHT_SYNTHESIS, SHT_ANALYSIS,
+ * SHT_ADJOINT_SYNTHESIS, SHT_ADJOINT_ANALYSIS; alm[] / map[] hold ncomp
+ * (spin 0) or 2 ncomp (spin != 0) device pointers.  Inputs are read, outputs
+ * overwritten (or accumulated with SHT_ADD_OUTPUT); pixels and a_lm entries
+ * outside the geometry / layout are not touched.  Asynchronous: returns after
+ * the launches are queued.  Calls that share a plan must not overlap (they use
+ * the plan's workspace).  Errors: SHT_ERR_INVALID_ARG, SHT_ERR_CUDA.
+ */
+SHT_API int sht_execute(sht_plan_t plan, int type, double *const *alm, double *const *map, int flags,
+                void *cuda_stream);
+
+/* Bytes of device workspace the plan holds (tables + phase arrays). */
+SHT_API int sht_plan_workspace(sht_plan_t plan, int64_t *bytes);
+
+/*
+ * Exact algorithmic work of one transform of this plan: the number of
+ * (m, l, ring-pair) recursion steps after the polar cut (flags as for
+ * sht_execute; SHT_NO_POLAR_OPT counts every step).
+ */
+SHT_API int sht_plan_triples(sht_plan_t plan, int flags, int64_t *triples);
+
+SHT_API void sht_plan_destroy(sht_plan_t plan);
+
+/* ---- measurement ----------------------------------------------------------
+ * Sect. 5.2 times whole transforms by wall clock; these two calls report the
+ * device time of each kernel stage instead.  While profiling is on,
+ * sht_execute records a CUDA event pair on its stream around every kernel it
+ * launches (stage 0 Legendre synthesis, 1 FFT synthesis, 2 FFT analysis,
+ * 3 Legendre analysis, 4 tile reduction of the analysis).  enable = 1 starts
+ * (and clears) the record, 0 stops it.  sht_plan_profile_read waits for the
+ * recorded events, then writes for each stage s < SHT_NSTAGES the summed
+ * milliseconds ms[s] and the number of launches count[s], and clears the
+ * record.  Errors: SHT_ERR_INVALID_ARG, SHT_ERR_CUDA.
+ */
+#define SHT_NSTAGES 5
+SHT_API int sht_plan_profile(sht_plan_t plan, int enable);
+SHT_API int sht_plan_profile_read(sht_plan_t plan, double *ms, int64_t *count);
+
+/* ---- errors --------------------------------------------------------------- */
+SHT_API const char *sht_strerror(int code);
+SHT_API const char *sht_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHT_GB300_H */

@@ -101,15 +101,18 @@ def lambda_(s: int, m: int, lmax: int, theta: float) -> np.ndarray:
 class Rings:
     """Iso-latitude ring description with unit pixel stride (Sect. 2)."""
 
-    def __init__(self, theta, nphi, phi0, weight):
+    def __init__(self, theta, nphi, phi0, weight, ofs=None):
         self.theta = np.ascontiguousarray(theta, dtype=np.float64)
         self.nphi = np.ascontiguousarray(nphi, dtype=np.int32)
         self.phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
         self.weight = np.ascontiguousarray(weight, dtype=np.float64)
-        self.ofs = np.zeros(len(self.theta), dtype=np.int64)
-        if len(self.theta) > 1:
-            self.ofs[1:] = np.cumsum(self.nphi[:-1], dtype=np.int64)
-        self.npix = int(self.nphi.sum(dtype=np.int64))
+        if ofs is None:
+            self.ofs = np.zeros(len(self.theta), dtype=np.int64)
+            if len(self.theta) > 1:
+                self.ofs[1:] = np.cumsum(self.nphi[:-1], dtype=np.int64)
+        else:
+            self.ofs = np.ascontiguousarray(ofs, dtype=np.int64)
+        self.npix = int(np.max(self.ofs + self.nphi)) if len(self.theta) else 0
 
     @property
     def nrings(self):

@@ -1,0 +1,62 @@
+"""Build libsht_gb300.so for sm_103a with nvcc (in-tree, under _build/).
+
+Each CUDA translation unit compiles in its own nvcc process (in parallel),
+then one nvcc call links the shared library.  No cmake, no torch extension
+machinery: the library has a plain C ABI (include/sht_gb300.h).
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT, "libsht_gb300.so")
+UNITS = ["sht_host.cu", "tables.cu", "legendre_fp64.cu", "legendre_mixed.cu", "fft.cu"]
+HEADERS = ["sht_internal.h", "sht_device.cuh"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-I", os.path.join(ROOT, "include")]
+
+
+def _stale(obj: str, src: str) -> bool:
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    deps = [src] + [os.path.join(SRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "sht_gb300.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def _compile(unit: str, verbose: bool) -> str:
+    src = os.path.join(SRC, unit)
+    obj = os.path.join(OUT, unit.replace(".cu", ".o"))
+    if _stale(obj, src):
+        cmd = ["nvcc", *ARCH, *FLAGS, "-c", src, "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {unit}:\n{r.stdout}\n{r.stderr}")
+        if verbose and r.stderr:
+            sys.stderr.write(r.stderr)
+    return obj
+
+
+def build(verbose: bool = False) -> str:
+    os.makedirs(OUT, exist_ok=True)
+    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        objs = list(ex.map(lambda u: _compile(u, verbose), UNITS))
+    if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
+        cmd = ["nvcc", *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv))

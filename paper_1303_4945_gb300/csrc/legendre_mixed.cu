@@ -1,0 +1,656 @@
+// legendre_mixed.cu -- Legendre stage (Eqs. syn2, ana1) in the mixed form.
+//
+// On GB300 the FP64 pipe issues 1/64 of the FP32 rate, so this form moves
+// the whole inner loop (the recursion of Sect. 4.1 and the accumulation of
+// Fig. 1 / Fig. 2) onto the FP32 pipe in compensated "double-float" pairs
+// (value = hi + lo, two FP32 numbers).  Products use the exact FMA split
+// (Dekker / Kahan two-product), sums Knuth's two-sum; about 46 significant
+// bits survive per operation, enough for ~1e-12 after thousands of steps.
+// FP64 remains for the recursion-coefficient tables, the start values, the
+// conversion of inputs/outputs and the ring FFTs.
+//
+// Structure, ring pairing, parity split, the coupled (lp, lm) recursion for
+// spin and the analysis reduction follow legendre_fp64.cu exactly; only the
+// arithmetic type differs.  The enhanced exponent uses steps of 2^104: pairs
+// above 2^52 are scaled down every 8 steps, and nothing below 2^-52 (relative
+// to its final scale) is ever accumulated.
+#include "sht_device.cuh"
+
+namespace sht {
+
+constexpr int kScaleStep32 = 104;
+constexpr float kScaleUp32 = 0x1p+52f;
+constexpr float kScaleFactor32 = 0x1p-104f;
+
+// ---- double-float arithmetic (no contraction: *_rn intrinsics) -------------
+struct f2 {
+  float h, l;
+};
+
+__device__ __forceinline__ f2 f2_of(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ double f2_val(f2 a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // needs |a| >= |b| (or a = 0)
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// a * b as an unevaluated pair
+__device__ __forceinline__ f2 mul(f2 a, f2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return {p, e};
+}
+__device__ __forceinline__ f2 neg(f2 a) { return {-a.h, -a.l}; }
+// a b + c d, normalised
+__device__ __forceinline__ f2 dot2(f2 a, f2 b, f2 c, f2 d) {
+  const f2 p = mul(a, b), q = mul(c, d);
+  const f2 s = two_sum(p.h, q.h);
+  return fast_two_sum(s.h, __fadd_rn(__fadd_rn(p.l, q.l), s.l));
+}
+// a b + c d + e f, normalised
+__device__ __forceinline__ f2 dot3(f2 a, f2 b, f2 c, f2 d, f2 e, f2 f) {
+  const f2 p = mul(a, b), q = mul(c, d), r = mul(e, f);
+  const f2 s1 = two_sum(p.h, q.h);
+  const f2 s2 = two_sum(s1.h, r.h);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p.l, q.l), r.l), __fadd_rn(s1.l, s2.l));
+  return fast_two_sum(s2.h, lo);
+}
+// acc += w * a with a lazily carried low word (renormalised every few steps)
+__device__ __forceinline__ void acc_mul(f2 &acc, f2 w, float ah, float al) {
+  const f2 p = mul(w, {ah, al});
+  const f2 s = two_sum(acc.h, p.h);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, p.l));
+}
+__device__ __forceinline__ void renorm(f2 &a) { a = fast_two_sum(a.h, a.l); }
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  const f2 s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l));
+}
+__device__ __forceinline__ f2 sel(bool c, f2 a) { return c ? a : f2{0.f, 0.f}; }
+
+// (mant * 2^E) -> (y, scale) with value = y * 2^(104 scale), y's exponent in [-52, 52)
+__device__ __forceinline__ f2 to_scaled32(double mant, int E, int *scale) {
+  if (mant == 0.0) {
+    *scale = 0;
+    return {0.f, 0.f};
+  }
+  const int h = kScaleStep32 / 2;
+  const int sc = (E + h) >= 0 ? (E + h) / kScaleStep32 : -((-(E + h) + kScaleStep32 - 1) / kScaleStep32);
+  *scale = sc;
+  return f2_of(ldexp(mant, E - kScaleStep32 * sc));
+}
+
+struct MixArgs {
+  int lmax, spin, npairs, nm;
+  const int *mval;
+  const int64_t *coef_off;
+  const float4 *coef32;  // per (m, l): {A.h, A.l, AK.h, AK.l}, {C.h, C.l, -, -}
+  const float4 *alm32;   // [array][ncoef] {re.h, re.l, im.h, im.l}
+  int64_t ncoef;
+  const double2 *mpre;
+  const PairDev *pairs;
+  double2 *phase;
+  const int2 *syn_items;
+  const int4 *ana_items;
+  const int64_t *part_off;
+  const int *tile0;
+  double *part;
+  int ana_tiles;
+};
+
+struct Coef32 {
+  f2 a, ak, c;
+};
+__device__ __forceinline__ Coef32 ld_coef32(const float4 *p) {
+  const float4 u = __ldg(p), v = __ldg(p + 1);
+  return {{u.x, u.y}, {u.z, u.w}, {v.x, v.y}};
+}
+
+// spin-0 / spin start in the double-float representation
+__device__ __forceinline__ void start_s0(int m, const PairDev &pd, double2 pre, f2 *lc, int *scale) {
+  double mant;
+  int E;
+  start_value(m, 0, pd, pre, &mant, &E);
+  *lc = to_scaled32(mant, E, scale);
+}
+__device__ __forceinline__ void start_s(int m, int s, const PairDev &pd, double2 pre, f2 *lc, int *scale) {
+  double mant;
+  int E;
+  start_value(m, s, pd, pre, &mant, &E);
+  *lc = to_scaled32(mant, E, scale);
+}
+// ---------------------------------------------------------------------------
+// a_lm (FP64, user layout) -> double-float table indexed like the coefficients
+// ---------------------------------------------------------------------------
+__global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, const int *__restrict__ mval,
+                          const int64_t *__restrict__ mstart, const int64_t *__restrict__ coef_off, int64_t ncoef,
+                          DevPtrs alm, float4 *__restrict__ out) {
+  const int mi = blockIdx.x;
+  const int j = blockIdx.y;
+  const int m = mval[mi];
+  const int as = spin < 0 ? -spin : spin;
+  const int l0 = m > as ? m : as;
+  if (spin == 0) {
+    const double2 *src = reinterpret_cast<const double2 *>(alm.p[j]) + mstart[mi];
+    float4 *dst = out + (int64_t)j * ncoef + coef_off[mi] - l0;
+    for (int l = l0 + threadIdx.x; l <= lmax; l += blockDim.x) {
+      const double2 v = src[(int64_t)l * astride];
+      const f2 re = f2_of(v.x), im = f2_of(v.y);
+      dst[l] = make_float4(re.h, re.l, im.h, im.l);
+    }
+    return;
+  }
+  // spin: P = E + iB and M = E - iB of job j (Im of m = 0 coefficients ignored)
+  const double2 *E = reinterpret_cast<const double2 *>(alm.p[2 * j]) + mstart[mi];
+  const double2 *B = reinterpret_cast<const double2 *>(alm.p[2 * j + 1]) + mstart[mi];
+  float4 *P = out + (int64_t)(2 * j) * ncoef + coef_off[mi] - l0;
+  float4 *M = out + (int64_t)(2 * j + 1) * ncoef + coef_off[mi] - l0;
+  for (int l = l0 + threadIdx.x; l <= lmax; l += blockDim.x) {
+    double2 e = E[(int64_t)l * astride], b = B[(int64_t)l * astride];
+    if (m == 0) e.y = b.y = 0.0;
+    const f2 pr = f2_of(e.x - b.y), pi = f2_of(e.y + b.x), mr = f2_of(e.x + b.y), mi_ = f2_of(e.y - b.x);
+    P[l] = make_float4(pr.h, pr.l, pi.h, pi.l);
+    M[l] = make_float4(mr.h, mr.l, mi_.h, mi_.l);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// synthesis, spin 0
+// ---------------------------------------------------------------------------
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
+  const int2 item = a.syn_items[blockIdx.x];
+  const int mi = item.x;
+  const int p = item.y + threadIdx.x;
+  const bool valid = p < a.npairs;
+  const int m = a.mval[mi];
+  const int l0 = m, lmax = a.lmax;
+  const int64_t co = a.coef_off[mi] - l0;
+  const float4 *__restrict__ cf = a.coef32 + 2 * co;
+  const PairDev pd = a.pairs[valid ? p : 0];
+  const f2 x = f2_of(pd.x);
+  f2 lc, lp = {0.f, 0.f};
+  int scale;
+  start_s0(m, pd, a.mpre[mi], &lc, &scale);
+  if (!valid) {
+    lc = {0.f, 0.f};
+    scale = 0;
+  }
+  f2 acc[2][NJ][2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[q][j][0] = acc[q][j][1] = f2{0.f, 0.f};
+
+  auto step = [&](int l, int par, bool act) {
+    const f2 w = sel(act || scale == 0, lc);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const float4 v = __ldg(a.alm32 + (int64_t)j * a.ncoef + co + l);
+      acc_mul(acc[par][j][0], w, v.x, v.y);
+      acc_mul(acc[par][j][1], w, v.z, v.w);
+    }
+    const Coef32 c = ld_coef32(cf + 2 * l);
+    const f2 t = mul(c.a, x);
+    const f2 ln = dot2(t, lc, neg(c.c), lp);
+    lp = lc;
+    lc = ln;
+  };
+  auto renorm_all = [&]() {
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        renorm(acc[q][j][0]);
+        renorm(acc[q][j][1]);
+      }
+  };
+
+  int l = l0;
+  while (l <= lmax && __any_sync(0xffffffffu, scale < 0)) {
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        if (l <= lmax) {
+          step(l, par, false);
+          ++l;
+        }
+      }
+    }
+    if (scale < 0 && fabsf(lc.h) > kScaleUp32) {
+      lc = {lc.h * kScaleFactor32, lc.l * kScaleFactor32};
+      lp = {lp.h * kScaleFactor32, lp.l * kScaleFactor32};
+      ++scale;
+    }
+    renorm_all();
+  }
+  while (l + 7 <= lmax) {
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      step(l + k, 0, true);
+      step(l + k + 1, 1, true);
+    }
+    l += 8;
+    renorm_all();
+  }
+  for (; l + 1 <= lmax; l += 2) {
+    step(l, 0, true);
+    step(l + 1, 1, true);
+  }
+  if (l <= lmax) step(l, 0, true);
+  if (!valid) return;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const double e0 = f2_val(acc[0][j][0]), e1 = f2_val(acc[0][j][1]);
+    const double o0 = f2_val(acc[1][j][0]), o1 = f2_val(acc[1][j][1]);
+    double2 fn = make_double2(e0 + o0, e1 + o1), fs = make_double2(e0 - o0, e1 - o1);
+    if (m == 0) fn.y = fs.y = 0.0;
+    double2 *o = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
+    o[0] = fn;
+    o[1] = fs;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// synthesis, spin s: separate +s / -s recursions (see legendre_fp64.cu)
+// ---------------------------------------------------------------------------
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
+  const int2 item = a.syn_items[blockIdx.x];
+  const int mi = item.x;
+  const int p = item.y + threadIdx.x;
+  const bool valid = p < a.npairs;
+  const int m = a.mval[mi];
+  const int s = a.spin, as = s < 0 ? -s : s;
+  const int l0 = m > as ? m : as, lmax = a.lmax;
+  const int64_t co = a.coef_off[mi] - l0;
+  const float4 *__restrict__ cf = a.coef32 + 2 * co;
+  const PairDev pd = a.pairs[valid ? p : 0];
+  const f2 x = f2_of(pd.x);
+  f2 lpc, lmc, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
+  int scp, scm;
+  start_s(m, s, pd, a.mpre[mi], &lpc, &scp);
+  start_s(m, -s, pd, a.mpre[mi], &lmc, &scm);
+  if (!valid) {
+    lpc = lmc = f2{0.f, 0.f};
+    scp = scm = 0;
+  }
+  // N1 = sum P l+, N2 = sum M l-, S3 = sum (-1)^(l-l0) P l-, S4 = sum (-1)^(l-l0) M l+
+  f2 r[NJ][4][2];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[j][k][0] = r[j][k][1] = f2{0.f, 0.f};
+
+  auto step = [&](int l, int par, bool act) {
+    const f2 wp = sel(act || scp == 0, lpc), wm = sel(act || scm == 0, lmc);
+    const f2 sp = par ? neg(wp) : wp, sm = par ? neg(wm) : wm;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const float4 P = __ldg(a.alm32 + (int64_t)(2 * j) * a.ncoef + co + l);
+      const float4 M = __ldg(a.alm32 + (int64_t)(2 * j + 1) * a.ncoef + co + l);
+      acc_mul(r[j][0][0], wp, P.x, P.y);
+      acc_mul(r[j][0][1], wp, P.z, P.w);
+      acc_mul(r[j][1][0], wm, M.x, M.y);
+      acc_mul(r[j][1][1], wm, M.z, M.w);
+      acc_mul(r[j][2][0], sm, P.x, P.y);
+      acc_mul(r[j][2][1], sm, P.z, P.w);
+      acc_mul(r[j][3][0], sp, M.x, M.y);
+      acc_mul(r[j][3][1], sp, M.z, M.w);
+    }
+    const Coef32 c = ld_coef32(cf + 2 * l);
+    const f2 t = mul(c.a, x);
+    const f2 nc = neg(c.c);
+    const f2 np_ = dot3(t, lpc, c.ak, lpc, nc, lpp);
+    const f2 nm_ = dot3(t, lmc, neg(c.ak), lmc, nc, lmp);
+    lpp = lpc;
+    lpc = np_;
+    lmp = lmc;
+    lmc = nm_;
+  };
+  auto renorm_all = [&]() {
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        renorm(r[j][k][0]);
+        renorm(r[j][k][1]);
+      }
+  };
+
+  int l = l0;
+  while (l <= lmax && __any_sync(0xffffffffu, scp < 0 || scm < 0)) {
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        if (l <= lmax) {
+          step(l, par, false);
+          ++l;
+        }
+      }
+    }
+    if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
+      lpc = {lpc.h * kScaleFactor32, lpc.l * kScaleFactor32};
+      lpp = {lpp.h * kScaleFactor32, lpp.l * kScaleFactor32};
+      ++scp;
+    }
+    if (scm < 0 && fabsf(lmc.h) > kScaleUp32) {
+      lmc = {lmc.h * kScaleFactor32, lmc.l * kScaleFactor32};
+      lmp = {lmp.h * kScaleFactor32, lmp.l * kScaleFactor32};
+      ++scm;
+    }
+    renorm_all();
+  }
+  while (l + 7 <= lmax) {
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      step(l + k, 0, true);
+      step(l + k + 1, 1, true);
+    }
+    l += 8;
+    renorm_all();
+  }
+  for (; l + 1 <= lmax; l += 2) {
+    step(l, 0, true);
+    step(l + 1, 1, true);
+  }
+  if (l <= lmax) step(l, 0, true);
+  if (!valid) return;
+
+  const double sig = (as & 1) ? -1.0 : 1.0;
+  const double h0 = ((l0 + m) & 1) ? -0.5 : 0.5;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const double n1r = f2_val(r[j][0][0]), n1i = f2_val(r[j][0][1]);
+    const double n2r = f2_val(r[j][1][0]), n2i = f2_val(r[j][1][1]);
+    const double s3r = f2_val(r[j][2][0]), s3i = f2_val(r[j][2][1]);
+    const double s4r = f2_val(r[j][3][0]), s4i = f2_val(r[j][3][1]);
+    const double ar = n1r + sig * n2r, ai = n1i + sig * n2i;
+    const double br = sig * n2r - n1r, bi = sig * n2i - n1i;
+    const double cr = s3r + sig * s4r, ci = s3i + sig * s4i;
+    const double dr = sig * s4r - s3r, di = sig * s4i - s3i;
+    double2 qn = make_double2(-0.5 * ar, -0.5 * ai);
+    double2 un = make_double2(0.5 * bi, -0.5 * br);
+    double2 qs = make_double2(-h0 * cr, -h0 * ci);
+    double2 us = make_double2(h0 * di, -h0 * dr);
+    if (m == 0) qn.y = qs.y = un.y = us.y = 0.0;
+    double2 *oq = a.phase + (((size_t)(2 * j) * a.nm + mi) * a.npairs + p) * 2;
+    double2 *ou = a.phase + (((size_t)(2 * j + 1) * a.nm + mi) * a.npairs + p) * 2;
+    oq[0] = qn;
+    oq[1] = qs;
+    ou[0] = un;
+    ou[1] = us;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// analysis (see legendre_fp64.cu for the tile / chunk / reduction scheme)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ f2 shfl_xor_f2(f2 v, int mask) {
+  return {__shfl_xor_sync(0xffffffffu, v.h, mask), __shfl_xor_sync(0xffffffffu, v.l, mask)};
+}
+
+// 32 double-float values per lane -> lane v holds the warp sum of value v
+__device__ __forceinline__ f2 warp_reduce_scatter32(f2 (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool up = lane & w;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const f2 send = up ? v[i] : v[i + w];
+      const f2 keep = up ? v[i + w] : v[i];
+      v[i] = f2_add(keep, shfl_xor_f2(send, w));
+    }
+  }
+  return v[0];
+}
+
+template <int NJ, int PPT, bool SPIN>
+__global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
+  constexpr int V = (SPIN ? 4 : 2) * NJ, LC = 32 / V;
+  __shared__ f2 red[kAnaThreads / 32][32];
+  const int4 item = a.ana_items[blockIdx.x];
+  const int mi = item.x, tile = item.y;
+  const int m = a.mval[mi];
+  const int s = a.spin, as = s < 0 ? -s : s;
+  const int l0 = m > as ? m : as, lmax = a.lmax, nl = lmax - l0 + 1;
+  const float4 *__restrict__ cf = a.coef32 + 2 * (a.coef_off[mi] - l0);
+  double *outp = a.part + a.part_off[mi] + (int64_t)(tile - a.tile0[mi]) * nl * V;
+  const double sg0 = ((l0 + m) & 1) ? -1.0 : 1.0;
+
+  f2 x[PPT], lpc[PPT], lmc[PPT], lpp[PPT], lmp[PPT];
+  int scp[PPT], scm[PPT];
+  // spin 0: g[k][j][0..1] = G_N +- G_S (complex) ; spin: Q+-, U+- (complex)
+  f2 g[PPT][NJ][SPIN ? 4 : 2][2];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int p = tile * (kAnaThreads * PPT) + threadIdx.x + k * kAnaThreads;
+    const bool valid = p < a.npairs;
+    const PairDev pd = a.pairs[valid ? p : 0];
+    x[k] = f2_of(pd.x);
+    if (SPIN) {
+      start_s(m, s, pd, a.mpre[mi], &lpc[k], &scp[k]);
+      start_s(m, -s, pd, a.mpre[mi], &lmc[k], &scm[k]);
+    } else {
+      start_s0(m, pd, a.mpre[mi], &lpc[k], &scp[k]);
+      lmc[k] = f2{0.f, 0.f};
+      scm[k] = 0;
+    }
+    if (!valid) {
+      lpc[k] = lmc[k] = f2{0.f, 0.f};
+      scp[k] = scm[k] = 0;
+    }
+    lpp[k] = lmp[k] = f2{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (!SPIN) {
+        double2 gn = make_double2(0, 0), gs = make_double2(0, 0);
+        if (valid) {
+          const double2 *gp = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
+          gn = gp[0];
+          if (pd.south) gs = gp[1];
+        }
+        g[k][j][0][0] = f2_of(gn.x + gs.x);
+        g[k][j][0][1] = f2_of(gn.y + gs.y);
+        g[k][j][1][0] = f2_of(gn.x - gs.x);
+        g[k][j][1][1] = f2_of(gn.y - gs.y);
+      } else {
+        double2 qn = make_double2(0, 0), qs = make_double2(0, 0), un = make_double2(0, 0), us = make_double2(0, 0);
+        if (valid) {
+          const double2 *gq = a.phase + (((size_t)(2 * j) * a.nm + mi) * a.npairs + p) * 2;
+          const double2 *gu = a.phase + (((size_t)(2 * j + 1) * a.nm + mi) * a.npairs + p) * 2;
+          qn = gq[0];
+          un = gu[0];
+          if (pd.south) {
+            qs = gq[1];
+            us = gu[1];
+          }
+        }
+        // W+ = GQ + i GU, W- = GQ - i GU (north; south ones times (-1)^(l0+m))
+        g[k][j][0][0] = f2_of(qn.x - un.y);
+        g[k][j][0][1] = f2_of(qn.y + un.x);
+        g[k][j][1][0] = f2_of(qn.x + un.y);
+        g[k][j][1][1] = f2_of(qn.y - un.x);
+        g[k][j][2][0] = f2_of(sg0 * (qs.x - us.y));
+        g[k][j][2][1] = f2_of(sg0 * (qs.y + us.x));
+        g[k][j][3][0] = f2_of(sg0 * (qs.x + us.y));
+        g[k][j][3][1] = f2_of(sg0 * (qs.y - us.x));
+      }
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int lb = l0; lb <= lmax; lb += LC) {
+    f2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = f2{0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < LC; ++q) {
+      const int l = lb + q;
+      if (l <= lmax) {
+        const Coef32 c = ld_coef32(cf + 2 * l);
+        const f2 nc = neg(c.c);
+        const bool even = ((l - l0) & 1) == 0;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          const f2 wp = sel(scp[k] == 0, lpc[k]);
+          if (!SPIN) {
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              const f2 gr = even ? g[k][j][0][0] : g[k][j][1][0];
+              const f2 gi = even ? g[k][j][0][1] : g[k][j][1][1];
+              acc_mul(v[q * V + 2 * j], wp, gr.h, gr.l);
+              acc_mul(v[q * V + 2 * j + 1], wp, gi.h, gi.l);
+            }
+            const f2 t = mul(c.a, x[k]);
+            const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
+            lpp[k] = lpc[k];
+            lpc[k] = ln;
+          } else {
+            const f2 wm = sel(scm[k] == 0, lmc[k]);
+            const f2 sp = even ? wp : neg(wp), sm = even ? wm : neg(wm);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              // T1 = W+_N l+ + (+-) W+_S l-,  T2 = W-_N l- + (+-) W-_S l+
+              const int o = q * V + 4 * j;
+              acc_mul(v[o + 0], wp, g[k][j][0][0].h, g[k][j][0][0].l);
+              acc_mul(v[o + 0], sm, g[k][j][2][0].h, g[k][j][2][0].l);
+              acc_mul(v[o + 1], wp, g[k][j][0][1].h, g[k][j][0][1].l);
+              acc_mul(v[o + 1], sm, g[k][j][2][1].h, g[k][j][2][1].l);
+              acc_mul(v[o + 2], wm, g[k][j][1][0].h, g[k][j][1][0].l);
+              acc_mul(v[o + 2], sp, g[k][j][3][0].h, g[k][j][3][0].l);
+              acc_mul(v[o + 3], wm, g[k][j][1][1].h, g[k][j][1][1].l);
+              acc_mul(v[o + 3], sp, g[k][j][3][1].h, g[k][j][3][1].l);
+            }
+            const f2 t = mul(c.a, x[k]);
+            const f2 np_ = dot3(t, lpc[k], c.ak, lpc[k], nc, lpp[k]);
+            const f2 nm_ = dot3(t, lmc[k], neg(c.ak), lmc[k], nc, lmp[k]);
+            lpp[k] = lpc[k];
+            lpc[k] = np_;
+            lmp[k] = lmc[k];
+            lmc[k] = nm_;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if (scp[k] < 0 && fabsf(lpc[k].h) > kScaleUp32) {
+        lpc[k] = {lpc[k].h * kScaleFactor32, lpc[k].l * kScaleFactor32};
+        lpp[k] = {lpp[k].h * kScaleFactor32, lpp[k].l * kScaleFactor32};
+        ++scp[k];
+      }
+      if (scm[k] < 0 && fabsf(lmc[k].h) > kScaleUp32) {
+        lmc[k] = {lmc[k].h * kScaleFactor32, lmc[k].l * kScaleFactor32};
+        lmp[k] = {lmp[k].h * kScaleFactor32, lmp[k].l * kScaleFactor32};
+        ++scm[k];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) renorm(v[i]);
+    const f2 wsum = warp_reduce_scatter32(v);
+    red[warp][lane] = wsum;
+    __syncthreads();
+    if (warp == 0) {
+      f2 t = red[0][lane];
+#pragma unroll
+      for (int w = 1; w < kAnaThreads / 32; ++w) t = f2_add(t, red[w][lane]);
+      const int q = lane / V;
+      if (lb + q <= lmax) outp[(int64_t)(lb - l0) * V + lane] = f2_val(t);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+static MixArgs make_mix(const sht_plan_s *P, int polar) {
+  MixArgs a;
+  a.lmax = P->lmax;
+  a.spin = P->spin;
+  a.npairs = P->npairs;
+  a.nm = P->nm;
+  a.mval = P->d_mval;
+  a.coef_off = P->d_coef_off;
+  a.coef32 = P->d_coef32;
+  a.alm32 = P->d_alm32;
+  a.ncoef = P->ncoef;
+  a.mpre = P->d_mpre;
+  a.pairs = P->d_pairs;
+  a.phase = P->d_phase;
+  a.syn_items = P->d_syn_items[polar];
+  a.ana_items = P->d_ana_items[polar];
+  a.part_off = P->d_ana_part_off[polar];
+  a.tile0 = P->d_ana_tile0[polar];
+  a.part = P->d_part;
+  a.ana_tiles = P->ana_tiles;
+  return a;
+}
+
+cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st) {
+  if (P->nm > 0) {
+    dim3 g(P->nm, P->spin ? P->njobs_pad : P->nmaps_pad);
+    alm_to_f2<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->nmaps_pad, P->astride, P->d_mval, P->d_mstart,
+                                 P->d_coef_off, P->ncoef, alm, P->d_alm32);
+  }
+  const int n = P->nsyn_items[polar];
+  if (n == 0) return cudaGetLastError();
+  MixArgs a = make_mix(P, polar);
+  const int nj = P->njobs_pad;
+  if (P->spin == 0) {
+    switch (nj) {
+      case 1: mix_syn_s0<1><<<n, kSynTile, 0, st>>>(a); break;
+      case 2: mix_syn_s0<2><<<n, kSynTile, 0, st>>>(a); break;
+      case 4: mix_syn_s0<4><<<n, kSynTile, 0, st>>>(a); break;
+      case 8: mix_syn_s0<8><<<n, kSynTile, 0, st>>>(a); break;
+      default: mix_syn_s0<16><<<n, kSynTile, 0, st>>>(a); break;
+    }
+  } else {
+    switch (nj) {
+      case 1: mix_syn_spin<1><<<n, kSynTile, 0, st>>>(a); break;
+      case 2: mix_syn_spin<2><<<n, kSynTile, 0, st>>>(a); break;
+      case 4: mix_syn_spin<4><<<n, kSynTile, 0, st>>>(a); break;
+      default: mix_syn_spin<8><<<n, kSynTile, 0, st>>>(a); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &, int polar, cudaStream_t st) {
+  const int n = P->nana_items[polar];
+  if (n == 0) return cudaSuccess;
+  MixArgs a = make_mix(P, polar);
+  const int nj = P->njobs_pad;
+  if (P->spin == 0) {
+    switch (nj) {
+      case 1: mix_ana<1, 4, false><<<n, kAnaThreads, 0, st>>>(a); break;
+      case 2: mix_ana<2, 4, false><<<n, kAnaThreads, 0, st>>>(a); break;
+      case 4: mix_ana<4, 2, false><<<n, kAnaThreads, 0, st>>>(a); break;
+      case 8: mix_ana<8, 2, false><<<n, kAnaThreads, 0, st>>>(a); break;
+      default: mix_ana<16, 2, false><<<n, kAnaThreads, 0, st>>>(a); break;
+    }
+  } else {
+    switch (nj) {
+      case 1: mix_ana<1, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
+      case 2: mix_ana<2, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
+      case 4: mix_ana<4, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
+      default: mix_ana<8, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sht

@@ -1,0 +1,902 @@
+// sht_host.cu -- C ABI entry points: geometry, a_lm layout, plans, execution.
+//
+// Host code only plans (ring pairing, polar-cut ranges, work lists, FFT
+// factorisations) and launches; every step of a transform runs in the CUDA
+// kernels of legendre_*.cu and fft.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <numeric>
+
+#include "sht_internal.h"
+
+using namespace sht;
+
+// ----------------------------------------------------------------------------
+// Errors
+// ----------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      if (e_ == cudaErrorMemoryAllocation) return fail(SHT_ERR_OOM, "%s: %s", #expr, cudaGetErrorString(e_)); \
+      return fail(SHT_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));               \
+    }                                                                                   \
+  } while (0)
+
+extern "C" const char *sht_strerror(int code) {
+  switch (code) {
+    case SHT_OK: return "ok";
+    case SHT_ERR_INVALID_ARG: return "invalid argument";
+    case SHT_ERR_UNSUPPORTED: return "unsupported";
+    case SHT_ERR_OOM: return "out of memory";
+    case SHT_ERR_CUDA: return "CUDA error";
+    case SHT_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+extern "C" const char *sht_last_error(void) { return g_last_error.c_str(); }
+
+// ----------------------------------------------------------------------------
+// Geometry
+// ----------------------------------------------------------------------------
+static const long double kPiL = 3.141592653589793238462643383279502884L;
+
+extern "C" int sht_geom_general(int nrings, const double *theta, const int *nphi, const double *phi0,
+                                const int64_t *ofs, const int *stride, const double *weight,
+                                sht_geom_t *out) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nrings < 1 || !theta || !nphi || !phi0 || !ofs)
+    return fail(SHT_ERR_INVALID_ARG, "nrings < 1 or a required array is NULL");
+  for (int i = 0; i < nrings; ++i) {
+    if (!(theta[i] >= 0.0 && theta[i] <= M_PI)) return fail(SHT_ERR_INVALID_ARG, "theta[%d] outside [0, pi]", i);
+    if (nphi[i] < 1) return fail(SHT_ERR_INVALID_ARG, "nphi[%d] < 1", i);
+    if (ofs[i] < 0) return fail(SHT_ERR_INVALID_ARG, "ofs[%d] < 0", i);
+    if (stride && stride[i] < 1) return fail(SHT_ERR_INVALID_ARG, "stride[%d] < 1", i);
+    if (!isfinite(phi0[i])) return fail(SHT_ERR_INVALID_ARG, "phi0[%d] not finite", i);
+    if (weight && !isfinite(weight[i])) return fail(SHT_ERR_INVALID_ARG, "weight[%d] not finite", i);
+  }
+  auto *g = new sht_geom_s;
+  g->nrings = nrings;
+  g->theta.assign(theta, theta + nrings);
+  g->nphi.assign(nphi, nphi + nrings);
+  g->phi0.assign(phi0, phi0 + nrings);
+  g->ofs.assign(ofs, ofs + nrings);
+  g->stride.assign(nrings, 1);
+  if (stride) g->stride.assign(stride, stride + nrings);
+  g->weight.assign(nrings, 1.0);
+  if (weight) g->weight.assign(weight, weight + nrings);
+  *out = g;
+  return SHT_OK;
+}
+
+// Gauss-Legendre nodes by Newton's method in theta.  P_n(1 - u) is evaluated
+// with the recursion written for u = 2 sin^2(theta/2) and the differences
+// D_k = P_k - P_{k-1}, which stays accurate next to the poles; at a root the
+// Gauss weight is 2 sin^2(theta) / (n P_{n-1})^2.
+static void gl_eval(int n, long double th, long double *pn, long double *dn) {
+  long double h = sinl(0.5L * th);
+  long double u = 2.0L * h * h;
+  long double p = 1.0L - u, d = -u;  // P_1, D_1
+  if (n == 0) {
+    *pn = 1.0L;
+    *dn = 1.0L;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    d = (k * d - (2 * k + 1) * u * p) / (k + 1);
+    p += d;
+  }
+  *pn = p;
+  *dn = d;
+}
+
+static void gl_nodes(int n, std::vector<double> &th, std::vector<double> &w) {
+  th.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    long double t = kPiL * (4 * i + 3) / (4 * n + 2);
+    bool mid = (2 * i + 1 == n);
+    if (mid) {
+      t = 0.5L * kPiL;
+    } else {
+      for (int it = 0; it < 64; ++it) {
+        long double pn, dn;
+        gl_eval(n, t, &pn, &dn);
+        long double h = sinl(0.5L * t);
+        long double step = pn * sinl(t) / (n * (dn - 2.0L * h * h * pn));
+        t -= step;
+        if (fabsl(step) <= 1e-18L * t && it > 1) break;
+      }
+    }
+    long double pn, dn;
+    gl_eval(n, t, &pn, &dn);
+    long double q = n * (pn - dn), s = sinl(t);
+    double wi = (double)(2.0L * s * s / (q * q));
+    th[i] = (double)t;
+    w[i] = wi;
+    th[n - 1 - i] = mid ? (double)t : (double)(kPiL - t);
+    w[n - 1 - i] = wi;
+  }
+}
+
+static int make_regular(const std::vector<double> &th, const std::vector<double> &wq, int nlon,
+                        sht_geom_t *out) {
+  int n = (int)th.size();
+  std::vector<int> nphi(n, nlon);
+  std::vector<double> phi0(n, 0.0), w(n);
+  std::vector<int64_t> ofs(n);
+  for (int i = 0; i < n; ++i) {
+    ofs[i] = (int64_t)i * nlon;
+    w[i] = wq[i] * 2.0 * M_PI / nlon;
+  }
+  return sht_geom_general(n, th.data(), nphi.data(), phi0.data(), ofs.data(), nullptr, w.data(), out);
+}
+
+extern "C" int sht_geom_gauss(int nlat, int nlon, sht_geom_t *out) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nlat < 1 || nlon < 1) return fail(SHT_ERR_INVALID_ARG, "nlat, nlon must be >= 1");
+  std::vector<double> th, w;
+  gl_nodes(nlat, th, w);
+  return make_regular(th, w, nlon, out);
+}
+
+// ECP colatitudes and quadrature weights on [-1, 1] (Fejer 1, Fejer 2,
+// Clenshaw-Curtis), by the cosine sums of the respective rules.
+extern "C" int sht_geom_ecp(int kind, int nlat, int nlon, sht_geom_t *out) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nlat < 1 || nlon < 1) return fail(SHT_ERR_INVALID_ARG, "nlat, nlon must be >= 1");
+  std::vector<double> th(nlat), w(nlat);
+  if (kind == SHT_ECP_FEJER1) {
+    const int N = nlat;
+    for (int i = 0; i < N; ++i) {
+      long double t = kPiL * (2 * i + 1) / (2 * N), acc = 0.0L;
+      for (int k = 1; 2 * k <= N; ++k) acc += cosl(2 * k * t) / (4.0L * k * k - 1.0L);
+      th[i] = (double)t;
+      w[i] = (double)((1.0L - 2.0L * acc) * 2.0L / N);
+    }
+  } else if (kind == SHT_ECP_FEJER2) {
+    const int N = nlat + 1;
+    for (int i = 1; i < N; ++i) {
+      long double t = kPiL * i / N, acc = 0.0L;
+      for (int k = 1; 2 * k <= N; ++k) acc += sinl((2 * k - 1) * t) / (2 * k - 1);
+      th[i - 1] = (double)t;
+      w[i - 1] = (double)(4.0L * sinl(t) * acc / N);
+    }
+  } else if (kind == SHT_ECP_CC) {
+    if (nlat < 2) return fail(SHT_ERR_INVALID_ARG, "Clenshaw-Curtis needs nlat >= 2");
+    const int N = nlat - 1;
+    for (int i = 0; i <= N; ++i) {
+      long double t = kPiL * i / N, acc = 0.0L;
+      for (int k = 1; 2 * k <= N; ++k) acc += ((2 * k == N) ? 1.0L : 2.0L) * cosl(2 * k * t) / (4.0L * k * k - 1.0L);
+      th[i] = (double)t;
+      w[i] = (double)(((i == 0 || i == N) ? 1.0L : 2.0L) * (1.0L - acc) / N);
+    }
+  } else {
+    return fail(SHT_ERR_INVALID_ARG, "unknown ECP kind %d", kind);
+  }
+  return make_regular(th, w, nlon, out);
+}
+
+extern "C" int sht_geom_healpix(int nside, sht_geom_t *out) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nside < 1 || nside > (1 << 20)) return fail(SHT_ERR_INVALID_ARG, "nside out of range");
+  const int nr = 4 * nside - 1;
+  std::vector<double> th(nr), p0(nr), w(nr, 4.0 * M_PI / (12.0 * (double)nside * nside));
+  std::vector<int> np(nr);
+  std::vector<int64_t> ofs(nr);
+  int64_t o = 0;
+  for (int r = 0; r < nr; ++r) {
+    int i = r + 1;                                // ring number from the north pole
+    int k = (i <= 2 * nside) ? i : 4 * nside - i;  // mirrored ring number
+    long double t;
+    if (k < nside) {  // polar cap: 1 - z = k^2 / (3 nside^2) = 2 sin^2(theta/2)
+      t = 2.0L * asinl(k / (sqrtl(6.0L) * nside));
+      np[r] = 4 * k;
+      p0[r] = (double)(kPiL / (4 * k));
+    } else {  // equatorial belt: z = 4/3 - 2k / (3 nside)
+      t = acosl((4.0L * nside - 2.0L * k) / (3.0L * nside));
+      np[r] = 4 * nside;
+      p0[r] = ((k - nside) % 2 == 0) ? (double)(kPiL / (4 * nside)) : 0.0;
+    }
+    th[r] = (i <= 2 * nside) ? (double)t : (double)(kPiL - t);
+    ofs[r] = o;
+    o += np[r];
+  }
+  return sht_geom_general(nr, th.data(), np.data(), p0.data(), ofs.data(), nullptr, w.data(), out);
+}
+
+extern "C" int sht_geom_subset(sht_geom_t g, int nsel, const int *rings, sht_geom_t *out) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g || nsel < 1 || !rings) return fail(SHT_ERR_INVALID_ARG, "bad subset arguments");
+  std::vector<char> seen(g->nrings, 0);
+  std::vector<double> th, p0, w;
+  std::vector<int> np, st;
+  std::vector<int64_t> ofs;
+  for (int k = 0; k < nsel; ++k) {
+    int r = rings[k];
+    if (r < 0 || r >= g->nrings) return fail(SHT_ERR_INVALID_ARG, "ring %d out of range", r);
+    if (seen[r]) return fail(SHT_ERR_INVALID_ARG, "ring %d listed twice", r);
+    seen[r] = 1;
+    th.push_back(g->theta[r]);
+    p0.push_back(g->phi0[r]);
+    w.push_back(g->weight[r]);
+    np.push_back(g->nphi[r]);
+    st.push_back(g->stride[r]);
+    ofs.push_back(g->ofs[r]);
+  }
+  return sht_geom_general(nsel, th.data(), np.data(), p0.data(), ofs.data(), st.data(), w.data(), out);
+}
+
+extern "C" int sht_geom_info(sht_geom_t g, int *nrings, int64_t *npix, int *npairs);
+
+extern "C" int sht_geom_rings(sht_geom_t g, double *theta, int *nphi, double *phi0, int64_t *ofs,
+                              int *stride, double *weight) {
+  if (!g) return fail(SHT_ERR_INVALID_ARG, "geometry is NULL");
+  for (int i = 0; i < g->nrings; ++i) {
+    if (theta) theta[i] = g->theta[i];
+    if (nphi) nphi[i] = g->nphi[i];
+    if (phi0) phi0[i] = g->phi0[i];
+    if (ofs) ofs[i] = g->ofs[i];
+    if (stride) stride[i] = g->stride[i];
+    if (weight) weight[i] = g->weight[i];
+  }
+  return SHT_OK;
+}
+
+extern "C" void sht_geom_destroy(sht_geom_t g) { delete g; }
+
+// Ring pairing: rings y, y' with theta_y' = pi - theta_y (to 1e-12) and the
+// same nphi share one Legendre evaluation through the parity relation
+// sLambda_lm(pi - theta) = (-1)^(l+m) (-s)Lambda_lm(theta).  Pairs are ordered
+// from the poles towards the equator so that the polar cut removes a prefix.
+static void pair_rings(const sht_geom_s *g, std::vector<int> &pn, std::vector<int> &ps) {
+  std::vector<int> idx(g->nrings);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    return g->theta[a] < g->theta[b] || (g->theta[a] == g->theta[b] && a < b);
+  });
+  pn.clear();
+  ps.clear();
+  int i = 0, j = g->nrings - 1;
+  while (i <= j) {
+    int a = idx[i], b = idx[j];
+    if (i == j) {
+      pn.push_back(a);
+      ps.push_back(-1);
+      break;
+    }
+    double d = g->theta[a] + g->theta[b] - M_PI;
+    if (fabs(d) <= 1e-12 && g->nphi[a] == g->nphi[b] && g->theta[a] < 0.5 * M_PI) {
+      pn.push_back(a);
+      ps.push_back(b);
+      ++i;
+      --j;
+    } else if (d < 0) {  // ring a has no southern mirror
+      pn.push_back(a);
+      ps.push_back(-1);
+      ++i;
+    } else {
+      pn.push_back(b);
+      ps.push_back(-1);
+      --j;
+    }
+  }
+  // order by distance from the nearest pole
+  std::vector<int> ord(pn.size());
+  std::iota(ord.begin(), ord.end(), 0);
+  auto pd = [&](int k) { double t = g->theta[pn[k]]; return std::min(t, M_PI - t); };
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return pd(a) < pd(b); });
+  std::vector<int> pn2, ps2;
+  for (int k : ord) {
+    pn2.push_back(pn[k]);
+    ps2.push_back(ps[k]);
+  }
+  pn.swap(pn2);
+  ps.swap(ps2);
+}
+
+extern "C" int sht_geom_info(sht_geom_t g, int *nrings, int64_t *npix, int *npairs) {
+  if (!g) return fail(SHT_ERR_INVALID_ARG, "geometry is NULL");
+  if (nrings) *nrings = g->nrings;
+  if (npix) {
+    int64_t mx = 0;
+    for (int i = 0; i < g->nrings; ++i)
+      mx = std::max<int64_t>(mx, g->ofs[i] + (int64_t)(g->nphi[i] - 1) * g->stride[i] + 1);
+    *npix = mx;
+  }
+  if (npairs) {
+    std::vector<int> pn, ps;
+    pair_rings(g, pn, ps);
+    *npairs = (int)pn.size();
+  }
+  return SHT_OK;
+}
+
+// ----------------------------------------------------------------------------
+// a_lm layout
+// ----------------------------------------------------------------------------
+extern "C" int sht_alm_create(int lmax, int mmax, int nm, const int *mval, const int64_t *mstart,
+                              int stride, sht_alm_t *out) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (lmax < 0 || mmax < 0 || mmax > lmax || lmax > 65535)
+    return fail(SHT_ERR_INVALID_ARG, "need 0 <= mmax <= lmax <= 65535");
+  if (stride < 1) return fail(SHT_ERR_INVALID_ARG, "stride < 1");
+  auto *a = new sht_alm_s;
+  a->lmax = lmax;
+  a->mmax = mmax;
+  a->stride = stride;
+  if (!mval) {
+    a->nm = mmax + 1;
+    for (int m = 0; m <= mmax; ++m) a->mval.push_back(m);
+  } else {
+    if (nm < 1 || nm > mmax + 1) {
+      delete a;
+      return fail(SHT_ERR_INVALID_ARG, "nm out of range");
+    }
+    std::vector<char> seen(mmax + 1, 0);
+    for (int i = 0; i < nm; ++i) {
+      if (mval[i] < 0 || mval[i] > mmax || seen[mval[i]]) {
+        delete a;
+        return fail(SHT_ERR_INVALID_ARG, "mval[%d] invalid or repeated", i);
+      }
+      seen[mval[i]] = 1;
+      a->mval.push_back(mval[i]);
+    }
+    a->nm = nm;
+  }
+  if (mstart) {
+    for (int i = 0; i < a->nm; ++i) {
+      if (mstart[i] + (int64_t)a->mval[i] * stride < 0) {
+        delete a;
+        return fail(SHT_ERR_INVALID_ARG, "mstart[%d] gives a negative index", i);
+      }
+      a->mstart.push_back(mstart[i]);
+    }
+  } else {
+    // triangular m-major over the listed m: entries l = m..lmax follow each other
+    int64_t o = 0;
+    for (int i = 0; i < a->nm; ++i) {
+      int m = a->mval[i];
+      a->mstart.push_back(o - (int64_t)m * stride);
+      o += (int64_t)(lmax + 1 - m) * stride;
+    }
+  }
+  *out = a;
+  return SHT_OK;
+}
+
+extern "C" int sht_alm_size(sht_alm_t a, int64_t *n) {
+  if (!a || !n) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  int64_t mx = 0;
+  for (int i = 0; i < a->nm; ++i)
+    mx = std::max<int64_t>(mx, a->mstart[i] + (int64_t)a->lmax * a->stride + 1);
+  *n = mx;
+  return SHT_OK;
+}
+
+extern "C" void sht_alm_destroy(sht_alm_t a) { delete a; }
+
+// ----------------------------------------------------------------------------
+// FFT planning (lengths, factorisations, Rader / Bluestein tables)
+// ----------------------------------------------------------------------------
+static bool factor_small(int n, std::vector<int> &rad) {
+  rad.clear();
+  while (n % 4 == 0) {
+    rad.push_back(4);
+    n /= 4;
+  }
+  if (n % 2 == 0) {
+    rad.push_back(2);
+    n /= 2;
+  }
+  for (int p = 3; p <= 31 && n > 1; p += 2) {
+    while (n % p == 0) {
+      rad.push_back(p);
+      n /= p;
+    }
+  }
+  return n == 1 && rad.size() <= 24;
+}
+
+static bool is_prime(int n) {
+  if (n < 2) return false;
+  for (int d = 2; (int64_t)d * d <= n; ++d)
+    if (n % d == 0) return false;
+  return true;
+}
+
+static int64_t powmod(int64_t b, int64_t e, int64_t m) {
+  int64_t r = 1;
+  b %= m;
+  while (e > 0) {
+    if (e & 1) r = r * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return r;
+}
+
+static int primitive_root(int p) {
+  std::vector<int> qs;
+  int n = p - 1;
+  for (int d = 2; (int64_t)d * d <= n; ++d)
+    if (n % d == 0) {
+      qs.push_back(d);
+      while (n % d == 0) n /= d;
+    }
+  if (n > 1) qs.push_back(n);
+  for (int g = 2; g < p; ++g) {
+    bool ok = true;
+    for (int q : qs)
+      if (powmod(g, (p - 1) / q, p) == 1) {
+        ok = false;
+        break;
+      }
+    if (ok) return g;
+  }
+  return -1;
+}
+
+template <class T>
+static int dev_upload(sht_plan_s *P, const std::vector<T> &h, const T **d) {
+  void *ptr = nullptr;
+  CUDA_TRY(cudaMalloc(&ptr, std::max<size_t>(1, h.size() * sizeof(T))));
+  P->fft_allocs.push_back(ptr);
+  P->workspace += h.size() * sizeof(T);
+  if (!h.empty()) CUDA_TRY(cudaMemcpy(ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *d = (const T *)ptr;
+  return SHT_OK;
+}
+
+static std::vector<double2> twiddles(int len) {
+  std::vector<double2> w(len);
+  for (int k = 0; k < len; ++k) {
+    long double a = -2.0L * kPiL * k / len;
+    w[k] = make_double2((double)cosl(a), (double)sinl(a));
+  }
+  return w;
+}
+
+static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scratch_dev) {
+  memset(&fp, 0, sizeof(fp));
+  fp.n = n;
+  std::vector<int> rad;
+  int rc;
+  if (n <= kFftMaxLen && factor_small(n, rad)) {
+    fp.kind = 0;
+    fp.len = n;
+  } else if (is_prime(n) && n - 1 <= kFftMaxLen && factor_small(n - 1, rad)) {
+    fp.kind = 1;
+    fp.len = n - 1;
+  } else {
+    int M = 1;
+    while (M < 2 * n - 1) M *= 2;
+    if (M > kFftMaxLen || !factor_small(M, rad))
+      return fail(SHT_ERR_UNSUPPORTED, "ring length %d: no FFT of size <= %d available", n, kFftMaxLen);
+    fp.kind = 2;
+    fp.len = M;
+  }
+  fp.nrad = (int)rad.size();
+  for (int i = 0; i < fp.nrad; ++i) fp.rad[i] = rad[i];
+  if ((rc = dev_upload(P, twiddles(fp.len), &fp.w)) != SHT_OK) return rc;
+
+  if (fp.kind == 1) {
+    const int g = primitive_root(n);
+    const int L = n - 1;
+    std::vector<int> pin(L), inv(n, 0);
+    int64_t ginv = powmod(g, n - 2, n);
+    int64_t a = 1, b = 1;
+    std::vector<double2> kern(L);
+    for (int q = 0; q < L; ++q) {
+      pin[q] = (int)a;     // g^q
+      inv[b] = q;          // g^{-q} = b
+      long double ang = -2.0L * kPiL * (long double)b / n;
+      kern[q] = make_double2((double)cosl(ang), (double)sinl(ang));
+      a = a * g % n;
+      b = b * ginv % n;
+    }
+    if ((rc = dev_upload(P, pin, &fp.perm_in)) != SHT_OK) return rc;
+    if ((rc = dev_upload(P, inv, &fp.inv_out)) != SHT_OK) return rc;
+    const double2 *dk;
+    if ((rc = dev_upload(P, kern, &dk)) != SHT_OK) return rc;
+    std::vector<double2> zero(L);
+    const double2 *ds;
+    if ((rc = dev_upload(P, zero, &ds)) != SHT_OK) return rc;
+    fp.spec = ds;
+    CUDA_TRY(cudaMemcpy(scratch_dev, &fp, sizeof(fp), cudaMemcpyHostToDevice));
+    CUDA_TRY(launch_fft_spectrum(&fp, scratch_dev, dk, (double2 *)ds, L, 1.0 / L, 0));
+    CUDA_TRY(cudaDeviceSynchronize());
+  } else if (fp.kind == 2) {
+    const int M = fp.len;
+    std::vector<double2> chirp(n), h(M, make_double2(0.0, 0.0));
+    for (int k = 0; k < n; ++k) {
+      int64_t q = ((int64_t)k * k) % (2 * (int64_t)n);  // e^{-pi i k^2 / n} depends on k^2 mod 2n
+      long double ang = -kPiL * (long double)q / n;
+      chirp[k] = make_double2((double)cosl(ang), (double)sinl(ang));
+      double2 c = make_double2(chirp[k].x, -chirp[k].y);
+      h[k] = c;
+      if (k > 0) h[M - k] = c;
+    }
+    if ((rc = dev_upload(P, chirp, &fp.chirp)) != SHT_OK) return rc;
+    const double2 *dh;
+    if ((rc = dev_upload(P, h, &dh)) != SHT_OK) return rc;
+    std::vector<double2> zero(M);
+    const double2 *ds;
+    if ((rc = dev_upload(P, zero, &ds)) != SHT_OK) return rc;
+    fp.spec = ds;
+    CUDA_TRY(cudaMemcpy(scratch_dev, &fp, sizeof(fp), cudaMemcpyHostToDevice));
+    CUDA_TRY(launch_fft_spectrum(&fp, scratch_dev, dh, (double2 *)ds, M, 1.0 / M, 0));
+    CUDA_TRY(cudaDeviceSynchronize());
+  }
+  return SHT_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Plans
+// ----------------------------------------------------------------------------
+static void free_plan(sht_plan_s *P) {
+  if (!P) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(P->device);
+  void *ptrs[] = {P->d_pairs, P->d_pair_rings, P->d_rings, P->d_mval, P->d_mstart, P->d_coef_off,
+                  P->d_coef, P->d_coef32, P->d_alm32, P->d_pm64, P->d_mpre, P->d_minv, P->d_phase, P->d_part, P->d_fft,
+                  P->d_pair_fft};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (int k = 0; k < 2; ++k) {
+    if (P->d_syn_items[k]) cudaFree(P->d_syn_items[k]);
+    if (P->d_syn_first[k]) cudaFree(P->d_syn_first[k]);
+    if (P->d_ana_items[k]) cudaFree(P->d_ana_items[k]);
+    if (P->d_ana_part_off[k]) cudaFree(P->d_ana_part_off[k]);
+    if (P->d_ana_tile0[k]) cudaFree(P->d_ana_tile0[k]);
+  }
+  for (void *p : P->fft_allocs) cudaFree(p);
+  for (auto &r : P->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  if (cur >= 0) cudaSetDevice(cur);
+  delete P;
+}
+
+template <class T>
+static int upload(sht_plan_s *P, const std::vector<T> &h, T **d) {
+  CUDA_TRY(cudaMalloc((void **)d, std::max<size_t>(1, h.size() * sizeof(T))));
+  P->workspace += h.size() * sizeof(T);
+  if (!h.empty()) CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SHT_OK;
+}
+
+static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
+  int rc;
+  // ---- ring pairs ----
+  pair_rings(g, P->pair_n, P->pair_s);
+  P->npairs = (int)P->pair_n.size();
+  P->nrings = g->nrings;
+  std::vector<PairDev> pd(P->npairs);
+  std::vector<int2> pr(P->npairs);
+  for (int p = 0; p < P->npairs; ++p) {
+    double th = g->theta[P->pair_n[p]];
+    long double t = th;
+    PairDev &d = pd[p];
+    d.x = cos(th);
+    long double sn = sinl(t), tn = tanl(0.5L * t);
+    long double l1 = (sn > 0) ? log2l(sn) : 0.0L, l2 = (tn > 0) ? log2l(tn) : 0.0L;
+    d.l1_hi = (double)l1;
+    d.l1_lo = (double)(l1 - (long double)d.l1_hi);
+    d.l2_hi = (double)l2;
+    d.l2_lo = (double)(l2 - (long double)d.l2_hi);
+    d.pole = (th == 0.0 || th == M_PI) ? 1 : 0;
+    d.south = P->pair_s[p] >= 0;
+    pr[p] = make_int2(P->pair_n[p], P->pair_s[p]);
+  }
+  if ((rc = upload(P, pd, &P->d_pairs)) != SHT_OK) return rc;
+  if ((rc = upload(P, pr, &P->d_pair_rings)) != SHT_OK) return rc;
+  std::vector<RingDev> rd(g->nrings);
+  for (int r = 0; r < g->nrings; ++r) {
+    rd[r].ofs = g->ofs[r];
+    rd[r].nphi = g->nphi[r];
+    rd[r].stride = g->stride[r];
+    rd[r].phi0 = g->phi0[r];
+    rd[r].weight = g->weight[r];
+  }
+  if ((rc = upload(P, rd, &P->d_rings)) != SHT_OK) return rc;
+
+  // ---- m list and coefficient table layout ----
+  const int as = abs(P->spin);
+  std::vector<int64_t> coff(P->nm);
+  int64_t nco = 0;
+  for (int i = 0; i < P->nm; ++i) {
+    int l0 = std::max(P->mval[i], as);
+    coff[i] = nco;
+    nco += std::max(0, P->lmax - l0 + 1);
+  }
+  P->coef_off = coff;
+  P->ncoef = nco;
+  std::vector<int> minv(P->mmax + 1, -1);
+  for (int i = 0; i < P->nm; ++i) minv[P->mval[i]] = i;
+  if ((rc = upload(P, P->mval, &P->d_mval)) != SHT_OK) return rc;
+  if ((rc = upload(P, P->mstart, &P->d_mstart)) != SHT_OK) return rc;
+  if ((rc = upload(P, coff, &P->d_coef_off)) != SHT_OK) return rc;
+  if ((rc = upload(P, minv, &P->d_minv)) != SHT_OK) return rc;
+  CUDA_TRY(cudaMalloc(&P->d_coef, std::max<int64_t>(1, nco) * sizeof(Coef)));
+  P->workspace += nco * sizeof(Coef);
+  if (P->precision == SHT_MIXED) {
+    CUDA_TRY(cudaMalloc(&P->d_coef32, std::max<int64_t>(1, nco) * 2 * sizeof(float4)));
+    P->workspace += nco * 2 * sizeof(float4);
+    CUDA_TRY(cudaMalloc(&P->d_alm32, std::max<int64_t>(1, nco) * P->nmaps_pad * sizeof(float4)));
+    P->workspace += nco * P->nmaps_pad * sizeof(float4);
+  }
+  if (P->precision == SHT_FP64 && P->spin != 0) {
+    CUDA_TRY(cudaMalloc(&P->d_pm64, std::max<int64_t>(1, nco) * P->nmaps_pad * sizeof(double2)));
+    P->workspace += nco * P->nmaps_pad * sizeof(double2);
+  }
+  CUDA_TRY(cudaMalloc(&P->d_mpre, P->nm * sizeof(double2)));
+  CUDA_TRY(launch_coef_tables(P, 0));
+  CUDA_TRY(cudaDeviceSynchronize());
+
+  // ---- polar cut (Sect. 3.3): skip (m, pair) when
+  //      sqrt(m^2 + s^2 - 2 m s cos theta) - lmax sin theta > T,  T = max(100, 0.01 lmax),
+  //      for both rings of the pair (cos theta and -cos theta).
+  const double T = std::max(100.0, 0.01 * P->lmax);
+  P->first_pair.assign(P->nm, 0);
+  for (int i = 0; i < P->nm; ++i) {
+    double m = P->mval[i], s = P->spin;
+    int first = P->npairs;
+    for (int p = 0; p < P->npairs; ++p) {
+      double th = g->theta[P->pair_n[p]];
+      double c = fabs(cos(th)), sn = sin(th);
+      double v = sqrt(std::max(0.0, m * m + s * s - 2.0 * fabs(m * s) * c)) - P->lmax * sn;
+      if (!(v > T)) {
+        first = p;
+        break;
+      }
+    }
+    P->first_pair[i] = first;
+  }
+
+  // ---- work lists ----
+  const int V = (P->spin ? 4 : 2) * P->njobs_pad;  // doubles per l in the analysis partials
+  P->ana_ppt = (P->spin || P->njobs_pad > 2) ? 2 : 4;
+  const int TA = kAnaThreads * P->ana_ppt;
+  P->ana_tiles = (P->npairs + TA - 1) / TA;
+  for (int polar = 0; polar < 2; ++polar) {
+    std::vector<std::pair<int64_t, int2>> syn;
+    std::vector<int> sfirst(P->nm);
+    std::vector<std::pair<int64_t, int4>> ana;
+    std::vector<int64_t> poff(P->nm);
+    std::vector<int> t0(P->nm);
+    int64_t off = 0, trip = 0;
+    for (int i = 0; i < P->nm; ++i) {
+      int l0 = std::max(P->mval[i], as);
+      int nl = P->lmax - l0 + 1;
+      if (nl <= 0) {
+        sfirst[i] = P->npairs;
+        t0[i] = P->ana_tiles;
+        poff[i] = off;
+        continue;
+      }
+      int fp = polar ? P->first_pair[i] : 0;
+      trip += (int64_t)(P->npairs - fp) * nl;
+      int sf = (fp / kSynTile) * kSynTile;
+      sfirst[i] = sf;
+      for (int p = sf; p < P->npairs; p += kSynTile)
+        syn.push_back({(int64_t)nl * std::min(kSynTile, P->npairs - p), make_int2(i, p)});
+      int tf = fp / TA;
+      t0[i] = tf;
+      poff[i] = off;
+      for (int t = tf; t < P->ana_tiles; ++t)
+        ana.push_back({(int64_t)nl * std::min(TA, P->npairs - t * TA), make_int4(i, t, 0, 0)});
+      off += (int64_t)(P->ana_tiles - tf) * nl * V;
+    }
+    P->triples[polar] = trip;
+    std::stable_sort(syn.begin(), syn.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    std::stable_sort(ana.begin(), ana.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    std::vector<int2> si;
+    for (auto &e : syn) si.push_back(e.second);
+    std::vector<int4> ai;
+    for (auto &e : ana) ai.push_back(e.second);
+    P->nsyn_items[polar] = (int)si.size();
+    P->nana_items[polar] = (int)ai.size();
+    if ((rc = upload(P, si, &P->d_syn_items[polar])) != SHT_OK) return rc;
+    if ((rc = upload(P, sfirst, &P->d_syn_first[polar])) != SHT_OK) return rc;
+    if ((rc = upload(P, ai, &P->d_ana_items[polar])) != SHT_OK) return rc;
+    if ((rc = upload(P, poff, &P->d_ana_part_off[polar])) != SHT_OK) return rc;
+    if ((rc = upload(P, t0, &P->d_ana_tile0[polar])) != SHT_OK) return rc;
+    P->part_doubles = std::max(P->part_doubles, off);
+  }
+  CUDA_TRY(cudaMalloc(&P->d_part, std::max<int64_t>(1, P->part_doubles) * sizeof(double)));
+  P->workspace += P->part_doubles * sizeof(double);
+
+  // ---- phase-array workspace F/G [nmaps][nm][npairs][2] ----
+  size_t nph = (size_t)P->nmaps_pad * P->nm * P->npairs * 2;
+  CUDA_TRY(cudaMalloc(&P->d_phase, std::max<size_t>(1, nph) * sizeof(double2)));
+  P->workspace += nph * sizeof(double2);
+
+  // ---- FFT plans per distinct ring length ----
+  std::map<int, int> lens;
+  std::vector<int> pf(P->npairs);
+  for (int p = 0; p < P->npairs; ++p) {
+    int n = g->nphi[P->pair_n[p]];
+    auto it = lens.find(n);
+    if (it == lens.end()) it = lens.emplace(n, (int)lens.size()).first;
+    pf[p] = it->second;
+  }
+  P->nfft = (int)lens.size();
+  std::vector<FftPlanDev> fps(P->nfft);
+  FftPlanDev *scratch = nullptr;
+  CUDA_TRY(cudaMalloc(&scratch, sizeof(FftPlanDev)));
+  P->fft_allocs.push_back(scratch);
+  int maxlen = 0;
+  for (auto &kv : lens) {
+    if ((rc = build_fft_plan(P, kv.first, fps[kv.second], scratch)) != SHT_OK) return rc;
+    maxlen = std::max(maxlen, fps[kv.second].len);
+  }
+  if ((rc = upload(P, fps, &P->d_fft)) != SHT_OK) return rc;
+  if ((rc = upload(P, pf, &P->d_pair_fft)) != SHT_OK) return rc;
+  P->fft_smem = maxlen * (int)sizeof(double2);
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_create(sht_geom_t geom, sht_alm_t alm, int spin, int ncomp, int precision,
+                               sht_plan_t *out) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!geom || !alm) return fail(SHT_ERR_INVALID_ARG, "geometry or a_lm descriptor is NULL");
+  if (precision != SHT_FP64 && precision != SHT_MIXED) return fail(SHT_ERR_INVALID_ARG, "bad precision");
+  if (ncomp < 1 || ncomp > kMaxJobs) return fail(SHT_ERR_INVALID_ARG, "ncomp must be in 1..%d", kMaxJobs);
+  if (abs(spin) > alm->lmax) return fail(SHT_ERR_UNSUPPORTED, "|spin| > lmax");
+  if (abs(spin) > 64) return fail(SHT_ERR_UNSUPPORTED, "|spin| > 64");
+  if (spin != 0 && ncomp > 8) return fail(SHT_ERR_UNSUPPORTED, "spin transforms take at most 8 (E,B) pairs");
+  auto *P = new sht_plan_s;
+  cudaGetDevice(&P->device);
+  P->lmax = alm->lmax;
+  P->mmax = alm->mmax;
+  P->nm = alm->nm;
+  P->astride = alm->stride;
+  P->mval = alm->mval;
+  P->mstart = alm->mstart;
+  P->spin = spin;
+  P->ncomp = ncomp;
+  P->precision = precision;
+  P->nmaps = spin ? 2 * ncomp : ncomp;
+  P->njobs_pad = 1;
+  while (P->njobs_pad < ncomp) P->njobs_pad *= 2;
+  P->nmaps_pad = spin ? 2 * P->njobs_pad : P->njobs_pad;
+  int rc = plan_build(P, geom);
+  if (rc != SHT_OK) {
+    cudaGetLastError();
+    free_plan(P);
+    return rc;
+  }
+  *out = P;
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_workspace(sht_plan_t P, int64_t *bytes) {
+  if (!P || !bytes) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  *bytes = P->workspace;
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_triples(sht_plan_t P, int flags, int64_t *t) {
+  if (!P || !t) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  *t = P->triples[(flags & SHT_NO_POLAR_OPT) ? 0 : 1];
+  return SHT_OK;
+}
+
+extern "C" void sht_plan_destroy(sht_plan_t P) { free_plan(P); }
+
+extern "C" int sht_plan_profile(sht_plan_t P, int enable) {
+  if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  for (auto &r : P->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  P->prof.clear();
+  P->prof_on = enable ? 1 : 0;
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_profile_read(sht_plan_t P, double *ms, int64_t *count) {
+  if (!P || !ms || !count) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  for (int s = 0; s < SHT_NSTAGES; ++s) {
+    ms[s] = 0.0;
+    count[s] = 0;
+  }
+  int rc = SHT_OK;
+  for (auto &r : P->prof) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess && rc == SHT_OK) rc = fail(SHT_ERR_CUDA, "profile events: %s", cudaGetErrorString(e));
+    ms[r.stage] += t;
+    count[r.stage] += 1;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  P->prof.clear();
+  return rc;
+}
+
+// ----------------------------------------------------------------------------
+// Execution
+// ----------------------------------------------------------------------------
+extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *const *map, int flags,
+                           void *stream) {
+  if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  if (type < SHT_SYNTHESIS || type > SHT_ADJOINT_ANALYSIS) return fail(SHT_ERR_INVALID_ARG, "bad type %d", type);
+  if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT)) return fail(SHT_ERR_INVALID_ARG, "unknown flags");
+  if (!alm || !map) return fail(SHT_ERR_INVALID_ARG, "pointer arrays are NULL");
+  DevPtrs A, M;
+  memset(&A, 0, sizeof(A));
+  memset(&M, 0, sizeof(M));
+  for (int j = 0; j < P->nmaps; ++j) {
+    if (!alm[j] || !map[j]) return fail(SHT_ERR_INVALID_ARG, "NULL device pointer at index %d", j);
+    A.p[j] = alm[j];
+    M.p[j] = map[j];
+  }
+  // padding jobs (kernels run a power-of-two job count) read job 0's input;
+  // their results stay in the plan's workspace and are never written out
+  const int per = P->spin ? 2 : 1;
+  for (int j = P->nmaps; j < P->nmaps_pad; ++j) A.p[j] = alm[j % per];
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int polar = (flags & SHT_NO_POLAR_OPT) ? 0 : 1;
+  const int add = (flags & SHT_ADD_OUTPUT) ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  // run one stage, bracketed by an event pair when profiling
+  auto stage = [&](int id, auto &&launch) {
+    if (e != cudaSuccess) return;
+    sht_plan_s::ProfRec r{id, nullptr, nullptr};
+    if (P->prof_on) {
+      if ((e = cudaEventCreate(&r.a)) != cudaSuccess) return;
+      if ((e = cudaEventCreate(&r.b)) != cudaSuccess) return;
+      if ((e = cudaEventRecord(r.a, st)) != cudaSuccess) return;
+    }
+    e = launch();
+    if (P->prof_on) {
+      if (e == cudaSuccess) e = cudaEventRecord(r.b, st);
+      P->prof.push_back(r);
+    }
+  };
+  const bool mixed = P->precision == SHT_MIXED;
+  if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS) {
+    stage(0, [&] { return mixed ? launch_leg_syn_mixed(P, A, polar, st) : launch_leg_syn_fp64(P, A, polar, st); });
+    stage(1, [&] { return launch_fft_syn(P, M, polar, type == SHT_ADJOINT_ANALYSIS, add, st); });
+  } else {
+    stage(2, [&] { return launch_fft_ana(P, M, type == SHT_ANALYSIS, st); });
+    stage(3, [&] { return mixed ? launch_leg_ana_mixed(P, A, polar, st) : launch_leg_ana_fp64(P, A, polar, st); });
+    stage(4, [&] { return launch_ana_reduce(P, A, polar, add, st); });
+  }
+  if (cur != P->device) cudaSetDevice(cur);
+  if (e != cudaSuccess) return fail(SHT_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return SHT_OK;
+}

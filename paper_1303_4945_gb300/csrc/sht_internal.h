@@ -1,0 +1,175 @@
+// sht_internal.h -- data structures shared by the translation units of libsht_gb300.
+//
+// Layout of the device data a plan holds (all in HBM, built once at plan time):
+//   pairs      PairDev[npairs]      ring pairs sorted pole -> equator (Sect. 3.3 order)
+//   coef       Coef[ncoef]          recursion coefficients {A, AK, C, 0} per (m, l), Sect. 4.1
+//   coef32     float4[2*ncoef]      the same split into FP32 pairs (mixed form)
+//   mpre       double2[nm]          start-value prefactor (mantissa, exponent) per m
+//   F / G      double2[nmaps][nm][npairs][2]   phase arrays of Eqs. syn2 / ana2 (north, south)
+//   part       double[..]           per-tile partial sums of the analysis Legendre stage
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sht_gb300.h"
+
+namespace sht {
+
+constexpr int kMaxPtr = 32;       // max device pointers per execute (maps or a_lm arrays)
+constexpr int kMaxJobs = 16;      // ncomp limit
+constexpr int kSynTile = 128;     // ring pairs per synthesis Legendre CTA (one per thread)
+constexpr int kAnaThreads = 128;  // threads per analysis Legendre CTA
+constexpr int kMaxRadix = 8 * 4;  // generic odd radix limit of the FFT engine (primes <= 31)
+constexpr int kFftThreads = 512;
+constexpr int kFftMaxOpt = 16;    // outputs held in registers per thread per pass
+constexpr int kFftMaxLen = kFftThreads * kFftMaxOpt;  // 8192
+
+// Extended exponent of the FP64 recursion: a pair (lambda_{l-1}, lambda_l) is
+// stored as value * 2^(kScaleStep * scale); it contributes only at scale 0.
+constexpr int kScaleStep = 600;
+constexpr double kScaleUp = 0x1p+300;     // rescale when |lambda| exceeds this
+constexpr double kScaleFactor = 0x1p-600;
+
+struct PairDev {
+  double x;        // cos(theta) of the ring in the north slot (libm cos of the given theta)
+  double l1_hi;    // log2(sin theta), double-double
+  double l1_lo;
+  double l2_hi;    // log2(tan(theta/2)), double-double
+  double l2_lo;
+  int pole;        // 1 if theta == 0 exactly (sin theta == 0)
+  int south;       // 1 if the pair has a mirrored southern ring
+};
+
+// Per-ring data for the FFT stage.
+struct RingDev {
+  int64_t ofs;
+  int nphi;
+  int stride;
+  double phi0;
+  double weight;
+};
+
+struct FftPlanDev {
+  int n;          // ring length
+  int kind;       // 0 mixed radix, 1 Rader, 2 Bluestein
+  int len;        // inner transform length (n, n-1 or the Bluestein size)
+  int nrad;
+  int rad[24];
+  const double2 *w;      // twiddles e^{-2 pi i k / len}, k < len
+  const int *perm_in;    // Rader: g^q mod n
+  const int *inv_out;    // Rader: index p with g^{-p} = k, for k = 1..n-1
+  const double2 *spec;   // Rader / Bluestein kernel spectrum (1/len folded in)
+  const double2 *chirp;  // Bluestein: e^{-pi i k^2 / n}
+};
+
+struct DevPtrs {
+  double *p[kMaxPtr];
+};
+
+// recursion coefficients of one (m, l): lambda_{l+1} = (a x + ak) lambda_l - c lambda_{l-1}
+struct __align__(32) Coef {
+  double a, ak, c, pad;
+};
+
+}  // namespace sht
+
+// ----------------------------------------------------------------------------
+// Opaque handles of the C ABI.
+// ----------------------------------------------------------------------------
+struct sht_geom_s {
+  int nrings = 0;
+  std::vector<double> theta, phi0, weight;
+  std::vector<int> nphi, stride;
+  std::vector<int64_t> ofs;
+};
+
+struct sht_alm_s {
+  int lmax = 0, mmax = 0, nm = 0, stride = 1;
+  std::vector<int> mval;
+  std::vector<int64_t> mstart;
+};
+
+struct sht_plan_s {
+  int device = 0;
+  int lmax = 0, mmax = 0, nm = 0, astride = 1, spin = 0, ncomp = 0, precision = 0;
+  int nmaps = 0;      // arrays per side (ncomp, or 2 ncomp for spin)
+  int njobs_pad = 1;  // ncomp rounded up to a power of two (kernel template size)
+  int nmaps_pad = 1;  // arrays per side for njobs_pad jobs
+  int nrings = 0, npairs = 0;
+  std::vector<int> mval;
+  std::vector<int64_t> mstart;
+  std::vector<int> pair_n, pair_s;         // ring index of the north / south slot (-1 none)
+  std::vector<int> first_pair;             // per m: first pair not removed by the polar cut
+  std::vector<int64_t> coef_off;           // per m: table index of l = l0
+  int64_t ncoef = 0;
+
+  // device arrays
+  sht::PairDev *d_pairs = nullptr;
+  int2 *d_pair_rings = nullptr;
+  sht::RingDev *d_rings = nullptr;
+  int *d_mval = nullptr;
+  int64_t *d_mstart = nullptr;
+  int64_t *d_coef_off = nullptr;
+  sht::Coef *d_coef = nullptr;
+  float4 *d_coef32 = nullptr;
+  float4 *d_alm32 = nullptr;
+  double2 *d_pm64 = nullptr;               // FP64 spin form: P = E + iB, M = E - iB [array][ncoef]               // mixed form: a_lm as double-float pairs [array][ncoef]
+  double2 *d_mpre = nullptr;
+  int *d_minv = nullptr;                   // m -> index in mval, or -1
+  double2 *d_phase = nullptr;              // F / G workspace
+  double *d_part = nullptr;                // analysis partials
+  int64_t part_doubles = 0;
+
+  // work lists (polar-cut / uncut): synthesis (mi, first pair) and analysis (mi, tile, part offset)
+  int2 *d_syn_items[2] = {nullptr, nullptr};
+  int nsyn_items[2] = {0, 0};
+  int *d_syn_first[2] = {nullptr, nullptr};  // per m: first pair the synthesis wrote (FFT reads 0 below)
+  int4 *d_ana_items[2] = {nullptr, nullptr};
+  int nana_items[2] = {0, 0};
+  int64_t *d_ana_part_off[2] = {nullptr, nullptr};  // per m
+  int *d_ana_tile0[2] = {nullptr, nullptr};         // per m: first tile
+  int ana_ppt = 4;                                  // pairs per analysis thread
+  int ana_tiles = 0;
+  int64_t triples[2] = {0, 0};
+
+  // FFT
+  std::vector<void *> fft_allocs;
+  sht::FftPlanDev *d_fft = nullptr;
+  int nfft = 0;
+  int *d_pair_fft = nullptr;  // per pair: plan index
+  int fft_smem = 0;           // bytes of dynamic shared memory for the FFT kernels
+
+  int64_t workspace = 0;
+
+  // measurement: event pairs around each launch while profiling is on
+  int prof_on = 0;
+  struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof;
+};
+
+// ----------------------------------------------------------------------------
+// Cross-TU launch helpers (all return cudaError_t of the launch).
+// ----------------------------------------------------------------------------
+namespace sht {
+// plan-time tables
+cudaError_t launch_coef_tables(const sht_plan_s *P, cudaStream_t st);
+cudaError_t launch_fft_spectrum(const FftPlanDev *host_plan, const FftPlanDev *dev_plan,
+                                const double2 *src, double2 *dst, int len, double scale,
+                                cudaStream_t st);
+// Legendre stage
+cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
+cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
+cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st);
+cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
+cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
+// ring FFTs
+cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, int weighted, int add,
+                           cudaStream_t st);
+cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted, cudaStream_t st);
+}  // namespace sht

@@ -1,0 +1,266 @@
+"""ctypes binding of the C ABI in include/sht_gb300.h (libsht_gb300.so).
+
+Argument marshalling only: every step of a transform runs in the library's
+CUDA kernels.  Function names follow the C ABI; handles are wrapped in small
+classes that call the matching *_destroy when collected.  Device buffers may
+be given as torch CUDA tensors (complex128 a_lm, float64 maps) or as raw
+integer device addresses.
+
+Importing this module loads the library and raises if it has not been built
+(``python -m paper_1303_4945_gb300.build``); there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+SHT_OK = 0
+SHT_ERR_INVALID_ARG = -1
+SHT_ERR_UNSUPPORTED = -2
+SHT_ERR_OOM = -3
+SHT_ERR_CUDA = -4
+SHT_ERR_TIMEOUT = -5
+
+SHT_ECP_FEJER1, SHT_ECP_FEJER2, SHT_ECP_CC = 0, 1, 2
+SHT_FP64, SHT_MIXED = 0, 1
+SHT_SYNTHESIS, SHT_ANALYSIS, SHT_ADJOINT_SYNTHESIS, SHT_ADJOINT_ANALYSIS = 0, 1, 2, 3
+SHT_ADD_OUTPUT, SHT_NO_POLAR_OPT = 1, 2
+SHT_NSTAGES = 5
+STAGE_NAMES = ("legendre_synthesis", "fft_synthesis", "fft_analysis", "legendre_analysis", "analysis_reduce")
+
+LIB_PATH = _build.LIB
+HEADER = os.path.join(_build.ROOT, "include", "sht_gb300.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1303_4945_gb300.build.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_sig = {
+    "sht_geom_general": [ctypes.c_int, _dp, _ip, _dp, _i64p, _ip, _dp, ctypes.POINTER(_vp)],
+    "sht_geom_gauss": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
+    "sht_geom_ecp": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
+    "sht_geom_healpix": [ctypes.c_int, ctypes.POINTER(_vp)],
+    "sht_geom_subset": [_vp, ctypes.c_int, _ip, ctypes.POINTER(_vp)],
+    "sht_geom_info": [_vp, _ip, _i64p, _ip],
+    "sht_geom_rings": [_vp, _dp, _ip, _dp, _i64p, _ip, _dp],
+    "sht_geom_destroy": [_vp],
+    "sht_alm_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _i64p, ctypes.c_int, ctypes.POINTER(_vp)],
+    "sht_alm_size": [_vp, _i64p],
+    "sht_alm_destroy": [_vp],
+    "sht_plan_create": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
+    "sht_execute": [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp],
+    "sht_plan_workspace": [_vp, _i64p],
+    "sht_plan_triples": [_vp, ctypes.c_int, _i64p],
+    "sht_plan_destroy": [_vp],
+    "sht_plan_profile": [_vp, ctypes.c_int],
+    "sht_plan_profile_read": [_vp, _dp, _i64p],
+    "sht_strerror": [ctypes.c_int],
+    "sht_last_error": [],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+for _name in ("sht_geom_destroy", "sht_alm_destroy", "sht_plan_destroy"):
+    getattr(_lib, _name).restype = None
+_lib.sht_strerror.restype = ctypes.c_char_p
+_lib.sht_last_error.restype = ctypes.c_char_p
+
+
+def exported_symbols_declared():
+    """Names of the functions include/sht_gb300.h declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(sht_\w+)\s*\(", txt)))
+
+
+class ShtError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.sht_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_lib.sht_strerror(code).decode()} ({code}): {msg}")
+
+
+def _check(rc, where):
+    if rc != SHT_OK:
+        raise ShtError(rc, where)
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a, ct):
+    return None if a is None else a.ctypes.data_as(ct)
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, h):
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h and self._destroy is not None:
+            getattr(_lib, self._destroy)(h)
+
+
+class Geometry(_Handle):
+    _destroy = "sht_geom_destroy"
+
+    def info(self):
+        nr, npix, npairs = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        _check(_lib.sht_geom_info(self._h, ctypes.byref(nr), ctypes.byref(npix), ctypes.byref(npairs)),
+               "sht_geom_info")
+        return nr.value, npix.value, npairs.value
+
+    @property
+    def nrings(self):
+        return self.info()[0]
+
+    @property
+    def npix(self):
+        return self.info()[1]
+
+    def rings(self):
+        n = self.nrings
+        th, p0, w = np.zeros(n), np.zeros(n), np.zeros(n)
+        nphi, st = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        ofs = np.zeros(n, np.int64)
+        _check(_lib.sht_geom_rings(self._h, _ptr(th, _dp), _ptr(nphi, _ip), _ptr(p0, _dp), _ptr(ofs, _i64p),
+                                   _ptr(st, _ip), _ptr(w, _dp)), "sht_geom_rings")
+        return dict(theta=th, nphi=nphi, phi0=p0, ofs=ofs, stride=st, weight=w)
+
+
+class AlmLayout(_Handle):
+    _destroy = "sht_alm_destroy"
+
+    def __init__(self, h, lmax, mmax):
+        super().__init__(h)
+        self.lmax, self.mmax = lmax, mmax
+
+    def size(self):
+        n = ctypes.c_int64()
+        _check(_lib.sht_alm_size(self._h, ctypes.byref(n)), "sht_alm_size")
+        return n.value
+
+
+class Plan(_Handle):
+    _destroy = "sht_plan_destroy"
+
+    def __init__(self, h, geom, alm, spin, ncomp, precision):
+        super().__init__(h)
+        self.geom, self.alm, self.spin, self.ncomp, self.precision = geom, alm, spin, ncomp, precision
+
+    @property
+    def narrays(self):
+        return 2 * self.ncomp if self.spin else self.ncomp
+
+    def workspace(self):
+        n = ctypes.c_int64()
+        _check(_lib.sht_plan_workspace(self._h, ctypes.byref(n)), "sht_plan_workspace")
+        return n.value
+
+    def profile(self, enable=True):
+        _check(_lib.sht_plan_profile(self._h, 1 if enable else 0), "sht_plan_profile")
+
+    def profile_read(self):
+        """{stage name: (total ms, launches)} recorded since profile(True)."""
+        ms = np.zeros(SHT_NSTAGES)
+        cnt = np.zeros(SHT_NSTAGES, np.int64)
+        _check(_lib.sht_plan_profile_read(self._h, _ptr(ms, _dp), _ptr(cnt, _i64p)), "sht_plan_profile_read")
+        return {STAGE_NAMES[i]: (float(ms[i]), int(cnt[i])) for i in range(SHT_NSTAGES)}
+
+    def triples(self, flags=0):
+        n = ctypes.c_int64()
+        _check(_lib.sht_plan_triples(self._h, flags, ctypes.byref(n)), "sht_plan_triples")
+        return n.value
+
+
+def sht_geom_general(theta, nphi, phi0, ofs, stride=None, weight=None) -> Geometry:
+    th = _arr(theta, np.float64)
+    n = len(th)
+    npf, p0, o = _arr(nphi, np.int32), _arr(phi0, np.float64), _arr(ofs, np.int64)
+    st = None if stride is None else _arr(stride, np.int32)
+    w = None if weight is None else _arr(weight, np.float64)
+    h = _vp()
+    _check(_lib.sht_geom_general(n, _ptr(th, _dp), _ptr(npf, _ip), _ptr(p0, _dp), _ptr(o, _i64p),
+                                 _ptr(st, _ip), _ptr(w, _dp), ctypes.byref(h)), "sht_geom_general")
+    return Geometry(h.value)
+
+
+def sht_geom_gauss(nlat, nlon) -> Geometry:
+    h = _vp()
+    _check(_lib.sht_geom_gauss(nlat, nlon, ctypes.byref(h)), "sht_geom_gauss")
+    return Geometry(h.value)
+
+
+def sht_geom_ecp(kind, nlat, nlon) -> Geometry:
+    h = _vp()
+    _check(_lib.sht_geom_ecp(kind, nlat, nlon, ctypes.byref(h)), "sht_geom_ecp")
+    return Geometry(h.value)
+
+
+def sht_geom_healpix(nside) -> Geometry:
+    h = _vp()
+    _check(_lib.sht_geom_healpix(nside, ctypes.byref(h)), "sht_geom_healpix")
+    return Geometry(h.value)
+
+
+def sht_geom_subset(geom: Geometry, rings) -> Geometry:
+    r = _arr(rings, np.int32)
+    h = _vp()
+    _check(_lib.sht_geom_subset(geom.handle, len(r), _ptr(r, _ip), ctypes.byref(h)), "sht_geom_subset")
+    return Geometry(h.value)
+
+
+def sht_alm_create(lmax, mmax, mval=None, mstart=None, stride=1) -> AlmLayout:
+    mv = None if mval is None else _arr(mval, np.int32)
+    ms = None if mstart is None else _arr(mstart, np.int64)
+    h = _vp()
+    _check(_lib.sht_alm_create(lmax, mmax, 0 if mv is None else len(mv), _ptr(mv, _ip), _ptr(ms, _i64p),
+                               stride, ctypes.byref(h)), "sht_alm_create")
+    return AlmLayout(h.value, lmax, mmax)
+
+
+def sht_plan_create(geom: Geometry, alm: AlmLayout, spin=0, ncomp=1, precision=SHT_FP64) -> Plan:
+    h = _vp()
+    _check(_lib.sht_plan_create(geom.handle, alm.handle, spin, ncomp, precision, ctypes.byref(h)),
+           "sht_plan_create")
+    return Plan(h.value, geom, alm, spin, ncomp, precision)
+
+
+def _devptr(x):
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())  # torch tensor
+
+
+def sht_execute(plan: Plan, type_, alm, maps, flags=0, stream=None):
+    """alm, maps: sequences of device buffers (torch tensors or addresses)."""
+    n = plan.narrays
+    if len(alm) != n or len(maps) != n:
+        raise ValueError(f"expected {n} a_lm and {n} map buffers")
+    ap = (_vp * n)(*[_devptr(a) for a in alm])
+    mp = (_vp * n)(*[_devptr(m) for m in maps])
+    st = None if stream is None else _vp(_devptr_stream(stream))
+    _check(_lib.sht_execute(plan.handle, type_, ap, mp, flags, st), "sht_execute")
+
+
+def _devptr_stream(stream):
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
