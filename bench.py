@@ -35,13 +35,25 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-LMAX, NLAT, NLON, SPIN, SEED = 4095, 4096, 8191, 2, 2
-METRIC = "ms per synth+analysis at lmax 4095 (spin 2, GL 4096x8191)"
-CONFIG = {"workload": "spin-2 synthesis+analysis, Gauss-Legendre nlat=4096 nlon=8191, lmax=mmax=4095, "
-                      "E/B a_lm C_l=1/(l+1)^2 seed 2",
-          "lmax": LMAX, "nlat": NLAT, "nlon": NLON, "spin": SPIN, "ncomp": 1,
-          "l2_policy": "inputs larger than L2 (268 MB a_lm, 537 MB maps)", "parallelism": "replicas"}
+SPIN, SEED = 2, 2
+LMAX = NLAT = NLON = METRIC = CONFIG = None
 SMS = 152
+
+
+def set_workload(lmax):
+    """GL nlat = lmax + 1, nlon = 2 lmax + 1; lmax 4095 is the headline configuration."""
+    global LMAX, NLAT, NLON, METRIC, CONFIG
+    LMAX, NLAT, NLON = lmax, lmax + 1, 2 * lmax + 1
+    METRIC = f"ms per synth+analysis at lmax {LMAX} (spin 2, GL {NLAT}x{NLON})"
+    nalm = (LMAX + 1) * (LMAX + 2) // 2
+    big = 16 * 2 * nalm > 129e6 and 8 * 2 * NLAT * NLON > 129e6
+    CONFIG = {"workload": f"spin-2 synthesis+analysis, Gauss-Legendre nlat={NLAT} nlon={NLON}, "
+                          f"lmax=mmax={LMAX}, E/B a_lm C_l=1/(l+1)^2 seed 2",
+              "lmax": LMAX, "nlat": NLAT, "nlon": NLON, "spin": SPIN, "ncomp": 1,
+              "l2_policy": ("inputs larger than L2 (%.0f MB a_lm, %.0f MB maps)"
+                            % (16 * 2 * nalm / 1e6, 8 * 2 * NLAT * NLON / 1e6)) if big
+              else "inputs smaller than L2: not a headline configuration",
+              "parallelism": "replicas"}
 
 
 def _peaks():
@@ -130,7 +142,7 @@ def max_over_ranks(x, world):
 
 
 # ------------------------------------------------------------------ oracle ---
-def oracle_sample(target_s=15.0, gpu_out=None):
+def oracle_sample(target_s=15.0, gpu_out=None, others=None):
     """Time the FP64 CPU oracle on a bounded sample of the workload and
     extrapolate to one full synthesis + analysis pair (ms).
 
@@ -152,7 +164,7 @@ def oracle_sample(target_s=15.0, gpu_out=None):
     cores = os.cpu_count() or 1
 
     if gpu_out is not None:
-        ana_in = gpu_out["maps"]  # the GPU's own synthesis output: compares the analyses on equal input
+        ana_in = gpu_out["maps"]  # a GPU synthesis output: the analyses are compared on equal input
     else:
         rng = np.random.default_rng(7)
         ana_in = [rng.standard_normal(rings.npix) for _ in range(2)]
@@ -182,16 +194,18 @@ def oracle_sample(target_s=15.0, gpu_out=None):
     if gpu_out is not None:
         acc = {}
         o = rings.ofs
-        for name, g_maps, o_maps in (("Q", gpu_out["maps"][0], maps[0]), ("U", gpu_out["maps"][1], maps[1])):
-            idx = np.concatenate([np.arange(o[y], o[y] + NLON) for y in rsel])
-            d = g_maps[idx] - o_maps[idx]
-            acc[f"synthesis_{name}_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(o_maps[idx]))
+        idx = np.concatenate([np.arange(o[y], o[y] + NLON) for y in rsel])
         l, m = inputs.lm_arrays(LMAX, LMAX)
         sel = np.isin(m, msel)
-        for name, g_a, o_a in (("E", gpu_out["alm"][0], back[0]), ("B", gpu_out["alm"][1], back[1])):
-            d = g_a[sel] - o_a[sel]
-            acc[f"analysis_{name}_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(o_a[sel]))
-        acc["sample"] = f"{len(rsel)} rings, {len(msel)} m values"
+        for form, out in [("head", gpu_out)] + list((others or {}).items()):
+            for k, name in enumerate("QU"):
+                d = out["maps"][k][idx] - maps[k][idx]
+                acc[f"{form}_synthesis_{name}_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(maps[k][idx]))
+            if out is gpu_out:  # the oracle analysed this output's maps
+                for k, name in enumerate("EB"):
+                    d = out["alm"][k][sel] - back[k][sel]
+                    acc[f"{form}_analysis_{name}_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(back[k][sel]))
+        acc["sample"] = f"{len(rsel)} rings, {len(msel)} m values, evenly spaced (both poles included)"
     return res, acc
 
 
@@ -272,7 +286,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--lmax", type=int, default=4095, help="smaller sizes for profiling captures")
     args = ap.parse_args()
+    set_workload(args.lmax)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -358,7 +374,8 @@ def main():
             "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": 5 * args.steps, "forms": results}
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
-        cb, acc = oracle_sample(args.cpu_seconds, gpu_out=outputs[head])
+        others = {k: v for k, v in outputs.items() if k != head}
+        cb, acc = oracle_sample(args.cpu_seconds, gpu_out=outputs[head], others=others)
         line["cpu_baseline"] = cb
         line["accuracy_vs_oracle_sample"] = acc
     if rank == 0:

@@ -12,8 +12,8 @@
 // Structure, ring pairing, parity split, the coupled (lp, lm) recursion for
 // spin and the analysis reduction follow legendre_fp64.cu exactly; only the
 // arithmetic type differs.  The enhanced exponent uses steps of 2^104: pairs
-// above 2^52 are scaled down every 8 steps, and nothing below 2^-52 (relative
-// to its final scale) is ever accumulated.
+// above 2^52 are scaled down every 8 steps; values at scale 0 and -1 are
+// accumulated (the latter times 2^-104), anything smaller is negligible.
 #include "sht_device.cuh"
 
 namespace sht {
@@ -52,6 +52,29 @@ __device__ __forceinline__ f2 mul(f2 a, f2 b) {
   return {p, e};
 }
 __device__ __forceinline__ f2 neg(f2 a) { return {-a.h, -a.l}; }
+
+// cos(theta) as three floats summing exactly to the FP64 value.  Next to the
+// poles x = 1 - O(theta^2) and a two-float x would carry a fixed error of
+// ~2^-48 that the recursion amplifies by ~l/theta; with three floats the
+// mixed form evaluates at exactly the same x as the FP64 form.
+struct f3 {
+  float h, m, l;
+};
+__device__ __forceinline__ f3 f3_of(double v) {
+  const float h = __double2float_rn(v);
+  const double r = v - (double)h;
+  const float m = __double2float_rn(r);
+  return {h, m, __double2float_rn(r - (double)m)};
+}
+// a * x for a two-float a and a three-float x, as an unevaluated pair
+__device__ __forceinline__ f2 mul(f2 a, f3 x) {
+  const float p = __fmul_rn(a.h, x.h);
+  float e = __fmaf_rn(a.h, x.h, -p);
+  e = __fmaf_rn(a.h, x.l, e);
+  e = __fmaf_rn(a.l, x.h, e);
+  e = __fmaf_rn(a.h, x.m, e);
+  return {p, e};
+}
 // a b + c d, normalised
 __device__ __forceinline__ f2 dot2(f2 a, f2 b, f2 c, f2 d) {
   const f2 p = mul(a, b), q = mul(c, d);
@@ -68,7 +91,7 @@ __device__ __forceinline__ f2 dot3(f2 a, f2 b, f2 c, f2 d, f2 e, f2 f) {
 }
 // acc += w * a with a lazily carried low word (renormalised every few steps)
 __device__ __forceinline__ void acc_mul(f2 &acc, f2 w, float ah, float al) {
-  const f2 p = mul(w, {ah, al});
+  const f2 p = mul(w, f2{ah, al});
   const f2 s = two_sum(acc.h, p.h);
   acc.h = s.h;
   acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, p.l));
@@ -78,7 +101,15 @@ __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
   const f2 s = two_sum(a.h, b.h);
   return fast_two_sum(s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l));
 }
-__device__ __forceinline__ f2 sel(bool c, f2 a) { return c ? a : f2{0.f, 0.f}; }
+// Accumulation weight of a recursion value y held at the given scale.  The
+// exponent is checked every 8 steps, so a value still labelled scale -1 may
+// already have grown past the 2^52 threshold by up to the 8-step growth of
+// the recursion (< 2^50): its true size y 2^-104 can reach 2^-2 and must be
+// accumulated.  Values at scale <= -2 are below 2^(52+50-208) and are dropped.
+__device__ __forceinline__ f2 weight(f2 y, int scale) {
+  const float f = (scale == 0) ? 1.f : ((scale == -1) ? kScaleFactor32 : 0.f);
+  return {y.h * f, y.l * f};
+}
 
 // (mant * 2^E) -> (y, scale) with value = y * 2^(104 scale), y's exponent in [-52, 52)
 __device__ __forceinline__ f2 to_scaled32(double mant, int E, int *scale) {
@@ -180,7 +211,7 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
   const int64_t co = a.coef_off[mi] - l0;
   const float4 *__restrict__ cf = a.coef32 + 2 * co;
   const PairDev pd = a.pairs[valid ? p : 0];
-  const f2 x = f2_of(pd.x);
+  const f3 x = f3_of(pd.x);
   f2 lc, lp = {0.f, 0.f};
   int scale;
   start_s0(m, pd, a.mpre[mi], &lc, &scale);
@@ -195,7 +226,7 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
     for (int j = 0; j < NJ; ++j) acc[q][j][0] = acc[q][j][1] = f2{0.f, 0.f};
 
   auto step = [&](int l, int par, bool act) {
-    const f2 w = sel(act || scale == 0, lc);
+    const f2 w = act ? lc : weight(lc, scale);
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const float4 v = __ldg(a.alm32 + (int64_t)j * a.ncoef + co + l);
@@ -279,7 +310,7 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
   const int64_t co = a.coef_off[mi] - l0;
   const float4 *__restrict__ cf = a.coef32 + 2 * co;
   const PairDev pd = a.pairs[valid ? p : 0];
-  const f2 x = f2_of(pd.x);
+  const f3 x = f3_of(pd.x);
   f2 lpc, lmc, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
   int scp, scm;
   start_s(m, s, pd, a.mpre[mi], &lpc, &scp);
@@ -296,7 +327,7 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
     for (int k = 0; k < 4; ++k) r[j][k][0] = r[j][k][1] = f2{0.f, 0.f};
 
   auto step = [&](int l, int par, bool act) {
-    const f2 wp = sel(act || scp == 0, lpc), wm = sel(act || scm == 0, lmc);
+    const f2 wp = act ? lpc : weight(lpc, scp), wm = act ? lmc : weight(lmc, scm);
     const f2 sp = par ? neg(wp) : wp, sm = par ? neg(wm) : wm;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -433,7 +464,8 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
   double *outp = a.part + a.part_off[mi] + (int64_t)(tile - a.tile0[mi]) * nl * V;
   const double sg0 = ((l0 + m) & 1) ? -1.0 : 1.0;
 
-  f2 x[PPT], lpc[PPT], lmc[PPT], lpp[PPT], lmp[PPT];
+  f3 x[PPT];
+  f2 lpc[PPT], lmc[PPT], lpp[PPT], lmp[PPT];
   int scp[PPT], scm[PPT];
   // spin 0: g[k][j][0..1] = G_N +- G_S (complex) ; spin: Q+-, U+- (complex)
   f2 g[PPT][NJ][SPIN ? 4 : 2][2];
@@ -442,7 +474,7 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
     const int p = tile * (kAnaThreads * PPT) + threadIdx.x + k * kAnaThreads;
     const bool valid = p < a.npairs;
     const PairDev pd = a.pairs[valid ? p : 0];
-    x[k] = f2_of(pd.x);
+    x[k] = f3_of(pd.x);
     if (SPIN) {
       start_s(m, s, pd, a.mpre[mi], &lpc[k], &scp[k]);
       start_s(m, -s, pd, a.mpre[mi], &lmc[k], &scm[k]);
@@ -493,6 +525,21 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
       }
     }
   }
+  auto rescale_all = [&]() {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if (scp[k] < 0 && fabsf(lpc[k].h) > kScaleUp32) {
+        lpc[k] = {lpc[k].h * kScaleFactor32, lpc[k].l * kScaleFactor32};
+        lpp[k] = {lpp[k].h * kScaleFactor32, lpp[k].l * kScaleFactor32};
+        ++scp[k];
+      }
+      if (scm[k] < 0 && fabsf(lmc[k].h) > kScaleUp32) {
+        lmc[k] = {lmc[k].h * kScaleFactor32, lmc[k].l * kScaleFactor32};
+        lmp[k] = {lmp[k].h * kScaleFactor32, lmp[k].l * kScaleFactor32};
+        ++scm[k];
+      }
+    }
+  };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int lb = l0; lb <= lmax; lb += LC) {
     f2 v[32];
@@ -501,13 +548,14 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
 #pragma unroll
     for (int q = 0; q < LC; ++q) {
       const int l = lb + q;
+      if (q > 0 && (q & 7) == 0) rescale_all();  // at most 8 steps between exponent checks
       if (l <= lmax) {
         const Coef32 c = ld_coef32(cf + 2 * l);
         const f2 nc = neg(c.c);
         const bool even = ((l - l0) & 1) == 0;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          const f2 wp = sel(scp[k] == 0, lpc[k]);
+          const f2 wp = weight(lpc[k], scp[k]);
           if (!SPIN) {
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
@@ -521,7 +569,7 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
             lpp[k] = lpc[k];
             lpc[k] = ln;
           } else {
-            const f2 wm = sel(scm[k] == 0, lmc[k]);
+            const f2 wm = weight(lmc[k], scm[k]);
             const f2 sp = even ? wp : neg(wp), sm = even ? wm : neg(wm);
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
@@ -547,21 +595,9 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
         }
       }
     }
+    rescale_all();
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      if (scp[k] < 0 && fabsf(lpc[k].h) > kScaleUp32) {
-        lpc[k] = {lpc[k].h * kScaleFactor32, lpc[k].l * kScaleFactor32};
-        lpp[k] = {lpp[k].h * kScaleFactor32, lpp[k].l * kScaleFactor32};
-        ++scp[k];
-      }
-      if (scm[k] < 0 && fabsf(lmc[k].h) > kScaleUp32) {
-        lmc[k] = {lmc[k].h * kScaleFactor32, lmc[k].l * kScaleFactor32};
-        lmp[k] = {lmp[k].h * kScaleFactor32, lmp[k].l * kScaleFactor32};
-        ++scm[k];
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) renorm(v[i]);
+    for (int i = 0; i < 32; ++i) v[i] = two_sum(v[i].h, v[i].l);  // exact even if the low word dominates
     const f2 wsum = warp_reduce_scatter32(v);
     red[warp][lane] = wsum;
     __syncthreads();
