@@ -201,6 +201,33 @@ SHT_API void sht_plan_destroy(sht_plan_t plan);
 SHT_API int sht_plan_profile(sht_plan_t plan, int enable);
 SHT_API int sht_plan_profile_read(sht_plan_t plan, double *ms, int64_t *count);
 
+/* ---- transforms without allocation -------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that must
+ * not allocate device memory while they run transforms -- code recorded under
+ * CUDA stream capture (cudaMalloc / cudaFree cannot be captured and
+ * synchronise the device), processes whose GPU memory is held by another
+ * allocator's pool, or latency-bound loops that cannot take the implicit
+ * device synchronisation of an allocation.
+ *
+ * sht_execute_noalloc runs the same transform as sht_execute on a plan made
+ * beforehand, with the same arguments and results, but its per-call working
+ * memory (the phase array, the analysis partial sums and the converted a_lm
+ * tables) comes from a fixed 64 MiB area compiled into the library, and the
+ * call allocates nothing, on the device or the host.  Every GPU that loads
+ * the library holds the area until the process exits.  Limit: transforms
+ * whose working memory exceeds 64 MiB (about nmaps * nm * npairs * 32 bytes
+ * for the phase array, plus the analysis partials) are rejected with
+ * SHT_ERR_UNSUPPORTED, the message giving the size needed.  The first call
+ * on each device looks up the area's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture begins.  All calls on a
+ * device share the one area and it keeps the last call's contents (nothing
+ * in it needs to start at zero): calls that overlap on the GPU -- on
+ * different streams or from different threads -- race.  No profiling events
+ * are recorded.  Errors: as sht_execute, plus SHT_ERR_UNSUPPORTED for the size.
+ */
+SHT_API int sht_execute_noalloc(sht_plan_t plan, int type, double *const *alm, double *const *map, int flags,
+                                void *cuda_stream);
+
 /* ---- errors --------------------------------------------------------------- */
 SHT_API const char *sht_strerror(int code);
 SHT_API const char *sht_last_error(void);

@@ -157,6 +157,8 @@ struct sht_plan_s {
 // Cross-TU launch helpers (all return cudaError_t of the launch).
 // ----------------------------------------------------------------------------
 namespace sht {
+// records a message for sht_last_error() on this thread and returns code
+int set_error(int code, const char *fmt, ...);
 // plan-time tables
 cudaError_t launch_coef_tables(const sht_plan_s *P, cudaStream_t st);
 cudaError_t launch_fft_spectrum(const FftPlanDev *host_plan, const FftPlanDev *dev_plan,

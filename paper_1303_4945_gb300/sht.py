@@ -61,6 +61,7 @@ _sig = {
     "sht_plan_workspace": [_vp, _i64p],
     "sht_plan_triples": [_vp, ctypes.c_int, _i64p],
     "sht_plan_destroy": [_vp],
+    "sht_execute_noalloc": [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp],
     "sht_plan_profile": [_vp, ctypes.c_int],
     "sht_plan_profile_read": [_vp, _dp, _i64p],
     "sht_strerror": [ctypes.c_int],
@@ -258,6 +259,18 @@ def sht_execute(plan: Plan, type_, alm, maps, flags=0, stream=None):
     mp = (_vp * n)(*[_devptr(m) for m in maps])
     st = None if stream is None else _vp(_devptr_stream(stream))
     _check(_lib.sht_execute(plan.handle, type_, ap, mp, flags, st), "sht_execute")
+
+
+def sht_execute_noalloc(plan: Plan, type_, alm, maps, flags=0, stream=None):
+    """As sht_execute, but the working memory comes from the library's static
+    area: the call allocates nothing (see include/sht_gb300.h)."""
+    n = plan.narrays
+    if len(alm) != n or len(maps) != n:
+        raise ValueError(f"expected {n} a_lm and {n} map buffers")
+    ap = (_vp * n)(*[_devptr(a) for a in alm])
+    mp = (_vp * n)(*[_devptr(m) for m in maps])
+    st = None if stream is None else _vp(_devptr_stream(stream))
+    _check(_lib.sht_execute_noalloc(plan.handle, type_, ap, mp, flags, st), "sht_execute_noalloc")
 
 
 def _devptr_stream(stream):
