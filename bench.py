@@ -256,26 +256,53 @@ def time_form(sht, torch, plan, alm_d, maps_d, out_d, steps, warmup, world, stre
     return max_over_ranks(ms, world), stages
 
 
-def roofline_for(stages, plan, spin, precision, peaks, steps):
-    """Dominant Legendre kernel vs the pipe it runs on."""
-    import numpy as np  # noqa: F401
+# FP32 operations of the double-float algorithm per (m, l, ring-pair) step, counted
+# from the kernel source (FMA = 2 flops): a compensated multiply-add is 15
+# (exact product 7, two-sum 6, low-word adds 2), the three-float product A cos(theta)
+# is 9, a normalised two-term dot product 25, a three-term one 40.
+#   spin s: 8 multiply-adds + A cos(theta) + two 3-term dots = 120 + 9 + 80 = 209
+#   spin 0: 2 multiply-adds + A cos(theta) + one 2-term dot  =  30 + 9 + 25 =  64
+def f32_flops_per_triple(spin, ncomp):
+    return (89 + 120 * ncomp) if spin else (34 + 30 * ncomp)
 
+
+def launches_per_step(spin, form):
+    """Kernels one synthesis + analysis launches: Legendre, FFT each way, the tile
+    reduction, and the a_lm conversion (spin, or the mixed form)."""
+    return 5 + (1 if (spin != 0 or form == "mixed") else 0)
+
+
+def roofline_for(stages, plan, spin, precision, peaks, steps):
+    """Dominant Legendre kernel vs the pipe it runs on.
+
+    FP64 form: algorithmic FP64 flops (flops_per_triple) against the FP64 pipe.
+    Mixed form: the FP32 flops the double-float algorithm performs
+    (f32_flops_per_triple) against the FP32 pipe; the FP64-equivalent rate
+    (algorithmic FP64 flops / time) is reported beside it.
+    """
     syn_ms, syn_n = stages["legendre_synthesis"]
     ana_ms, ana_n = stages["legendre_analysis"]
     name, t_ms, n = ("legendre_synthesis", syn_ms, syn_n) if syn_ms >= ana_ms else ("legendre_analysis", ana_ms, ana_n)
     per_launch_ms = t_ms / max(n, 1)
-    flops = plan.triples(0) * flops_per_triple(spin, 1)
+    triples = plan.triples(0)
     clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fp64_flops = triples * flops_per_triple(spin, 1)
     if precision == "fp64":
         peak = SMS * 4 * clock / 1e12  # 2 FP64 FMA lanes per SM per clock (measured DFMA rate)
+        flops = fp64_flops
         how = "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x sm_max clock"
     else:
         peak = SMS * 256 * clock / 1e12  # 128 FP32 FMA lanes per SM per clock
+        flops = triples * f32_flops_per_triple(spin, 1)
         how = "FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x sm_max clock"
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
-    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": how,
-            "algorithmic_flops_per_launch": flops, "ms_per_launch": per_launch_ms}
+    out = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "traffic": None, "peak_source": how,
+           "algorithmic_flops_per_launch": flops, "ms_per_launch": per_launch_ms, "triples_per_launch": triples}
+    if precision != "fp64":
+        out["fp64_equivalent_tflops"] = fp64_flops / (per_launch_ms * 1e-3) / 1e12
+        out["fp64_equivalent_frac_of_fp64_peak"] = out["fp64_equivalent_tflops"] / (SMS * 4 * clock / 1e12)
+    return out
 
 
 def main():
@@ -372,7 +399,7 @@ def main():
             "dtype": "f32x2" if head == "mixed" else "f64", "data": "synthetic", "config": CONFIG,
             "form": head, "roofline": results[head]["roofline"], "clocks": clocks,
             "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "gpu_launches": 5 * args.steps, "forms": results}
+            "gpu_launches": launches_per_step(SPIN, head) * args.steps, "forms": results}
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         others = {k: v for k, v in outputs.items() if k != head}
         cb, acc = oracle_sample(args.cpu_seconds, gpu_out=outputs[head], others=others)

@@ -81,6 +81,7 @@ extern "C" {
 typedef struct sht_geom_s *sht_geom_t;
 typedef struct sht_alm_s *sht_alm_t;
 typedef struct sht_plan_s *sht_plan_t;
+typedef struct sht_batch_s *sht_batch_t;
 
 /* ---- geometry (Sect. 2, Sect. 4.4) -------------------------------------- */
 
@@ -227,6 +228,38 @@ SHT_API int sht_plan_profile_read(sht_plan_t plan, double *ms, int64_t *count);
  */
 SHT_API int sht_execute_noalloc(sht_plan_t plan, int type, double *const *alm, double *const *map, int flags,
                                 void *cuda_stream);
+
+/* ---- batches of independent transforms ----------------------------------------
+ * Sect. 3.2 runs several transforms of one plan together; a batch goes further
+ * and runs the transforms of many distinct plans -- different lmax, grids,
+ * ncomp, spins or precisions -- through the same launches.  The work items of
+ * all plans are merged per kernel and ordered longest first, so one grid per
+ * stage covers the whole batch and the GPU's block scheduler balances the
+ * uneven problems.
+ *
+ * sht_batch_create takes nplans distinct plans (all made on one device) and
+ * builds the merged work lists and per-plan argument records on that device;
+ * the batch refers to the plans, which must outlive it.  Limit: the plans'
+ * arrays per side, each plan's count rounded up to a power of two, sum to at
+ * most 1024 (SHT_ERR_UNSUPPORTED otherwise).  Errors: SHT_ERR_INVALID_ARG
+ * (NULL, repeated plan, mixed devices), SHT_ERR_UNSUPPORTED, SHT_ERR_CUDA.
+ *
+ * sht_batch_execute runs transform `type` of every plan at once on
+ * cuda_stream.  alm[k] and map[k] are host arrays holding plan k's device
+ * pointers, exactly as sht_execute takes them; flags apply to all plans.
+ * Results equal those of sht_execute per plan.  The call neither allocates
+ * nor copies nor synchronises (pointers travel as kernel parameters), so it
+ * can be captured in a CUDA graph; a captured graph keeps the pointers of the
+ * call that was captured.  Each plan's workspace is used, so no plan of the
+ * batch may run elsewhere meanwhile, and calls on one batch must not overlap.
+ * Errors: SHT_ERR_INVALID_ARG, SHT_ERR_CUDA.
+ */
+SHT_API int sht_batch_create(int nplans, const sht_plan_t *plans, sht_batch_t *out);
+SHT_API int sht_batch_execute(sht_batch_t batch, int type, double *const *const *alm, double *const *const *map,
+                              int flags, void *cuda_stream);
+/* number of plans in the batch (0 for NULL) */
+SHT_API int sht_batch_size(sht_batch_t batch);
+SHT_API void sht_batch_destroy(sht_batch_t batch);
 
 /* ---- errors --------------------------------------------------------------- */
 SHT_API const char *sht_strerror(int code);

@@ -14,6 +14,9 @@
 //   c_m = F_m e^{i m phi0} (m >= 0), c_{-m} = conj(c_m); m is folded modulo N
 //   when N <= 2 mmax (aliasing, Eq. syn1).
 // Analysis, per ring:   G_m = w e^{-i m phi0} sum_x p_x e^{-2 pi i m x / N}  (Eq. ana2).
+#include <mutex>
+#include <set>
+
 #include "sht_internal.h"
 
 namespace sht {
@@ -141,6 +144,7 @@ struct FftArgs {
   double2 *phase;
   DevPtrs map;
   int weighted, add;
+  int ptr_off;
 };
 
 // ---------------------------------------------------------------------------
@@ -172,11 +176,10 @@ __device__ double2 spectrum_at(const FftArgs &a, int j, int p, int k, int N, dou
   return z;
 }
 
-__global__ void __launch_bounds__(kFftThreads) fft_syn_kernel(FftArgs a) {
+__device__ __forceinline__ void fft_syn_kernel_body(const FftArgs &a, double *const *ptrs, const int p, const int j) {
   extern __shared__ double2 buf[];
   __shared__ double2 sh_x0, sh_a0;
-  const int p = blockIdx.x, j = blockIdx.y;
-  const FftPlanDev fp = a.plans[a.pair_fft[p]];
+    const FftPlanDev fp = a.plans[a.pair_fft[p]];
   const int2 rr = a.pair_rings[p];
   const RingDev rn = a.rings[rr.x];
   const bool south = rr.y >= 0;
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_syn_kernel(FftArgs a) {
   __syncthreads();
   dft_run(buf, fp, &sh_x0, &sh_a0);
   const double2 x0 = sh_x0, a0 = sh_a0;
-  double *mp = a.map.p[j];
+  double *mp = ptrs[j];
   const double wn = a.weighted ? rn.weight : 1.0, ws = a.weighted ? rs.weight : 1.0;
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     const double2 X = dft_at(buf, fp, x, x0, a0);
@@ -215,21 +218,29 @@ __global__ void __launch_bounds__(kFftThreads) fft_syn_kernel(FftArgs a) {
     }
   }
 }
+__global__ void __launch_bounds__(kFftThreads) fft_syn_kernel(FftArgs a) {
+  fft_syn_kernel_body(a, a.map.p, blockIdx.x, blockIdx.y);
+}
+__global__ void __launch_bounds__(kFftThreads) fft_syn_kernel_batch(const FftArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const FftArgs &a = args[it.w];
+  fft_syn_kernel_body(a, tbl.p + a.ptr_off, it.x, it.y);
+}
 
 // ---------------------------------------------------------------------------
 // analysis: ring pixels -> G (per m)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kFftThreads) fft_ana_kernel(FftArgs a) {
+__device__ __forceinline__ void fft_ana_kernel_body(const FftArgs &a, double *const *ptrs, const int p, const int j) {
   extern __shared__ double2 buf[];
   __shared__ double2 sh_x0, sh_a0;
-  const int p = blockIdx.x, j = blockIdx.y;
-  const FftPlanDev fp = a.plans[a.pair_fft[p]];
+    const FftPlanDev fp = a.plans[a.pair_fft[p]];
   const int2 rr = a.pair_rings[p];
   const RingDev rn = a.rings[rr.x];
   const bool south = rr.y >= 0;
   const RingDev rs = a.rings[south ? rr.y : rr.x];
   const int N = fp.n;
-  const double *mp = a.map.p[j];
+  const double *mp = ptrs[j];
   auto zin = [&](int x) {
     const double vn = mp[rn.ofs + (int64_t)x * rn.stride];
     const double vs = south ? mp[rs.ofs + (int64_t)x * rs.stride] : 0.0;
@@ -268,6 +279,15 @@ __global__ void __launch_bounds__(kFftThreads) fft_ana_kernel(FftArgs a) {
     g[1] = gs;
   }
 }
+__global__ void __launch_bounds__(kFftThreads) fft_ana_kernel(FftArgs a) {
+  fft_ana_kernel_body(a, a.map.p, blockIdx.x, blockIdx.y);
+}
+__global__ void __launch_bounds__(kFftThreads) fft_ana_kernel_batch(const FftArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const FftArgs &a = args[it.w];
+  fft_ana_kernel_body(a, tbl.p + a.ptr_off, it.x, it.y);
+}
 
 static FftArgs make_fft_args(const sht_plan_s *P, const DevPtrs &map, int polar) {
   FftArgs a;
@@ -293,8 +313,6 @@ cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, i
   FftArgs a = make_fft_args(P, map, polar);
   a.weighted = weighted;
   a.add = add;
-  cudaError_t e = cudaFuncSetAttribute(fft_syn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, P->fft_smem);
-  if (e != cudaSuccess) return e;
   dim3 grid(P->npairs, P->nmaps);
   fft_syn_kernel<<<grid, kFftThreads, P->fft_smem, st>>>(a);
   return cudaGetLastError();
@@ -303,10 +321,59 @@ cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, i
 cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted, cudaStream_t st) {
   FftArgs a = make_fft_args(P, map, 1);
   a.weighted = weighted;
-  cudaError_t e = cudaFuncSetAttribute(fft_ana_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, P->fft_smem);
-  if (e != cudaSuccess) return e;
   dim3 grid(P->npairs, P->nmaps);
   fft_ana_kernel<<<grid, kFftThreads, P->fft_smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sht
+
+// ---------------------------------------------------------------------------
+// batches (sht_batch_execute)
+// ---------------------------------------------------------------------------
+namespace sht {
+
+size_t fft_args_size() { return sizeof(FftArgs); }
+
+void fft_fill_args(const sht_plan_s *P, int polar, int weighted, int add, int ptr_off, void *out) {
+  DevPtrs none;
+  memset(&none, 0, sizeof(none));
+  FftArgs a = make_fft_args(P, none, polar);
+  a.weighted = weighted;
+  a.add = add;
+  a.ptr_off = ptr_off;
+  memcpy(out, &a, sizeof(a));
+}
+
+cudaError_t fft_prepare_device(int device) {
+  static std::mutex mu;
+  static std::set<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(device)) return cudaSuccess;
+  int smem = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  const void *fns[4] = {(const void *)fft_syn_kernel, (const void *)fft_ana_kernel,
+                        (const void *)fft_syn_kernel_batch, (const void *)fft_ana_kernel_batch};
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    // static + dynamic shared memory may not exceed the opt-in size
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fns[i]);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, smem - (int)fa.sharedSizeBytes);
+  }
+  if (e == cudaSuccess) done.insert(device);
+  return e;
+}
+
+// synthesis (stage 0) or analysis (stage 1) ring FFTs of every item (pair, map, -, args index)
+cudaError_t launch_fft_batch(int stage, const void *args, const int4 *items, int n, int smem, const PtrTable &tbl,
+                             cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const FftArgs *a = static_cast<const FftArgs *>(args);
+  if (stage == 0)
+    fft_syn_kernel_batch<<<n, kFftThreads, smem, st>>>(a, items, tbl);
+  else
+    fft_ana_kernel_batch<<<n, kFftThreads, smem, st>>>(a, items, tbl);
   return cudaGetLastError();
 }
 

@@ -7,12 +7,12 @@
 //   sLambda_lm(pi - t) = (-1)^(l+m) (-s)Lambda_lm(t):
 // even and odd (l+m) terms are kept apart and combined at the end.
 //
-// Spin s != 0 runs the +s and -s recursions as the coupled pair
-//   lp = (sLambda + (-1)^s (-s)Lambda) / 2,  lm = (sLambda - (-1)^s (-s)Lambda) / 2
-//   lp_{l+1} = A x lp + AK lm - C lp_{l-1},   lm_{l+1} = A x lm + AK lp - C lm_{l-1},
-// which is what the E/B <-> Q/U combination needs:
-//   Q: q_m = -sum_l (E lp + i B lm),   U: u_m = -sum_l (B lp - i E lm),
-// with lp(pi - t) = (-1)^(l+m+s) lp(t), lm(pi - t) = -(-1)^(l+m+s) lm(t).
+// Spin s != 0 runs the +s and -s recursions side by side, each with its own
+// exponent, and contracts them with P = E + iB and M = E - iB:
+//   Q + iU = sum_m e^{im phi} [ -(1/2) sum_l (P (s)Lambda + (-1)^s M (-s)Lambda) ] + c.c. terms,
+// see leg_syn_spin; the analysis uses W+- = G_Q +- i G_U the same way.
+// Blocks of the growth phase in which no lane has reached scale 0 run the
+// recursion alone.
 //
 // Enhanced exponent range (Sect. 4.1): the recursion pair is held as
 // y * 2^(600 scale); while scale < 0 the terms are below ~2^-300 and are not
@@ -39,6 +39,7 @@ struct LegArgs {
   const int *tile0;
   double *part;
   int ana_tiles, ppt, add;
+  int ptr_off;  // batch: first entry of this plan in the pointer table
 };
 
 __device__ __forceinline__ int warp_any(bool b) { return __any_sync(0xffffffffu, b); }
@@ -47,8 +48,7 @@ __device__ __forceinline__ int warp_any(bool b) { return __any_sync(0xffffffffu,
 // Synthesis, spin 0:  F_{m,y} = sum_l a_lm lambda_lm(theta_y)   (Eq. syn2)
 // ---------------------------------------------------------------------------
 template <int NJ>
-__global__ void __launch_bounds__(kSynTile) leg_syn_s0(LegArgs a) {
-  const int2 item = a.syn_items[blockIdx.x];
+__device__ __forceinline__ void leg_syn_s0_body(const LegArgs &a, double *const *ptrs, const int2 item) {
   const int mi = item.x;
   const int p = item.y + threadIdx.x;
   const bool valid = p < a.npairs;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kSynTile) leg_syn_s0(LegArgs a) {
   const int64_t st = a.astride;
   const double2 *al[NJ];
 #pragma unroll
-  for (int j = 0; j < NJ; ++j) al[j] = reinterpret_cast<const double2 *>(a.alm.p[j]) + a.mstart[mi];
+  for (int j = 0; j < NJ; ++j) al[j] = reinterpret_cast<const double2 *>(ptrs[j]) + a.mstart[mi];
 
   const PairDev pd = a.pairs[valid ? p : 0];
   const double x = pd.x;
@@ -76,7 +76,27 @@ __global__ void __launch_bounds__(kSynTile) leg_syn_s0(LegArgs a) {
 
   int l = l0;
   // growth phase: 8 steps per check, terms accumulate only at scale 0
+  // (values at scale < 0 are below 2^-250); blocks in which no lane of the
+  // warp has reached scale 0 run the recursion alone
   while (l <= lmax && warp_any(scale < 0)) {
+    if (!warp_any(scale == 0)) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (l <= lmax) {
+          const Coef c = ldg_coef(cf + l);
+          const double ln = fma(c.a * x, lc, -c.c * lp);
+          lp = lc;
+          lc = ln;
+          ++l;
+        }
+      }
+      if (scale < 0 && fabs(lc) > kScaleUp) {
+        lc *= kScaleFactor;
+        lp *= kScaleFactor;
+        ++scale;
+      }
+      continue;
+    }
 #pragma unroll
     for (int k = 0; k < 8; k += 2) {
 #pragma unroll
@@ -139,8 +159,18 @@ __global__ void __launch_bounds__(kSynTile) leg_syn_s0(LegArgs a) {
     o[1] = fs;
   }
 }
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) leg_syn_s0(LegArgs a) {
+  leg_syn_s0_body<NJ>(a, a.alm.p, a.syn_items[blockIdx.x]);
+}
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) leg_syn_s0_batch(const LegArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const LegArgs &a = args[it.w];
+  leg_syn_s0_body<NJ>(a, tbl.p + a.ptr_off, make_int2(it.x, it.y));
+}
 
-// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Synthesis, spin s.  The +s and -s recursions run separately, each with its
 // own exponent (near the poles one is smaller than the other by
@@ -152,8 +182,7 @@ __global__ void __launch_bounds__(kSynTile) leg_syn_s0(LegArgs a) {
 // with sig = (-1)^s, from sLambda(pi - t) = (-1)^(l+m) (-s)Lambda(t).
 // ---------------------------------------------------------------------------
 template <int NJ>
-__global__ void __launch_bounds__(kSynTile) leg_syn_spin(LegArgs a) {
-  const int2 item = a.syn_items[blockIdx.x];
+__device__ __forceinline__ void leg_syn_spin_body(const LegArgs &a, double *const *ptrs, const int2 item) {
   const int mi = item.x;
   const int p = item.y + threadIdx.x;
   const bool valid = p < a.npairs;
@@ -205,13 +234,30 @@ __global__ void __launch_bounds__(kSynTile) leg_syn_spin(LegArgs a) {
 
   int l = l0;
   while (l <= lmax && warp_any(scp < 0 || scm < 0)) {
+    if (!warp_any(scp == 0 || scm == 0)) {  // every term of the warp below 2^-250
 #pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-#pragma unroll
-      for (int par = 0; par < 2; ++par) {
+      for (int k = 0; k < 8; ++k) {
         if (l <= lmax) {
-          step(l, par, false);
+          const Coef c = ldg_coef(cf + l);
+          const double t = c.a * x;
+          const double np_ = fma(t + c.ak, lpc, -c.c * lpp);
+          const double nm_ = fma(t - c.ak, lmc, -c.c * lmp);
+          lpp = lpc;
+          lpc = np_;
+          lmp = lmc;
+          lmc = nm_;
           ++l;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+          if (l <= lmax) {
+            step(l, par, false);
+            ++l;
+          }
         }
       }
     }
@@ -254,6 +300,17 @@ __global__ void __launch_bounds__(kSynTile) leg_syn_spin(LegArgs a) {
     ou[0] = un;
     ou[1] = us;
   }
+}
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) leg_syn_spin(LegArgs a) {
+  leg_syn_spin_body<NJ>(a, a.alm.p, a.syn_items[blockIdx.x]);
+}
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) leg_syn_spin_batch(const LegArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const LegArgs &a = args[it.w];
+  leg_syn_spin_body<NJ>(a, tbl.p + a.ptr_off, make_int2(it.x, it.y));
 }
 // ---------------------------------------------------------------------------
 // Analysis (Eq. ana1): a_lm = sum_y G_{m,y} lambda_lm(theta_y).
@@ -306,10 +363,9 @@ __device__ __forceinline__ double warp_reduce_scatter32(double (&v)[32]) {
 }
 
 template <int NJ, int PPT>
-__global__ void __launch_bounds__(kAnaThreads) leg_ana_s0(LegArgs a) {
+__device__ __forceinline__ void leg_ana_s0_body(const LegArgs &a, double *const *ptrs, const int4 item) {
   constexpr int V = 2 * NJ, LC = 32 / V;
   __shared__ double red[kAnaThreads / 32][32];
-  const int4 item = a.ana_items[blockIdx.x];
   const int mi = item.x, tile = item.y;
   const int m = a.mval[mi];
   const int l0 = m, lmax = a.lmax, nl = lmax - l0 + 1;
@@ -347,6 +403,34 @@ __global__ void __launch_bounds__(kAnaThreads) leg_ana_s0(LegArgs a) {
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int lb = l0; lb <= lmax; lb += LC) {
+    bool mine = false;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) mine = mine || scale[k] == 0;
+    if (!__syncthreads_or(mine)) {  // no term of this tile above 2^-250 yet: recursion only
+#pragma unroll
+      for (int q = 0; q < LC; ++q) {
+        const int l = lb + q;
+        if (l <= lmax) {
+          const Coef c = ldg_coef(cf + l);
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const double ln = fma(c.a * x[k], lc[k], -c.c * lp[k]);
+            lp[k] = lc[k];
+            lc[k] = ln;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (scale[k] < 0 && fabs(lc[k]) > kScaleUp) {
+          lc[k] *= kScaleFactor;
+          lp[k] *= kScaleFactor;
+          ++scale[k];
+        }
+      }
+      if (warp == 0 && lb + lane / V <= lmax) outp[(int64_t)(lb - l0) * V + lane] = 0.0;
+      continue;
+    }
     double v[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = 0.0;
@@ -393,16 +477,26 @@ __global__ void __launch_bounds__(kAnaThreads) leg_ana_s0(LegArgs a) {
     __syncthreads();
   }
 }
+template <int NJ, int PPT>
+__global__ void __launch_bounds__(kAnaThreads) leg_ana_s0(LegArgs a) {
+  leg_ana_s0_body<NJ, PPT>(a, a.alm.p, a.ana_items[blockIdx.x]);
+}
+template <int NJ, int PPT>
+__global__ void __launch_bounds__(kAnaThreads) leg_ana_s0_batch(const LegArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const LegArgs &a = args[it.w];
+  leg_ana_s0_body<NJ, PPT>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, 0, 0));
+}
 
 // Spin analysis with separate +s / -s recursions.  Per ring W+ = GQ + i GU,
 // W- = GQ - i GU; per degree l the pair contributes
 //   T1 = W+_N l+ + (-1)^(l+m) W+_S l-,   T2 = W-_N l- + (-1)^(l+m) W-_S l+,
 // and the reduction kernel forms E = -(T1 + sig T2)/2, B = -(i/2)(sig T2 - T1).
 template <int NJ, int PPT>
-__global__ void __launch_bounds__(kAnaThreads) leg_ana_spin(LegArgs a) {
+__device__ __forceinline__ void leg_ana_spin_body(const LegArgs &a, double *const *ptrs, const int4 item) {
   constexpr int V = 4 * NJ, LC = 32 / V;
   __shared__ double red[kAnaThreads / 32][32];
-  const int4 item = a.ana_items[blockIdx.x];
   const int mi = item.x, tile = item.y;
   const int m = a.mval[mi];
   const int s = a.spin, as = s < 0 ? -s : s;
@@ -454,6 +548,43 @@ __global__ void __launch_bounds__(kAnaThreads) leg_ana_spin(LegArgs a) {
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int lb = l0; lb <= lmax; lb += LC) {
+    bool mine = false;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) mine = mine || scp[k] == 0 || scm[k] == 0;
+    if (!__syncthreads_or(mine)) {  // no term of this tile above 2^-250 yet: recursion only
+#pragma unroll
+      for (int q = 0; q < LC; ++q) {
+        const int l = lb + q;
+        if (l <= lmax) {
+          const Coef c = ldg_coef(cf + l);
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const double t = c.a * x[k];
+            const double np_ = fma(t + c.ak, lpc[k], -c.c * lpp[k]);
+            const double nm_ = fma(t - c.ak, lmc[k], -c.c * lmp[k]);
+            lpp[k] = lpc[k];
+            lpc[k] = np_;
+            lmp[k] = lmc[k];
+            lmc[k] = nm_;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (scp[k] < 0 && fabs(lpc[k]) > kScaleUp) {
+          lpc[k] *= kScaleFactor;
+          lpp[k] *= kScaleFactor;
+          ++scp[k];
+        }
+        if (scm[k] < 0 && fabs(lmc[k]) > kScaleUp) {
+          lmc[k] *= kScaleFactor;
+          lmp[k] *= kScaleFactor;
+          ++scm[k];
+        }
+      }
+      if (warp == 0 && lb + lane / V <= lmax) outp[(int64_t)(lb - l0) * V + lane] = 0.0;
+      continue;
+    }
     double v[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = 0.0;
@@ -512,6 +643,17 @@ __global__ void __launch_bounds__(kAnaThreads) leg_ana_spin(LegArgs a) {
     }
     __syncthreads();
   }
+}
+template <int NJ, int PPT>
+__global__ void __launch_bounds__(kAnaThreads) leg_ana_spin(LegArgs a) {
+  leg_ana_spin_body<NJ, PPT>(a, a.alm.p, a.ana_items[blockIdx.x]);
+}
+template <int NJ, int PPT>
+__global__ void __launch_bounds__(kAnaThreads) leg_ana_spin_batch(const LegArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const LegArgs &a = args[it.w];
+  leg_ana_spin_body<NJ, PPT>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, 0, 0));
 }
 
 // Adds the tiles of every (m, l) in tile order and writes a_lm.
@@ -679,6 +821,74 @@ cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar
   ana_reduce<<<grid, 128, 0, st>>>(P->lmax, P->spin, P->nm, P->njobs_pad, P->ncomp, P->ana_tiles, P->astride, add,
                                    P->d_mval, P->d_mstart, P->d_ana_part_off[polar], P->d_ana_tile0[polar],
                                    P->d_part, alm);
+  return cudaGetLastError();
+}
+
+}  // namespace sht
+
+// ---------------------------------------------------------------------------
+// batches (sht_batch_execute): per-plan argument records and batched launches
+// ---------------------------------------------------------------------------
+namespace sht {
+
+size_t leg_fp64_args_size() { return sizeof(LegArgs); }
+
+void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out) {
+  DevPtrs none;
+  memset(&none, 0, sizeof(none));
+  LegArgs a = make_args(P, none, polar);
+  a.ptr_off = ptr_off;
+  memcpy(out, &a, sizeof(a));
+}
+
+cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st) {
+  if (P->spin == 0 || P->nm == 0) return cudaSuccess;
+  dim3 g(P->nm, P->njobs_pad);
+  alm_to_pm<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->astride, P->d_mval, P->d_mstart, P->d_coef_off,
+                               P->ncoef, alm, P->d_pm64);
+  return cudaGetLastError();
+}
+
+// stage 0: synthesis, 1: analysis; all plans of the launch share spin class and njobs_pad
+cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, const void *args, const int4 *items, int n,
+                                  const PtrTable &tbl, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const LegArgs *a = static_cast<const LegArgs *>(args);
+  if (stage == 0) {
+    if (spin == 0) {
+      switch (nj) {
+        case 1: leg_syn_s0_batch<1><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 2: leg_syn_s0_batch<2><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 4: leg_syn_s0_batch<4><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 8: leg_syn_s0_batch<8><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        default: leg_syn_s0_batch<16><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+      }
+    } else {
+      switch (nj) {
+        case 1: leg_syn_spin_batch<1><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 2: leg_syn_spin_batch<2><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 4: leg_syn_spin_batch<4><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        default: leg_syn_spin_batch<8><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+      }
+    }
+  } else {
+    if (spin == 0) {
+      switch (nj) {
+        case 1: leg_ana_s0_batch<1, 4><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 2: leg_ana_s0_batch<2, 4><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 4: leg_ana_s0_batch<4, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 8: leg_ana_s0_batch<8, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        default: leg_ana_s0_batch<16, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+      }
+    } else {
+      switch (nj) {
+        case 1: leg_ana_spin_batch<1, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 2: leg_ana_spin_batch<2, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 4: leg_ana_spin_batch<4, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        default: leg_ana_spin_batch<8, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+      }
+    }
+  }
   return cudaGetLastError();
 }
 

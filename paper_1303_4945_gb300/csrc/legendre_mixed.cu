@@ -75,19 +75,21 @@ __device__ __forceinline__ f2 mul(f2 a, f3 x) {
   e = __fmaf_rn(a.h, x.m, e);
   return {p, e};
 }
-// a b + c d, normalised
+// a b + c d, normalised.  The final fast two-sum is needed: when the
+// recursion's terms cancel (oscillatory regime) the low word of the raw sum
+// can be as large as the high word, and the next product would then drop
+// bits at FP32 precision.
 __device__ __forceinline__ f2 dot2(f2 a, f2 b, f2 c, f2 d) {
   const f2 p = mul(a, b), q = mul(c, d);
   const f2 s = two_sum(p.h, q.h);
   return fast_two_sum(s.h, __fadd_rn(__fadd_rn(p.l, q.l), s.l));
 }
-// a b + c d + e f, normalised
+// a b + c d + e f, normalised (see dot2)
 __device__ __forceinline__ f2 dot3(f2 a, f2 b, f2 c, f2 d, f2 e, f2 f) {
   const f2 p = mul(a, b), q = mul(c, d), r = mul(e, f);
   const f2 s1 = two_sum(p.h, q.h);
   const f2 s2 = two_sum(s1.h, r.h);
-  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p.l, q.l), r.l), __fadd_rn(s1.l, s2.l));
-  return fast_two_sum(s2.h, lo);
+  return fast_two_sum(s2.h, __fadd_rn(__fadd_rn(__fadd_rn(p.l, q.l), r.l), __fadd_rn(s1.l, s2.l)));
 }
 // acc += w * a with a lazily carried low word (renormalised every few steps)
 __device__ __forceinline__ void acc_mul(f2 &acc, f2 w, float ah, float al) {
@@ -109,6 +111,13 @@ __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
 __device__ __forceinline__ f2 weight(f2 y, int scale) {
   const float f = (scale == 0) ? 1.f : ((scale == -1) ? kScaleFactor32 : 0.f);
   return {y.h * f, y.l * f};
+}
+
+// True value below 2^-74 (scale -1: y 2^-104 with |y| < 2^30; scale <= -2:
+// |y| < 2^102 between checks): even after two more steps (growth < 2^14) it
+// stays below 2^-60 and its terms can be skipped.
+__device__ __forceinline__ bool negligible(f2 y, int scale) {
+  return scale <= -2 || (scale == -1 && fabsf(y.h) < 0x1p30f);
 }
 
 // (mant * 2^E) -> (y, scale) with value = y * 2^(104 scale), y's exponent in [-52, 52)
@@ -139,6 +148,7 @@ struct MixArgs {
   const int *tile0;
   double *part;
   int ana_tiles;
+  int ptr_off;
 };
 
 struct Coef32 {
@@ -199,10 +209,13 @@ __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, con
 
 // ---------------------------------------------------------------------------
 // synthesis, spin 0
+//
+// Loop bodies hold two steps (static even/odd parity) and are not unrolled
+// further: the double-float step is ~170 instructions, and longer unrolled
+// bodies stalled the issue on instruction fetch.
 // ---------------------------------------------------------------------------
 template <int NJ>
-__global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
-  const int2 item = a.syn_items[blockIdx.x];
+__device__ __forceinline__ void mix_syn_s0_body(const MixArgs &a, double *const *ptrs, const int2 item) {
   const int mi = item.x;
   const int p = item.y + threadIdx.x;
   const bool valid = p < a.npairs;
@@ -239,6 +252,13 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
     lp = lc;
     lc = ln;
   };
+  auto recur = [&](int l) {  // recursion only (every lane's term negligible)
+    const Coef32 c = ld_coef32(cf + 2 * l);
+    const f2 t = mul(c.a, x);
+    const f2 ln = dot2(t, lc, neg(c.c), lp);
+    lp = lc;
+    lc = ln;
+  };
   auto renorm_all = [&]() {
 #pragma unroll
     for (int q = 0; q < 2; ++q)
@@ -251,14 +271,14 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
 
   int l = l0;
   while (l <= lmax && __any_sync(0xffffffffu, scale < 0)) {
-#pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-#pragma unroll
-      for (int par = 0; par < 2; ++par) {
-        if (l <= lmax) {
-          step(l, par, false);
-          ++l;
-        }
+#pragma unroll 1
+    for (int k = 0; k < 4 && l <= lmax; ++k, l += 2) {
+      if (__all_sync(0xffffffffu, negligible(lc, scale))) {
+        recur(l);
+        if (l + 1 <= lmax) recur(l + 1);
+      } else {
+        step(l, 0, false);
+        if (l + 1 <= lmax) step(l + 1, 1, false);
       }
     }
     if (scale < 0 && fabsf(lc.h) > kScaleUp32) {
@@ -268,18 +288,15 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
     }
     renorm_all();
   }
-  while (l + 7 <= lmax) {
-#pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-      step(l + k, 0, true);
-      step(l + k + 1, 1, true);
-    }
-    l += 8;
-    renorm_all();
-  }
+  int since = 0;
+#pragma unroll 1
   for (; l + 1 <= lmax; l += 2) {
     step(l, 0, true);
     step(l + 1, 1, true);
+    if (++since == 8) {
+      renorm_all();
+      since = 0;
+    }
   }
   if (l <= lmax) step(l, 0, true);
   if (!valid) return;
@@ -294,13 +311,23 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
     o[1] = fs;
   }
 }
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) mix_syn_s0(MixArgs a) {
+  mix_syn_s0_body<NJ>(a, nullptr, a.syn_items[blockIdx.x]);
+}
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) mix_syn_s0_batch(const MixArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const MixArgs &a = args[it.w];
+  mix_syn_s0_body<NJ>(a, tbl.p + a.ptr_off, make_int2(it.x, it.y));
+}
 
 // ---------------------------------------------------------------------------
 // synthesis, spin s: separate +s / -s recursions (see legendre_fp64.cu)
 // ---------------------------------------------------------------------------
 template <int NJ>
-__global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
-  const int2 item = a.syn_items[blockIdx.x];
+__device__ __forceinline__ void mix_syn_spin_body(const MixArgs &a, double *const *ptrs, const int2 item) {
   const int mi = item.x;
   const int p = item.y + threadIdx.x;
   const bool valid = p < a.npairs;
@@ -352,6 +379,17 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
     lmp = lmc;
     lmc = nm_;
   };
+  auto recur = [&](int l) {  // recursion only (every lane's terms negligible)
+    const Coef32 c = ld_coef32(cf + 2 * l);
+    const f2 t = mul(c.a, x);
+    const f2 nc = neg(c.c);
+    const f2 np_ = dot3(t, lpc, c.ak, lpc, nc, lpp);
+    const f2 nm_ = dot3(t, lmc, neg(c.ak), lmc, nc, lmp);
+    lpp = lpc;
+    lpc = np_;
+    lmp = lmc;
+    lmc = nm_;
+  };
   auto renorm_all = [&]() {
 #pragma unroll
     for (int j = 0; j < NJ; ++j)
@@ -364,14 +402,14 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
 
   int l = l0;
   while (l <= lmax && __any_sync(0xffffffffu, scp < 0 || scm < 0)) {
-#pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-#pragma unroll
-      for (int par = 0; par < 2; ++par) {
-        if (l <= lmax) {
-          step(l, par, false);
-          ++l;
-        }
+#pragma unroll 1
+    for (int k = 0; k < 4 && l <= lmax; ++k, l += 2) {
+      if (__all_sync(0xffffffffu, negligible(lpc, scp) && negligible(lmc, scm))) {
+        recur(l);
+        if (l + 1 <= lmax) recur(l + 1);
+      } else {
+        step(l, 0, false);
+        if (l + 1 <= lmax) step(l + 1, 1, false);
       }
     }
     if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
@@ -386,18 +424,15 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
     }
     renorm_all();
   }
-  while (l + 7 <= lmax) {
-#pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-      step(l + k, 0, true);
-      step(l + k + 1, 1, true);
-    }
-    l += 8;
-    renorm_all();
-  }
+  int since = 0;
+#pragma unroll 1
   for (; l + 1 <= lmax; l += 2) {
     step(l, 0, true);
     step(l + 1, 1, true);
+    if (++since == 8) {
+      renorm_all();
+      since = 0;
+    }
   }
   if (l <= lmax) step(l, 0, true);
   if (!valid) return;
@@ -427,35 +462,34 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
     ou[1] = us;
   }
 }
-
-// ---------------------------------------------------------------------------
-// analysis (see legendre_fp64.cu for the tile / chunk / reduction scheme)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ f2 shfl_xor_f2(f2 v, int mask) {
-  return {__shfl_xor_sync(0xffffffffu, v.h, mask), __shfl_xor_sync(0xffffffffu, v.l, mask)};
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) mix_syn_spin(MixArgs a) {
+  mix_syn_spin_body<NJ>(a, nullptr, a.syn_items[blockIdx.x]);
+}
+template <int NJ>
+__global__ void __launch_bounds__(kSynTile) mix_syn_spin_batch(const MixArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const MixArgs &a = args[it.w];
+  mix_syn_spin_body<NJ>(a, tbl.p + a.ptr_off, make_int2(it.x, it.y));
 }
 
-// 32 double-float values per lane -> lane v holds the warp sum of value v
-__device__ __forceinline__ f2 warp_reduce_scatter32(f2 (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const bool up = lane & w;
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      const f2 send = up ? v[i] : v[i + w];
-      const f2 keep = up ? v[i + w] : v[i];
-      v[i] = f2_add(keep, shfl_xor_f2(send, w));
-    }
-  }
-  return v[0];
-}
-
+// ---------------------------------------------------------------------------
+// analysis (tiles and partial sums as in legendre_fp64.cu).
+//
+// Each thread walks PPT ring pairs.  For every degree l it sums its pairs'
+// V contributions in registers and stores them to a shared-memory slot
+// table [32 slots = LC degrees x V values][threads]; after LC degrees the
+// 32 slots are reduced over the CTA's threads (4 threads per slot, then 4
+// partial sums per slot) and written as the tile's partial sums.  Degrees
+// are walked two at a time so the even/odd parity is static.
+// ---------------------------------------------------------------------------
 template <int NJ, int PPT, bool SPIN>
-__global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
+__device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *ptrs, const int4 item) {
   constexpr int V = (SPIN ? 4 : 2) * NJ, LC = 32 / V;
-  __shared__ f2 red[kAnaThreads / 32][32];
-  const int4 item = a.ana_items[blockIdx.x];
+  static_assert(V * LC == 32, "32 slots per chunk");
+  __shared__ f2 slot[32][kAnaThreads + 1];
+  __shared__ f2 quart[kAnaThreads / 32][32];
   const int mi = item.x, tile = item.y;
   const int m = a.mval[mi];
   const int s = a.spin, as = s < 0 ? -s : s;
@@ -463,15 +497,17 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
   const float4 *__restrict__ cf = a.coef32 + 2 * (a.coef_off[mi] - l0);
   double *outp = a.part + a.part_off[mi] + (int64_t)(tile - a.tile0[mi]) * nl * V;
   const double sg0 = ((l0 + m) & 1) ? -1.0 : 1.0;
+  const int tid = threadIdx.x;
 
   f3 x[PPT];
   f2 lpc[PPT], lmc[PPT], lpp[PPT], lmp[PPT];
   int scp[PPT], scm[PPT];
-  // spin 0: g[k][j][0..1] = G_N +- G_S (complex) ; spin: Q+-, U+- (complex)
+  // spin 0: g[k][j][0..1] = G_N + G_S, G_N - G_S (complex);
+  // spin:   g[k][j][0..3] = W+_N, W-_N, (-1)^(l0+m) W+_S, (-1)^(l0+m) W-_S (complex)
   f2 g[PPT][NJ][SPIN ? 4 : 2][2];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int p = tile * (kAnaThreads * PPT) + threadIdx.x + k * kAnaThreads;
+    const int p = tile * (kAnaThreads * PPT) + tid + k * kAnaThreads;
     const bool valid = p < a.npairs;
     const PairDev pd = a.pairs[valid ? p : 0];
     x[k] = f3_of(pd.x);
@@ -513,7 +549,6 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
             us = gu[1];
           }
         }
-        // W+ = GQ + i GU, W- = GQ - i GU (north; south ones times (-1)^(l0+m))
         g[k][j][0][0] = f2_of(qn.x - un.y);
         g[k][j][0][1] = f2_of(qn.y + un.x);
         g[k][j][1][0] = f2_of(qn.x + un.y);
@@ -525,6 +560,56 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
       }
     }
   }
+
+  // one degree: this thread's V contributions (summed over its pairs) into c[]
+  auto step = [&](int l, bool odd, bool act, f2 (&c)[V]) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) c[v] = f2{0.f, 0.f};
+    // past lmax (second half of the last pair of degrees) the coefficients of
+    // lmax stand in: the values are finite, never stored, and no table entry
+    // outside this m is read
+    const Coef32 cc = ld_coef32(cf + 2 * (l <= lmax ? l : lmax));
+    const f2 nc = neg(cc.c);
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const f2 wp = act ? lpc[k] : weight(lpc[k], scp[k]);
+      if (!SPIN) {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const f2 gr = odd ? g[k][j][1][0] : g[k][j][0][0];
+          const f2 gi = odd ? g[k][j][1][1] : g[k][j][0][1];
+          acc_mul(c[2 * j], wp, gr.h, gr.l);
+          acc_mul(c[2 * j + 1], wp, gi.h, gi.l);
+        }
+        const f2 t = mul(cc.a, x[k]);
+        const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
+        lpp[k] = lpc[k];
+        lpc[k] = ln;
+      } else {
+        const f2 wm = act ? lmc[k] : weight(lmc[k], scm[k]);
+        const f2 sp = odd ? neg(wp) : wp, sm = odd ? neg(wm) : wm;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          // T1 = W+_N l+ + (+-) W+_S l-,  T2 = W-_N l- + (+-) W-_S l+
+          acc_mul(c[4 * j + 0], wp, g[k][j][0][0].h, g[k][j][0][0].l);
+          acc_mul(c[4 * j + 0], sm, g[k][j][2][0].h, g[k][j][2][0].l);
+          acc_mul(c[4 * j + 1], wp, g[k][j][0][1].h, g[k][j][0][1].l);
+          acc_mul(c[4 * j + 1], sm, g[k][j][2][1].h, g[k][j][2][1].l);
+          acc_mul(c[4 * j + 2], wm, g[k][j][1][0].h, g[k][j][1][0].l);
+          acc_mul(c[4 * j + 2], sp, g[k][j][3][0].h, g[k][j][3][0].l);
+          acc_mul(c[4 * j + 3], wm, g[k][j][1][1].h, g[k][j][1][1].l);
+          acc_mul(c[4 * j + 3], sp, g[k][j][3][1].h, g[k][j][3][1].l);
+        }
+        const f2 t = mul(cc.a, x[k]);
+        const f2 np_ = dot3(t, lpc[k], cc.ak, lpc[k], nc, lpp[k]);
+        const f2 nm_ = dot3(t, lmc[k], neg(cc.ak), lmc[k], nc, lmp[k]);
+        lpp[k] = lpc[k];
+        lpc[k] = np_;
+        lmp[k] = lmc[k];
+        lmc[k] = nm_;
+      }
+    }
+  };
   auto rescale_all = [&]() {
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
@@ -540,76 +625,111 @@ __global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
       }
     }
   };
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int lb = l0; lb <= lmax; lb += LC) {
-    f2 v[32];
+  auto put = [&](int q, const f2 (&c)[V]) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = f2{0.f, 0.f};
+    for (int v = 0; v < V; ++v) slot[q * V + v][tid] = c[v];
+  };
+
+  auto recur = [&](int l) {  // recursion only
+    const Coef32 cc = ld_coef32(cf + 2 * (l <= lmax ? l : lmax));
+    const f2 nc = neg(cc.c);
 #pragma unroll
-    for (int q = 0; q < LC; ++q) {
-      const int l = lb + q;
-      if (q > 0 && (q & 7) == 0) rescale_all();  // at most 8 steps between exponent checks
-      if (l <= lmax) {
-        const Coef32 c = ld_coef32(cf + 2 * l);
-        const f2 nc = neg(c.c);
-        const bool even = ((l - l0) & 1) == 0;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          const f2 wp = weight(lpc[k], scp[k]);
-          if (!SPIN) {
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-              const f2 gr = even ? g[k][j][0][0] : g[k][j][1][0];
-              const f2 gi = even ? g[k][j][0][1] : g[k][j][1][1];
-              acc_mul(v[q * V + 2 * j], wp, gr.h, gr.l);
-              acc_mul(v[q * V + 2 * j + 1], wp, gi.h, gi.l);
-            }
-            const f2 t = mul(c.a, x[k]);
-            const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
-            lpp[k] = lpc[k];
-            lpc[k] = ln;
-          } else {
-            const f2 wm = weight(lmc[k], scm[k]);
-            const f2 sp = even ? wp : neg(wp), sm = even ? wm : neg(wm);
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-              // T1 = W+_N l+ + (+-) W+_S l-,  T2 = W-_N l- + (+-) W-_S l+
-              const int o = q * V + 4 * j;
-              acc_mul(v[o + 0], wp, g[k][j][0][0].h, g[k][j][0][0].l);
-              acc_mul(v[o + 0], sm, g[k][j][2][0].h, g[k][j][2][0].l);
-              acc_mul(v[o + 1], wp, g[k][j][0][1].h, g[k][j][0][1].l);
-              acc_mul(v[o + 1], sm, g[k][j][2][1].h, g[k][j][2][1].l);
-              acc_mul(v[o + 2], wm, g[k][j][1][0].h, g[k][j][1][0].l);
-              acc_mul(v[o + 2], sp, g[k][j][3][0].h, g[k][j][3][0].l);
-              acc_mul(v[o + 3], wm, g[k][j][1][1].h, g[k][j][1][1].l);
-              acc_mul(v[o + 3], sp, g[k][j][3][1].h, g[k][j][3][1].l);
-            }
-            const f2 t = mul(c.a, x[k]);
-            const f2 np_ = dot3(t, lpc[k], c.ak, lpc[k], nc, lpp[k]);
-            const f2 nm_ = dot3(t, lmc[k], neg(c.ak), lmc[k], nc, lmp[k]);
-            lpp[k] = lpc[k];
-            lpc[k] = np_;
-            lmp[k] = lmc[k];
-            lmc[k] = nm_;
-          }
-        }
+    for (int k = 0; k < PPT; ++k) {
+      const f2 t = mul(cc.a, x[k]);
+      if (!SPIN) {
+        const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
+        lpp[k] = lpc[k];
+        lpc[k] = ln;
+      } else {
+        const f2 np_ = dot3(t, lpc[k], cc.ak, lpc[k], nc, lpp[k]);
+        const f2 nm_ = dot3(t, lmc[k], neg(cc.ak), lmc[k], nc, lmp[k]);
+        lpp[k] = lpc[k];
+        lpc[k] = np_;
+        lmp[k] = lmc[k];
+        lmc[k] = nm_;
       }
     }
-    rescale_all();
+  };
+  auto mode = [&]() {  // 0: all terms at scale 0, 2: all negligible, 1: weighted
+    bool ok = true, dead = true;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = two_sum(v[i].h, v[i].l);  // exact even if the low word dominates
-    const f2 wsum = warp_reduce_scatter32(v);
-    red[warp][lane] = wsum;
-    __syncthreads();
-    if (warp == 0) {
-      f2 t = red[0][lane];
-#pragma unroll
-      for (int w = 1; w < kAnaThreads / 32; ++w) t = f2_add(t, red[w][lane]);
-      const int q = lane / V;
-      if (lb + q <= lmax) outp[(int64_t)(lb - l0) * V + lane] = f2_val(t);
+    for (int k = 0; k < PPT; ++k) {
+      ok = ok && scp[k] == 0 && scm[k] == 0;
+      dead = dead && negligible(lpc[k], scp[k]) && (!SPIN || negligible(lmc[k], scm[k]));
+    }
+    return __all_sync(0xffffffffu, ok) ? 0 : (__all_sync(0xffffffffu, dead) ? 2 : 1);
+  };
+  const f2 zero[V] = {};
+
+  int since = 0;  // steps since the last exponent check
+  for (int lb = l0; lb <= lmax; lb += LC) {
+    if (LC >= 2) {
+#pragma unroll 1
+      for (int q = 0; q < LC; q += 2) {
+        const int l = lb + q;
+        if (l > lmax) break;
+        const int md = mode();
+        if (md == 2) {
+          recur(l);
+          recur(l + 1);
+          put(q, zero);
+          put(q + 1, zero);
+        } else {
+          f2 c0[V], c1[V];
+          if (md == 0) {
+            step(l, false, true, c0);
+            step(l + 1, true, true, c1);
+          } else {
+            step(l, false, false, c0);
+            step(l + 1, true, false, c1);
+          }
+          put(q, c0);
+          put(q + 1, c1);
+        }
+        since += 2;
+        if (since >= 8) {
+          rescale_all();
+          since = 0;
+        }
+      }
+    } else {  // one degree per chunk: parity alternates between chunks
+      f2 c0[V];
+      const bool odd = ((lb - l0) & 1) != 0;
+      if (mode() == 0) step(lb, odd, true, c0); else step(lb, odd, false, c0);
+      put(0, c0);
+      if (++since >= 8) {
+        rescale_all();
+        since = 0;
+      }
     }
     __syncthreads();
+    {  // 32 slots x kAnaThreads values: 4 threads per slot, then 4 partials per slot
+      const int sl = tid & 31, part = tid >> 5;
+      const f2 *row = &slot[sl][part * 32];
+      f2 t = row[0];
+#pragma unroll 8
+      for (int i = 1; i < 32; ++i) t = f2_add(t, row[i]);
+      quart[part][sl] = t;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      f2 t = quart[0][tid];
+#pragma unroll
+      for (int w = 1; w < kAnaThreads / 32; ++w) t = f2_add(t, quart[w][tid]);
+      if (lb + tid / V <= lmax) outp[(int64_t)(lb - l0) * V + tid] = f2_val(t);
+    }
   }
+}
+template <int NJ, int PPT, bool SPIN>
+__global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
+  mix_ana_body<NJ, PPT, SPIN>(a, nullptr, a.ana_items[blockIdx.x]);
+}
+template <int NJ, int PPT, bool SPIN>
+__global__ void __launch_bounds__(kAnaThreads) mix_ana_batch(const MixArgs *__restrict__ args,
+    const int4 *__restrict__ items, const PtrTable tbl) {
+  const int4 it = items[blockIdx.x];
+  const MixArgs &a = args[it.w];
+  mix_ana_body<NJ, PPT, SPIN>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, 0, 0));
 }
 
 // ---------------------------------------------------------------------------
@@ -684,6 +804,71 @@ cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &, int polar
       case 2: mix_ana<2, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
       case 4: mix_ana<4, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
       default: mix_ana<8, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sht
+
+// ---------------------------------------------------------------------------
+// batches (sht_batch_execute)
+// ---------------------------------------------------------------------------
+namespace sht {
+
+size_t leg_mixed_args_size() { return sizeof(MixArgs); }
+
+void leg_mixed_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out) {
+  MixArgs a = make_mix(P, polar);
+  a.ptr_off = ptr_off;
+  memcpy(out, &a, sizeof(a));
+}
+
+cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st) {
+  if (P->nm == 0) return cudaSuccess;
+  dim3 g(P->nm, P->spin ? P->njobs_pad : P->nmaps_pad);
+  alm_to_f2<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->nmaps_pad, P->astride, P->d_mval, P->d_mstart,
+                               P->d_coef_off, P->ncoef, alm, P->d_alm32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leg_mixed_batch(int stage, int spin, int nj, const void *args, const int4 *items, int n,
+                                   const PtrTable &tbl, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const MixArgs *a = static_cast<const MixArgs *>(args);
+  if (stage == 0) {
+    if (spin == 0) {
+      switch (nj) {
+        case 1: mix_syn_s0_batch<1><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 2: mix_syn_s0_batch<2><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 4: mix_syn_s0_batch<4><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 8: mix_syn_s0_batch<8><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        default: mix_syn_s0_batch<16><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+      }
+    } else {
+      switch (nj) {
+        case 1: mix_syn_spin_batch<1><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 2: mix_syn_spin_batch<2><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        case 4: mix_syn_spin_batch<4><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+        default: mix_syn_spin_batch<8><<<n, kSynTile, 0, st>>>(a, items, tbl); break;
+      }
+    }
+  } else {
+    if (spin == 0) {
+      switch (nj) {
+        case 1: mix_ana_batch<1, 4, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 2: mix_ana_batch<2, 4, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 4: mix_ana_batch<4, 2, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 8: mix_ana_batch<8, 2, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        default: mix_ana_batch<16, 2, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+      }
+    } else {
+      switch (nj) {
+        case 1: mix_ana_batch<1, 2, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 2: mix_ana_batch<2, 2, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        case 4: mix_ana_batch<4, 2, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+        default: mix_ana_batch<8, 2, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
+      }
     }
   }
   return cudaGetLastError();

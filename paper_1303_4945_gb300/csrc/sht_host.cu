@@ -731,6 +731,8 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
     for (auto &e : syn) si.push_back(e.second);
     std::vector<int4> ai;
     for (auto &e : ana) ai.push_back(e.second);
+    P->syn_list[polar] = syn;
+    P->ana_list[polar] = ana;
     P->nsyn_items[polar] = (int)si.size();
     P->nana_items[polar] = (int)ai.size();
     if ((rc = upload(P, si, &P->d_syn_items[polar])) != SHT_OK) return rc;
@@ -770,6 +772,13 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   if ((rc = upload(P, fps, &P->d_fft)) != SHT_OK) return rc;
   if ((rc = upload(P, pf, &P->d_pair_fft)) != SHT_OK) return rc;
   P->fft_smem = maxlen * (int)sizeof(double2);
+  P->pair_len.resize(P->npairs);
+  for (int p = 0; p < P->npairs; ++p) {
+    int n = g->nphi[P->pair_n[p]];
+    if (P->pair_s[p] >= 0) n = std::max(n, g->nphi[P->pair_s[p]]);
+    P->pair_len[p] = n;
+  }
+  CUDA_TRY(fft_prepare_device(P->device));
   return SHT_OK;
 }
 

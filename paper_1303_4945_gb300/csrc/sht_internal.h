@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/sht_gb300.h"
@@ -69,6 +70,12 @@ struct DevPtrs {
   double *p[kMaxPtr];
 };
 
+// device pointers of every plan of a batch, passed by value to the batched kernels
+constexpr int kMaxBatchPtr = 1024;
+struct PtrTable {
+  double *p[kMaxBatchPtr];
+};
+
 // recursion coefficients of one (m, l): lambda_{l+1} = (a x + ak) lambda_l - c lambda_{l-1}
 struct __align__(32) Coef {
   double a, ak, c, pad;
@@ -115,8 +122,8 @@ struct sht_plan_s {
   int64_t *d_coef_off = nullptr;
   sht::Coef *d_coef = nullptr;
   float4 *d_coef32 = nullptr;
-  float4 *d_alm32 = nullptr;
-  double2 *d_pm64 = nullptr;               // FP64 spin form: P = E + iB, M = E - iB [array][ncoef]               // mixed form: a_lm as double-float pairs [array][ncoef]
+  float4 *d_alm32 = nullptr;               // mixed form: a_lm as double-float pairs [array][ncoef]
+  double2 *d_pm64 = nullptr;               // FP64 spin form: P = E + iB, M = E - iB [array][ncoef]
   double2 *d_mpre = nullptr;
   int *d_minv = nullptr;                   // m -> index in mval, or -1
   double2 *d_phase = nullptr;              // F / G workspace
@@ -132,6 +139,9 @@ struct sht_plan_s {
   int64_t *d_ana_part_off[2] = {nullptr, nullptr};  // per m
   int *d_ana_tile0[2] = {nullptr, nullptr};         // per m: first tile
   int ana_ppt = 4;                                  // pairs per analysis thread
+  // host copies of the work lists with their costs (l count x pairs), for merging into batches
+  std::vector<std::pair<int64_t, int2>> syn_list[2];
+  std::vector<std::pair<int64_t, int4>> ana_list[2];
   int ana_tiles = 0;
   int64_t triples[2] = {0, 0};
 
@@ -141,6 +151,7 @@ struct sht_plan_s {
   int nfft = 0;
   int *d_pair_fft = nullptr;  // per pair: plan index
   int fft_smem = 0;           // bytes of dynamic shared memory for the FFT kernels
+  std::vector<int> pair_len;  // per pair: the longer ring length (FFT cost)
 
   int64_t workspace = 0;
 
@@ -174,4 +185,26 @@ cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int po
 cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, int weighted, int add,
                            cudaStream_t st);
 cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted, cudaStream_t st);
+// lets every FFT kernel use the device's opt-in shared memory (once per device, at plan time:
+// the limit is one value per kernel and process, so it is only ever raised, never per call)
+cudaError_t fft_prepare_device(int device);
+
+// batches: per-plan argument records (copied to the device once, at batch creation) and
+// launches over merged work lists; item.w selects the record, PtrTable holds the caller's
+// arrays, each plan's from record.ptr_off on
+size_t leg_fp64_args_size();
+size_t leg_mixed_args_size();
+size_t fft_args_size();
+void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
+void leg_mixed_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
+void fft_fill_args(const sht_plan_s *P, int polar, int weighted, int add, int ptr_off, void *out);
+cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st);
+cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st);
+// stage 0: synthesis, 1: analysis
+cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, const void *args, const int4 *items, int n,
+                                  const PtrTable &tbl, cudaStream_t st);
+cudaError_t launch_leg_mixed_batch(int stage, int spin, int nj, const void *args, const int4 *items, int n,
+                                   const PtrTable &tbl, cudaStream_t st);
+cudaError_t launch_fft_batch(int stage, const void *args, const int4 *items, int n, int smem, const PtrTable &tbl,
+                             cudaStream_t st);
 }  // namespace sht

@@ -63,6 +63,11 @@ _sig = {
     "sht_plan_destroy": [_vp],
     "sht_execute_noalloc": [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp],
     "sht_plan_profile": [_vp, ctypes.c_int],
+    "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
+    "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
+                          ctypes.c_int, _vp],
+    "sht_batch_size": [_vp],
+    "sht_batch_destroy": [_vp],
     "sht_plan_profile_read": [_vp, _dp, _i64p],
     "sht_strerror": [ctypes.c_int],
     "sht_last_error": [],
@@ -71,7 +76,7 @@ for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = ctypes.c_int
-for _name in ("sht_geom_destroy", "sht_alm_destroy", "sht_plan_destroy"):
+for _name in ("sht_geom_destroy", "sht_alm_destroy", "sht_plan_destroy", "sht_batch_destroy"):
     getattr(_lib, _name).restype = None
 _lib.sht_strerror.restype = ctypes.c_char_p
 _lib.sht_last_error.restype = ctypes.c_char_p
@@ -271,6 +276,47 @@ def sht_execute_noalloc(plan: Plan, type_, alm, maps, flags=0, stream=None):
     mp = (_vp * n)(*[_devptr(m) for m in maps])
     st = None if stream is None else _vp(_devptr_stream(stream))
     _check(_lib.sht_execute_noalloc(plan.handle, type_, ap, mp, flags, st), "sht_execute_noalloc")
+
+
+class Batch(_Handle):
+    """Distinct plans run through merged launches (see include/sht_gb300.h).
+    Holds references to its plans so they outlive it."""
+    _destroy = "sht_batch_destroy"
+
+    def __init__(self, h, plans):
+        super().__init__(h)
+        self.plans = list(plans)
+
+    def __len__(self):
+        return _lib.sht_batch_size(self._h)
+
+
+def sht_batch_create(plans) -> Batch:
+    plans = list(plans)
+    hp = (_vp * len(plans))(*[p.handle for p in plans])
+    h = _vp()
+    _check(_lib.sht_batch_create(len(plans), hp, ctypes.byref(h)), "sht_batch_create")
+    return Batch(h.value, plans)
+
+
+def sht_batch_execute(batch: Batch, type_, alm, maps, flags=0, stream=None):
+    """alm[k], maps[k]: plan k's device buffers, as sht_execute takes them."""
+    if len(alm) != len(batch.plans) or len(maps) != len(batch.plans):
+        raise ValueError(f"expected buffer lists for {len(batch.plans)} plans")
+    keep = []
+    ap = (ctypes.POINTER(_vp) * len(alm))()
+    mp = (ctypes.POINTER(_vp) * len(maps))()
+    for k, p in enumerate(batch.plans):
+        n = p.narrays
+        if len(alm[k]) != n or len(maps[k]) != n:
+            raise ValueError(f"plan {k}: expected {n} a_lm and {n} map buffers")
+        a = (_vp * n)(*[_devptr(x) for x in alm[k]])
+        m = (_vp * n)(*[_devptr(x) for x in maps[k]])
+        keep += [a, m]
+        ap[k] = ctypes.cast(a, ctypes.POINTER(_vp))
+        mp[k] = ctypes.cast(m, ctypes.POINTER(_vp))
+    st = None if stream is None else _vp(_devptr_stream(stream))
+    _check(_lib.sht_batch_execute(batch.handle, type_, ap, mp, flags, st), "sht_batch_execute")
 
 
 def _devptr_stream(stream):
