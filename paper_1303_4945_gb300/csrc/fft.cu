@@ -3,12 +3,14 @@
 // One CTA transforms one north/south ring pair of one map: the two real
 // rings are packed as z = p_north + i p_south into a single complex DFT of
 // length Nphi (pairs always share Nphi).  The whole ring lives in shared
-// memory; the engine is a mixed-radix Stockham (autosort) transform whose
-// passes compute every output of a radix-R butterfly directly (R multiply-
-// adds per output, twiddles from a table), so any radix works the same way.
-// Lengths with a prime factor above 31 go through Rader's algorithm (prime
-// n, n-1 smooth: a cyclic convolution of length n-1) or Bluestein's (chirp
-// convolution of power-of-two length >= 2n-1).
+// memory and is transformed in place: mixed-radix decimation-in-frequency
+// passes (radix 2, 4 and odd radices up to 31), each thread running whole
+// butterflies, one barrier per pass; the output comes out digit-reversed and
+// is read back through a position table.  Lengths with a prime factor above
+// 31 go through Rader's algorithm (prime n, n-1 smooth: a cyclic convolution
+// of length n-1) or Bluestein's (chirp convolution of smooth length >= 2n-1);
+// both convolutions run DIF forward and the transposed (DIT) passes back, so
+// the result returns to natural order without a permutation pass.
 //
 // Synthesis, per ring:  p_x = sum_{m=-mmax}^{mmax} c_m e^{2 pi i m x / N},
 //   c_m = F_m e^{i m phi0} (m >= 0), c_{-m} = conj(c_m); m is folded modulo N
@@ -27,49 +29,131 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
-// One Stockham pass of radix R over buf[0..len) (forward, e^{-i}).
-// Output o = (j / Ns) Ns R + s Ns + (j % Ns) receives
-//   sum_r buf[j + r len/R] W^{r (k len/(Ns R) + s len/R)},  k = j % Ns.
-__device__ void fft_pass(double2 *buf, int len, int R, int Ns, const double2 *__restrict__ W) {
-  double2 out[kFftMaxOpt];
-  const int nt = blockDim.x;
-  const int step = len / R;
-  const int NsR = Ns * R;
-  const int tws = len / NsR;
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// cos(2 pi t / R) and sin(2 pi t / R) for odd radices R <= kMaxRadix, t = 1..(R-1)/2,
+// written once per device (fft_prepare_device).  The butterflies index them with
+// compile-time constants, so they are read as constant-bank operands.
+__constant__ double c_cos[kMaxRadix + 1][kMaxRadix / 2 + 1];
+__constant__ double c_sin[kMaxRadix + 1][kMaxRadix / 2 + 1];
+
+// y_s = sum_r x_r e^{-2 pi i r s / R} for s < R; out(s, y_s) receives each output.
+// Odd R uses the symmetric form: with S_j = x_j + x_{R-j}, D_j = x_j - x_{R-j},
+//   y_k = A_k - i B_k,  y_{R-k} = A_k + i B_k,
+//   A_k = x_0 + sum_j S_j cos(2 pi j k / R),  B_k = sum_j D_j sin(2 pi j k / R),
+// i.e. 4 h^2 real multiply-adds for R points (h = (R-1)/2) instead of 4 R^2.
+template <int R, class Out>
+__device__ __forceinline__ void dft_small(double2 (&x)[R], Out &&out) {
+  if constexpr (R == 2) {
+    out(0, cadd(x[0], x[1]));
+    out(1, csub(x[0], x[1]));
+  } else if constexpr (R == 4) {
+    const double2 s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
+    const double2 s13 = cadd(x[1], x[3]), d13 = csub(x[1], x[3]);
+    out(0, cadd(s02, s13));
+    out(1, make_double2(d02.x + d13.y, d02.y - d13.x));  // d02 - i d13
+    out(2, csub(s02, s13));
+    out(3, make_double2(d02.x - d13.y, d02.y + d13.x));  // d02 + i d13
+  } else {
+    static_assert(R % 2 == 1 && R <= kMaxRadix, "odd radix");
+    constexpr int h = (R - 1) / 2;
+    const double2 x0 = x[0];
+    double2 y0 = x0;
 #pragma unroll
-  for (int i = 0; i < kFftMaxOpt; ++i) {
-    const int o = threadIdx.x + i * nt;
-    if (o < len) {
-      const int q = o / NsR;
-      const int rem = o - q * NsR;
-      const int s = rem / Ns;
-      const int k = rem - s * Ns;
-      const int j = q * Ns + k;
-      const int base = k * tws + s * step;  // < len
-      double2 acc = buf[j];
-      int t = 0;
-      for (int r = 1; r < R; ++r) {
-        t += base;
-        if (t >= len) t -= len;
-        acc = cadd(acc, cmul(buf[j + r * step], __ldg(W + t)));
+    for (int j = 1; j <= h; ++j) {  // S_j into x[j], D_j into x[R-j]
+      const double2 a = x[j], b = x[R - j];
+      x[j] = cadd(a, b);
+      x[R - j] = csub(a, b);
+      y0 = cadd(y0, x[j]);
+    }
+    out(0, y0);
+#pragma unroll
+    for (int k = 1; k <= h; ++k) {
+      double2 A = x0, B = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 1; j <= h; ++j) {
+        const int t = (j * k) % R;
+        const double c = t <= h ? c_cos[R][t] : c_cos[R][R - t];
+        const double sn = t <= h ? c_sin[R][t] : -c_sin[R][R - t];
+        A.x = fma(x[j].x, c, A.x);
+        A.y = fma(x[j].y, c, A.y);
+        B.x = fma(x[R - j].x, sn, B.x);
+        B.y = fma(x[R - j].y, sn, B.y);
       }
-      out[i] = acc;
+      out(k, make_double2(A.x + B.y, A.y - B.x));
+      out(R - k, make_double2(A.x - B.y, A.y + B.x));
     }
   }
-  __syncthreads();
+}
+
+// The ring buffer: the kernels' dynamic shared memory, named at namespace scope
+// so the out-of-line passes address it as shared memory.
+extern __shared__ double2 s_ring[];
+
+// One in-place pass of radix R over the len / L blocks of length L of s_ring.
+// Butterfly (block B, offset b < L/R) works on s_ring[B L + b + r L/R], r < R:
+//   decimation in frequency (DIT = false): DFT_R, then output s times W_L^{s b};
+//   its transpose (DIT = true): input r times W_L^{r b}, then DFT_R.
+// Each butterfly touches only its own R slots, so one barrier per pass suffices.
+// W holds e^{-2 pi i k / len}; W_L^e = W[e len / L].
+template <int R, bool DIT>
+__device__ __noinline__ void fft_stage(int len, int L, const double2 *__restrict__ W) {
+  const int LR = L / R;
+  const int nb = len / R;
+  const int tw = len / L;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+    const int B = q / LR, b = q - B * LR;
+    double2 *p = s_ring + B * L + b;
+    double2 x[R];
 #pragma unroll
-  for (int i = 0; i < kFftMaxOpt; ++i) {
-    const int o = threadIdx.x + i * nt;
-    if (o < len) buf[o] = out[i];
+    for (int r = 0; r < R; ++r) x[r] = p[r * LR];
+    if (DIT && b != 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], __ldg(W + r * b * tw));
+    }
+    dft_small<R>(x, [&](int s, double2 y) {
+      if (!DIT && s != 0 && b != 0) y = cmul(y, __ldg(W + s * b * tw));
+      p[s * LR] = y;
+    });
   }
   __syncthreads();
 }
 
-__device__ void fft_forward(double2 *buf, const FftPlanDev &fp) {
-  int Ns = 1;
+template <bool DIT>
+__device__ void fft_stage_any(int len, int L, int R, const double2 *W) {
+  switch (R) {
+    case 2: fft_stage<2, DIT>(len, L, W); break;
+    case 3: fft_stage<3, DIT>(len, L, W); break;
+    case 4: fft_stage<4, DIT>(len, L, W); break;
+    case 5: fft_stage<5, DIT>(len, L, W); break;
+    case 7: fft_stage<7, DIT>(len, L, W); break;
+    case 11: fft_stage<11, DIT>(len, L, W); break;
+    case 13: fft_stage<13, DIT>(len, L, W); break;
+    case 17: fft_stage<17, DIT>(len, L, W); break;
+    case 19: fft_stage<19, DIT>(len, L, W); break;
+    case 23: fft_stage<23, DIT>(len, L, W); break;
+    case 29: fft_stage<29, DIT>(len, L, W); break;
+    default: fft_stage<31, DIT>(len, L, W); break;
+  }
+}
+
+// Forward DFT of s_ring[0..fp.len) by decimation in frequency: natural-order input,
+// output X_k at position fp.pos[k] (mixed-radix digit reversal).
+__device__ void fft_dif(const FftPlanDev &fp) {
+  int L = fp.len;
   for (int i = 0; i < fp.nrad; ++i) {
-    fft_pass(buf, fp.len, fp.rad[i], Ns, fp.w);
-    Ns *= fp.rad[i];
+    fft_stage_any<false>(fp.len, L, fp.rad[i], fp.w);
+    L /= fp.rad[i];
+  }
+}
+
+// The transpose of fft_dif (its passes transposed, in reverse order): input
+// z_k at position fp.pos[k], output the forward DFT of z in natural order.
+__device__ void fft_dit(const FftPlanDev &fp) {
+  int L = 1;
+  for (int i = fp.nrad - 1; i >= 0; --i) {
+    L *= fp.rad[i];
+    fft_stage_any<true>(fp.len, L, fp.rad[i], fp.w);
   }
 }
 
@@ -77,21 +161,23 @@ __device__ void fft_forward(double2 *buf, const FftPlanDev &fp) {
 //   kind 0: buf[k] = x_k (k < n);
 //   kind 1: buf[q] = x_{g^q} (q < n-1), *x0 = x_0;
 //   kind 2: buf[k] = x_k chirp_k (k < n), 0 up to len.
-// Afterwards dft_at(k) returns X_k.
+// Afterwards dft_at(k) returns X_k.  Kinds 1 and 2 are cyclic convolutions with
+// a kernel whose spectrum was made by fft_dif (so it is digit-reversed like the
+// data): DIF, pointwise product, then the inverse as conj(DIT(conj)), which
+// returns to natural order with no permutation pass.
 __device__ void dft_run(double2 *buf, const FftPlanDev &fp, double2 *sh_x0, double2 *sh_a0) {
-  fft_forward(buf, fp);
+  fft_dif(fp);
   if (fp.kind == 0) return;
-  if (fp.kind == 1 && threadIdx.x == 0) *sh_a0 = buf[0];
+  if (fp.kind == 1 && threadIdx.x == 0) *sh_a0 = buf[0];  // X_0 sits at position 0
   __syncthreads();
-  // multiply by the kernel spectrum and transform back: IDFT(y) = conj(DFT(conj(y)))
   for (int i = threadIdx.x; i < fp.len; i += blockDim.x) buf[i] = cconj(cmul(buf[i], fp.spec[i]));
   __syncthreads();
-  fft_forward(buf, fp);
+  fft_dit(fp);
 }
 
 __device__ __forceinline__ double2 dft_at(const double2 *buf, const FftPlanDev &fp, int k, double2 x0,
                                           double2 a0) {
-  if (fp.kind == 0) return buf[k];
+  if (fp.kind == 0) return buf[__ldg(fp.pos + k)];
   if (fp.kind == 1) {
     if (k == 0) return cadd(x0, a0);
     return cadd(x0, cconj(buf[fp.inv_out[k]]));
@@ -104,19 +190,17 @@ __device__ __forceinline__ double2 dft_at(const double2 *buf, const FftPlanDev &
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFftThreads) spectrum_kernel(const FftPlanDev *fpd, const double2 *src,
                                                               double2 *dst, int len, double scale) {
-  extern __shared__ double2 buf[];
+  double2 *const buf = s_ring;
   const FftPlanDev fp = *fpd;
   for (int i = threadIdx.x; i < len; i += blockDim.x) buf[i] = src[i];
   __syncthreads();
-  fft_forward(buf, fp);
+  fft_dif(fp);
   for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = make_double2(buf[i].x * scale, buf[i].y * scale);
 }
 
 cudaError_t launch_fft_spectrum(const FftPlanDev *hp, const FftPlanDev *dp, const double2 *src, double2 *dst,
                                 int len, double scale, cudaStream_t st) {
-  const int smem = len * (int)sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  const int smem = len * (int)sizeof(double2);  // limit raised by fft_prepare_device
   spectrum_kernel<<<1, kFftThreads, smem, st>>>(dp, src, dst, len, scale);
   return cudaGetLastError();
 }
@@ -177,7 +261,7 @@ __device__ double2 spectrum_at(const FftArgs &a, int j, int p, int k, int N, dou
 }
 
 __device__ __forceinline__ void fft_syn_kernel_body(const FftArgs &a, double *const *ptrs, const int p, const int j) {
-  extern __shared__ double2 buf[];
+  double2 *const buf = s_ring;
   __shared__ double2 sh_x0, sh_a0;
     const FftPlanDev fp = a.plans[a.pair_fft[p]];
   const int2 rr = a.pair_rings[p];
@@ -232,7 +316,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_syn_kernel_batch(const FftArg
 // analysis: ring pixels -> G (per m)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void fft_ana_kernel_body(const FftArgs &a, double *const *ptrs, const int p, const int j) {
-  extern __shared__ double2 buf[];
+  double2 *const buf = s_ring;
   __shared__ double2 sh_x0, sh_a0;
     const FftPlanDev fp = a.plans[a.pair_fft[p]];
   const int2 rr = a.pair_rings[p];
@@ -352,9 +436,21 @@ cudaError_t fft_prepare_device(int device) {
   if (done.count(device)) return cudaSuccess;
   int smem = 0;
   cudaError_t e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  const void *fns[4] = {(const void *)fft_syn_kernel, (const void *)fft_ana_kernel,
-                        (const void *)fft_syn_kernel_batch, (const void *)fft_ana_kernel_batch};
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+  if (e == cudaSuccess) {  // radix constants, from long double
+    static double hc[kMaxRadix + 1][kMaxRadix / 2 + 1], hs[kMaxRadix + 1][kMaxRadix / 2 + 1];
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int R = 3; R <= kMaxRadix; R += 2)
+      for (int t = 1; t <= R / 2; ++t) {
+        hc[R][t] = (double)cosl(2.0L * pi * t / R);
+        hs[R][t] = (double)sinl(2.0L * pi * t / R);
+      }
+    e = cudaMemcpyToSymbol(c_cos, hc, sizeof(hc));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sin, hs, sizeof(hs));
+  }
+  const void *fns[5] = {(const void *)fft_syn_kernel, (const void *)fft_ana_kernel,
+                        (const void *)fft_syn_kernel_batch, (const void *)fft_ana_kernel_batch,
+                        (const void *)spectrum_kernel};
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
     // static + dynamic shared memory may not exceed the opt-in size
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, fns[i]);

@@ -503,9 +503,9 @@ static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scra
     fp.kind = 1;
     fp.len = n - 1;
   } else {
-    int M = 1;
-    while (M < 2 * n - 1) M *= 2;
-    if (M > kFftMaxLen || !factor_small(M, rad))
+    int M = 2 * n - 1;  // smallest smooth convolution length
+    while (M <= kFftMaxLen && !factor_small(M, rad)) ++M;
+    if (M > kFftMaxLen)
       return fail(SHT_ERR_UNSUPPORTED, "ring length %d: no FFT of size <= %d available", n, kFftMaxLen);
     fp.kind = 2;
     fp.len = M;
@@ -513,6 +513,19 @@ static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scra
   fp.nrad = (int)rad.size();
   for (int i = 0; i < fp.nrad; ++i) fp.rad[i] = rad[i];
   if ((rc = dev_upload(P, twiddles(fp.len), &fp.w)) != SHT_OK) return rc;
+  if (fp.kind == 0) {  // X_k ends at sum_i (k_i) len / (R_0 ... R_i), k = k_0 + R_0 (k_1 + R_1 (...))
+    std::vector<int> pos(n);
+    for (int k = 0; k < n; ++k) {
+      int kk = k, L = n, at = 0;
+      for (int r : rad) {
+        L /= r;
+        at += (kk % r) * L;
+        kk /= r;
+      }
+      pos[k] = at;
+    }
+    if ((rc = dev_upload(P, pos, &fp.pos)) != SHT_OK) return rc;
+  }
 
   if (fp.kind == 1) {
     const int g = primitive_root(n);
@@ -760,6 +773,8 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
     pf[p] = it->second;
   }
   P->nfft = (int)lens.size();
+  // kernel limits and radix constants first: the spectra below already run the FFT
+  CUDA_TRY(fft_prepare_device(P->device));
   std::vector<FftPlanDev> fps(P->nfft);
   FftPlanDev *scratch = nullptr;
   CUDA_TRY(cudaMalloc(&scratch, sizeof(FftPlanDev)));
@@ -778,7 +793,6 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
     if (P->pair_s[p] >= 0) n = std::max(n, g->nphi[P->pair_s[p]]);
     P->pair_len[p] = n;
   }
-  CUDA_TRY(fft_prepare_device(P->device));
   return SHT_OK;
 }
 

@@ -25,8 +25,9 @@ constexpr int kSynTile = 128;     // ring pairs per synthesis Legendre CTA (one 
 constexpr int kAnaThreads = 128;  // threads per analysis Legendre CTA
 constexpr int kMaxRadix = 8 * 4;  // generic odd radix limit of the FFT engine (primes <= 31)
 constexpr int kFftThreads = 512;
-constexpr int kFftMaxOpt = 16;    // outputs held in registers per thread per pass
-constexpr int kFftMaxLen = kFftThreads * kFftMaxOpt;  // 8192
+// longest in-place transform: the ring buffer (16 bytes a point) must fit the
+// opt-in shared memory of one CTA (227 KB on sm_103a)
+constexpr int kFftMaxLen = 14336;
 
 // Extended exponent of the FP64 recursion: a pair (lambda_{l-1}, lambda_l) is
 // stored as value * 2^(kScaleStep * scale); it contributes only at scale 0.
@@ -60,6 +61,7 @@ struct FftPlanDev {
   int nrad;
   int rad[24];
   const double2 *w;      // twiddles e^{-2 pi i k / len}, k < len
+  const int *pos;        // plain: position of X_k after the DIF passes (digit reversal)
   const int *perm_in;    // Rader: g^q mod n
   const int *inv_out;    // Rader: index p with g^{-p} = k, for k = 1..n-1
   const double2 *spec;   // Rader / Bluestein kernel spectrum (1/len folded in)
