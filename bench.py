@@ -349,6 +349,7 @@ def main():
     sampler = ClockSampler(local)
     for name, prec in forms.items():
         plan = sht.sht_plan_create(geom, lay, SPIN, 1, prec)
+        tune = plan.autotune(stream)  # analysis tiling, chosen by timing (outside the timed region)
         if name == list(forms)[-1]:
             sampler.start()
         ms, stages = time_form(sht, torch, plan, alm_d, maps_d, out_d, args.steps, args.warmup, world, stream)
@@ -356,7 +357,9 @@ def main():
             clocks = sampler.stop()
         results[name] = {"ms_per_step": ms, "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
                          "roofline": roofline_for(stages, plan, SPIN, name, peaks, args.steps),
-                         "triples": plan.triples(0), "workspace_bytes": plan.workspace()}
+                         "triples": plan.triples(0), "workspace_bytes": plan.workspace(),
+                         "tiling": {"analysis_pairs_per_thread": plan.tiling()[0],
+                                    "autotune_ms_per_candidate": {str(k): v for k, v in tune.items()}}}
         outputs[name] = {"maps": [m.cpu().numpy() for m in maps_d], "alm": [a.cpu().numpy() for a in out_d]}
         del plan
     head = "mixed" if "mixed" in forms else "fp64"
@@ -372,6 +375,7 @@ def main():
 
     # end to end through the public API from pinned host memory
     plan = sht.sht_plan_create(geom, lay, SPIN, 1, forms[head])
+    plan.set_tiling(results[head]["tiling"]["analysis_pairs_per_thread"])
     host_in = [torch.from_numpy(a).pin_memory() for a in alm_h]
     host_out = [torch.empty(a.shape, dtype=torch.complex128).pin_memory() for a in alm_h]
     for it in range(args.warmup + args.steps):

@@ -187,6 +187,30 @@ SHT_API int sht_plan_triples(sht_plan_t plan, int flags, int64_t *triples);
 
 SHT_API void sht_plan_destroy(sht_plan_t plan);
 
+/* ---- analysis tiling and autotuning -------------------------------------------
+ * The paper tunes its kernels by hand for each CPU; here the one shape the
+ * analysis Legendre kernel leaves open -- how many ring pairs each thread
+ * walks (more pairs amortise the per-degree reduction across the CTA, fewer
+ * leave room for more resident warps) -- is chosen per plan by measurement.
+ * A plan offers the tilings its kernels are built for (1 to 3 values,
+ * depending on spin class and ncomp); the first is the default.
+ *
+ * sht_plan_get_tiling writes the current pairs per thread and, when the
+ * pointers are not NULL, the number of candidates and the candidates (at most
+ * 4).  sht_plan_set_tiling selects a candidate (SHT_ERR_UNSUPPORTED for any
+ * other value).  sht_plan_autotune runs the plan's analysis Legendre kernel
+ * once untimed and twice timed per candidate on cuda_stream, keeps the
+ * fastest and, if ms_per_candidate is not NULL, writes each candidate's time
+ * per run.  It overwrites the plan's phase workspace, synchronises the stream
+ * and must not be captured.  Results do not depend on the tiling beyond
+ * rounding.  Neither call may change a plan that a batch refers to
+ * (SHT_ERR_INVALID_ARG).  Errors: SHT_ERR_INVALID_ARG, SHT_ERR_UNSUPPORTED,
+ * SHT_ERR_OOM, SHT_ERR_CUDA.
+ */
+SHT_API int sht_plan_get_tiling(sht_plan_t plan, int *pairs_per_thread, int *ncandidates, int *candidates);
+SHT_API int sht_plan_set_tiling(sht_plan_t plan, int pairs_per_thread);
+SHT_API int sht_plan_autotune(sht_plan_t plan, void *cuda_stream, float *ms_per_candidate);
+
 /* ---- measurement ----------------------------------------------------------
  * Sect. 5.2 times whole transforms by wall clock; these two calls report the
  * device time of each kernel stage instead.  While profiling is on,
@@ -250,7 +274,8 @@ SHT_API int sht_execute_noalloc(sht_plan_t plan, int type, double *const *alm, d
  * Results equal those of sht_execute per plan.  The call neither allocates
  * nor copies nor synchronises (pointers travel as kernel parameters), so it
  * can be captured in a CUDA graph; a captured graph keeps the pointers of the
- * call that was captured.  Each plan's workspace is used, so no plan of the
+ * call that was captured.  Each plan runs with the analysis tiling it had
+ * when the batch was created.  Each plan's workspace is used, so no plan of the
  * batch may run elsewhere meanwhile, and calls on one batch must not overlap.
  * Errors: SHT_ERR_INVALID_ARG, SHT_ERR_CUDA.
  */

@@ -7,7 +7,8 @@
 // whole batch is one grid: the block scheduler hands CTAs out in index order
 // as SMs free up, i.e. greedy longest-processing-time list scheduling over the
 // uneven problems.  Plans whose Legendre kernels differ (precision, spin
-// class, padded job count) form separate groups, one launch each; every item
+// class, padded job count, analysis tiling) form separate groups, one launch
+// each; every item
 // carries the index of its plan's argument record, which lives on the device
 // from creation on.  Per call only the caller's array pointers change; they
 // travel in the kernel parameters (PtrTable), so an execute neither
@@ -15,7 +16,8 @@
 // The per-plan pre- and post-processing (a_lm conversion before synthesis,
 // the reduction of analysis tile sums) runs as one small launch per plan.
 // Every plan keeps using its own workspace, so the plans of a batch must be
-// distinct, and a plan must not run elsewhere while its batch runs.
+// distinct, and a plan must not run elsewhere while its batch runs; a plan
+// cannot change its tiling while a batch refers to it.
 #include <stdio.h>
 #include <string.h>
 
@@ -27,7 +29,7 @@
 namespace {
 
 struct Group {
-  int precision = 0, spin = 0, nj = 1;
+  int precision = 0, spin = 0, nj = 1, ppt = 2;
   std::vector<int> plans;            // batch indices; item.w is the position in this list
   void *d_args[2] = {nullptr, nullptr};  // per polar: one argument record per plan
   int4 *d_syn[2] = {nullptr, nullptr};
@@ -107,13 +109,14 @@ int build(sht_batch_s *B) {
     const int spin_class = P->spin ? 1 : 0;
     Group *g = nullptr;
     for (auto &c : B->groups)
-      if (c.precision == P->precision && c.spin == spin_class && c.nj == P->njobs_pad) g = &c;
+      if (c.precision == P->precision && c.spin == spin_class && c.nj == P->njobs_pad && c.ppt == P->ana_ppt) g = &c;
     if (!g) {
       B->groups.emplace_back();
       g = &B->groups.back();
       g->precision = P->precision;
       g->spin = spin_class;
       g->nj = P->njobs_pad;
+      g->ppt = P->ana_ppt;
     }
     g->plans.push_back(k);
   }
@@ -200,6 +203,7 @@ extern "C" int sht_batch_create(int nplans, const sht_plan_t *plans, sht_batch_t
     free_batch(B);
     return rc;
   }
+  for (auto *P : B->plans) ++P->batch_refs;
   *out = B;
   return SHT_OK;
 }
@@ -212,6 +216,7 @@ extern "C" void sht_batch_destroy(sht_batch_t B) {
   for (void *p : B->allocs) cudaFree(p);
   B->allocs.clear();
   if (cur != B->device) cudaSetDevice(cur);
+  for (auto *P : B->plans) --P->batch_refs;
   delete B;
 }
 
@@ -265,8 +270,8 @@ extern "C" int sht_batch_execute(sht_batch_t B, int type, double *const *const *
     for (auto &g : B->groups) {
       if (e != cudaSuccess) break;
       e = g.precision == SHT_MIXED
-              ? launch_leg_mixed_batch(0, g.spin, g.nj, g.d_args[polar], g.d_syn[polar], g.nsyn[polar], TA, st)
-              : launch_leg_fp64_batch(0, g.spin, g.nj, g.d_args[polar], g.d_syn[polar], g.nsyn[polar], TA, st);
+              ? launch_leg_mixed_batch(0, g.spin, g.nj, g.ppt, g.d_args[polar], g.d_syn[polar], g.nsyn[polar], TA, st)
+              : launch_leg_fp64_batch(0, g.spin, g.nj, g.ppt, g.d_args[polar], g.d_syn[polar], g.nsyn[polar], TA, st);
     }
     if (e == cudaSuccess)
       e = launch_fft_batch(0, B->d_fft_syn[polar][weighted][add], B->d_fft_items, B->nfft_items, B->fft_smem, TM, st);
@@ -276,8 +281,8 @@ extern "C" int sht_batch_execute(sht_batch_t B, int type, double *const *const *
     for (auto &g : B->groups) {
       if (e != cudaSuccess) break;
       e = g.precision == SHT_MIXED
-              ? launch_leg_mixed_batch(1, g.spin, g.nj, g.d_args[polar], g.d_ana[polar], g.nana[polar], TA, st)
-              : launch_leg_fp64_batch(1, g.spin, g.nj, g.d_args[polar], g.d_ana[polar], g.nana[polar], TA, st);
+              ? launch_leg_mixed_batch(1, g.spin, g.nj, g.ppt, g.d_args[polar], g.d_ana[polar], g.nana[polar], TA, st)
+              : launch_leg_fp64_batch(1, g.spin, g.nj, g.ppt, g.d_args[polar], g.d_ana[polar], g.nana[polar], TA, st);
     }
     for (int k = 0; k < n && e == cudaSuccess; ++k) e = launch_ana_reduce(B->plans[k], A[k], polar, add, st);
   }

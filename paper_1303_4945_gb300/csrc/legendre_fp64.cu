@@ -794,24 +794,15 @@ cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int pol
 cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st) {
   const int n = P->nana_items[polar];
   LegArgs a = make_args(P, alm, polar);
-  const int nj = P->njobs_pad;
   if (n > 0) {
-    if (P->spin == 0) {
-      switch (nj) {
-        case 1: leg_ana_s0<1, 4><<<n, kAnaThreads, 0, st>>>(a); break;
-        case 2: leg_ana_s0<2, 4><<<n, kAnaThreads, 0, st>>>(a); break;
-        case 4: leg_ana_s0<4, 2><<<n, kAnaThreads, 0, st>>>(a); break;
-        case 8: leg_ana_s0<8, 2><<<n, kAnaThreads, 0, st>>>(a); break;
-        default: leg_ana_s0<16, 2><<<n, kAnaThreads, 0, st>>>(a); break;
-      }
-    } else {
-      switch (nj) {
-        case 1: leg_ana_spin<1, 2><<<n, kAnaThreads, 0, st>>>(a); break;
-        case 2: leg_ana_spin<2, 2><<<n, kAnaThreads, 0, st>>>(a); break;
-        case 4: leg_ana_spin<4, 2><<<n, kAnaThreads, 0, st>>>(a); break;
-        default: leg_ana_spin<8, 2><<<n, kAnaThreads, 0, st>>>(a); break;
-      }
-    }
+    if (P->spin == 0)
+      ana_shape_s0(P->njobs_pad, P->ana_ppt, [&](auto sh) {
+        leg_ana_s0<decltype(sh)::nj, decltype(sh)::ppt><<<n, kAnaThreads, 0, st>>>(a);
+      });
+    else
+      ana_shape_spin(P->njobs_pad, P->ana_ppt, [&](auto sh) {
+        leg_ana_spin<decltype(sh)::nj, decltype(sh)::ppt><<<n, kAnaThreads, 0, st>>>(a);
+      });
   }
   return cudaGetLastError();
 }
@@ -849,9 +840,9 @@ cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cud
   return cudaGetLastError();
 }
 
-// stage 0: synthesis, 1: analysis; all plans of the launch share spin class and njobs_pad
-cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, const void *args, const int4 *items, int n,
-                                  const PtrTable &tbl, cudaStream_t st) {
+// stage 0: synthesis, 1: analysis; all plans of the launch share spin class, njobs_pad and tiling
+cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, int ppt, const void *args, const int4 *items,
+                                  int n, const PtrTable &tbl, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const LegArgs *a = static_cast<const LegArgs *>(args);
   if (stage == 0) {
@@ -872,22 +863,14 @@ cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, const void *args,
       }
     }
   } else {
-    if (spin == 0) {
-      switch (nj) {
-        case 1: leg_ana_s0_batch<1, 4><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 2: leg_ana_s0_batch<2, 4><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 4: leg_ana_s0_batch<4, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 8: leg_ana_s0_batch<8, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        default: leg_ana_s0_batch<16, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-      }
-    } else {
-      switch (nj) {
-        case 1: leg_ana_spin_batch<1, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 2: leg_ana_spin_batch<2, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 4: leg_ana_spin_batch<4, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        default: leg_ana_spin_batch<8, 2><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-      }
-    }
+    if (spin == 0)
+      ana_shape_s0(nj, ppt, [&](auto sh) {
+        leg_ana_s0_batch<decltype(sh)::nj, decltype(sh)::ppt><<<n, kAnaThreads, 0, st>>>(a, items, tbl);
+      });
+    else
+      ana_shape_spin(nj, ppt, [&](auto sh) {
+        leg_ana_spin_batch<decltype(sh)::nj, decltype(sh)::ppt><<<n, kAnaThreads, 0, st>>>(a, items, tbl);
+      });
   }
   return cudaGetLastError();
 }

@@ -789,23 +789,14 @@ cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &, int polar
   const int n = P->nana_items[polar];
   if (n == 0) return cudaSuccess;
   MixArgs a = make_mix(P, polar);
-  const int nj = P->njobs_pad;
-  if (P->spin == 0) {
-    switch (nj) {
-      case 1: mix_ana<1, 4, false><<<n, kAnaThreads, 0, st>>>(a); break;
-      case 2: mix_ana<2, 4, false><<<n, kAnaThreads, 0, st>>>(a); break;
-      case 4: mix_ana<4, 2, false><<<n, kAnaThreads, 0, st>>>(a); break;
-      case 8: mix_ana<8, 2, false><<<n, kAnaThreads, 0, st>>>(a); break;
-      default: mix_ana<16, 2, false><<<n, kAnaThreads, 0, st>>>(a); break;
-    }
-  } else {
-    switch (nj) {
-      case 1: mix_ana<1, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
-      case 2: mix_ana<2, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
-      case 4: mix_ana<4, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
-      default: mix_ana<8, 2, true><<<n, kAnaThreads, 0, st>>>(a); break;
-    }
-  }
+  if (P->spin == 0)
+    ana_shape_s0(P->njobs_pad, P->ana_ppt, [&](auto sh) {
+      mix_ana<decltype(sh)::nj, decltype(sh)::ppt, false><<<n, kAnaThreads, 0, st>>>(a);
+    });
+  else
+    ana_shape_spin(P->njobs_pad, P->ana_ppt, [&](auto sh) {
+      mix_ana<decltype(sh)::nj, decltype(sh)::ppt, true><<<n, kAnaThreads, 0, st>>>(a);
+    });
   return cudaGetLastError();
 }
 
@@ -832,8 +823,8 @@ cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_leg_mixed_batch(int stage, int spin, int nj, const void *args, const int4 *items, int n,
-                                   const PtrTable &tbl, cudaStream_t st) {
+cudaError_t launch_leg_mixed_batch(int stage, int spin, int nj, int ppt, const void *args, const int4 *items,
+                                   int n, const PtrTable &tbl, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const MixArgs *a = static_cast<const MixArgs *>(args);
   if (stage == 0) {
@@ -854,22 +845,14 @@ cudaError_t launch_leg_mixed_batch(int stage, int spin, int nj, const void *args
       }
     }
   } else {
-    if (spin == 0) {
-      switch (nj) {
-        case 1: mix_ana_batch<1, 4, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 2: mix_ana_batch<2, 4, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 4: mix_ana_batch<4, 2, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 8: mix_ana_batch<8, 2, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        default: mix_ana_batch<16, 2, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-      }
-    } else {
-      switch (nj) {
-        case 1: mix_ana_batch<1, 2, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 2: mix_ana_batch<2, 2, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        case 4: mix_ana_batch<4, 2, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-        default: mix_ana_batch<8, 2, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl); break;
-      }
-    }
+    if (spin == 0)
+      ana_shape_s0(nj, ppt, [&](auto sh) {
+        mix_ana_batch<decltype(sh)::nj, decltype(sh)::ppt, false><<<n, kAnaThreads, 0, st>>>(a, items, tbl);
+      });
+    else
+      ana_shape_spin(nj, ppt, [&](auto sh) {
+        mix_ana_batch<decltype(sh)::nj, decltype(sh)::ppt, true><<<n, kAnaThreads, 0, st>>>(a, items, tbl);
+      });
   }
   return cudaGetLastError();
 }

@@ -99,4 +99,31 @@ __device__ __forceinline__ double to_scaled(double mant, int E, int *scale) {
   return ldexp(mant, E - kScaleStep * sc);
 }
 
+// Analysis tilings the kernels are built for: f(AnaShape<NJ, PPT>{}) runs the
+// instance for padded job count nj and ppt ring pairs per thread (the
+// candidates the host offers per spin class; anything else maps to the default).
+template <int NJ, int PPT>
+struct AnaShape {
+  static constexpr int nj = NJ, ppt = PPT;
+};
+template <class F>
+inline void ana_shape_s0(int nj, int ppt, F &&f) {
+  switch (nj) {
+    case 1: if (ppt == 8) f(AnaShape<1, 8>{}); else f(AnaShape<1, 4>{}); break;
+    case 2: if (ppt == 2) f(AnaShape<2, 2>{}); else f(AnaShape<2, 4>{}); break;
+    case 4: f(AnaShape<4, 2>{}); break;
+    case 8: f(AnaShape<8, 2>{}); break;
+    default: f(AnaShape<16, 2>{}); break;
+  }
+}
+template <class F>
+inline void ana_shape_spin(int nj, int ppt, F &&f) {
+  switch (nj) {
+    case 1: if (ppt == 4) f(AnaShape<1, 4>{}); else f(AnaShape<1, 2>{}); break;
+    case 2: if (ppt == 1) f(AnaShape<2, 1>{}); else f(AnaShape<2, 2>{}); break;
+    case 4: f(AnaShape<4, 2>{}); break;
+    default: f(AnaShape<8, 2>{}); break;
+  }
+}
+
 }  // namespace sht

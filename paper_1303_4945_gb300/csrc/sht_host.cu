@@ -615,6 +615,77 @@ static int upload(sht_plan_s *P, const std::vector<T> &h, T **d) {
   return SHT_OK;
 }
 
+// Tilings of the analysis Legendre kernels (ring pairs per thread) built for a
+// spin class and padded job count; the first is the default.
+static std::vector<int> ana_ppt_candidates(int spin, int nj) {
+  if (spin == 0) {
+    if (nj == 1) return {4, 8};
+    if (nj == 2) return {4, 2};
+    return {2};
+  }
+  if (nj == 1) return {2, 4};
+  if (nj == 2) return {2, 1};
+  return {2};
+}
+
+// Analysis work lists for tiles of kAnaThreads * ppt ring pairs: per polar
+// variant the cost-sorted (m, tile) items, each m's offset into the tile-sum
+// array and its first tile; grows the tile-sum array when needed.
+static int build_ana_lists(sht_plan_s *P, int ppt) {
+  int rc;
+  const int as = abs(P->spin);
+  const int V = (P->spin ? 4 : 2) * P->njobs_pad;  // doubles per l in the analysis partials
+  const int TA = kAnaThreads * ppt;
+  const int tiles = (P->npairs + TA - 1) / TA;
+  int64_t need = 0;
+  for (int polar = 0; polar < 2; ++polar) {
+    std::vector<std::pair<int64_t, int4>> ana;
+    std::vector<int64_t> poff(P->nm);
+    std::vector<int> t0(P->nm);
+    int64_t off = 0;
+    for (int i = 0; i < P->nm; ++i) {
+      int l0 = std::max(P->mval[i], as);
+      int nl = P->lmax - l0 + 1;
+      poff[i] = off;
+      if (nl <= 0) {
+        t0[i] = tiles;
+        continue;
+      }
+      int fp = polar ? P->first_pair[i] : 0;
+      int tf = fp / TA;
+      t0[i] = tf;
+      for (int t = tf; t < tiles; ++t)
+        ana.push_back({(int64_t)nl * std::min(TA, P->npairs - t * TA), make_int4(i, t, 0, 0)});
+      off += (int64_t)(tiles - tf) * nl * V;
+    }
+    std::stable_sort(ana.begin(), ana.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    std::vector<int4> ai;
+    for (auto &e : ana) ai.push_back(e.second);
+    if (P->d_ana_items[polar]) cudaFree(P->d_ana_items[polar]);
+    if (P->d_ana_part_off[polar]) cudaFree(P->d_ana_part_off[polar]);
+    if (P->d_ana_tile0[polar]) cudaFree(P->d_ana_tile0[polar]);
+    P->d_ana_items[polar] = nullptr;
+    P->d_ana_part_off[polar] = nullptr;
+    P->d_ana_tile0[polar] = nullptr;
+    P->ana_list[polar] = ana;
+    P->nana_items[polar] = (int)ai.size();
+    if ((rc = upload(P, ai, &P->d_ana_items[polar])) != SHT_OK) return rc;
+    if ((rc = upload(P, poff, &P->d_ana_part_off[polar])) != SHT_OK) return rc;
+    if ((rc = upload(P, t0, &P->d_ana_tile0[polar])) != SHT_OK) return rc;
+    need = std::max(need, off);
+  }
+  if (need > P->part_doubles || !P->d_part) {
+    if (P->d_part) cudaFree(P->d_part);
+    P->d_part = nullptr;
+    P->workspace += (need - P->part_doubles) * (int64_t)sizeof(double);
+    P->part_doubles = need;
+    CUDA_TRY(cudaMalloc(&P->d_part, std::max<int64_t>(1, P->part_doubles) * sizeof(double)));
+  }
+  P->ana_ppt = ppt;
+  P->ana_tiles = tiles;
+  return SHT_OK;
+}
+
 static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   int rc;
   // ---- ring pairs ----
@@ -704,24 +775,15 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   }
 
   // ---- work lists ----
-  const int V = (P->spin ? 4 : 2) * P->njobs_pad;  // doubles per l in the analysis partials
-  P->ana_ppt = (P->spin || P->njobs_pad > 2) ? 2 : 4;
-  const int TA = kAnaThreads * P->ana_ppt;
-  P->ana_tiles = (P->npairs + TA - 1) / TA;
   for (int polar = 0; polar < 2; ++polar) {
     std::vector<std::pair<int64_t, int2>> syn;
     std::vector<int> sfirst(P->nm);
-    std::vector<std::pair<int64_t, int4>> ana;
-    std::vector<int64_t> poff(P->nm);
-    std::vector<int> t0(P->nm);
-    int64_t off = 0, trip = 0;
+    int64_t trip = 0;
     for (int i = 0; i < P->nm; ++i) {
       int l0 = std::max(P->mval[i], as);
       int nl = P->lmax - l0 + 1;
       if (nl <= 0) {
         sfirst[i] = P->npairs;
-        t0[i] = P->ana_tiles;
-        poff[i] = off;
         continue;
       }
       int fp = polar ? P->first_pair[i] : 0;
@@ -730,33 +792,17 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
       sfirst[i] = sf;
       for (int p = sf; p < P->npairs; p += kSynTile)
         syn.push_back({(int64_t)nl * std::min(kSynTile, P->npairs - p), make_int2(i, p)});
-      int tf = fp / TA;
-      t0[i] = tf;
-      poff[i] = off;
-      for (int t = tf; t < P->ana_tiles; ++t)
-        ana.push_back({(int64_t)nl * std::min(TA, P->npairs - t * TA), make_int4(i, t, 0, 0)});
-      off += (int64_t)(P->ana_tiles - tf) * nl * V;
     }
     P->triples[polar] = trip;
     std::stable_sort(syn.begin(), syn.end(), [](auto &a, auto &b) { return a.first > b.first; });
-    std::stable_sort(ana.begin(), ana.end(), [](auto &a, auto &b) { return a.first > b.first; });
     std::vector<int2> si;
     for (auto &e : syn) si.push_back(e.second);
-    std::vector<int4> ai;
-    for (auto &e : ana) ai.push_back(e.second);
     P->syn_list[polar] = syn;
-    P->ana_list[polar] = ana;
     P->nsyn_items[polar] = (int)si.size();
-    P->nana_items[polar] = (int)ai.size();
     if ((rc = upload(P, si, &P->d_syn_items[polar])) != SHT_OK) return rc;
     if ((rc = upload(P, sfirst, &P->d_syn_first[polar])) != SHT_OK) return rc;
-    if ((rc = upload(P, ai, &P->d_ana_items[polar])) != SHT_OK) return rc;
-    if ((rc = upload(P, poff, &P->d_ana_part_off[polar])) != SHT_OK) return rc;
-    if ((rc = upload(P, t0, &P->d_ana_tile0[polar])) != SHT_OK) return rc;
-    P->part_doubles = std::max(P->part_doubles, off);
   }
-  CUDA_TRY(cudaMalloc(&P->d_part, std::max<int64_t>(1, P->part_doubles) * sizeof(double)));
-  P->workspace += P->part_doubles * sizeof(double);
+  if ((rc = build_ana_lists(P, ana_ppt_candidates(P->spin, P->njobs_pad)[0])) != SHT_OK) return rc;
 
   // ---- phase-array workspace F/G [nmaps][nm][npairs][2] ----
   size_t nph = (size_t)P->nmaps_pad * P->nm * P->npairs * 2;
@@ -828,6 +874,84 @@ extern "C" int sht_plan_create(sht_geom_t geom, sht_alm_t alm, int spin, int nco
     return rc;
   }
   *out = P;
+  return SHT_OK;
+}
+
+// ---- analysis tiling -------------------------------------------------------
+static int retile(sht_plan_s *P, int ppt) {
+  if (P->batch_refs)
+    return fail(SHT_ERR_INVALID_ARG, "the plan belongs to %d batch(es); destroy them before changing its tiling",
+                P->batch_refs);
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  const int rc = build_ana_lists(P, ppt);
+  if (cur != P->device) cudaSetDevice(cur);
+  return rc;
+}
+
+extern "C" int sht_plan_set_tiling(sht_plan_t P, int pairs_per_thread) {
+  if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  const auto c = ana_ppt_candidates(P->spin, P->njobs_pad);
+  if (std::find(c.begin(), c.end(), pairs_per_thread) == c.end())
+    return fail(SHT_ERR_UNSUPPORTED, "no analysis kernel with %d ring pairs per thread for this plan",
+                pairs_per_thread);
+  if (pairs_per_thread == P->ana_ppt) return SHT_OK;
+  return retile(P, pairs_per_thread);
+}
+
+extern "C" int sht_plan_get_tiling(sht_plan_t P, int *pairs_per_thread, int *ncandidates, int *candidates) {
+  if (!P || !pairs_per_thread) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  *pairs_per_thread = P->ana_ppt;
+  const auto c = ana_ppt_candidates(P->spin, P->njobs_pad);
+  if (ncandidates) *ncandidates = (int)c.size();
+  if (candidates)
+    for (size_t i = 0; i < c.size(); ++i) candidates[i] = c[i];
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_autotune(sht_plan_t P, void *stream, float *ms_per_candidate) {
+  if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  if (P->batch_refs) return retile(P, P->ana_ppt);  // reports the error
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto cands = ana_ppt_candidates(P->spin, P->njobs_pad);
+  // the analysis kernels read the phase array: give it defined contents
+  const size_t nph = (size_t)P->nmaps_pad * P->nm * P->npairs * 2;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int rc = SHT_OK, best = P->ana_ppt;
+  float best_ms = 0.f;
+  cudaError_t e = cudaMemsetAsync(P->d_phase, 0, std::max<size_t>(1, nph) * sizeof(double2), st);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  DevPtrs none;
+  memset(&none, 0, sizeof(none));
+  for (size_t i = 0; i < cands.size() && e == cudaSuccess && rc == SHT_OK; ++i) {
+    if ((rc = build_ana_lists(P, cands[i])) != SHT_OK) break;
+    // one untimed and two timed runs of the analysis Legendre stage (polar cut on)
+    for (int it = 0; it < 3 && e == cudaSuccess; ++it) {
+      if (it == 1) e = cudaEventRecord(ev[0], st);
+      if (e == cudaSuccess)
+        e = P->precision == SHT_MIXED ? launch_leg_ana_mixed(P, none, 1, st) : launch_leg_ana_fp64(P, none, 1, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (ms_per_candidate) ms_per_candidate[i] = ms / 2;
+    if (e == cudaSuccess && (i == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = cands[i];
+    }
+  }
+  if (rc == SHT_OK && e == cudaSuccess && P->ana_ppt != best) rc = build_ana_lists(P, best);
+  for (auto x : ev)
+    if (x) cudaEventDestroy(x);
+  if (cur != P->device) cudaSetDevice(cur);
+  if (rc != SHT_OK) return rc;
+  if (e != cudaSuccess) return fail(SHT_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
   return SHT_OK;
 }
 

@@ -140,7 +140,8 @@ struct sht_plan_s {
   int nana_items[2] = {0, 0};
   int64_t *d_ana_part_off[2] = {nullptr, nullptr};  // per m
   int *d_ana_tile0[2] = {nullptr, nullptr};         // per m: first tile
-  int ana_ppt = 4;                                  // pairs per analysis thread
+  int ana_ppt = 4;                                  // ring pairs per analysis thread (tiling)
+  int batch_refs = 0;                               // batches built on this plan's work lists
   // host copies of the work lists with their costs (l count x pairs), for merging into batches
   std::vector<std::pair<int64_t, int2>> syn_list[2];
   std::vector<std::pair<int64_t, int4>> ana_list[2];
@@ -203,10 +204,10 @@ void fft_fill_args(const sht_plan_s *P, int polar, int weighted, int add, int pt
 cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st);
 cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st);
 // stage 0: synthesis, 1: analysis
-cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, const void *args, const int4 *items, int n,
-                                  const PtrTable &tbl, cudaStream_t st);
-cudaError_t launch_leg_mixed_batch(int stage, int spin, int nj, const void *args, const int4 *items, int n,
-                                   const PtrTable &tbl, cudaStream_t st);
+cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, int ppt, const void *args, const int4 *items,
+                                  int n, const PtrTable &tbl, cudaStream_t st);
+cudaError_t launch_leg_mixed_batch(int stage, int spin, int nj, int ppt, const void *args, const int4 *items,
+                                   int n, const PtrTable &tbl, cudaStream_t st);
 cudaError_t launch_fft_batch(int stage, const void *args, const int4 *items, int n, int smem, const PtrTable &tbl,
                              cudaStream_t st);
 }  // namespace sht

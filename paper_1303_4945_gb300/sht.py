@@ -63,6 +63,9 @@ _sig = {
     "sht_plan_destroy": [_vp],
     "sht_execute_noalloc": [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp],
     "sht_plan_profile": [_vp, ctypes.c_int],
+    "sht_plan_get_tiling": [_vp, _ip, _ip, _ip],
+    "sht_plan_set_tiling": [_vp, ctypes.c_int],
+    "sht_plan_autotune": [_vp, _vp, ctypes.POINTER(ctypes.c_float)],
     "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
                           ctypes.c_int, _vp],
@@ -189,6 +192,24 @@ class Plan(_Handle):
         cnt = np.zeros(SHT_NSTAGES, np.int64)
         _check(_lib.sht_plan_profile_read(self._h, _ptr(ms, _dp), _ptr(cnt, _i64p)), "sht_plan_profile_read")
         return {STAGE_NAMES[i]: (float(ms[i]), int(cnt[i])) for i in range(SHT_NSTAGES)}
+
+    def tiling(self):
+        """(current ring pairs per analysis thread, candidates)."""
+        cur, n = ctypes.c_int(), ctypes.c_int()
+        c = (ctypes.c_int * 4)()
+        _check(_lib.sht_plan_get_tiling(self._h, ctypes.byref(cur), ctypes.byref(n), c), "sht_plan_get_tiling")
+        return cur.value, [c[i] for i in range(n.value)]
+
+    def set_tiling(self, pairs_per_thread):
+        _check(_lib.sht_plan_set_tiling(self._h, pairs_per_thread), "sht_plan_set_tiling")
+
+    def autotune(self, stream=None):
+        """Times every candidate tiling, keeps the fastest; returns {candidate: ms per run}."""
+        _, cands = self.tiling()
+        ms = (ctypes.c_float * 4)()
+        st = None if stream is None else _vp(_devptr_stream(stream))
+        _check(_lib.sht_plan_autotune(self._h, st, ms), "sht_plan_autotune")
+        return {c: float(ms[i]) for i, c in enumerate(cands)}
 
     def triples(self, flags=0):
         n = ctypes.c_int64()
