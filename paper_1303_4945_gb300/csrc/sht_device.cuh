@@ -109,7 +109,11 @@ struct AnaShape {
 template <class F>
 inline void ana_shape_s0(int nj, int ppt, F &&f) {
   switch (nj) {
-    case 1: if (ppt == 8) f(AnaShape<1, 8>{}); else f(AnaShape<1, 4>{}); break;
+    case 1:
+      if (ppt == 8) f(AnaShape<1, 8>{});
+      else if (ppt == 2) f(AnaShape<1, 2>{});
+      else f(AnaShape<1, 4>{});
+      break;
     case 2: if (ppt == 2) f(AnaShape<2, 2>{}); else f(AnaShape<2, 4>{}); break;
     case 4: f(AnaShape<4, 2>{}); break;
     case 8: f(AnaShape<8, 2>{}); break;
@@ -119,7 +123,11 @@ inline void ana_shape_s0(int nj, int ppt, F &&f) {
 template <class F>
 inline void ana_shape_spin(int nj, int ppt, F &&f) {
   switch (nj) {
-    case 1: if (ppt == 4) f(AnaShape<1, 4>{}); else f(AnaShape<1, 2>{}); break;
+    case 1:
+      if (ppt == 4) f(AnaShape<1, 4>{});
+      else if (ppt == 1) f(AnaShape<1, 1>{});
+      else f(AnaShape<1, 2>{});
+      break;
     case 2: if (ppt == 1) f(AnaShape<2, 1>{}); else f(AnaShape<2, 2>{}); break;
     case 4: f(AnaShape<4, 2>{}); break;
     default: f(AnaShape<8, 2>{}); break;

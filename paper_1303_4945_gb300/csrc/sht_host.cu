@@ -619,11 +619,11 @@ static int upload(sht_plan_s *P, const std::vector<T> &h, T **d) {
 // spin class and padded job count; the first is the default.
 static std::vector<int> ana_ppt_candidates(int spin, int nj) {
   if (spin == 0) {
-    if (nj == 1) return {4, 8};
+    if (nj == 1) return {4, 8, 2};
     if (nj == 2) return {4, 2};
     return {2};
   }
-  if (nj == 1) return {2, 4};
+  if (nj == 1) return {2, 4, 1};
   if (nj == 2) return {2, 1};
   return {2};
 }
