@@ -561,10 +561,9 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
     }
   }
 
-  // one degree: this thread's V contributions (summed over its pairs) into c[]
+  // one degree: this thread's V contributions (summed over its pairs) into c[];
+  // the first term of each output is its exact product (no sum with zero)
   auto step = [&](int l, bool odd, bool act, f2 (&c)[V]) {
-#pragma unroll
-    for (int v = 0; v < V; ++v) c[v] = f2{0.f, 0.f};
     // past lmax (second half of the last pair of degrees) the coefficients of
     // lmax stand in: the values are finite, never stored, and no table entry
     // outside this m is read
@@ -578,8 +577,13 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
         for (int j = 0; j < NJ; ++j) {
           const f2 gr = odd ? g[k][j][1][0] : g[k][j][0][0];
           const f2 gi = odd ? g[k][j][1][1] : g[k][j][0][1];
-          acc_mul(c[2 * j], wp, gr.h, gr.l);
-          acc_mul(c[2 * j + 1], wp, gi.h, gi.l);
+          if (k == 0) {
+            c[2 * j] = mul(wp, gr);
+            c[2 * j + 1] = mul(wp, gi);
+          } else {
+            acc_mul(c[2 * j], wp, gr.h, gr.l);
+            acc_mul(c[2 * j + 1], wp, gi.h, gi.l);
+          }
         }
         const f2 t = mul(cc.a, x[k]);
         const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
@@ -591,13 +595,20 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
           // T1 = W+_N l+ + (+-) W+_S l-,  T2 = W-_N l- + (+-) W-_S l+
-          acc_mul(c[4 * j + 0], wp, g[k][j][0][0].h, g[k][j][0][0].l);
+          if (k == 0) {
+            c[4 * j + 0] = mul(wp, g[k][j][0][0]);
+            c[4 * j + 1] = mul(wp, g[k][j][0][1]);
+            c[4 * j + 2] = mul(wm, g[k][j][1][0]);
+            c[4 * j + 3] = mul(wm, g[k][j][1][1]);
+          } else {
+            acc_mul(c[4 * j + 0], wp, g[k][j][0][0].h, g[k][j][0][0].l);
+            acc_mul(c[4 * j + 1], wp, g[k][j][0][1].h, g[k][j][0][1].l);
+            acc_mul(c[4 * j + 2], wm, g[k][j][1][0].h, g[k][j][1][0].l);
+            acc_mul(c[4 * j + 3], wm, g[k][j][1][1].h, g[k][j][1][1].l);
+          }
           acc_mul(c[4 * j + 0], sm, g[k][j][2][0].h, g[k][j][2][0].l);
-          acc_mul(c[4 * j + 1], wp, g[k][j][0][1].h, g[k][j][0][1].l);
           acc_mul(c[4 * j + 1], sm, g[k][j][2][1].h, g[k][j][2][1].l);
-          acc_mul(c[4 * j + 2], wm, g[k][j][1][0].h, g[k][j][1][0].l);
           acc_mul(c[4 * j + 2], sp, g[k][j][3][0].h, g[k][j][3][0].l);
-          acc_mul(c[4 * j + 3], wm, g[k][j][1][1].h, g[k][j][1][1].l);
           acc_mul(c[4 * j + 3], sp, g[k][j][3][1].h, g[k][j][3][1].l);
         }
         const f2 t = mul(cc.a, x[k]);

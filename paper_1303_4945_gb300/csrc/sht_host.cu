@@ -630,7 +630,7 @@ static std::vector<int> ana_ppt_candidates(int spin, int nj) {
 
 // Analysis work lists for tiles of kAnaThreads * ppt ring pairs: per polar
 // variant the cost-sorted (m, tile) items, each m's offset into the tile-sum
-// array and its first tile; grows the tile-sum array when needed.
+// array and its first tile; sizes the tile-sum array for this tiling.
 static int build_ana_lists(sht_plan_s *P, int ppt) {
   int rc;
   const int as = abs(P->spin);
@@ -674,7 +674,7 @@ static int build_ana_lists(sht_plan_s *P, int ppt) {
     if ((rc = upload(P, t0, &P->d_ana_tile0[polar])) != SHT_OK) return rc;
     need = std::max(need, off);
   }
-  if (need > P->part_doubles || !P->d_part) {
+  if (need != P->part_doubles || !P->d_part) {  // sized for the current tiling
     if (P->d_part) cudaFree(P->d_part);
     P->d_part = nullptr;
     P->workspace += (need - P->part_doubles) * (int64_t)sizeof(double);
