@@ -256,14 +256,39 @@ def time_form(sht, torch, plan, alm_d, maps_d, out_d, steps, warmup, world, stre
     return max_over_ranks(ms, world), stages
 
 
-# FP32 operations of the double-float algorithm per (m, l, ring-pair) step, counted
-# from the kernel source (FMA = 2 flops): a compensated multiply-add is 15
-# (exact product 7, two-sum 6, low-word adds 2), the three-float product A cos(theta)
-# is 9, a normalised two-term dot product 25, a three-term one 40.
-#   spin s: 8 multiply-adds + A cos(theta) + two 3-term dots = 120 + 9 + 80 = 209
-#   spin 0: 2 multiply-adds + A cos(theta) + one 2-term dot  =  30 + 9 + 25 =  64
-def f32_flops_per_triple(spin, ncomp):
-    return (89 + 120 * ncomp) if spin else (34 + 30 * ncomp)
+# FP32-pipe operations (FADD, FMUL and FFMA count one each: the pipe issues one
+# of them per lane per clock) of the double-float arithmetic per (m, l,
+# ring-pair) step, counted from the kernel source: a compensated multiply-add
+# is 12 (exact product 4, two-sum 6, low-word adds 2), the product A cos(theta)
+# with a three-float cos(theta) 5, a normalised two-term dot product 19, a
+# three-term one 31.
+#   spin s: two recursions (5 + 2 x 31) + 8 ncomp multiply-adds = 67 + 96 ncomp
+#   spin 0: one recursion (5 + 19)       + 2 ncomp multiply-adds = 24 + 24 ncomp
+def f32_ops_per_triple(spin, ncomp):
+    return (67 + 96 * ncomp) if spin else (24 + 24 * ncomp)
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernels, from the ncu captures summarised under profiles/, with the
+# SHA-256 of the kernel's source file when they were taken: a changed source
+# makes the figure stale and the bench reports null.
+MEASURED_TRAFFIC = {
+    # profiles/dram_traffic_spin2_lmax4095.md (spin 2, GL 4096 x 8191, lmax 4095, one launch each)
+    "fp64:legendre_analysis": {"bytes": 707017984 + 940671744, "sha256": "b2575d776a552384c84c7ff2f2680d62735b6f33db732cb8071de66d54d3e8bb"},
+    "mixed:legendre_analysis": {"bytes": 674624512 + 1784637952, "sha256": "f73c05456a06ed4321343f03c8a004bb0a5af0877cb4f782e6289be4d32707ec"},
+    "mixed:legendre_synthesis": {"bytes": 546653952 + 321911808, "sha256": "f73c05456a06ed4321343f03c8a004bb0a5af0877cb4f782e6289be4d32707ec"},
+}
+
+
+def _traffic(kernel_file, key):
+    import hashlib
+    rec = MEASURED_TRAFFIC.get(key)
+    if not rec:
+        return None
+    path = os.path.join(ROOT, "paper_1303_4945_gb300", "csrc", kernel_file)
+    with open(path, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    return rec["bytes"] if rec["sha256"] == digest else None
 
 
 def launches_per_step(spin, form):
@@ -273,12 +298,13 @@ def launches_per_step(spin, form):
 
 
 def roofline_for(stages, plan, spin, precision, peaks, steps):
-    """Dominant Legendre kernel vs the pipe it runs on.
+    """Dominant Legendre kernel against the pipe it runs on.
 
-    FP64 form: algorithmic FP64 flops (flops_per_triple) against the FP64 pipe.
-    Mixed form: the FP32 flops the double-float algorithm performs
-    (f32_flops_per_triple) against the FP32 pipe; the FP64-equivalent rate
-    (algorithmic FP64 flops / time) is reported beside it.
+    FP64 form: algorithmic FP64 flops (flops_per_triple, FMA = 2) against the
+    FP64 pipe (152 SMs x 2 DFMA lanes x 2 flops x clock).  Mixed form: the
+    FP32-pipe operations of the double-float algorithm (f32_ops_per_triple)
+    against the FP32 pipe's issue rate (152 SMs x 128 lanes x clock); the same
+    work as FMA-counted flops and the FP64-equivalent rate are given beside it.
     """
     syn_ms, syn_n = stages["legendre_synthesis"]
     ana_ms, ana_n = stages["legendre_analysis"]
@@ -287,21 +313,25 @@ def roofline_for(stages, plan, spin, precision, peaks, steps):
     triples = plan.triples(0)
     clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     fp64_flops = triples * flops_per_triple(spin, 1)
+    sec = per_launch_ms * 1e-3
     if precision == "fp64":
-        peak = SMS * 4 * clock / 1e12  # 2 FP64 FMA lanes per SM per clock (measured DFMA rate)
-        flops = fp64_flops
-        how = "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x sm_max clock"
+        kfile = "legendre_fp64.cu"
+        out = {"bound": "alu", "kernel": name, "achieved": fp64_flops / sec / 1e12,
+               "peak": SMS * 4 * clock / 1e12, "unit": "TFLOP/s",
+               "peak_source": "FP64 pipe: 152 SMs x 2 DFMA lanes/clk x 2 flop x sm_max clock (of nominal clock)",
+               "algorithmic_flops_per_launch": fp64_flops}
     else:
-        peak = SMS * 256 * clock / 1e12  # 128 FP32 FMA lanes per SM per clock
-        flops = triples * f32_flops_per_triple(spin, 1)
-        how = "FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x sm_max clock"
-    achieved = flops / (per_launch_ms * 1e-3) / 1e12
-    out = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-           "frac": achieved / peak, "traffic": None, "peak_source": how,
-           "algorithmic_flops_per_launch": flops, "ms_per_launch": per_launch_ms, "triples_per_launch": triples}
-    if precision != "fp64":
-        out["fp64_equivalent_tflops"] = fp64_flops / (per_launch_ms * 1e-3) / 1e12
-        out["fp64_equivalent_frac_of_fp64_peak"] = out["fp64_equivalent_tflops"] / (SMS * 4 * clock / 1e12)
+        kfile = "legendre_mixed.cu"
+        ops = triples * f32_ops_per_triple(spin, 1)
+        out = {"bound": "alu", "kernel": name, "achieved": ops / sec / 1e12,
+               "peak": SMS * 128 * clock / 1e12, "unit": "T FP32-pipe ops/s",
+               "peak_source": "FP32 pipe issue: 152 SMs x 128 lanes/clk x sm_max clock (FADD/FMUL/FFMA one op each)",
+               "algorithmic_fp32_ops_per_launch": ops,
+               "fp64_equivalent_tflops": fp64_flops / sec / 1e12}
+    out["frac"] = out["achieved"] / out["peak"]
+    key = ("fp64:" if precision == "fp64" else "mixed:") + name
+    out["traffic"] = _traffic(kfile, key)
+    out.update({"ms_per_launch": per_launch_ms, "triples_per_launch": triples})
     return out
 
 

@@ -1,0 +1,79 @@
+"""Host-side logic of bench.py, on the CPU: names, work counts and roofline arithmetic."""
+import builtins
+import os
+import symtable
+
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def undefined_globals(path):
+    """Global names referenced in a module but bound nowhere in it (nor builtins)."""
+    src = open(path).read()
+    top = symtable.symtable(src, path, "exec")
+    bound = {s.get_name() for s in top.get_symbols() if s.is_assigned() or s.is_imported()}
+    bound |= set(dir(builtins)) | {"__file__", "__name__", "__doc__", "__spec__", "__path__"}
+    missing = set()
+
+    def walk(t):
+        for s in t.get_symbols():
+            glob = t.get_type() == "module" or s.is_global()
+            if glob and s.is_referenced() and s.get_name() not in bound:
+                missing.add(s.get_name())
+        for c in t.get_children():
+            walk(c)
+
+    walk(top)
+    return missing
+
+
+@pytest.mark.parametrize("name", ["bench.py", "__graft_entry__.py"])
+def test_no_undefined_globals(name):
+    assert undefined_globals(os.path.join(ROOT, name)) == set()
+
+
+def test_checker_catches_a_missing_name(tmp_path):
+    p = tmp_path / "m.py"
+    p.write_text("def f():\n    return g(1)\n")
+    assert undefined_globals(str(p)) == {"g"}
+
+
+def test_work_counts():
+    # FP64 algorithmic flops per (m, l, ring-pair) step: recursion + 2 real FMAs
+    # per complex output and component (spin: 4 complex outputs per E/B pair)
+    assert bench.flops_per_triple(0, 1) == 7 and bench.flops_per_triple(2, 1) == 26
+    assert bench.flops_per_triple(2, 3) == 10 + 48
+    # double-float FP32-pipe ops: compensated multiply-add 12, recursion 24 / 67
+    assert bench.f32_ops_per_triple(0, 1) == 48 and bench.f32_ops_per_triple(2, 1) == 163
+    assert bench.launches_per_step(2, "fp64") == 6 and bench.launches_per_step(0, "fp64") == 5
+    assert bench.launches_per_step(0, "mixed") == 6
+
+
+class _Plan:
+    def triples(self, flags=0):
+        return 10 ** 10
+
+
+def test_roofline_arithmetic(monkeypatch):
+    stages = {"legendre_synthesis": (300.0, 3), "legendre_analysis": (450.0, 3)}
+    peaks = {"sm_max_mhz": 2000.0}
+    r = bench.roofline_for(stages, _Plan(), 2, "fp64", peaks, 3)
+    assert r["kernel"] == "legendre_analysis" and r["ms_per_launch"] == pytest.approx(150.0)
+    assert r["achieved"] == pytest.approx(26e10 / 0.150 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 4 * 2e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    m = bench.roofline_for(stages, _Plan(), 2, "mixed", peaks, 3)
+    assert m["achieved"] == pytest.approx(163e10 / 0.150 / 1e12)
+    assert m["peak"] == pytest.approx(152 * 128 * 2e9 / 1e12)
+    # traffic: only while the kernel source still hashes as recorded
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", {"mixed:legendre_analysis": {"bytes": 123, "sha256": "0" * 64}})
+    assert bench.roofline_for(stages, _Plan(), 2, "mixed", peaks, 3)["traffic"] is None
+
+
+def test_headline_config_exceeds_l2():
+    bench.set_workload(4095)
+    assert bench.CONFIG["lmax"] == 4095 and bench.CONFIG["nlon"] == 8191
+    assert bench.CONFIG["l2_policy"].startswith("inputs larger than L2")
