@@ -1,0 +1,84 @@
+"""The paper's accuracy experiment (Sect. 5.1.2) on the GPU through the C ABI.
+
+Spin-0 a_lm with real and imaginary parts uniform in [-1, 1) (imaginary part 0
+for m = 0) go through synthesis onto a reduced Gauss-Legendre grid and back
+through analysis; the rms and maximum errors of the round trip must stay near
+double precision (the paper reports rms growing roughly linearly and the
+maximum roughly as lmax^(3/2), both close to the IEEE limit).  The reduced
+grid gives ring y the smallest 2^a 3^b 5^c length >= 2 m_y + 1, with m_y the
+largest m the polar optimisation (Sect. 3.3) keeps on that ring; the per-pixel
+weight is the Gauss-Legendre weight times 2 pi / Nphi_y.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1303_4945_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sht():
+    from paper_1303_4945_gb300 import build
+
+    build.build()
+    from paper_1303_4945_gb300 import sht as m
+
+    assert torch.cuda.is_available()
+    return m
+
+
+def smooth_at_least(n):
+    best = None
+    p2 = 1
+    while p2 < 4 * n:
+        p3 = p2
+        while p3 < 4 * n:
+            p5 = p3
+            while p5 < 4 * n:
+                if p5 >= n and (best is None or p5 < best):
+                    best = p5
+                p5 *= 5
+            p3 *= 3
+        p2 *= 2
+    return best
+
+
+def reduced_gl(sht, lmax):
+    nlat, nlon = lmax + 1, 2 * lmax + 1
+    full = sht.sht_geom_gauss(nlat, nlon).rings()
+    T = max(100.0, 0.01 * lmax)
+    theta = full["theta"]
+    mmax_y = np.minimum(lmax, np.floor(lmax * np.sin(theta) + T)).astype(int)
+    nphi = np.array([smooth_at_least(2 * m + 1) for m in mmax_y])
+    weight = full["weight"] * nlon / nphi  # GL weight x 2 pi / Nphi_y
+    ofs = np.concatenate([[0], np.cumsum(nphi[:-1])]).astype(np.int64)
+    return sht.sht_geom_general(theta, nphi, np.zeros(nlat), ofs, weight=weight), int(nphi.sum()), nlat * nlon
+
+
+@pytest.mark.parametrize("lmax", [127, 511, 1023])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reduced_gl_round_trip(sht, lmax, precision):
+    geom, npix, npix_full = reduced_gl(sht, lmax)
+    if lmax > 200:
+        assert npix < 0.95 * npix_full  # the grid is really reduced
+    rng = np.random.default_rng(lmax)
+    a = inputs.uniform_alm(rng, lmax, lmax)
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), 0, 1, precision)
+    a_d = torch.from_numpy(a).cuda()
+    m_d = torch.empty(npix, dtype=torch.float64, device="cuda")
+    b_d = torch.empty_like(a_d)
+    sht.sht_execute(plan, sht.SHT_SYNTHESIS, [a_d], [m_d])
+    sht.sht_execute(plan, sht.SHT_ANALYSIS, [b_d], [m_d])
+    torch.cuda.synchronize()
+    d = (b_d - a_d).cpu().numpy()
+    eps_rms = math.sqrt(np.sum(np.abs(d) ** 2) / np.sum(np.abs(a) ** 2))
+    eps_max = float(np.max(np.abs(d)))
+    if precision == 0:
+        # near double precision, growing slowly with lmax (Fig. fig_accuracy)
+        assert eps_rms < 2e-16 * lmax and eps_max < 2e-16 * lmax ** 1.5, (eps_rms, eps_max)
+    else:
+        assert eps_rms < 1e-10 and eps_max < 1e-9, (eps_rms, eps_max)
