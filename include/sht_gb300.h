@@ -211,6 +211,24 @@ SHT_API int sht_plan_get_tiling(sht_plan_t plan, int *pairs_per_thread, int *nca
 SHT_API int sht_plan_set_tiling(sht_plan_t plan, int pairs_per_thread);
 SHT_API int sht_plan_autotune(sht_plan_t plan, void *cuda_stream, float *ms_per_candidate);
 
+/* ---- FP64 columns of the mixed form --------------------------------------------
+ * The paper computes in double precision throughout; the mixed form (not in the
+ * paper) runs the recursion and sums in pairs of FP32 numbers, ~48 significant
+ * bits.  Near the poles the Legendre functions of small m respond to an error d
+ * in the recursion's A_l cos(theta) like l^2 d, so those columns lose accuracy
+ * first as lmax grows.  A mixed plan therefore runs the columns m < m_below in
+ * the FP64 kernels (same results as an FP64 plan for those columns, ~5x their
+ * cost).  The default is floor((lmax / 2700)^3): 0 below lmax 2700, 3 at lmax
+ * 4095, 28 at 8191, which keeps every column's relative error near or below
+ * 1e-10 on white-noise inputs.  sht_plan_set_fp64_columns changes it (any
+ * m_below >= 0; it rebuilds the work lists and may allocate a P/M table of
+ * ncoef x arrays x 16 bytes); sht_plan_get_fp64_columns reads it.  Errors:
+ * SHT_ERR_INVALID_ARG (NULL, an FP64 plan, a plan in a batch, m_below < 0),
+ * SHT_ERR_OOM, SHT_ERR_CUDA.
+ */
+SHT_API int sht_plan_set_fp64_columns(sht_plan_t plan, int m_below);
+SHT_API int sht_plan_get_fp64_columns(sht_plan_t plan, int *m_below);
+
 /* ---- measurement ----------------------------------------------------------
  * Sect. 5.2 times whole transforms by wall clock; these two calls report the
  * device time of each kernel stage instead.  While profiling is on,

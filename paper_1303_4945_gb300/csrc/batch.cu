@@ -31,6 +31,7 @@ namespace {
 struct Group {
   int precision = 0, spin = 0, nj = 1, ppt = 2;
   std::vector<int> plans;            // batch indices; item.w is the position in this list
+  std::vector<char> lo;              // per entry: the mixed plan's FP64 columns (FP64 group)
   void *d_args[2] = {nullptr, nullptr};  // per polar: one argument record per plan
   int4 *d_syn[2] = {nullptr, nullptr};
   int nsyn[2] = {0, 0};
@@ -103,22 +104,29 @@ int build(sht_batch_s *B) {
   if (slots > kMaxBatchPtr)
     return set_error(SHT_ERR_UNSUPPORTED, "a batch holds at most %d arrays per side (padded); this one needs %d",
                      kMaxBatchPtr, slots);
-  // Legendre groups
-  for (int k = 0; k < n; ++k) {
+  // Legendre groups; a mixed plan with FP64 columns is also an entry of an FP64 group
+  auto join = [&](int k, int precision, bool lo) {
     const sht_plan_s *P = B->plans[k];
     const int spin_class = P->spin ? 1 : 0;
     Group *g = nullptr;
     for (auto &c : B->groups)
-      if (c.precision == P->precision && c.spin == spin_class && c.nj == P->njobs_pad && c.ppt == P->ana_ppt) g = &c;
+      if (c.precision == precision && c.spin == spin_class && c.nj == P->njobs_pad && c.ppt == P->ana_ppt) g = &c;
     if (!g) {
       B->groups.emplace_back();
       g = &B->groups.back();
-      g->precision = P->precision;
+      g->precision = precision;
       g->spin = spin_class;
       g->nj = P->njobs_pad;
       g->ppt = P->ana_ppt;
     }
     g->plans.push_back(k);
+    g->lo.push_back(lo ? 1 : 0);
+  };
+  for (int k = 0; k < n; ++k) {
+    const sht_plan_s *P = B->plans[k];
+    join(k, P->precision, false);
+    if (P->precision == SHT_MIXED && (P->nsyn_lo[0] || P->nsyn_lo[1] || P->nana_lo[0] || P->nana_lo[1]))
+      join(k, SHT_FP64, true);
   }
   cudaError_t e = cudaSuccess;
   for (auto &g : B->groups) {
@@ -129,13 +137,16 @@ int build(sht_batch_s *B) {
       std::vector<std::pair<int64_t, int4>> syn, ana;
       for (size_t i = 0; i < g.plans.size(); ++i) {
         const int k = g.plans[i];
+        const bool lo = g.lo[i] != 0;
         const sht_plan_s *P = B->plans[k];
         if (mixed)
           leg_mixed_fill_args(P, polar, B->ptr_off[k], args.data() + i * rec);
         else
-          leg_fp64_fill_args(P, polar, B->ptr_off[k], args.data() + i * rec);
-        for (auto &it : P->syn_list[polar]) syn.push_back({it.first, make_int4(it.second.x, it.second.y, 0, (int)i)});
-        for (auto &it : P->ana_list[polar]) ana.push_back({it.first, make_int4(it.second.x, it.second.y, 0, (int)i)});
+          leg_fp64_fill_args(P, polar, B->ptr_off[k], args.data() + i * rec, lo);
+        for (auto &it : (lo ? P->syn_list_lo : P->syn_list)[polar])
+          syn.push_back({it.first, make_int4(it.second.x, it.second.y, 0, (int)i)});
+        for (auto &it : (lo ? P->ana_list_lo : P->ana_list)[polar])
+          ana.push_back({it.first, make_int4(it.second.x, it.second.y, 0, (int)i)});
       }
       sort_by_cost(syn);
       sort_by_cost(ana);
@@ -187,6 +198,9 @@ extern "C" int sht_batch_create(int nplans, const sht_plan_t *plans, sht_batch_t
   for (int k = 0; k < nplans; ++k) {
     if (!plans[k]) return set_error(SHT_ERR_INVALID_ARG, "plan %d is NULL", k);
     if (!seen.insert(plans[k]).second) return set_error(SHT_ERR_INVALID_ARG, "plan %d appears twice", k);
+    if (plans[k]->d_fft_scratch)
+      return set_error(SHT_ERR_UNSUPPORTED, "plan %d has rings longer than %d points; run it with sht_execute", k,
+                       kFftMaxLen);
     if (plans[k]->device != plans[0]->device)
       return set_error(SHT_ERR_INVALID_ARG, "plan %d lives on device %d, plan 0 on device %d", k, plans[k]->device,
                        plans[0]->device);
@@ -266,6 +280,8 @@ extern "C" int sht_batch_execute(sht_batch_t B, int type, double *const *const *
     for (int k = 0; k < n && e == cudaSuccess; ++k) {
       const sht_plan_s *P = B->plans[k];
       e = P->precision == SHT_MIXED ? launch_alm_prepare_mixed(P, A[k], st) : launch_alm_prepare_fp64(P, A[k], st);
+      if (e == cudaSuccess && P->precision == SHT_MIXED && P->nsyn_lo[polar])  // its FP64 columns
+        e = launch_alm_prepare_fp64(P, A[k], st);
     }
     for (auto &g : B->groups) {
       if (e != cudaSuccess) break;

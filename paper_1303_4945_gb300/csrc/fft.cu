@@ -16,6 +16,7 @@
 //   c_m = F_m e^{i m phi0} (m >= 0), c_{-m} = conj(c_m); m is folded modulo N
 //   when N <= 2 mmax (aliasing, Eq. syn1).
 // Analysis, per ring:   G_m = w e^{-i m phi0} sum_x p_x e^{-2 pi i m x / N}  (Eq. ana2).
+#include <algorithm>
 #include <mutex>
 #include <set>
 
@@ -90,20 +91,32 @@ __device__ __forceinline__ void dft_small(double2 (&x)[R], Out &&out) {
 // so the out-of-line passes address it as shared memory.
 extern __shared__ double2 s_ring[];
 
-// One in-place pass of radix R over the len / L blocks of length L of s_ring.
-// Butterfly (block B, offset b < L/R) works on s_ring[B L + b + r L/R], r < R:
+// Where a ring lives while it is transformed: shared memory (every length up to
+// kFftMaxLen), or a CTA-private slot of global scratch for longer rings, which
+// stays in L2 (the engine is the same; barriers order global accesses within
+// the CTA as they do shared ones).
+struct SharedRing {
+  __device__ __forceinline__ double2 *at(int i) const { return s_ring + i; }
+};
+struct GlobalRing {
+  double2 *p;
+  __device__ __forceinline__ double2 *at(int i) const { return p + i; }
+};
+
+// One in-place pass of radix R over the len / L blocks of length L of the ring.
+// Butterfly (block B, offset b < L/R) works on ring[B L + b + r L/R], r < R:
 //   decimation in frequency (DIT = false): DFT_R, then output s times W_L^{s b};
 //   its transpose (DIT = true): input r times W_L^{r b}, then DFT_R.
 // Each butterfly touches only its own R slots, so one barrier per pass suffices.
 // W holds e^{-2 pi i k / len}; W_L^e = W[e len / L].
-template <int R, bool DIT>
-__device__ __noinline__ void fft_stage(int len, int L, const double2 *__restrict__ W) {
+template <int R, bool DIT, class Ring>
+__device__ __noinline__ void fft_stage(Ring ring, int len, int L, const double2 *__restrict__ W) {
   const int LR = L / R;
   const int nb = len / R;
   const int tw = len / L;
   for (int q = threadIdx.x; q < nb; q += blockDim.x) {
     const int B = q / LR, b = q - B * LR;
-    double2 *p = s_ring + B * L + b;
+    double2 *p = ring.at(B * L + b);
     double2 x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = p[r * LR];
@@ -119,41 +132,43 @@ __device__ __noinline__ void fft_stage(int len, int L, const double2 *__restrict
   __syncthreads();
 }
 
-template <bool DIT>
-__device__ void fft_stage_any(int len, int L, int R, const double2 *W) {
+template <bool DIT, class Ring>
+__device__ void fft_stage_any(Ring ring, int len, int L, int R, const double2 *W) {
   switch (R) {
-    case 2: fft_stage<2, DIT>(len, L, W); break;
-    case 3: fft_stage<3, DIT>(len, L, W); break;
-    case 4: fft_stage<4, DIT>(len, L, W); break;
-    case 5: fft_stage<5, DIT>(len, L, W); break;
-    case 7: fft_stage<7, DIT>(len, L, W); break;
-    case 11: fft_stage<11, DIT>(len, L, W); break;
-    case 13: fft_stage<13, DIT>(len, L, W); break;
-    case 17: fft_stage<17, DIT>(len, L, W); break;
-    case 19: fft_stage<19, DIT>(len, L, W); break;
-    case 23: fft_stage<23, DIT>(len, L, W); break;
-    case 29: fft_stage<29, DIT>(len, L, W); break;
-    default: fft_stage<31, DIT>(len, L, W); break;
+    case 2: fft_stage<2, DIT>(ring, len, L, W); break;
+    case 3: fft_stage<3, DIT>(ring, len, L, W); break;
+    case 4: fft_stage<4, DIT>(ring, len, L, W); break;
+    case 5: fft_stage<5, DIT>(ring, len, L, W); break;
+    case 7: fft_stage<7, DIT>(ring, len, L, W); break;
+    case 11: fft_stage<11, DIT>(ring, len, L, W); break;
+    case 13: fft_stage<13, DIT>(ring, len, L, W); break;
+    case 17: fft_stage<17, DIT>(ring, len, L, W); break;
+    case 19: fft_stage<19, DIT>(ring, len, L, W); break;
+    case 23: fft_stage<23, DIT>(ring, len, L, W); break;
+    case 29: fft_stage<29, DIT>(ring, len, L, W); break;
+    default: fft_stage<31, DIT>(ring, len, L, W); break;
   }
 }
 
-// Forward DFT of s_ring[0..fp.len) by decimation in frequency: natural-order input,
+// Forward DFT of ring[0..fp.len) by decimation in frequency: natural-order input,
 // output X_k at position fp.pos[k] (mixed-radix digit reversal).
-__device__ void fft_dif(const FftPlanDev &fp) {
+template <class Ring>
+__device__ void fft_dif(Ring ring, const FftPlanDev &fp) {
   int L = fp.len;
   for (int i = 0; i < fp.nrad; ++i) {
-    fft_stage_any<false>(fp.len, L, fp.rad[i], fp.w);
+    fft_stage_any<false>(ring, fp.len, L, fp.rad[i], fp.w);
     L /= fp.rad[i];
   }
 }
 
 // The transpose of fft_dif (its passes transposed, in reverse order): input
 // z_k at position fp.pos[k], output the forward DFT of z in natural order.
-__device__ void fft_dit(const FftPlanDev &fp) {
+template <class Ring>
+__device__ void fft_dit(Ring ring, const FftPlanDev &fp) {
   int L = 1;
   for (int i = fp.nrad - 1; i >= 0; --i) {
     L *= fp.rad[i];
-    fft_stage_any<true>(fp.len, L, fp.rad[i], fp.w);
+    fft_stage_any<true>(ring, fp.len, L, fp.rad[i], fp.w);
   }
 }
 
@@ -165,14 +180,16 @@ __device__ void fft_dit(const FftPlanDev &fp) {
 // a kernel whose spectrum was made by fft_dif (so it is digit-reversed like the
 // data): DIF, pointwise product, then the inverse as conj(DIT(conj)), which
 // returns to natural order with no permutation pass.
-__device__ void dft_run(double2 *buf, const FftPlanDev &fp, double2 *sh_x0, double2 *sh_a0) {
-  fft_dif(fp);
+template <class Ring>
+__device__ void dft_run(Ring ring, const FftPlanDev &fp, double2 *sh_x0, double2 *sh_a0) {
+  double2 *const buf = ring.at(0);
+  fft_dif(ring, fp);
   if (fp.kind == 0) return;
   if (fp.kind == 1 && threadIdx.x == 0) *sh_a0 = buf[0];  // X_0 sits at position 0
   __syncthreads();
   for (int i = threadIdx.x; i < fp.len; i += blockDim.x) buf[i] = cconj(cmul(buf[i], fp.spec[i]));
   __syncthreads();
-  fft_dit(fp);
+  fft_dit(ring, fp);
 }
 
 __device__ __forceinline__ double2 dft_at(const double2 *buf, const FftPlanDev &fp, int k, double2 x0,
@@ -194,14 +211,27 @@ __global__ void __launch_bounds__(kFftThreads) spectrum_kernel(const FftPlanDev 
   const FftPlanDev fp = *fpd;
   for (int i = threadIdx.x; i < len; i += blockDim.x) buf[i] = src[i];
   __syncthreads();
-  fft_dif(fp);
+  fft_dif(SharedRing{}, fp);
   for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = make_double2(buf[i].x * scale, buf[i].y * scale);
+}
+// the same for lengths beyond shared memory: transformed in place in dst
+__global__ void __launch_bounds__(kFftThreads) spectrum_kernel_global(const FftPlanDev *fpd, const double2 *src,
+                                                                     double2 *dst, int len, double scale) {
+  const FftPlanDev fp = *fpd;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  fft_dif(GlobalRing{dst}, fp);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = make_double2(dst[i].x * scale, dst[i].y * scale);
 }
 
 cudaError_t launch_fft_spectrum(const FftPlanDev *hp, const FftPlanDev *dp, const double2 *src, double2 *dst,
                                 int len, double scale, cudaStream_t st) {
-  const int smem = len * (int)sizeof(double2);  // limit raised by fft_prepare_device
-  spectrum_kernel<<<1, kFftThreads, smem, st>>>(dp, src, dst, len, scale);
+  if (len > kFftMaxLen) {
+    spectrum_kernel_global<<<1, kFftThreads, 0, st>>>(dp, src, dst, len, scale);
+  } else {
+    const int smem = len * (int)sizeof(double2);  // limit raised by fft_prepare_device
+    spectrum_kernel<<<1, kFftThreads, smem, st>>>(dp, src, dst, len, scale);
+  }
   return cudaGetLastError();
 }
 
@@ -229,6 +259,7 @@ struct FftArgs {
   DevPtrs map;
   int weighted, add;
   int ptr_off;
+  int nmaps_run;  // maps per side (global-ring kernels walk npairs x nmaps_run items)
 };
 
 // ---------------------------------------------------------------------------
@@ -260,10 +291,12 @@ __device__ double2 spectrum_at(const FftArgs &a, int j, int p, int k, int N, dou
   return z;
 }
 
-__device__ __forceinline__ void fft_syn_kernel_body(const FftArgs &a, double *const *ptrs, const int p, const int j) {
-  double2 *const buf = s_ring;
+template <class Ring>
+__device__ __forceinline__ void fft_syn_kernel_body(Ring ring, const FftArgs &a, double *const *ptrs, const int p,
+                                     const int j) {
+  double2 *const buf = ring.at(0);
   __shared__ double2 sh_x0, sh_a0;
-    const FftPlanDev fp = a.plans[a.pair_fft[p]];
+  const FftPlanDev fp = a.plans[a.pair_fft[p]];
   const int2 rr = a.pair_rings[p];
   const RingDev rn = a.rings[rr.x];
   const bool south = rr.y >= 0;
@@ -283,7 +316,7 @@ __device__ __forceinline__ void fft_syn_kernel_body(const FftArgs &a, double *co
                        : make_double2(0.0, 0.0);
   }
   __syncthreads();
-  dft_run(buf, fp, &sh_x0, &sh_a0);
+  dft_run(ring, fp, &sh_x0, &sh_a0);
   const double2 x0 = sh_x0, a0 = sh_a0;
   double *mp = ptrs[j];
   const double wn = a.weighted ? rn.weight : 1.0, ws = a.weighted ? rs.weight : 1.0;
@@ -303,22 +336,24 @@ __device__ __forceinline__ void fft_syn_kernel_body(const FftArgs &a, double *co
   }
 }
 __global__ void __launch_bounds__(kFftThreads) fft_syn_kernel(FftArgs a) {
-  fft_syn_kernel_body(a, a.map.p, blockIdx.x, blockIdx.y);
+  fft_syn_kernel_body(SharedRing{}, a, a.map.p, blockIdx.x, blockIdx.y);
 }
 __global__ void __launch_bounds__(kFftThreads) fft_syn_kernel_batch(const FftArgs *__restrict__ args,
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const FftArgs &a = args[it.w];
-  fft_syn_kernel_body(a, tbl.p + a.ptr_off, it.x, it.y);
+  fft_syn_kernel_body(SharedRing{}, a, tbl.p + a.ptr_off, it.x, it.y);
 }
 
 // ---------------------------------------------------------------------------
 // analysis: ring pixels -> G (per m)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void fft_ana_kernel_body(const FftArgs &a, double *const *ptrs, const int p, const int j) {
-  double2 *const buf = s_ring;
+template <class Ring>
+__device__ __forceinline__ void fft_ana_kernel_body(Ring ring, const FftArgs &a, double *const *ptrs, const int p,
+                                     const int j) {
+  double2 *const buf = ring.at(0);
   __shared__ double2 sh_x0, sh_a0;
-    const FftPlanDev fp = a.plans[a.pair_fft[p]];
+  const FftPlanDev fp = a.plans[a.pair_fft[p]];
   const int2 rr = a.pair_rings[p];
   const RingDev rn = a.rings[rr.x];
   const bool south = rr.y >= 0;
@@ -340,7 +375,7 @@ __device__ __forceinline__ void fft_ana_kernel_body(const FftArgs &a, double *co
       buf[k] = (k < N) ? cmul(zin(k), fp.chirp[k]) : make_double2(0.0, 0.0);
   }
   __syncthreads();
-  dft_run(buf, fp, &sh_x0, &sh_a0);
+  dft_run(ring, fp, &sh_x0, &sh_a0);
   const double2 x0 = sh_x0, a0 = sh_a0;
   const double wn = a.weighted ? rn.weight : 1.0, ws = a.weighted ? rs.weight : 1.0;
   for (int mi = threadIdx.x; mi < a.nm; mi += blockDim.x) {
@@ -364,13 +399,34 @@ __device__ __forceinline__ void fft_ana_kernel_body(const FftArgs &a, double *co
   }
 }
 __global__ void __launch_bounds__(kFftThreads) fft_ana_kernel(FftArgs a) {
-  fft_ana_kernel_body(a, a.map.p, blockIdx.x, blockIdx.y);
+  fft_ana_kernel_body(SharedRing{}, a, a.map.p, blockIdx.x, blockIdx.y);
 }
 __global__ void __launch_bounds__(kFftThreads) fft_ana_kernel_batch(const FftArgs *__restrict__ args,
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const FftArgs &a = args[it.w];
-  fft_ana_kernel_body(a, tbl.p + a.ptr_off, it.x, it.y);
+  fft_ana_kernel_body(SharedRing{}, a, tbl.p + a.ptr_off, it.x, it.y);
+}
+
+// Rings longer than shared memory holds: a persistent grid, each CTA owning one
+// scratch slot of slot_len points, walks the (pair, map) items in turn.
+__global__ void __launch_bounds__(kFftThreads) fft_syn_kernel_global(FftArgs a, double2 *scratch,
+                                                                     int slot_len) {
+  const GlobalRing ring{scratch + (size_t)blockIdx.x * slot_len};
+  const int n = a.npairs * a.nmaps_run;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    fft_syn_kernel_body(ring, a, a.map.p, it % a.npairs, it / a.npairs);
+    __syncthreads();  // the slot is rewritten by the next item
+  }
+}
+__global__ void __launch_bounds__(kFftThreads) fft_ana_kernel_global(FftArgs a, double2 *scratch,
+                                                                     int slot_len) {
+  const GlobalRing ring{scratch + (size_t)blockIdx.x * slot_len};
+  const int n = a.npairs * a.nmaps_run;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    fft_ana_kernel_body(ring, a, a.map.p, it % a.npairs, it / a.npairs);
+    __syncthreads();
+  }
 }
 
 static FftArgs make_fft_args(const sht_plan_s *P, const DevPtrs &map, int polar) {
@@ -389,6 +445,8 @@ static FftArgs make_fft_args(const sht_plan_s *P, const DevPtrs &map, int polar)
   a.map = map;
   a.weighted = 0;
   a.add = 0;
+  a.ptr_off = 0;
+  a.nmaps_run = P->nmaps;
   return a;
 }
 
@@ -397,6 +455,11 @@ cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, i
   FftArgs a = make_fft_args(P, map, polar);
   a.weighted = weighted;
   a.add = add;
+  if (P->d_fft_scratch) {
+    const int g = (int)std::min<int64_t>((int64_t)P->npairs * P->nmaps, P->fft_slots);
+    fft_syn_kernel_global<<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
+    return cudaGetLastError();
+  }
   dim3 grid(P->npairs, P->nmaps);
   fft_syn_kernel<<<grid, kFftThreads, P->fft_smem, st>>>(a);
   return cudaGetLastError();
@@ -405,6 +468,11 @@ cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, i
 cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted, cudaStream_t st) {
   FftArgs a = make_fft_args(P, map, 1);
   a.weighted = weighted;
+  if (P->d_fft_scratch) {
+    const int g = (int)std::min<int64_t>((int64_t)P->npairs * P->nmaps, P->fft_slots);
+    fft_ana_kernel_global<<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
+    return cudaGetLastError();
+  }
   dim3 grid(P->npairs, P->nmaps);
   fft_ana_kernel<<<grid, kFftThreads, P->fft_smem, st>>>(a);
   return cudaGetLastError();

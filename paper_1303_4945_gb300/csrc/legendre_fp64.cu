@@ -734,7 +734,7 @@ __global__ void alm_to_pm(int lmax, int spin, int nm, int astride, const int *__
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar) {
+static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar, bool lo = false) {
   LegArgs a;
   a.lmax = P->lmax;
   a.spin = P->spin;
@@ -751,8 +751,8 @@ static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar) {
   a.pairs = P->d_pairs;
   a.alm = alm;
   a.phase = P->d_phase;
-  a.syn_items = P->d_syn_items[polar];
-  a.ana_items = P->d_ana_items[polar];
+  a.syn_items = lo ? P->d_syn_lo[polar] : P->d_syn_items[polar];
+  a.ana_items = lo ? P->d_ana_lo[polar] : P->d_ana_items[polar];
   a.part_off = P->d_ana_part_off[polar];
   a.tile0 = P->d_ana_tile0[polar];
   a.part = P->d_part;
@@ -762,15 +762,15 @@ static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar) {
   return a;
 }
 
-cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st) {
-  const int n = P->nsyn_items[polar];
+cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
+  const int n = lo ? P->nsyn_lo[polar] : P->nsyn_items[polar];
   if (n == 0) return cudaSuccess;
   if (P->spin != 0) {
     dim3 g(P->nm, P->njobs_pad);
     alm_to_pm<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->astride, P->d_mval, P->d_mstart, P->d_coef_off,
                                  P->ncoef, alm, P->d_pm64);
   }
-  LegArgs a = make_args(P, alm, polar);
+  LegArgs a = make_args(P, alm, polar, lo);
   const int nj = P->njobs_pad;
   if (P->spin == 0) {
     switch (nj) {
@@ -791,9 +791,9 @@ cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int pol
   return cudaGetLastError();
 }
 
-cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st) {
-  const int n = P->nana_items[polar];
-  LegArgs a = make_args(P, alm, polar);
+cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
+  const int n = lo ? P->nana_lo[polar] : P->nana_items[polar];
+  LegArgs a = make_args(P, alm, polar, lo);
   if (n > 0) {
     if (P->spin == 0)
       ana_shape_s0(P->njobs_pad, P->ana_ppt, [&](auto sh) {
@@ -824,10 +824,10 @@ namespace sht {
 
 size_t leg_fp64_args_size() { return sizeof(LegArgs); }
 
-void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out) {
+void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out, bool lo) {
   DevPtrs none;
   memset(&none, 0, sizeof(none));
-  LegArgs a = make_args(P, none, polar);
+  LegArgs a = make_args(P, none, polar, lo);
   a.ptr_off = ptr_off;
   memcpy(out, &a, sizeof(a));
 }

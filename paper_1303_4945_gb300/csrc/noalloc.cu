@@ -7,7 +7,8 @@
 // afford the implicit device synchronisation of cudaMalloc / cudaFree.
 // This entry point runs the transform of an existing plan exactly like
 // sht_execute, but takes all of its per-call working memory -- the phase
-// array F/G, the analysis tile sums and the converted a_lm tables -- from
+// array F/G, the analysis tile sums and the converted a_lm tables (both, for a
+// mixed plan with FP64 columns) -- from
 // one fixed area compiled into the library (kNoallocBytes below), so the
 // call itself makes no allocation of any kind and does not use the plan's
 // own workspace.  Every GPU that loads the library holds this area until the
@@ -65,7 +66,9 @@ extern "C" int sht_execute_noalloc(sht_plan_t P, int type, double *const *alm, d
   const int64_t b_phase = align256((int64_t)P->nmaps_pad * P->nm * P->npairs * 2 * (int64_t)sizeof(double2));
   const int64_t b_part = synth ? 0 : align256(P->part_doubles * (int64_t)sizeof(double));
   const int64_t b_alm32 = (synth && mixed) ? align256(P->ncoef * P->nmaps_pad * (int64_t)sizeof(float4)) : 0;
-  const int64_t b_pm64 = (synth && !mixed && P->spin) ? align256(P->ncoef * P->nmaps_pad * (int64_t)sizeof(double2)) : 0;
+  const bool lo = mixed && (P->nsyn_lo[0] || P->nsyn_lo[1]);  // mixed plan with FP64 columns
+  const int64_t b_pm64 =
+      (synth && P->spin && (!mixed || lo)) ? align256(P->ncoef * P->nmaps_pad * (int64_t)sizeof(double2)) : 0;
   const int64_t need = b_phase + b_part + b_alm32 + b_pm64;
   if (need > kNoallocBytes)
     return set_error(SHT_ERR_UNSUPPORTED, "this transform needs %lld bytes of working memory; the static area holds %lld",
@@ -102,17 +105,19 @@ extern "C" int sht_execute_noalloc(sht_plan_t P, int type, double *const *alm, d
   P->d_phase = reinterpret_cast<double2 *>(base);
   if (b_part) P->d_part = reinterpret_cast<double *>(base + b_phase);
   if (b_alm32) P->d_alm32 = reinterpret_cast<float4 *>(base + b_phase);
-  if (b_pm64) P->d_pm64 = reinterpret_cast<double2 *>(base + b_phase);
+  if (b_pm64) P->d_pm64 = reinterpret_cast<double2 *>(base + b_phase + b_alm32);
   cudaStream_t st = (cudaStream_t)stream;
   const int polar = (flags & SHT_NO_POLAR_OPT) ? 0 : 1;
   const int add = (flags & SHT_ADD_OUTPUT) ? 1 : 0;
   cudaError_t e;
   if (synth) {
     e = mixed ? launch_leg_syn_mixed(P, A, polar, st) : launch_leg_syn_fp64(P, A, polar, st);
+    if (e == cudaSuccess && mixed && P->nsyn_lo[polar]) e = launch_leg_syn_fp64(P, A, polar, st, true);
     if (e == cudaSuccess) e = launch_fft_syn(P, M, polar, type == SHT_ADJOINT_ANALYSIS, add, st);
   } else {
     e = launch_fft_ana(P, M, type == SHT_ANALYSIS, st);
     if (e == cudaSuccess) e = mixed ? launch_leg_ana_mixed(P, A, polar, st) : launch_leg_ana_fp64(P, A, polar, st);
+    if (e == cudaSuccess && mixed && P->nana_lo[polar]) e = launch_leg_ana_fp64(P, A, polar, st, true);
     if (e == cudaSuccess) e = launch_ana_reduce(P, A, polar, add, st);
   }
   P->d_phase = phase0;

@@ -496,17 +496,17 @@ static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scra
   fp.n = n;
   std::vector<int> rad;
   int rc;
-  if (n <= kFftMaxLen && factor_small(n, rad)) {
+  if (n <= kFftMaxGlobalLen && factor_small(n, rad)) {
     fp.kind = 0;
     fp.len = n;
-  } else if (is_prime(n) && n - 1 <= kFftMaxLen && factor_small(n - 1, rad)) {
+  } else if (is_prime(n) && n - 1 <= kFftMaxGlobalLen && factor_small(n - 1, rad)) {
     fp.kind = 1;
     fp.len = n - 1;
   } else {
     int M = 2 * n - 1;  // smallest smooth convolution length
-    while (M <= kFftMaxLen && !factor_small(M, rad)) ++M;
-    if (M > kFftMaxLen)
-      return fail(SHT_ERR_UNSUPPORTED, "ring length %d: no FFT of size <= %d available", n, kFftMaxLen);
+    while (M <= kFftMaxGlobalLen && !factor_small(M, rad)) ++M;
+    if (M > kFftMaxGlobalLen)
+      return fail(SHT_ERR_UNSUPPORTED, "ring length %d: no FFT of size <= %d available", n, kFftMaxGlobalLen);
     fp.kind = 2;
     fp.len = M;
   }
@@ -588,7 +588,7 @@ static void free_plan(sht_plan_s *P) {
   cudaSetDevice(P->device);
   void *ptrs[] = {P->d_pairs, P->d_pair_rings, P->d_rings, P->d_mval, P->d_mstart, P->d_coef_off,
                   P->d_coef, P->d_coef32, P->d_alm32, P->d_pm64, P->d_mpre, P->d_minv, P->d_phase, P->d_part, P->d_fft,
-                  P->d_pair_fft};
+                  P->d_pair_fft, P->d_fft_scratch};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 2; ++k) {
@@ -597,6 +597,8 @@ static void free_plan(sht_plan_s *P) {
     if (P->d_ana_items[k]) cudaFree(P->d_ana_items[k]);
     if (P->d_ana_part_off[k]) cudaFree(P->d_ana_part_off[k]);
     if (P->d_ana_tile0[k]) cudaFree(P->d_ana_tile0[k]);
+    if (P->d_syn_lo[k]) cudaFree(P->d_syn_lo[k]);
+    if (P->d_ana_lo[k]) cudaFree(P->d_ana_lo[k]);
   }
   for (void *p : P->fft_allocs) cudaFree(p);
   for (auto &r : P->prof) {
@@ -631,6 +633,70 @@ static std::vector<int> ana_ppt_candidates(int spin, int nj) {
 // Analysis work lists for tiles of kAnaThreads * ppt ring pairs: per polar
 // variant the cost-sorted (m, tile) items, each m's offset into the tile-sum
 // array and its first tile; sizes the tile-sum array for this tiling.
+// Mixed form: columns m below this run in FP64.  The double-float recursion keeps
+// ~48 bits of A_l x; near the poles the Legendre functions of small m respond to
+// an error d in x like l^2 d, and the measured error of a column grows like
+// lmax^2.4 (m+1)^-0.85 (white-noise inputs, against the FP64 form and the oracle).
+// (lmax / 2700)^3 keeps every column near or below 1e-10: 3 columns at lmax 4095,
+// 28 at 8191, none below lmax 2700.
+static int default_fp64_columns(int lmax) {
+  const double r = lmax / 2700.0;
+  return (int)std::floor(r * r * r);
+}
+
+static bool lo_column(const sht_plan_s *P, int mi) {
+  return P->precision == SHT_MIXED && P->mval[mi] < P->fp64_m_below;
+}
+
+template <class T>
+static int upload_list(sht_plan_s *P, const std::vector<std::pair<int64_t, T>> &list, T **d, int *n) {
+  std::vector<T> v;
+  for (auto &e : list) v.push_back(e.second);
+  if (*d) cudaFree(*d);
+  *d = nullptr;
+  *n = (int)v.size();
+  return upload(P, v, d);
+}
+
+// Synthesis work lists: per polar variant the cost-sorted (m, first pair)
+// tiles (the mixed form's FP64 columns in lists of their own), each m's first
+// synthesised pair, and the exact triple count.
+static int build_syn_lists(sht_plan_s *P) {
+  int rc;
+  const int as = abs(P->spin);
+  for (int polar = 0; polar < 2; ++polar) {
+    std::vector<std::pair<int64_t, int2>> syn, lo;
+    std::vector<int> sfirst(P->nm);
+    int64_t trip = 0;
+    for (int i = 0; i < P->nm; ++i) {
+      int l0 = std::max(P->mval[i], as);
+      int nl = P->lmax - l0 + 1;
+      if (nl <= 0) {
+        sfirst[i] = P->npairs;
+        continue;
+      }
+      int fp = polar ? P->first_pair[i] : 0;
+      trip += (int64_t)(P->npairs - fp) * nl;
+      int sf = (fp / kSynTile) * kSynTile;
+      sfirst[i] = sf;
+      auto &dst = lo_column(P, i) ? lo : syn;
+      for (int p = sf; p < P->npairs; p += kSynTile)
+        dst.push_back({(int64_t)nl * std::min(kSynTile, P->npairs - p), make_int2(i, p)});
+    }
+    P->triples[polar] = trip;
+    std::stable_sort(syn.begin(), syn.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    std::stable_sort(lo.begin(), lo.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    P->syn_list[polar] = syn;
+    P->syn_list_lo[polar] = lo;
+    if ((rc = upload_list(P, syn, &P->d_syn_items[polar], &P->nsyn_items[polar])) != SHT_OK) return rc;
+    if ((rc = upload_list(P, lo, &P->d_syn_lo[polar], &P->nsyn_lo[polar])) != SHT_OK) return rc;
+    if (P->d_syn_first[polar]) cudaFree(P->d_syn_first[polar]);
+    P->d_syn_first[polar] = nullptr;
+    if ((rc = upload(P, sfirst, &P->d_syn_first[polar])) != SHT_OK) return rc;
+  }
+  return SHT_OK;
+}
+
 static int build_ana_lists(sht_plan_s *P, int ppt) {
   int rc;
   const int as = abs(P->spin);
@@ -639,7 +705,7 @@ static int build_ana_lists(sht_plan_s *P, int ppt) {
   const int tiles = (P->npairs + TA - 1) / TA;
   int64_t need = 0;
   for (int polar = 0; polar < 2; ++polar) {
-    std::vector<std::pair<int64_t, int4>> ana;
+    std::vector<std::pair<int64_t, int4>> ana, lo;
     std::vector<int64_t> poff(P->nm);
     std::vector<int> t0(P->nm);
     int64_t off = 0;
@@ -654,22 +720,21 @@ static int build_ana_lists(sht_plan_s *P, int ppt) {
       int fp = polar ? P->first_pair[i] : 0;
       int tf = fp / TA;
       t0[i] = tf;
+      auto &dst = lo_column(P, i) ? lo : ana;
       for (int t = tf; t < tiles; ++t)
-        ana.push_back({(int64_t)nl * std::min(TA, P->npairs - t * TA), make_int4(i, t, 0, 0)});
+        dst.push_back({(int64_t)nl * std::min(TA, P->npairs - t * TA), make_int4(i, t, 0, 0)});
       off += (int64_t)(tiles - tf) * nl * V;
     }
     std::stable_sort(ana.begin(), ana.end(), [](auto &a, auto &b) { return a.first > b.first; });
-    std::vector<int4> ai;
-    for (auto &e : ana) ai.push_back(e.second);
-    if (P->d_ana_items[polar]) cudaFree(P->d_ana_items[polar]);
+    std::stable_sort(lo.begin(), lo.end(), [](auto &a, auto &b) { return a.first > b.first; });
     if (P->d_ana_part_off[polar]) cudaFree(P->d_ana_part_off[polar]);
     if (P->d_ana_tile0[polar]) cudaFree(P->d_ana_tile0[polar]);
-    P->d_ana_items[polar] = nullptr;
     P->d_ana_part_off[polar] = nullptr;
     P->d_ana_tile0[polar] = nullptr;
     P->ana_list[polar] = ana;
-    P->nana_items[polar] = (int)ai.size();
-    if ((rc = upload(P, ai, &P->d_ana_items[polar])) != SHT_OK) return rc;
+    P->ana_list_lo[polar] = lo;
+    if ((rc = upload_list(P, ana, &P->d_ana_items[polar], &P->nana_items[polar])) != SHT_OK) return rc;
+    if ((rc = upload_list(P, lo, &P->d_ana_lo[polar], &P->nana_lo[polar])) != SHT_OK) return rc;
     if ((rc = upload(P, poff, &P->d_ana_part_off[polar])) != SHT_OK) return rc;
     if ((rc = upload(P, t0, &P->d_ana_tile0[polar])) != SHT_OK) return rc;
     need = std::max(need, off);
@@ -746,7 +811,7 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
     CUDA_TRY(cudaMalloc(&P->d_alm32, std::max<int64_t>(1, nco) * P->nmaps_pad * sizeof(float4)));
     P->workspace += nco * P->nmaps_pad * sizeof(float4);
   }
-  if (P->precision == SHT_FP64 && P->spin != 0) {
+  if (P->spin != 0 && (P->precision == SHT_FP64 || default_fp64_columns(P->lmax) > 0)) {
     CUDA_TRY(cudaMalloc(&P->d_pm64, std::max<int64_t>(1, nco) * P->nmaps_pad * sizeof(double2)));
     P->workspace += nco * P->nmaps_pad * sizeof(double2);
   }
@@ -775,33 +840,8 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   }
 
   // ---- work lists ----
-  for (int polar = 0; polar < 2; ++polar) {
-    std::vector<std::pair<int64_t, int2>> syn;
-    std::vector<int> sfirst(P->nm);
-    int64_t trip = 0;
-    for (int i = 0; i < P->nm; ++i) {
-      int l0 = std::max(P->mval[i], as);
-      int nl = P->lmax - l0 + 1;
-      if (nl <= 0) {
-        sfirst[i] = P->npairs;
-        continue;
-      }
-      int fp = polar ? P->first_pair[i] : 0;
-      trip += (int64_t)(P->npairs - fp) * nl;
-      int sf = (fp / kSynTile) * kSynTile;
-      sfirst[i] = sf;
-      for (int p = sf; p < P->npairs; p += kSynTile)
-        syn.push_back({(int64_t)nl * std::min(kSynTile, P->npairs - p), make_int2(i, p)});
-    }
-    P->triples[polar] = trip;
-    std::stable_sort(syn.begin(), syn.end(), [](auto &a, auto &b) { return a.first > b.first; });
-    std::vector<int2> si;
-    for (auto &e : syn) si.push_back(e.second);
-    P->syn_list[polar] = syn;
-    P->nsyn_items[polar] = (int)si.size();
-    if ((rc = upload(P, si, &P->d_syn_items[polar])) != SHT_OK) return rc;
-    if ((rc = upload(P, sfirst, &P->d_syn_first[polar])) != SHT_OK) return rc;
-  }
+  P->fp64_m_below = P->precision == SHT_MIXED ? default_fp64_columns(P->lmax) : 0;
+  if ((rc = build_syn_lists(P)) != SHT_OK) return rc;
   if ((rc = build_ana_lists(P, ana_ppt_candidates(P->spin, P->njobs_pad)[0])) != SHT_OK) return rc;
 
   // ---- phase-array workspace F/G [nmaps][nm][npairs][2] ----
@@ -832,7 +872,17 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   }
   if ((rc = upload(P, fps, &P->d_fft)) != SHT_OK) return rc;
   if ((rc = upload(P, pf, &P->d_pair_fft)) != SHT_OK) return rc;
-  P->fft_smem = maxlen * (int)sizeof(double2);
+  if (maxlen <= kFftMaxLen) {
+    P->fft_smem = maxlen * (int)sizeof(double2);
+  } else {  // rings beyond shared memory: one L2-resident scratch slot per SM (one CTA each)
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
+    P->fft_slots = sms;
+    P->fft_slot_len = maxlen;
+    const size_t bytes = (size_t)sms * maxlen * sizeof(double2);
+    CUDA_TRY(cudaMalloc(&P->d_fft_scratch, bytes));
+    P->workspace += bytes;
+  }
   P->pair_len.resize(P->npairs);
   for (int p = 0; p < P->npairs; ++p) {
     int n = g->nphi[P->pair_n[p]];
@@ -910,6 +960,36 @@ extern "C" int sht_plan_get_tiling(sht_plan_t P, int *pairs_per_thread, int *nca
   return SHT_OK;
 }
 
+extern "C" int sht_plan_set_fp64_columns(sht_plan_t P, int m_below) {
+  if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  if (P->precision != SHT_MIXED) return fail(SHT_ERR_INVALID_ARG, "only mixed-form plans have FP64 columns");
+  if (m_below < 0) return fail(SHT_ERR_INVALID_ARG, "m_below must be >= 0");
+  if (P->batch_refs)
+    return fail(SHT_ERR_INVALID_ARG, "the plan belongs to %d batch(es); destroy them first", P->batch_refs);
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  int rc = SHT_OK;
+  if (P->spin != 0 && !P->d_pm64 && m_below > 0) {  // the FP64 spin kernels read P = E+iB, M = E-iB
+    const size_t bytes = std::max<int64_t>(1, P->ncoef) * P->nmaps_pad * sizeof(double2);
+    if (cudaMalloc(&P->d_pm64, bytes) != cudaSuccess) rc = fail(SHT_ERR_OOM, "P/M table");
+    else P->workspace += bytes;
+  }
+  if (rc == SHT_OK) {
+    P->fp64_m_below = m_below;
+    rc = build_syn_lists(P);
+    if (rc == SHT_OK) rc = build_ana_lists(P, P->ana_ppt);
+  }
+  if (cur != P->device) cudaSetDevice(cur);
+  return rc;
+}
+
+extern "C" int sht_plan_get_fp64_columns(sht_plan_t P, int *m_below) {
+  if (!P || !m_below) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  *m_below = P->fp64_m_below;
+  return SHT_OK;
+}
+
 extern "C" int sht_plan_autotune(sht_plan_t P, void *stream, float *ms_per_candidate) {
   if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
   if (P->batch_refs) return retile(P, P->ana_ppt);  // reports the error
@@ -935,6 +1015,7 @@ extern "C" int sht_plan_autotune(sht_plan_t P, void *stream, float *ms_per_candi
       if (it == 1) e = cudaEventRecord(ev[0], st);
       if (e == cudaSuccess)
         e = P->precision == SHT_MIXED ? launch_leg_ana_mixed(P, none, 1, st) : launch_leg_ana_fp64(P, none, 1, st);
+      if (e == cudaSuccess && P->precision == SHT_MIXED && P->nana_lo[1]) e = launch_leg_ana_fp64(P, none, 1, st, true);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
@@ -1046,11 +1127,19 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
   };
   const bool mixed = P->precision == SHT_MIXED;
   if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS) {
-    stage(0, [&] { return mixed ? launch_leg_syn_mixed(P, A, polar, st) : launch_leg_syn_fp64(P, A, polar, st); });
+    stage(0, [&] {
+      if (!mixed) return launch_leg_syn_fp64(P, A, polar, st);
+      cudaError_t r = launch_leg_syn_mixed(P, A, polar, st);
+      return (r == cudaSuccess && P->nsyn_lo[polar]) ? launch_leg_syn_fp64(P, A, polar, st, true) : r;
+    });
     stage(1, [&] { return launch_fft_syn(P, M, polar, type == SHT_ADJOINT_ANALYSIS, add, st); });
   } else {
     stage(2, [&] { return launch_fft_ana(P, M, type == SHT_ANALYSIS, st); });
-    stage(3, [&] { return mixed ? launch_leg_ana_mixed(P, A, polar, st) : launch_leg_ana_fp64(P, A, polar, st); });
+    stage(3, [&] {
+      if (!mixed) return launch_leg_ana_fp64(P, A, polar, st);
+      cudaError_t r = launch_leg_ana_mixed(P, A, polar, st);
+      return (r == cudaSuccess && P->nana_lo[polar]) ? launch_leg_ana_fp64(P, A, polar, st, true) : r;
+    });
     stage(4, [&] { return launch_ana_reduce(P, A, polar, add, st); });
   }
   if (cur != P->device) cudaSetDevice(cur);

@@ -28,6 +28,9 @@ constexpr int kFftThreads = 512;
 // longest in-place transform: the ring buffer (16 bytes a point) must fit the
 // opt-in shared memory of one CTA (227 KB on sm_103a)
 constexpr int kFftMaxLen = 14336;
+// longest transform at all: longer rings run from a global scratch slot per CTA
+// (1 MiB each), which stays in L2
+constexpr int kFftMaxGlobalLen = 65536;
 
 // Extended exponent of the FP64 recursion: a pair (lambda_{l-1}, lambda_l) is
 // stored as value * 2^(kScaleStep * scale); it contributes only at scale 0.
@@ -145,6 +148,15 @@ struct sht_plan_s {
   // host copies of the work lists with their costs (l count x pairs), for merging into batches
   std::vector<std::pair<int64_t, int2>> syn_list[2];
   std::vector<std::pair<int64_t, int4>> ana_list[2];
+  // mixed form: the columns m < fp64_m_below run in the FP64 kernels (their own work lists);
+  // near the poles the recursion at small m amplifies the rounding of A x by ~l^2
+  int fp64_m_below = 0;
+  int2 *d_syn_lo[2] = {nullptr, nullptr};
+  int nsyn_lo[2] = {0, 0};
+  int4 *d_ana_lo[2] = {nullptr, nullptr};
+  int nana_lo[2] = {0, 0};
+  std::vector<std::pair<int64_t, int2>> syn_list_lo[2];
+  std::vector<std::pair<int64_t, int4>> ana_list_lo[2];
   int ana_tiles = 0;
   int64_t triples[2] = {0, 0};
 
@@ -155,6 +167,8 @@ struct sht_plan_s {
   int *d_pair_fft = nullptr;  // per pair: plan index
   int fft_smem = 0;           // bytes of dynamic shared memory for the FFT kernels
   std::vector<int> pair_len;  // per pair: the longer ring length (FFT cost)
+  double2 *d_fft_scratch = nullptr;  // rings beyond kFftMaxLen: one slot of fft_slot_len points per CTA
+  int fft_slots = 0, fft_slot_len = 0;
 
   int64_t workspace = 0;
 
@@ -179,8 +193,11 @@ cudaError_t launch_fft_spectrum(const FftPlanDev *host_plan, const FftPlanDev *d
                                 const double2 *src, double2 *dst, int len, double scale,
                                 cudaStream_t st);
 // Legendre stage
-cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
-cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
+// lo: run the mixed plan's FP64 columns (work lists d_syn_lo / d_ana_lo)
+cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st,
+                                bool lo = false);
+cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st,
+                                bool lo = false);
 cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st);
 cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
 cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
@@ -198,7 +215,7 @@ cudaError_t fft_prepare_device(int device);
 size_t leg_fp64_args_size();
 size_t leg_mixed_args_size();
 size_t fft_args_size();
-void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
+void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out, bool lo = false);
 void leg_mixed_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
 void fft_fill_args(const sht_plan_s *P, int polar, int weighted, int add, int ptr_off, void *out);
 cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st);

@@ -66,6 +66,8 @@ _sig = {
     "sht_plan_get_tiling": [_vp, _ip, _ip, _ip],
     "sht_plan_set_tiling": [_vp, ctypes.c_int],
     "sht_plan_autotune": [_vp, _vp, ctypes.POINTER(ctypes.c_float)],
+    "sht_plan_set_fp64_columns": [_vp, ctypes.c_int],
+    "sht_plan_get_fp64_columns": [_vp, _ip],
     "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
                           ctypes.c_int, _vp],
@@ -211,6 +213,17 @@ class Plan(_Handle):
         _check(_lib.sht_plan_autotune(self._h, st, ms), "sht_plan_autotune")
         return {c: float(ms[i]) for i, c in enumerate(cands)}
 
+    @property
+    def fp64_columns(self):
+        """Mixed form: columns m below this run in the FP64 kernels."""
+        n = ctypes.c_int()
+        _check(_lib.sht_plan_get_fp64_columns(self._h, ctypes.byref(n)), "sht_plan_get_fp64_columns")
+        return n.value
+
+    @fp64_columns.setter
+    def fp64_columns(self, m_below):
+        _check(_lib.sht_plan_set_fp64_columns(self._h, m_below), "sht_plan_set_fp64_columns")
+
     def triples(self, flags=0):
         n = ctypes.c_int64()
         _check(_lib.sht_plan_triples(self._h, flags, ctypes.byref(n)), "sht_plan_triples")
@@ -260,7 +273,9 @@ def sht_alm_create(lmax, mmax, mval=None, mstart=None, stride=1) -> AlmLayout:
     h = _vp()
     _check(_lib.sht_alm_create(lmax, mmax, 0 if mv is None else len(mv), _ptr(mv, _ip), _ptr(ms, _i64p),
                                stride, ctypes.byref(h)), "sht_alm_create")
-    return AlmLayout(h.value, lmax, mmax)
+    lay = AlmLayout(h.value, lmax, mmax)
+    lay.custom = mval is not None or mstart is not None or stride != 1  # not the default triangular layout
+    return lay
 
 
 def sht_plan_create(geom: Geometry, alm: AlmLayout, spin=0, ncomp=1, precision=SHT_FP64) -> Plan:

@@ -1,0 +1,125 @@
+"""Mixed-form plans whose small-m columns run in the FP64 kernels.
+
+The default threshold is 0 below lmax 2700, so these tests force one on small
+plans: results must match the oracle for every transform type (those columns
+to the FP64 tolerance, the plan as a whole to the mixed one), inside a batch
+and through the no-alloc entry point; the threshold's default and its error
+cases are checked too.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1303_4945_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sht():
+    from paper_1303_4945_gb300 import build
+
+    build.build()
+    from paper_1303_4945_gb300 import sht as m
+
+    assert torch.cuda.is_available()
+    return m
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rings_of(geom):
+    r = geom.rings()
+    return oracle.Rings(r["theta"], r["nphi"], r["phi0"], r["weight"], ofs=r["ofs"])
+
+
+@pytest.mark.parametrize("spin,make", [(0, lambda s: s.sht_geom_gauss(50, 99)),
+                                       (2, lambda s: s.sht_geom_gauss(50, 99)),
+                                       (0, lambda s: s.sht_geom_healpix(16)),
+                                       (1, lambda s: s.sht_geom_healpix(16))])
+@pytest.mark.parametrize("flags", [0, 2])
+def test_forced_fp64_columns_match_oracle(sht, spin, make, flags):
+    lmax = 47
+    geom = make(sht)
+    rings = rings_of(geom)
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), spin, 1, sht.SHT_MIXED)
+    assert plan.fp64_columns == 0
+    plan.fp64_columns = 9
+    assert plan.fp64_columns == 9
+    narr = plan.narrays
+    rng = np.random.default_rng(300 + spin)
+    alm = [inputs.gaussian_alm(rng, lmax, lmax, lmin=abs(spin)) for _ in range(narr)]
+    maps = [rng.standard_normal(geom.npix) for _ in range(narr)]
+    _, m = inputs.lm_arrays(lmax, lmax)
+    n = oracle.nalm(lmax, lmax)
+    cases = [
+        (sht.SHT_SYNTHESIS, alm, oracle.synthesis(spin, lmax, lmax, alm, rings), True),
+        (sht.SHT_ADJOINT_ANALYSIS, alm, oracle.synthesis(spin, lmax, lmax, alm, rings, weighted=True), True),
+        (sht.SHT_ANALYSIS, maps, oracle.analysis(spin, lmax, lmax, maps, rings), False),
+        (sht.SHT_ADJOINT_SYNTHESIS, maps, oracle.analysis(spin, lmax, lmax, maps, rings, adjoint=True), False),
+    ]
+    for type_, inp, ref, to_map in cases:
+        src = [torch.from_numpy(x).cuda() for x in inp]
+        if to_map:
+            out = [torch.full((geom.npix,), np.nan, dtype=torch.float64, device="cuda") for _ in range(narr)]
+            sht.sht_execute(plan, type_, src, out, flags)
+        else:
+            out = [torch.full((n,), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+                   for _ in range(narr)]
+            sht.sht_execute(plan, type_, out, src, flags)
+        torch.cuda.synchronize()
+        for g, r in zip(out, ref):
+            g = g.cpu().numpy()
+            assert rel_l2(g, r) <= 1e-10, (type_, rel_l2(g, r))
+            if not to_map:  # the FP64 columns to the FP64 tolerance
+                lo = m < 9
+                assert rel_l2(g[lo], r[lo]) <= 1e-12, (type_, rel_l2(g[lo], r[lo]))
+
+
+def test_fp64_columns_in_batch_and_noalloc(sht):
+    lmax = 40
+    geom = sht.sht_geom_gauss(42, 81)
+    rings = rings_of(geom)
+    lay = sht.sht_alm_create(lmax, lmax)
+    mixed = sht.sht_plan_create(geom, lay, 2, 1, sht.SHT_MIXED)
+    mixed.fp64_columns = 6
+    other = sht.sht_plan_create(geom, lay, 0, 1, sht.SHT_FP64)
+    rng = np.random.default_rng(310)
+    alm_m = [inputs.gaussian_alm(rng, lmax, lmax, lmin=2) for _ in range(2)]
+    alm_o = [inputs.gaussian_alm(rng, lmax, lmax)]
+    ref_m = oracle.synthesis(2, lmax, lmax, alm_m, rings)
+    ref_o = oracle.synthesis(0, lmax, lmax, alm_o, rings)
+    batch = sht.sht_batch_create([mixed, other])
+    a_in = [[torch.from_numpy(x).cuda() for x in alm_m], [torch.from_numpy(x).cuda() for x in alm_o]]
+    m_out = [[torch.zeros(geom.npix, dtype=torch.float64, device="cuda") for _ in range(2)],
+             [torch.zeros(geom.npix, dtype=torch.float64, device="cuda")]]
+    sht.sht_batch_execute(batch, sht.SHT_SYNTHESIS, a_in, m_out)
+    torch.cuda.synchronize()
+    for g, r in zip(m_out[0], ref_m):
+        assert rel_l2(g.cpu().numpy(), r) <= 1e-10
+    assert rel_l2(m_out[1][0].cpu().numpy(), ref_o[0]) <= 1e-12
+    with pytest.raises(sht.ShtError):
+        mixed.fp64_columns = 3  # locked while the batch exists
+    del batch
+    # the no-alloc entry point uses both converted a_lm tables for such a plan
+    out = [torch.full((geom.npix,), np.nan, dtype=torch.float64, device="cuda") for _ in range(2)]
+    sht.sht_execute_noalloc(mixed, sht.SHT_SYNTHESIS, a_in[0], out)
+    torch.cuda.synchronize()
+    for g, r in zip(out, ref_m):
+        assert rel_l2(g.cpu().numpy(), r) <= 1e-10
+
+
+def test_default_and_errors(sht):
+    lay = sht.sht_alm_create(8, 8)
+    geom = sht.sht_geom_gauss(10, 17)
+    fp = sht.sht_plan_create(geom, lay, 0, 1, sht.SHT_FP64)
+    with pytest.raises(sht.ShtError):
+        fp.fp64_columns = 2  # FP64 plans have no mixed columns
+    mx = sht.sht_plan_create(geom, lay, 0, 1, sht.SHT_MIXED)
+    with pytest.raises(sht.ShtError):
+        mx.fp64_columns = -1
+    big = sht.sht_plan_create(sht.sht_geom_gauss(4097, 5), sht.sht_alm_create(4095, 2), 0, 1, sht.SHT_MIXED)
+    assert big.fp64_columns == 3  # floor((4095 / 2700)^3)

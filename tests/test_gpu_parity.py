@@ -323,3 +323,12 @@ def test_mixed_config1_round_trip(sht):
     mp = gpu_synthesis(sht, plan, alm, geom.npix)
     back = gpu_analysis(sht, plan, mp, len(alm[0]))[0]
     assert rel_l2(back, alm[0]) < MIX_L2
+
+
+@pytest.mark.parametrize("nlon", [16383, 20011, 20480])
+def test_long_rings(sht, nlon):
+    # rings longer than one CTA's shared memory holds run from a global scratch
+    # slot: 16383 = 3 43 127 (Bluestein at 32768), 20011 prime (Rader over
+    # 20010 = 2 3 5 23 29), 20480 = 2^12 5 (plain mixed radix)
+    check_pair(sht, sht.sht_geom_gauss(30, nlon), 28, 28, 0, seed=nlon, with_adjoint=True)
+    check_pair(sht, sht.sht_geom_gauss(23, nlon), 20, 20, 2, seed=nlon + 1)
