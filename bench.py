@@ -336,6 +336,159 @@ def roofline_for(stages, plan, spin, precision, peaks, steps):
     return out
 
 
+def _line(metric, ms, args, world, config, dtype, extra):
+    line = {"metric": metric, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config, "roofline": None}
+    line.update(extra)
+    return line
+
+
+def _events_ms(torch, stream, fn, steps, warmup, world):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return max_over_ranks(e0.elapsed_time(e1) / steps, world)
+
+
+def run_batch_workload(args, world, rank, local):
+    """64 scalar Gauss-Legendre problems, lmax log-uniform in [64, 2048] (nlat = lmax+1,
+    nlon = 2 lmax+1, seed 3) plus 8 maps at lmax 2047: one batched synthesis + analysis,
+    replayed from a CUDA graph, against the same transforms as 65 per-plan calls."""
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1303_4945_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1303_4945_gb300 import inputs, sht
+
+    stream = torch.cuda.current_stream()
+    rng, lmaxes = inputs.batched_lmax(seed=3)
+    specs = [(int(l), 1) for l in lmaxes] + [(2047, 8)]
+    alms = [[inputs.gaussian_alm(rng, l, l) for _ in range(n)] for l, n in specs]
+    geoms = [sht.sht_geom_gauss(l + 1, 2 * l + 1) for l, _ in specs]
+    forms = {}
+    sampler = ClockSampler(local)
+    for name, prec in (("fp64", sht.SHT_FP64), ("mixed", sht.SHT_MIXED)):
+        plans = [sht.sht_plan_create(g, sht.sht_alm_create(l, l), 0, n, prec) for g, (l, n) in zip(geoms, specs)]
+        for pl in plans:
+            pl.autotune(stream)
+        a_d = [[torch.from_numpy(x).cuda() for x in al] for al in alms]
+        m_d = [[torch.empty(g.npix, dtype=torch.float64, device="cuda") for _ in al] for g, al in zip(geoms, alms)]
+        o_d = [[torch.empty_like(x) for x in al] for al in a_d]
+        batch = sht.sht_batch_create(plans)
+
+        def direct():
+            sht.sht_batch_execute(batch, sht.SHT_SYNTHESIS, a_d, m_d, 0, stream)
+            sht.sht_batch_execute(batch, sht.SHT_ANALYSIS, o_d, m_d, 0, stream)
+
+        direct()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            cs = torch.cuda.current_stream()
+            sht.sht_batch_execute(batch, sht.SHT_SYNTHESIS, a_d, m_d, 0, cs)
+            sht.sht_batch_execute(batch, sht.SHT_ANALYSIS, o_d, m_d, 0, cs)
+
+        def per_plan():
+            for pl, a, m, o in zip(plans, a_d, m_d, o_d):
+                sht.sht_execute(pl, sht.SHT_SYNTHESIS, a, m, 0, stream)
+                sht.sht_execute(pl, sht.SHT_ANALYSIS, o, m, 0, stream)
+
+        if name == "mixed":
+            sampler.start()
+        ms_graph = _events_ms(torch, stream, graph.replay, args.steps, args.warmup, world)
+        if name == "mixed":
+            clocks = sampler.stop()
+        ms_batch = _events_ms(torch, stream, direct, args.steps, args.warmup, world)
+        ms_plans = _events_ms(torch, stream, per_plan, args.steps, args.warmup, world)
+        err = max(float(torch.linalg.norm(o[0] - a[0]) / torch.linalg.norm(a[0])) for a, o in zip(a_d, o_d))
+        # our kernels per batched pair: Legendre synthesis and analysis per group (ncomp class x
+        # tiling), one FFT launch each way, the tile reduction per plan, the a_lm conversion per
+        # plan in the mixed form
+        groups = len({(n, pl.tiling()[0]) for (l, n), pl in zip(specs, plans)})
+        launches = 2 * groups + 2 + len(plans) + (len(plans) if prec == sht.SHT_MIXED else 0)
+        forms[name] = {"ms_graph_batch": ms_graph, "ms_batch": ms_batch, "ms_per_plan_calls": ms_plans,
+                       "gpu_launches_per_step": launches,
+                       "triples": sum(pl.triples(0) for pl in plans), "max_round_trip_rel_l2": err,
+                       "tilings": sorted({pl.tiling()[0] for pl in plans})}
+        del graph, batch, plans
+    config = {"workload": "64 scalar GL problems, lmax log-uniform in [64, 2048] (seed 3), nlat = lmax+1, "
+                          "nlon = 2 lmax+1, plus ncomp 8 at lmax 2047; one batched synthesis + analysis "
+                          "replayed from a CUDA graph", "parallelism": "replicas"}
+    line = _line("ms per batched synth+analysis of 65 uneven problems", forms["mixed"]["ms_graph_batch"], args,
+                 world, config, "f32x2", {"form": "mixed", "forms": forms, "clocks": clocks,
+                                          "gpu_launches": forms["mixed"]["gpu_launches_per_step"] * args.steps})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_grad_workload(args, world, rank, local):
+    """L = ||synthesis(a_lm) - d||^2 at lmax 8191 on Gauss-Legendre 8192 x 16383 (a_lm with
+    C_l = 1/(l+1)^2 from rng(4), then d ~ N(0,1)): forward synthesis + backward through the
+    adjoint-synthesis kernel under torch.autograd, per step."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1303_4945_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1303_4945_gb300 import autograd, inputs, sht
+
+    stream = torch.cuda.current_stream()
+    lmax = 8191
+    geom = sht.sht_geom_gauss(lmax + 1, 2 * lmax + 1)
+    lay = sht.sht_alm_create(lmax, lmax)
+    rng = np.random.default_rng(4)
+    a = torch.from_numpy(inputs.gaussian_alm(rng, lmax, lmax, cl=inputs.cl_inverse_square)).cuda().reshape(1, -1)
+    d = torch.from_numpy(rng.standard_normal(geom.npix)).cuda().reshape(1, -1)
+    forms, grads = {}, {}
+    sampler = ClockSampler(local)
+    for name, prec in (("fp64", sht.SHT_FP64), ("mixed", sht.SHT_MIXED)):
+        plan = sht.sht_plan_create(geom, lay, 0, 1, prec)
+        plan.autotune(stream)
+        x = a.clone().requires_grad_(True)
+
+        def step():
+            x.grad = None
+            ((autograd.synthesis(plan, x) - d) ** 2).sum().backward()
+
+        if name == "mixed":
+            sampler.start()
+        ms = _events_ms(torch, stream, step, args.steps, args.warmup, world)
+        if name == "mixed":
+            clocks = sampler.stop()
+        grads[name] = x.grad.detach().clone()
+        lo = plan.fp64_columns if prec == sht.SHT_MIXED else 0
+        # synthesis: (conversion) Legendre (+FP64 columns) FFT; adjoint: FFT Legendre (+FP64 columns) reduction
+        launches = (2 + (prec == sht.SHT_MIXED) + (lo > 0)) + (3 + (lo > 0))
+        forms[name] = {"ms_per_step": ms, "triples": plan.triples(0), "fp64_columns": lo,
+                       "gpu_launches_per_step": launches}
+        del plan
+        torch.cuda.empty_cache()
+    forms["mixed"]["grad_vs_fp64_rel_l2"] = float(torch.linalg.norm(grads["mixed"] - grads["fp64"])
+                                                  / torch.linalg.norm(grads["fp64"]))
+    config = {"workload": "loss ||synthesis(a_lm) - d||^2 and its gradient through the adjoint-synthesis "
+                          "kernel, GL nlat=8192 nlon=16383, lmax=mmax=8191, spin 0, seeds rng(4)",
+              "parallelism": "replicas"}
+    line = _line("ms per loss+gradient at lmax 8191 (GL 8192x16383)", forms["mixed"]["ms_per_step"], args, world,
+                 config, "f32x2", {"form": "mixed", "forms": forms, "clocks": clocks,
+                                   "gpu_launches": forms["mixed"]["gpu_launches_per_step"] * args.steps})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,11 +498,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--lmax", type=int, default=4095, help="smaller sizes for profiling captures")
+    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad"],
+                    help="spin2: the headline (spin-2 lmax 4095 pair); batch: 64 uneven scalar problems + "
+                         "8 maps at lmax 2047 in one batch; grad: loss + gradient at lmax 8191")
     args = ap.parse_args()
     set_workload(args.lmax)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload != "spin2":
+        (run_batch_workload if args.workload == "batch" else run_grad_workload)(args, world, rank, local)
         return
     import numpy as np
     import torch

@@ -52,6 +52,9 @@ struct sht_batch_s {
   int nfft_items = 0;
   int fft_smem = 0;
   std::vector<void *> allocs;
+  // FP64 groups run beside mixed groups: a side stream forked and joined by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -60,6 +63,9 @@ using sht::set_error;
 
 void free_batch(sht_batch_s *B) {
   for (void *p : B->allocs) cudaFree(p);
+  if (B->side) cudaStreamDestroy(B->side);
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  if (B->ev_join) cudaEventDestroy(B->ev_join);
   delete B;
 }
 
@@ -183,6 +189,11 @@ int build(sht_batch_s *B) {
   auto fv = strip(fi);
   B->nfft_items = (int)fv.size();
   if (e == cudaSuccess) e = upload(B, fv.data(), fv.size(), &B->d_fft_items);
+  int least = 0, greatest = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&B->side, cudaStreamNonBlocking, greatest);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) return set_error(SHT_ERR_CUDA, "batch set-up: %s", cudaGetErrorString(e));
   return SHT_OK;
 }
@@ -225,13 +236,12 @@ extern "C" int sht_batch_create(int nplans, const sht_plan_t *plans, sht_batch_t
 extern "C" void sht_batch_destroy(sht_batch_t B) {
   if (!B) return;
   int cur = -1;
+  const int dev = B->device;
   cudaGetDevice(&cur);
-  if (cur != B->device) cudaSetDevice(B->device);
-  for (void *p : B->allocs) cudaFree(p);
-  B->allocs.clear();
-  if (cur != B->device) cudaSetDevice(cur);
+  if (cur != dev) cudaSetDevice(dev);
   for (auto *P : B->plans) --P->batch_refs;
-  delete B;
+  free_batch(B);
+  if (cur != dev) cudaSetDevice(cur);
 }
 
 extern "C" int sht_batch_size(sht_batch_t B) { return B ? (int)B->plans.size() : 0; }
@@ -275,6 +285,27 @@ extern "C" int sht_batch_execute(sht_batch_t B, int type, double *const *const *
   const int polar = (flags & SHT_NO_POLAR_OPT) ? 0 : 1;
   const int add = (flags & SHT_ADD_OUTPUT) ? 1 : 0;
   cudaError_t e = cudaSuccess;
+  // Legendre stage of every group; FP64 groups beside mixed ones when both exist
+  auto legendre = [&](int stage) -> cudaError_t {
+    bool has[2] = {false, false};
+    for (auto &g : B->groups) has[g.precision == SHT_MIXED ? 1 : 0] = true;
+    auto run = [&](bool mixed_groups, cudaStream_t s) -> cudaError_t {
+      cudaError_t r = cudaSuccess;
+      for (auto &g : B->groups) {
+        if ((g.precision == SHT_MIXED) != mixed_groups || r != cudaSuccess) continue;
+        const int4 *items = stage ? g.d_ana[polar] : g.d_syn[polar];
+        const int ni = stage ? g.nana[polar] : g.nsyn[polar];
+        r = mixed_groups ? launch_leg_mixed_batch(stage, g.spin, g.nj, g.ppt, g.d_args[polar], items, ni, TA, s)
+                         : launch_leg_fp64_batch(stage, g.spin, g.nj, g.ppt, g.d_args[polar], items, ni, TA, s);
+      }
+      return r;
+    };
+    if (has[0] && has[1])
+      return fork_join(
+          st, B->side, B->ev_fork, B->ev_join, [&](cudaStream_t s) { return run(true, s); },
+          [&](cudaStream_t s) { return run(false, s); });
+    return run(has[1], st);
+  };
   if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS) {
     const int weighted = type == SHT_ADJOINT_ANALYSIS;
     for (int k = 0; k < n && e == cudaSuccess; ++k) {
@@ -283,23 +314,13 @@ extern "C" int sht_batch_execute(sht_batch_t B, int type, double *const *const *
       if (e == cudaSuccess && P->precision == SHT_MIXED && P->nsyn_lo[polar])  // its FP64 columns
         e = launch_alm_prepare_fp64(P, A[k], st);
     }
-    for (auto &g : B->groups) {
-      if (e != cudaSuccess) break;
-      e = g.precision == SHT_MIXED
-              ? launch_leg_mixed_batch(0, g.spin, g.nj, g.ppt, g.d_args[polar], g.d_syn[polar], g.nsyn[polar], TA, st)
-              : launch_leg_fp64_batch(0, g.spin, g.nj, g.ppt, g.d_args[polar], g.d_syn[polar], g.nsyn[polar], TA, st);
-    }
+    if (e == cudaSuccess) e = legendre(0);
     if (e == cudaSuccess)
       e = launch_fft_batch(0, B->d_fft_syn[polar][weighted][add], B->d_fft_items, B->nfft_items, B->fft_smem, TM, st);
   } else {
     const int weighted = type == SHT_ANALYSIS;
     e = launch_fft_batch(1, B->d_fft_ana[weighted], B->d_fft_items, B->nfft_items, B->fft_smem, TM, st);
-    for (auto &g : B->groups) {
-      if (e != cudaSuccess) break;
-      e = g.precision == SHT_MIXED
-              ? launch_leg_mixed_batch(1, g.spin, g.nj, g.ppt, g.d_args[polar], g.d_ana[polar], g.nana[polar], TA, st)
-              : launch_leg_fp64_batch(1, g.spin, g.nj, g.ppt, g.d_args[polar], g.d_ana[polar], g.nana[polar], TA, st);
-    }
+    if (e == cudaSuccess) e = legendre(1);
     for (int k = 0; k < n && e == cudaSuccess; ++k) e = launch_ana_reduce(B->plans[k], A[k], polar, add, st);
   }
   if (cur != B->device) cudaSetDevice(cur);

@@ -111,13 +111,23 @@ extern "C" int sht_execute_noalloc(sht_plan_t P, int type, double *const *alm, d
   const int add = (flags & SHT_ADD_OUTPUT) ? 1 : 0;
   cudaError_t e;
   if (synth) {
-    e = mixed ? launch_leg_syn_mixed(P, A, polar, st) : launch_leg_syn_fp64(P, A, polar, st);
-    if (e == cudaSuccess && mixed && P->nsyn_lo[polar]) e = launch_leg_syn_fp64(P, A, polar, st, true);
+    if (mixed && P->nsyn_lo[polar])  // FP64 columns beside the mixed kernel
+      e = fork_join(
+          st, P->side, P->ev_fork, P->ev_join, [&](cudaStream_t s) { return launch_leg_syn_mixed(P, A, polar, s); },
+          [&](cudaStream_t s) { return launch_leg_syn_fp64(P, A, polar, s, true); });
+    else
+      e = mixed ? launch_leg_syn_mixed(P, A, polar, st) : launch_leg_syn_fp64(P, A, polar, st);
     if (e == cudaSuccess) e = launch_fft_syn(P, M, polar, type == SHT_ADJOINT_ANALYSIS, add, st);
   } else {
     e = launch_fft_ana(P, M, type == SHT_ANALYSIS, st);
-    if (e == cudaSuccess) e = mixed ? launch_leg_ana_mixed(P, A, polar, st) : launch_leg_ana_fp64(P, A, polar, st);
-    if (e == cudaSuccess && mixed && P->nana_lo[polar]) e = launch_leg_ana_fp64(P, A, polar, st, true);
+    if (e == cudaSuccess) {
+      if (mixed && P->nana_lo[polar])
+        e = fork_join(
+            st, P->side, P->ev_fork, P->ev_join, [&](cudaStream_t s) { return launch_leg_ana_mixed(P, A, polar, s); },
+            [&](cudaStream_t s) { return launch_leg_ana_fp64(P, A, polar, s, true); });
+      else
+        e = mixed ? launch_leg_ana_mixed(P, A, polar, st) : launch_leg_ana_fp64(P, A, polar, st);
+    }
     if (e == cudaSuccess) e = launch_ana_reduce(P, A, polar, add, st);
   }
   P->d_phase = phase0;

@@ -601,6 +601,9 @@ static void free_plan(sht_plan_s *P) {
     if (P->d_ana_lo[k]) cudaFree(P->d_ana_lo[k]);
   }
   for (void *p : P->fft_allocs) cudaFree(p);
+  if (P->side) cudaStreamDestroy(P->side);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
   for (auto &r : P->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -633,19 +636,24 @@ static std::vector<int> ana_ppt_candidates(int spin, int nj) {
 // Analysis work lists for tiles of kAnaThreads * ppt ring pairs: per polar
 // variant the cost-sorted (m, tile) items, each m's offset into the tile-sum
 // array and its first tile; sizes the tile-sum array for this tiling.
-// Mixed form: columns m below this run in FP64.  The double-float recursion keeps
-// ~48 bits of A_l x; near the poles the Legendre functions of small m respond to
-// an error d in x like l^2 d, and the measured error of a column grows like
-// lmax^2.4 (m+1)^-0.85 (white-noise inputs, against the FP64 form and the oracle).
-// (lmax / 2700)^3 keeps every column near or below 1e-10: 3 columns at lmax 4095,
-// 28 at 8191, none below lmax 2700.
+// Mixed form: columns m below this run in FP64 on the rings near the poles.  The
+// double-float recursion keeps ~48 bits; for small m near the poles it is
+// non-oscillatory over l < ~1/theta, where its per-step rounding grows like a
+// power of l, and the measured error of a column grows like lmax^2.4 (m+1)^-0.85
+// (white-noise inputs, against the FP64 form and the oracle).  (lmax / 2700)^3
+// keeps every column near or below 1e-10: 3 columns at lmax 4095, 28 at 8191,
+// none below lmax 2700.
 static int default_fp64_columns(int lmax) {
   const double r = lmax / 2700.0;
   return (int)std::floor(r * r * r);
 }
 
-static bool lo_column(const sht_plan_s *P, int mi) {
-  return P->precision == SHT_MIXED && P->mval[mi] < P->fp64_m_below;
+// an item of column mi over ring pairs [p0, p1) runs in FP64 (mixed plans only)
+static bool lo_item(const sht_plan_s *P, int mi, int p0, int p1) {
+  if (P->precision != SHT_MIXED || P->mval[mi] >= P->fp64_m_below) return false;
+  for (int p = p0; p < p1 && p < P->npairs; ++p)
+    if (P->pair_pole[p] < kFp64PolarCap) return true;
+  return false;
 }
 
 template <class T>
@@ -679,9 +687,9 @@ static int build_syn_lists(sht_plan_s *P) {
       trip += (int64_t)(P->npairs - fp) * nl;
       int sf = (fp / kSynTile) * kSynTile;
       sfirst[i] = sf;
-      auto &dst = lo_column(P, i) ? lo : syn;
       for (int p = sf; p < P->npairs; p += kSynTile)
-        dst.push_back({(int64_t)nl * std::min(kSynTile, P->npairs - p), make_int2(i, p)});
+        (lo_item(P, i, p, p + kSynTile) ? lo : syn)
+            .push_back({(int64_t)nl * std::min(kSynTile, P->npairs - p), make_int2(i, p)});
     }
     P->triples[polar] = trip;
     std::stable_sort(syn.begin(), syn.end(), [](auto &a, auto &b) { return a.first > b.first; });
@@ -720,9 +728,9 @@ static int build_ana_lists(sht_plan_s *P, int ppt) {
       int fp = polar ? P->first_pair[i] : 0;
       int tf = fp / TA;
       t0[i] = tf;
-      auto &dst = lo_column(P, i) ? lo : ana;
       for (int t = tf; t < tiles; ++t)
-        dst.push_back({(int64_t)nl * std::min(TA, P->npairs - t * TA), make_int4(i, t, 0, 0)});
+        (lo_item(P, i, t * TA, (t + 1) * TA) ? lo : ana)
+            .push_back({(int64_t)nl * std::min(TA, P->npairs - t * TA), make_int4(i, t, 0, 0)});
       off += (int64_t)(tiles - tf) * nl * V;
     }
     std::stable_sort(ana.begin(), ana.end(), [](auto &a, auto &b) { return a.first > b.first; });
@@ -759,8 +767,10 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   P->nrings = g->nrings;
   std::vector<PairDev> pd(P->npairs);
   std::vector<int2> pr(P->npairs);
+  P->pair_pole.resize(P->npairs);
   for (int p = 0; p < P->npairs; ++p) {
     double th = g->theta[P->pair_n[p]];
+    P->pair_pole[p] = std::min(th, (double)kPiL - th);
     long double t = th;
     PairDev &d = pd[p];
     d.x = cos(th);
@@ -841,6 +851,15 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
 
   // ---- work lists ----
   P->fp64_m_below = P->precision == SHT_MIXED ? default_fp64_columns(P->lmax) : 0;
+  if (P->precision == SHT_MIXED) {
+    // high priority: the few long FP64 CTAs should start among the first, not
+    // after the thousands of mixed CTAs queued beside them
+    int least = 0, greatest = 0;
+    CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CUDA_TRY(cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, greatest));
+    CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  }
   if ((rc = build_syn_lists(P)) != SHT_OK) return rc;
   if ((rc = build_ana_lists(P, ana_ppt_candidates(P->spin, P->njobs_pad)[0])) != SHT_OK) return rc;
 
@@ -1129,16 +1148,20 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
   if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS) {
     stage(0, [&] {
       if (!mixed) return launch_leg_syn_fp64(P, A, polar, st);
-      cudaError_t r = launch_leg_syn_mixed(P, A, polar, st);
-      return (r == cudaSuccess && P->nsyn_lo[polar]) ? launch_leg_syn_fp64(P, A, polar, st, true) : r;
+      if (!P->nsyn_lo[polar]) return launch_leg_syn_mixed(P, A, polar, st);
+      return fork_join(
+          st, P->side, P->ev_fork, P->ev_join, [&](cudaStream_t s) { return launch_leg_syn_mixed(P, A, polar, s); },
+          [&](cudaStream_t s) { return launch_leg_syn_fp64(P, A, polar, s, true); });
     });
     stage(1, [&] { return launch_fft_syn(P, M, polar, type == SHT_ADJOINT_ANALYSIS, add, st); });
   } else {
     stage(2, [&] { return launch_fft_ana(P, M, type == SHT_ANALYSIS, st); });
     stage(3, [&] {
       if (!mixed) return launch_leg_ana_fp64(P, A, polar, st);
-      cudaError_t r = launch_leg_ana_mixed(P, A, polar, st);
-      return (r == cudaSuccess && P->nana_lo[polar]) ? launch_leg_ana_fp64(P, A, polar, st, true) : r;
+      if (!P->nana_lo[polar]) return launch_leg_ana_mixed(P, A, polar, st);
+      return fork_join(
+          st, P->side, P->ev_fork, P->ev_join, [&](cudaStream_t s) { return launch_leg_ana_mixed(P, A, polar, s); },
+          [&](cudaStream_t s) { return launch_leg_ana_fp64(P, A, polar, s, true); });
     });
     stage(4, [&] { return launch_ana_reduce(P, A, polar, add, st); });
   }

@@ -28,6 +28,7 @@ constexpr int kFftThreads = 512;
 // longest in-place transform: the ring buffer (16 bytes a point) must fit the
 // opt-in shared memory of one CTA (227 KB on sm_103a)
 constexpr int kFftMaxLen = 14336;
+constexpr double kFp64PolarCap = 0.05;  // rad; see sht_plan_s::fp64_m_below
 // longest transform at all: longer rings run from a global scratch slot per CTA
 // (1 MiB each), which stays in L2
 constexpr int kFftMaxGlobalLen = 65536;
@@ -114,6 +115,7 @@ struct sht_plan_s {
   std::vector<int> mval;
   std::vector<int64_t> mstart;
   std::vector<int> pair_n, pair_s;         // ring index of the north / south slot (-1 none)
+  std::vector<double> pair_pole;           // per pair: distance of its rings from the nearer pole (rad)
   std::vector<int> first_pair;             // per m: first pair not removed by the polar cut
   std::vector<int64_t> coef_off;           // per m: table index of l = l0
   int64_t ncoef = 0;
@@ -148,9 +150,14 @@ struct sht_plan_s {
   // host copies of the work lists with their costs (l count x pairs), for merging into batches
   std::vector<std::pair<int64_t, int2>> syn_list[2];
   std::vector<std::pair<int64_t, int4>> ana_list[2];
-  // mixed form: the columns m < fp64_m_below run in the FP64 kernels (their own work lists);
-  // near the poles the recursion at small m amplifies the rounding of A x by ~l^2
+  // mixed form: the work items of columns m < fp64_m_below that touch a ring within
+  // kFp64PolarCap of a pole run in the FP64 kernels (work lists of their own): there
+  // the small-m recursion is non-oscillatory for l < ~1/theta and amplifies its
+  // per-step rounding by a power of l
   int fp64_m_below = 0;
+  // the FP64 columns run beside the mixed kernels: a side stream forked and joined by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int2 *d_syn_lo[2] = {nullptr, nullptr};
   int nsyn_lo[2] = {0, 0};
   int4 *d_ana_lo[2] = {nullptr, nullptr};
@@ -185,6 +192,25 @@ struct sht_plan_s {
 // Cross-TU launch helpers (all return cudaError_t of the launch).
 // ----------------------------------------------------------------------------
 namespace sht {
+// Runs side_fn on stream `side` concurrently with main_fn on `st`: `side` waits for
+// the work queued on `st` so far, side_fn is launched first (its CTAs are the
+// long ones), and `st` waits for it before anything queued later.  The pattern
+// is capturable in a CUDA graph.
+template <class MainFn, class SideFn>
+inline cudaError_t fork_join(cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
+                             MainFn &&main_fn, SideFn &&side_fn) {
+  cudaError_t e = cudaEventRecord(fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+  if (e != cudaSuccess) return e;
+  cudaError_t es = side_fn(side);
+  e = cudaEventRecord(join, side);
+  cudaError_t em = main_fn(st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
+  if (es != cudaSuccess) return es;
+  if (em != cudaSuccess) return em;
+  return e;
+}
+
 // records a message for sht_last_error() on this thread and returns code
 int set_error(int code, const char *fmt, ...);
 // plan-time tables
