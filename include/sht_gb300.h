@@ -214,17 +214,18 @@ SHT_API int sht_plan_autotune(sht_plan_t plan, void *cuda_stream, float *ms_per_
 /* ---- FP64 columns of the mixed form --------------------------------------------
  * The paper computes in double precision throughout; the mixed form (not in the
  * paper) runs the recursion and sums in pairs of FP32 numbers, ~48 significant
- * bits.  Near the poles the Legendre functions of small m respond to an error d
- * in the recursion's A_l cos(theta) like l^2 d, so those columns lose accuracy
- * first as lmax grows.  A mixed plan therefore runs the columns m < m_below in
- * the FP64 kernels (same results as an FP64 plan for those columns, ~5x their
- * cost).  The default is floor((lmax / 2700)^3): 0 below lmax 2700, 3 at lmax
- * 4095, 28 at 8191, which keeps every column's relative error near or below
- * 1e-10 on white-noise inputs.  sht_plan_set_fp64_columns changes it (any
- * m_below >= 0; it rebuilds the work lists and may allocate a P/M table of
- * ncoef x arrays x 16 bytes); sht_plan_get_fp64_columns reads it.  Errors:
- * SHT_ERR_INVALID_ARG (NULL, an FP64 plan, a plan in a batch, m_below < 0),
- * SHT_ERR_OOM, SHT_ERR_CUDA.
+ * bits.  For small m, on rings near the poles, the recursion is non-oscillatory
+ * over l < ~1/theta and amplifies its per-step rounding by a power of l, so those
+ * values lose accuracy first as lmax grows.  A mixed plan therefore runs the work
+ * items of the columns m < m_below that touch a ring within 0.05 rad of a pole in
+ * the FP64 kernels (same results as an FP64 plan there), on a high-priority side
+ * stream beside the mixed kernels.  The default is floor((lmax / 2700)^3): 0
+ * below lmax 2700, 3 at lmax 4095, 28 at 8191 (white-noise adjoint synthesis at
+ * lmax 8191: 1.3e-11 relative to the FP64 form).  sht_plan_set_fp64_columns
+ * changes it (any m_below >= 0; it rebuilds the work lists and may allocate a
+ * P/M table of ncoef x arrays x 16 bytes); sht_plan_get_fp64_columns reads it.
+ * Errors: SHT_ERR_INVALID_ARG (NULL, an FP64 plan, a plan in a batch,
+ * m_below < 0), SHT_ERR_OOM, SHT_ERR_CUDA.
  */
 SHT_API int sht_plan_set_fp64_columns(sht_plan_t plan, int m_below);
 SHT_API int sht_plan_get_fp64_columns(sht_plan_t plan, int *m_below);
