@@ -307,10 +307,12 @@ def roofline_for(stages, plan, spin, precision, peaks, steps):
     against the FP32 pipe's issue rate (152 SMs x 128 lanes x clock); the same
     work as FMA-counted flops and the FP64-equivalent rate are given beside it.
     """
-    syn_ms, syn_n = stages["legendre_synthesis"]
-    ana_ms, ana_n = stages["legendre_analysis"]
-    name, t_ms, n = ("legendre_synthesis", syn_ms, syn_n) if syn_ms >= ana_ms else ("legendre_analysis", ana_ms, ana_n)
-    per_launch_ms = t_ms / max(n, 1)
+    # per transform: the stage's launches (one per ring-pair range, plus the a_lm
+    # conversion in the synthesis stage) summed, divided by the timed steps
+    syn_ms, _ = stages["legendre_synthesis"]
+    ana_ms, _ = stages["legendre_analysis"]
+    name, t_ms = ("legendre_synthesis", syn_ms) if syn_ms >= ana_ms else ("legendre_analysis", ana_ms)
+    per_launch_ms = t_ms / max(steps, 1)
     triples = plan.triples(0)
     clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     fp64_flops = triples * flops_per_triple(spin, 1)

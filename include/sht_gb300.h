@@ -233,15 +233,17 @@ SHT_API int sht_plan_get_fp64_columns(sht_plan_t plan, int *m_below);
 /* ---- measurement ----------------------------------------------------------
  * Sect. 5.2 times whole transforms by wall clock; these two calls report the
  * device time of each kernel stage instead.  While profiling is on,
- * sht_execute records a CUDA event pair on its stream around every kernel it
- * launches (stage 0 Legendre synthesis, 1 FFT synthesis, 2 FFT analysis,
- * 3 Legendre analysis, 4 tile reduction of the analysis).  enable = 1 starts
+ * sht_execute records a CUDA event pair around every kernel it launches, on
+ * the stream that kernel runs on (stage 0 Legendre synthesis with the a_lm
+ * conversion, 1 FFT synthesis, 2 FFT analysis, 3 Legendre analysis, 4 tile
+ * reduction of the analysis, 5 the FP64 items of a mixed plan, which overlap
+ * stage 0 or 3 on a stream of their own).  enable = 1 starts
  * (and clears) the record, 0 stops it.  sht_plan_profile_read waits for the
  * recorded events, then writes for each stage s < SHT_NSTAGES the summed
  * milliseconds ms[s] and the number of launches count[s], and clears the
  * record.  Errors: SHT_ERR_INVALID_ARG, SHT_ERR_CUDA.
  */
-#define SHT_NSTAGES 5
+#define SHT_NSTAGES 6
 SHT_API int sht_plan_profile(sht_plan_t plan, int enable);
 SHT_API int sht_plan_profile_read(sht_plan_t plan, double *ms, int64_t *count);
 

@@ -259,7 +259,8 @@ struct FftArgs {
   DevPtrs map;
   int weighted, add;
   int ptr_off;
-  int nmaps_run;  // maps per side (global-ring kernels walk npairs x nmaps_run items)
+  int nmaps_run;  // maps per side (global-ring kernels walk npairs_run x nmaps_run items)
+  int pair0, npairs_run;  // the ring pairs [pair0, pair0 + npairs_run) one launch transforms
 };
 
 // ---------------------------------------------------------------------------
@@ -335,10 +336,10 @@ __device__ __forceinline__ void fft_syn_kernel_body(Ring ring, const FftArgs &a,
     }
   }
 }
-__global__ void __launch_bounds__(kFftThreads) fft_syn_kernel(FftArgs a) {
-  fft_syn_kernel_body(SharedRing{}, a, a.map.p, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) fft_syn_kernel(FftArgs a) {
+  fft_syn_kernel_body(SharedRing{}, a, a.map.p, a.pair0 + blockIdx.x, blockIdx.y);
 }
-__global__ void __launch_bounds__(kFftThreads) fft_syn_kernel_batch(const FftArgs *__restrict__ args,
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) fft_syn_kernel_batch(const FftArgs *__restrict__ args,
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const FftArgs &a = args[it.w];
@@ -398,10 +399,10 @@ __device__ __forceinline__ void fft_ana_kernel_body(Ring ring, const FftArgs &a,
     g[1] = gs;
   }
 }
-__global__ void __launch_bounds__(kFftThreads) fft_ana_kernel(FftArgs a) {
-  fft_ana_kernel_body(SharedRing{}, a, a.map.p, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) fft_ana_kernel(FftArgs a) {
+  fft_ana_kernel_body(SharedRing{}, a, a.map.p, a.pair0 + blockIdx.x, blockIdx.y);
 }
-__global__ void __launch_bounds__(kFftThreads) fft_ana_kernel_batch(const FftArgs *__restrict__ args,
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) fft_ana_kernel_batch(const FftArgs *__restrict__ args,
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const FftArgs &a = args[it.w];
@@ -413,18 +414,18 @@ __global__ void __launch_bounds__(kFftThreads) fft_ana_kernel_batch(const FftArg
 __global__ void __launch_bounds__(kFftThreads) fft_syn_kernel_global(FftArgs a, double2 *scratch,
                                                                      int slot_len) {
   const GlobalRing ring{scratch + (size_t)blockIdx.x * slot_len};
-  const int n = a.npairs * a.nmaps_run;
+  const int n = a.npairs_run * a.nmaps_run;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    fft_syn_kernel_body(ring, a, a.map.p, it % a.npairs, it / a.npairs);
+    fft_syn_kernel_body(ring, a, a.map.p, a.pair0 + it % a.npairs_run, it / a.npairs_run);
     __syncthreads();  // the slot is rewritten by the next item
   }
 }
 __global__ void __launch_bounds__(kFftThreads) fft_ana_kernel_global(FftArgs a, double2 *scratch,
                                                                      int slot_len) {
   const GlobalRing ring{scratch + (size_t)blockIdx.x * slot_len};
-  const int n = a.npairs * a.nmaps_run;
+  const int n = a.npairs_run * a.nmaps_run;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    fft_ana_kernel_body(ring, a, a.map.p, it % a.npairs, it / a.npairs);
+    fft_ana_kernel_body(ring, a, a.map.p, a.pair0 + it % a.npairs_run, it / a.npairs_run);
     __syncthreads();
   }
 }
@@ -447,33 +448,44 @@ static FftArgs make_fft_args(const sht_plan_s *P, const DevPtrs &map, int polar)
   a.add = 0;
   a.ptr_off = 0;
   a.nmaps_run = P->nmaps;
+  a.pair0 = 0;
+  a.npairs_run = P->npairs;
   return a;
 }
 
 cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, int weighted, int add,
-                           cudaStream_t st) {
+                           cudaStream_t st, int p0, int p1) {
+  if (p1 < 0) p1 = P->npairs;
+  if (p1 <= p0) return cudaSuccess;
   FftArgs a = make_fft_args(P, map, polar);
   a.weighted = weighted;
   a.add = add;
+  a.pair0 = p0;
+  a.npairs_run = p1 - p0;
   if (P->d_fft_scratch) {
-    const int g = (int)std::min<int64_t>((int64_t)P->npairs * P->nmaps, P->fft_slots);
+    const int g = (int)std::min<int64_t>((int64_t)a.npairs_run * P->nmaps, P->fft_slots);
     fft_syn_kernel_global<<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
     return cudaGetLastError();
   }
-  dim3 grid(P->npairs, P->nmaps);
+  dim3 grid(a.npairs_run, P->nmaps);
   fft_syn_kernel<<<grid, kFftThreads, P->fft_smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted, cudaStream_t st) {
+cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted, cudaStream_t st, int p0,
+                           int p1) {
+  if (p1 < 0) p1 = P->npairs;
+  if (p1 <= p0) return cudaSuccess;
   FftArgs a = make_fft_args(P, map, 1);
   a.weighted = weighted;
+  a.pair0 = p0;
+  a.npairs_run = p1 - p0;
   if (P->d_fft_scratch) {
-    const int g = (int)std::min<int64_t>((int64_t)P->npairs * P->nmaps, P->fft_slots);
+    const int g = (int)std::min<int64_t>((int64_t)a.npairs_run * P->nmaps, P->fft_slots);
     fft_ana_kernel_global<<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
     return cudaGetLastError();
   }
-  dim3 grid(P->npairs, P->nmaps);
+  dim3 grid(a.npairs_run, P->nmaps);
   fft_ana_kernel<<<grid, kFftThreads, P->fft_smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -762,49 +762,58 @@ static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar, boo
   return a;
 }
 
-cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
-  const int n = lo ? P->nsyn_lo[polar] : P->nsyn_items[polar];
+// Legendre stage over an explicit work list (stage 0: synthesis items int2, 1:
+// analysis items int4); no a_lm conversion (launch_alm_prepare_fp64 does it)
+cudaError_t launch_leg_fp64_items(const sht_plan_s *P, int stage, const DevPtrs &alm, int polar, const void *items,
+                                  int n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  if (P->spin != 0) {
-    dim3 g(P->nm, P->njobs_pad);
-    alm_to_pm<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->astride, P->d_mval, P->d_mstart, P->d_coef_off,
-                                 P->ncoef, alm, P->d_pm64);
-  }
-  LegArgs a = make_args(P, alm, polar, lo);
+  LegArgs a = make_args(P, alm, polar);
   const int nj = P->njobs_pad;
-  if (P->spin == 0) {
-    switch (nj) {
-      case 1: leg_syn_s0<1><<<n, kSynTile, 0, st>>>(a); break;
-      case 2: leg_syn_s0<2><<<n, kSynTile, 0, st>>>(a); break;
-      case 4: leg_syn_s0<4><<<n, kSynTile, 0, st>>>(a); break;
-      case 8: leg_syn_s0<8><<<n, kSynTile, 0, st>>>(a); break;
-      default: leg_syn_s0<16><<<n, kSynTile, 0, st>>>(a); break;
+  if (stage == 0) {
+    a.syn_items = static_cast<const int2 *>(items);
+    if (P->spin == 0) {
+      switch (nj) {
+        case 1: leg_syn_s0<1><<<n, kSynTile, 0, st>>>(a); break;
+        case 2: leg_syn_s0<2><<<n, kSynTile, 0, st>>>(a); break;
+        case 4: leg_syn_s0<4><<<n, kSynTile, 0, st>>>(a); break;
+        case 8: leg_syn_s0<8><<<n, kSynTile, 0, st>>>(a); break;
+        default: leg_syn_s0<16><<<n, kSynTile, 0, st>>>(a); break;
+      }
+    } else {
+      switch (nj) {
+        case 1: leg_syn_spin<1><<<n, kSynTile, 0, st>>>(a); break;
+        case 2: leg_syn_spin<2><<<n, kSynTile, 0, st>>>(a); break;
+        case 4: leg_syn_spin<4><<<n, kSynTile, 0, st>>>(a); break;
+        default: leg_syn_spin<8><<<n, kSynTile, 0, st>>>(a); break;
+      }
     }
   } else {
-    switch (nj) {
-      case 1: leg_syn_spin<1><<<n, kSynTile, 0, st>>>(a); break;
-      case 2: leg_syn_spin<2><<<n, kSynTile, 0, st>>>(a); break;
-      case 4: leg_syn_spin<4><<<n, kSynTile, 0, st>>>(a); break;
-      default: leg_syn_spin<8><<<n, kSynTile, 0, st>>>(a); break;
-    }
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
-  const int n = lo ? P->nana_lo[polar] : P->nana_items[polar];
-  LegArgs a = make_args(P, alm, polar, lo);
-  if (n > 0) {
+    a.ana_items = static_cast<const int4 *>(items);
     if (P->spin == 0)
-      ana_shape_s0(P->njobs_pad, P->ana_ppt, [&](auto sh) {
+      ana_shape_s0(nj, P->ana_ppt, [&](auto sh) {
         leg_ana_s0<decltype(sh)::nj, decltype(sh)::ppt><<<n, kAnaThreads, 0, st>>>(a);
       });
     else
-      ana_shape_spin(P->njobs_pad, P->ana_ppt, [&](auto sh) {
+      ana_shape_spin(nj, P->ana_ppt, [&](auto sh) {
         leg_ana_spin<decltype(sh)::nj, decltype(sh)::ppt><<<n, kAnaThreads, 0, st>>>(a);
       });
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
+  const int n = lo ? P->nsyn_lo[polar] : P->nsyn_items[polar];
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = launch_alm_prepare_fp64(P, alm, st);
+  if (e != cudaSuccess) return e;
+  return launch_leg_fp64_items(P, 0, alm, polar, lo ? (const void *)P->d_syn_lo[polar] : P->d_syn_items[polar], n,
+                               st);
+}
+
+cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
+  const int n = lo ? P->nana_lo[polar] : P->nana_items[polar];
+  return launch_leg_fp64_items(P, 1, alm, polar, lo ? (const void *)P->d_ana_lo[polar] : P->d_ana_items[polar], n,
+                               st);
 }
 
 cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st) {

@@ -767,48 +767,53 @@ static MixArgs make_mix(const sht_plan_s *P, int polar) {
   return a;
 }
 
-cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st) {
-  if (P->nm > 0) {
-    dim3 g(P->nm, P->spin ? P->njobs_pad : P->nmaps_pad);
-    alm_to_f2<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->nmaps_pad, P->astride, P->d_mval, P->d_mstart,
-                                 P->d_coef_off, P->ncoef, alm, P->d_alm32);
-  }
-  const int n = P->nsyn_items[polar];
-  if (n == 0) return cudaGetLastError();
+// Legendre stage over an explicit work list (stage 0: synthesis items int2, 1:
+// analysis items int4); no a_lm conversion (launch_alm_prepare_mixed does it)
+cudaError_t launch_leg_mixed_items(const sht_plan_s *P, int stage, int polar, const void *items, int n,
+                                   cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
   MixArgs a = make_mix(P, polar);
   const int nj = P->njobs_pad;
-  if (P->spin == 0) {
-    switch (nj) {
-      case 1: mix_syn_s0<1><<<n, kSynTile, 0, st>>>(a); break;
-      case 2: mix_syn_s0<2><<<n, kSynTile, 0, st>>>(a); break;
-      case 4: mix_syn_s0<4><<<n, kSynTile, 0, st>>>(a); break;
-      case 8: mix_syn_s0<8><<<n, kSynTile, 0, st>>>(a); break;
-      default: mix_syn_s0<16><<<n, kSynTile, 0, st>>>(a); break;
+  if (stage == 0) {
+    a.syn_items = static_cast<const int2 *>(items);
+    if (P->spin == 0) {
+      switch (nj) {
+        case 1: mix_syn_s0<1><<<n, kSynTile, 0, st>>>(a); break;
+        case 2: mix_syn_s0<2><<<n, kSynTile, 0, st>>>(a); break;
+        case 4: mix_syn_s0<4><<<n, kSynTile, 0, st>>>(a); break;
+        case 8: mix_syn_s0<8><<<n, kSynTile, 0, st>>>(a); break;
+        default: mix_syn_s0<16><<<n, kSynTile, 0, st>>>(a); break;
+      }
+    } else {
+      switch (nj) {
+        case 1: mix_syn_spin<1><<<n, kSynTile, 0, st>>>(a); break;
+        case 2: mix_syn_spin<2><<<n, kSynTile, 0, st>>>(a); break;
+        case 4: mix_syn_spin<4><<<n, kSynTile, 0, st>>>(a); break;
+        default: mix_syn_spin<8><<<n, kSynTile, 0, st>>>(a); break;
+      }
     }
   } else {
-    switch (nj) {
-      case 1: mix_syn_spin<1><<<n, kSynTile, 0, st>>>(a); break;
-      case 2: mix_syn_spin<2><<<n, kSynTile, 0, st>>>(a); break;
-      case 4: mix_syn_spin<4><<<n, kSynTile, 0, st>>>(a); break;
-      default: mix_syn_spin<8><<<n, kSynTile, 0, st>>>(a); break;
-    }
+    a.ana_items = static_cast<const int4 *>(items);
+    if (P->spin == 0)
+      ana_shape_s0(nj, P->ana_ppt, [&](auto sh) {
+        mix_ana<decltype(sh)::nj, decltype(sh)::ppt, false><<<n, kAnaThreads, 0, st>>>(a);
+      });
+    else
+      ana_shape_spin(nj, P->ana_ppt, [&](auto sh) {
+        mix_ana<decltype(sh)::nj, decltype(sh)::ppt, true><<<n, kAnaThreads, 0, st>>>(a);
+      });
   }
   return cudaGetLastError();
 }
 
+cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st) {
+  cudaError_t e = launch_alm_prepare_mixed(P, alm, st);
+  if (e != cudaSuccess) return e;
+  return launch_leg_mixed_items(P, 0, polar, P->d_syn_items[polar], P->nsyn_items[polar], st);
+}
+
 cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &, int polar, cudaStream_t st) {
-  const int n = P->nana_items[polar];
-  if (n == 0) return cudaSuccess;
-  MixArgs a = make_mix(P, polar);
-  if (P->spin == 0)
-    ana_shape_s0(P->njobs_pad, P->ana_ppt, [&](auto sh) {
-      mix_ana<decltype(sh)::nj, decltype(sh)::ppt, false><<<n, kAnaThreads, 0, st>>>(a);
-    });
-  else
-    ana_shape_spin(P->njobs_pad, P->ana_ppt, [&](auto sh) {
-      mix_ana<decltype(sh)::nj, decltype(sh)::ppt, true><<<n, kAnaThreads, 0, st>>>(a);
-    });
-  return cudaGetLastError();
+  return launch_leg_mixed_items(P, 1, polar, P->d_ana_items[polar], P->nana_items[polar], st);
 }
 
 }  // namespace sht

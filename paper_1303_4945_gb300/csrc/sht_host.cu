@@ -604,6 +604,7 @@ static void free_plan(sht_plan_s *P) {
   if (P->side) cudaStreamDestroy(P->side);
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
+  if (P->ev_lo) cudaEventDestroy(P->ev_lo);
   for (auto &r : P->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -857,8 +858,8 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
     int least = 0, greatest = 0;
     CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     CUDA_TRY(cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, greatest));
-    CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
-    CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    for (cudaEvent_t *ev : {&P->ev_fork, &P->ev_join, &P->ev_lo})
+      CUDA_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   }
   if ((rc = build_syn_lists(P)) != SHT_OK) return rc;
   if ((rc = build_ana_lists(P, ana_ppt_candidates(P->spin, P->njobs_pad)[0])) != SHT_OK) return rc;
@@ -1129,41 +1130,68 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
   const int polar = (flags & SHT_NO_POLAR_OPT) ? 0 : 1;
   const int add = (flags & SHT_ADD_OUTPUT) ? 1 : 0;
   cudaError_t e = cudaSuccess;
-  // run one stage, bracketed by an event pair when profiling
-  auto stage = [&](int id, auto &&launch) {
+  // run one stage on stream s, bracketed by an event pair on s when profiling
+  auto stage = [&](int id, cudaStream_t s, auto &&launch) {
     if (e != cudaSuccess) return;
     sht_plan_s::ProfRec r{id, nullptr, nullptr};
     if (P->prof_on) {
       if ((e = cudaEventCreate(&r.a)) != cudaSuccess) return;
       if ((e = cudaEventCreate(&r.b)) != cudaSuccess) return;
-      if ((e = cudaEventRecord(r.a, st)) != cudaSuccess) return;
+      if ((e = cudaEventRecord(r.a, s)) != cudaSuccess) return;
     }
     e = launch();
     if (P->prof_on) {
-      if (e == cudaSuccess) e = cudaEventRecord(r.b, st);
+      if (e == cudaSuccess) e = cudaEventRecord(r.b, s);
       P->prof.push_back(r);
     }
   };
+  auto record = [&](cudaEvent_t ev, cudaStream_t s) {
+    if (e == cudaSuccess) e = cudaEventRecord(ev, s);
+  };
+  auto wait = [&](cudaStream_t s, cudaEvent_t ev) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+  };
   const bool mixed = P->precision == SHT_MIXED;
+  auto leg = [&](int stg, const void *items, int n, cudaStream_t s) {
+    return mixed ? launch_leg_mixed_items(P, stg, polar, items, n, s)
+                 : launch_leg_fp64_items(P, stg, A, polar, items, n, s);
+  };
+  // A mixed plan's FP64 items (small m near the poles) run on the high-priority
+  // side stream beside its mixed Legendre kernel; the ring FFT waits for both.
   if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS) {
-    stage(0, [&] {
-      if (!mixed) return launch_leg_syn_fp64(P, A, polar, st);
-      if (!P->nsyn_lo[polar]) return launch_leg_syn_mixed(P, A, polar, st);
-      return fork_join(
-          st, P->side, P->ev_fork, P->ev_join, [&](cudaStream_t s) { return launch_leg_syn_mixed(P, A, polar, s); },
-          [&](cudaStream_t s) { return launch_leg_syn_fp64(P, A, polar, s, true); });
+    const int weighted = type == SHT_ADJOINT_ANALYSIS;
+    const bool lo = mixed && P->nsyn_lo[polar] > 0;
+    stage(0, st, [&] {
+      cudaError_t r = mixed ? launch_alm_prepare_mixed(P, A, st) : launch_alm_prepare_fp64(P, A, st);
+      if (r == cudaSuccess && lo) r = launch_alm_prepare_fp64(P, A, st);  // the FP64 items read P/M
+      return r;
     });
-    stage(1, [&] { return launch_fft_syn(P, M, polar, type == SHT_ADJOINT_ANALYSIS, add, st); });
+    if (lo) {
+      record(P->ev_fork, st);
+      wait(P->side, P->ev_fork);
+      stage(5, P->side, [&] {
+        return launch_leg_fp64_items(P, 0, A, polar, P->d_syn_lo[polar], P->nsyn_lo[polar], P->side);
+      });
+      record(P->ev_lo, P->side);
+    }
+    stage(0, st, [&] { return leg(0, P->d_syn_items[polar], P->nsyn_items[polar], st); });
+    if (lo) wait(st, P->ev_lo);
+    stage(1, st, [&] { return launch_fft_syn(P, M, polar, weighted, add, st); });
   } else {
-    stage(2, [&] { return launch_fft_ana(P, M, type == SHT_ANALYSIS, st); });
-    stage(3, [&] {
-      if (!mixed) return launch_leg_ana_fp64(P, A, polar, st);
-      if (!P->nana_lo[polar]) return launch_leg_ana_mixed(P, A, polar, st);
-      return fork_join(
-          st, P->side, P->ev_fork, P->ev_join, [&](cudaStream_t s) { return launch_leg_ana_mixed(P, A, polar, s); },
-          [&](cudaStream_t s) { return launch_leg_ana_fp64(P, A, polar, s, true); });
-    });
-    stage(4, [&] { return launch_ana_reduce(P, A, polar, add, st); });
+    const int weighted = type == SHT_ANALYSIS;
+    const bool lo = mixed && P->nana_lo[polar] > 0;
+    stage(2, st, [&] { return launch_fft_ana(P, M, weighted, st); });
+    if (lo) {
+      record(P->ev_fork, st);
+      wait(P->side, P->ev_fork);
+      stage(5, P->side, [&] {
+        return launch_leg_fp64_items(P, 1, A, polar, P->d_ana_lo[polar], P->nana_lo[polar], P->side);
+      });
+      record(P->ev_lo, P->side);
+    }
+    stage(3, st, [&] { return leg(1, P->d_ana_items[polar], P->nana_items[polar], st); });
+    if (lo) wait(st, P->ev_lo);
+    stage(4, st, [&] { return launch_ana_reduce(P, A, polar, add, st); });
   }
   if (cur != P->device) cudaSetDevice(cur);
   if (e != cudaSuccess) return fail(SHT_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));

@@ -25,6 +25,7 @@ constexpr int kSynTile = 128;     // ring pairs per synthesis Legendre CTA (one 
 constexpr int kAnaThreads = 128;  // threads per analysis Legendre CTA
 constexpr int kMaxRadix = 8 * 4;  // generic odd radix limit of the FFT engine (primes <= 31)
 constexpr int kFftThreads = 512;
+constexpr int kFftMinBlocks = 512 / kFftThreads;  // launch bound: at most 128 registers a thread
 // longest in-place transform: the ring buffer (16 bytes a point) must fit the
 // opt-in shared memory of one CTA (227 KB on sm_103a)
 constexpr int kFftMaxLen = 14336;
@@ -158,6 +159,8 @@ struct sht_plan_s {
   // the FP64 columns run beside the mixed kernels: a side stream forked and joined by events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
+  cudaEvent_t ev_lo = nullptr;
   int2 *d_syn_lo[2] = {nullptr, nullptr};
   int nsyn_lo[2] = {0, 0};
   int4 *d_ana_lo[2] = {nullptr, nullptr};
@@ -226,11 +229,18 @@ cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int pol
                                 bool lo = false);
 cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st);
 cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
+// the Legendre stage over an explicit work list (stage 0 synthesis, 1 analysis), no a_lm conversion
+cudaError_t launch_leg_fp64_items(const sht_plan_s *P, int stage, const DevPtrs &alm, int polar, const void *items,
+                                  int n, cudaStream_t st);
+cudaError_t launch_leg_mixed_items(const sht_plan_s *P, int stage, int polar, const void *items, int n,
+                                   cudaStream_t st);
 cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
 // ring FFTs
+// ring pairs [p0, p1) (p1 < 0: to the last pair)
 cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, int weighted, int add,
-                           cudaStream_t st);
-cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted, cudaStream_t st);
+                           cudaStream_t st, int p0 = 0, int p1 = -1);
+cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted, cudaStream_t st, int p0 = 0,
+                           int p1 = -1);
 // lets every FFT kernel use the device's opt-in shared memory (once per device, at plan time:
 // the limit is one value per kernel and process, so it is only ever raised, never per call)
 cudaError_t fft_prepare_device(int device);

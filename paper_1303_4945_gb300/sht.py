@@ -30,8 +30,9 @@ SHT_ECP_FEJER1, SHT_ECP_FEJER2, SHT_ECP_CC = 0, 1, 2
 SHT_FP64, SHT_MIXED = 0, 1
 SHT_SYNTHESIS, SHT_ANALYSIS, SHT_ADJOINT_SYNTHESIS, SHT_ADJOINT_ANALYSIS = 0, 1, 2, 3
 SHT_ADD_OUTPUT, SHT_NO_POLAR_OPT = 1, 2
-SHT_NSTAGES = 5
-STAGE_NAMES = ("legendre_synthesis", "fft_synthesis", "fft_analysis", "legendre_analysis", "analysis_reduce")
+SHT_NSTAGES = 6
+STAGE_NAMES = ("legendre_synthesis", "fft_synthesis", "fft_analysis", "legendre_analysis", "analysis_reduce",
+               "fp64_polar_items")
 
 LIB_PATH = _build.LIB
 HEADER = os.path.join(_build.ROOT, "include", "sht_gb300.h")
