@@ -220,7 +220,7 @@ SHT_API int sht_plan_autotune(sht_plan_t plan, void *cuda_stream, float *ms_per_
  * items of the columns m < m_below that touch a ring within 0.05 rad of a pole in
  * the FP64 kernels (same results as an FP64 plan there), on a high-priority side
  * stream beside the mixed kernels.  The default is floor((lmax / 2700)^3): 0
- * below lmax 2700, 3 at lmax 4095, 28 at 8191 (white-noise adjoint synthesis at
+ * below lmax 2700, 3 at lmax 4095, 27 at 8191 (white-noise adjoint synthesis at
  * lmax 8191: 1.3e-11 relative to the FP64 form).  sht_plan_set_fp64_columns
  * changes it (any m_below >= 0; it rebuilds the work lists and may allocate a
  * P/M table of ncoef x arrays x 16 bytes); sht_plan_get_fp64_columns reads it.

@@ -642,7 +642,7 @@ static std::vector<int> ana_ppt_candidates(int spin, int nj) {
 // non-oscillatory over l < ~1/theta, where its per-step rounding grows like a
 // power of l, and the measured error of a column grows like lmax^2.4 (m+1)^-0.85
 // (white-noise inputs, against the FP64 form and the oracle).  (lmax / 2700)^3
-// keeps every column near or below 1e-10: 3 columns at lmax 4095, 28 at 8191,
+// keeps every column near or below 1e-10: 3 columns at lmax 4095, 27 at 8191,
 // none below lmax 2700.
 static int default_fp64_columns(int lmax) {
   const double r = lmax / 2700.0;
