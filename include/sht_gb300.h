@@ -74,6 +74,11 @@ extern "C" {
 #define SHT_ANALYSIS 1          /* map -> a_lm, Eq. ana_used (with the ring weights) */
 #define SHT_ADJOINT_SYNTHESIS 2 /* map -> a_lm, Y^T p: analysis with all weights 1 (Sect. 4.5) */
 #define SHT_ADJOINT_ANALYSIS 3  /* a_lm -> map, W Y a: synthesis times the ring weights (Sect. 4.5) */
+/* spin-0 a_lm -> the two maps df/dtheta and df/(sin(theta) dphi) (Sect. 4.3); plans of spin 1:
+ * the spin-1 synthesis of E = sqrt(l(l+1)) a_lm, B = 0 (with the E/B convention of reading R5,
+ * Q + iU = -sum E_lm 1Y_lm = (d/dtheta + i/sin(theta) d/dphi) f).  alm[] holds ncomp arrays,
+ * map[] 2 ncomp (derivative in theta, then in phi, per component). */
+#define SHT_DERIV_SYNTHESIS 4
 
 #define SHT_ADD_OUTPUT 1   /* add the result to the output arrays instead of overwriting them */
 #define SHT_NO_POLAR_OPT 2 /* evaluate every (m, ring) term, skipping none (Sect. 3.3) */
@@ -165,8 +170,9 @@ SHT_API int sht_plan_create(sht_geom_t geom, sht_alm_t alm, int spin, int ncomp,
 /*
  * Run one transform of the planned kind on stream cuda_stream (a cudaStream_t,
  * NULL = legacy default stream).  type is one of SHT_SYNTHESIS, SHT_ANALYSIS,
- * SHT_ADJOINT_SYNTHESIS, SHT_ADJOINT_ANALYSIS; alm[] / map[] hold ncomp
- * (spin 0) or 2 ncomp (spin != 0) device pointers.  Inputs are read, outputs
+ * SHT_ADJOINT_SYNTHESIS, SHT_ADJOINT_ANALYSIS, or SHT_DERIV_SYNTHESIS (spin-1
+ * plans only: ncomp spin-0 a_lm arrays in, 2 ncomp maps out); alm[] / map[]
+ * hold ncomp (spin 0) or 2 ncomp (spin != 0) device pointers.  Inputs are read, outputs
  * overwritten (or accumulated with SHT_ADD_OUTPUT); pixels and a_lm entries
  * outside the geometry / layout are not touched.  Asynchronous: returns after
  * the launches are queued.  Calls that share a plan must not overlap (they use

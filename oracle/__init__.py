@@ -196,6 +196,24 @@ def synthesis(spin: int, lmax: int, mmax: int, alm, rings: Rings, rings_sel=None
     return maps
 
 
+def deriv_synthesis(lmax: int, mmax: int, alm, rings: Rings):
+    """Sect. 4.3: maps of df/dtheta and df/(sin(theta) dphi) from spin-0 a_lm.
+
+    Reading: the spin-raising operator gives eth Y_lm = -(d/dtheta + i/sin(theta)
+    d/dphi) Y_lm = sqrt(l(l+1)) 1Y_lm, so with the E/B convention of the spin
+    synthesis (Q + iU = -sum E_lm 1Y_lm) the spin-1 synthesis of
+    E = sqrt(l(l+1)) a_lm, B = 0 returns Q = df/dtheta, U = df/(sin(theta) dphi).
+    Returns [dtheta_0, dphi_0, dtheta_1, dphi_1, ...].
+    """
+    out = []
+    for a in _as_list(alm):
+        a = np.asarray(a, dtype=np.complex128)
+        l = np.concatenate([np.arange(m, lmax + 1) for m in range(mmax + 1)]).astype(np.float64)
+        e = a * np.sqrt(l * (l + 1.0))
+        out += synthesis(1, lmax, mmax, [e, np.zeros_like(e)], rings)
+    return out
+
+
 def analysis(spin: int, lmax: int, mmax: int, maps, rings: Rings, m_sel=None,
              adjoint: bool = False):
     """Eq. ana_used (adjoint=True: all weights 1, i.e. adjoint synthesis).

@@ -715,17 +715,23 @@ __global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp,
 // P = E + iB, M = E - iB for every (m, l) of a spin plan, indexed like the coefficient table
 __global__ void alm_to_pm(int lmax, int spin, int nm, int astride, const int *__restrict__ mval,
                           const int64_t *__restrict__ mstart, const int64_t *__restrict__ coef_off, int64_t ncoef,
-                          DevPtrs alm, double2 *__restrict__ out) {
+                          DevPtrs alm, double2 *__restrict__ out, int deriv) {
   const int mi = blockIdx.x, j = blockIdx.y;
   const int m = mval[mi];
   const int as = spin < 0 ? -spin : spin;
   const int l0 = m > as ? m : as;
-  const double2 *E = reinterpret_cast<const double2 *>(alm.p[2 * j]) + mstart[mi];
-  const double2 *B = reinterpret_cast<const double2 *>(alm.p[2 * j + 1]) + mstart[mi];
+  // deriv (Sect. 4.3): E = sqrt(l(l+1)) a_lm of the spin-0 array j, B = 0
+  const double2 *E = reinterpret_cast<const double2 *>(alm.p[deriv ? j : 2 * j]) + mstart[mi];
+  const double2 *B = reinterpret_cast<const double2 *>(alm.p[deriv ? j : 2 * j + 1]) + mstart[mi];
   double2 *P = out + (int64_t)(2 * j) * ncoef + coef_off[mi] - l0;
   double2 *M = out + (int64_t)(2 * j + 1) * ncoef + coef_off[mi] - l0;
   for (int l = l0 + threadIdx.x; l <= lmax; l += blockDim.x) {
     double2 e = E[(int64_t)l * astride], b = B[(int64_t)l * astride];
+    if (deriv) {
+      const double f = sqrt((double)l * (double)(l + 1));
+      e = make_double2(e.x * f, e.y * f);
+      b = make_double2(0.0, 0.0);
+    }
     if (m == 0) e.y = b.y = 0.0;  // Im of m = 0 coefficients is ignored
     P[l] = make_double2(e.x - b.y, e.y + b.x);
     M[l] = make_double2(e.x + b.y, e.y - b.x);
@@ -841,11 +847,11 @@ void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out, 
   memcpy(out, &a, sizeof(a));
 }
 
-cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st) {
+cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, bool deriv) {
   if (P->spin == 0 || P->nm == 0) return cudaSuccess;
   dim3 g(P->nm, P->njobs_pad);
   alm_to_pm<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->astride, P->d_mval, P->d_mstart, P->d_coef_off,
-                               P->ncoef, alm, P->d_pm64);
+                               P->ncoef, alm, P->d_pm64, deriv ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -177,7 +177,7 @@ __device__ __forceinline__ void start_s(int m, int s, const PairDev &pd, double2
 // ---------------------------------------------------------------------------
 __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, const int *__restrict__ mval,
                           const int64_t *__restrict__ mstart, const int64_t *__restrict__ coef_off, int64_t ncoef,
-                          DevPtrs alm, float4 *__restrict__ out) {
+                          DevPtrs alm, float4 *__restrict__ out, int deriv) {
   const int mi = blockIdx.x;
   const int j = blockIdx.y;
   const int m = mval[mi];
@@ -193,13 +193,19 @@ __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, con
     }
     return;
   }
-  // spin: P = E + iB and M = E - iB of job j (Im of m = 0 coefficients ignored)
-  const double2 *E = reinterpret_cast<const double2 *>(alm.p[2 * j]) + mstart[mi];
-  const double2 *B = reinterpret_cast<const double2 *>(alm.p[2 * j + 1]) + mstart[mi];
+  // spin: P = E + iB and M = E - iB of job j (Im of m = 0 coefficients ignored);
+  // deriv (Sect. 4.3): E = sqrt(l(l+1)) a_lm of the spin-0 array j, B = 0
+  const double2 *E = reinterpret_cast<const double2 *>(alm.p[deriv ? j : 2 * j]) + mstart[mi];
+  const double2 *B = reinterpret_cast<const double2 *>(alm.p[deriv ? j : 2 * j + 1]) + mstart[mi];
   float4 *P = out + (int64_t)(2 * j) * ncoef + coef_off[mi] - l0;
   float4 *M = out + (int64_t)(2 * j + 1) * ncoef + coef_off[mi] - l0;
   for (int l = l0 + threadIdx.x; l <= lmax; l += blockDim.x) {
     double2 e = E[(int64_t)l * astride], b = B[(int64_t)l * astride];
+    if (deriv) {
+      const double f = sqrt((double)l * (double)(l + 1));
+      e = make_double2(e.x * f, e.y * f);
+      b = make_double2(0.0, 0.0);
+    }
     if (m == 0) e.y = b.y = 0.0;
     const f2 pr = f2_of(e.x - b.y), pi = f2_of(e.y + b.x), mr = f2_of(e.x + b.y), mi_ = f2_of(e.y - b.x);
     P[l] = make_float4(pr.h, pr.l, pi.h, pi.l);
@@ -831,11 +837,11 @@ void leg_mixed_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out)
   memcpy(out, &a, sizeof(a));
 }
 
-cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st) {
+cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, bool deriv) {
   if (P->nm == 0) return cudaSuccess;
   dim3 g(P->nm, P->spin ? P->njobs_pad : P->nmaps_pad);
   alm_to_f2<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->nmaps_pad, P->astride, P->d_mval, P->d_mstart,
-                               P->d_coef_off, P->ncoef, alm, P->d_alm32);
+                               P->d_coef_off, P->ncoef, alm, P->d_alm32, deriv ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -1108,21 +1108,24 @@ extern "C" int sht_plan_profile_read(sht_plan_t P, double *ms, int64_t *count) {
 extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *const *map, int flags,
                            void *stream) {
   if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
-  if (type < SHT_SYNTHESIS || type > SHT_ADJOINT_ANALYSIS) return fail(SHT_ERR_INVALID_ARG, "bad type %d", type);
+  if (type < SHT_SYNTHESIS || type > SHT_DERIV_SYNTHESIS) return fail(SHT_ERR_INVALID_ARG, "bad type %d", type);
+  const bool deriv = type == SHT_DERIV_SYNTHESIS;
+  if (deriv && P->spin != 1) return fail(SHT_ERR_INVALID_ARG, "SHT_DERIV_SYNTHESIS needs a plan of spin 1");
   if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT)) return fail(SHT_ERR_INVALID_ARG, "unknown flags");
   if (!alm || !map) return fail(SHT_ERR_INVALID_ARG, "pointer arrays are NULL");
   DevPtrs A, M;
   memset(&A, 0, sizeof(A));
   memset(&M, 0, sizeof(M));
+  const int nin = deriv ? P->ncomp : P->nmaps;  // a_lm arrays read
   for (int j = 0; j < P->nmaps; ++j) {
-    if (!alm[j] || !map[j]) return fail(SHT_ERR_INVALID_ARG, "NULL device pointer at index %d", j);
-    A.p[j] = alm[j];
+    if (!map[j] || (j < nin && !alm[j])) return fail(SHT_ERR_INVALID_ARG, "NULL device pointer at index %d", j);
+    if (j < nin) A.p[j] = alm[j];
     M.p[j] = map[j];
   }
   // padding jobs (kernels run a power-of-two job count) read job 0's input;
   // their results stay in the plan's workspace and are never written out
-  const int per = P->spin ? 2 : 1;
-  for (int j = P->nmaps; j < P->nmaps_pad; ++j) A.p[j] = alm[j % per];
+  const int per = (P->spin && !deriv) ? 2 : 1;
+  for (int j = nin; j < P->nmaps_pad; ++j) A.p[j] = alm[j % per];
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != P->device) CUDA_TRY(cudaSetDevice(P->device));
@@ -1158,12 +1161,12 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
   };
   // A mixed plan's FP64 items (small m near the poles) run on the high-priority
   // side stream beside its mixed Legendre kernel; the ring FFT waits for both.
-  if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS) {
+  if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS || deriv) {
     const int weighted = type == SHT_ADJOINT_ANALYSIS;
     const bool lo = mixed && P->nsyn_lo[polar] > 0;
     stage(0, st, [&] {
-      cudaError_t r = mixed ? launch_alm_prepare_mixed(P, A, st) : launch_alm_prepare_fp64(P, A, st);
-      if (r == cudaSuccess && lo) r = launch_alm_prepare_fp64(P, A, st);  // the FP64 items read P/M
+      cudaError_t r = mixed ? launch_alm_prepare_mixed(P, A, st, deriv) : launch_alm_prepare_fp64(P, A, st, deriv);
+      if (r == cudaSuccess && lo) r = launch_alm_prepare_fp64(P, A, st, deriv);  // the FP64 items read P/M
       return r;
     });
     if (lo) {

@@ -254,8 +254,10 @@ size_t fft_args_size();
 void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out, bool lo = false);
 void leg_mixed_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
 void fft_fill_args(const sht_plan_s *P, int polar, int weighted, int add, int ptr_off, void *out);
-cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st);
-cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st);
+// a_lm -> the P = E+iB / M = E-iB tables (FP64 spin) or double-float tables (mixed); deriv: the
+// first-derivative mode of Sect. 4.3 (spin-1 plan, E = sqrt(l(l+1)) a of ncomp spin-0 arrays, B = 0)
+cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, bool deriv = false);
+cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, bool deriv = false);
 // stage 0: synthesis, 1: analysis
 cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, int ppt, const void *args, const int4 *items,
                                   int n, const PtrTable &tbl, cudaStream_t st);

@@ -29,6 +29,7 @@ SHT_ERR_TIMEOUT = -5
 SHT_ECP_FEJER1, SHT_ECP_FEJER2, SHT_ECP_CC = 0, 1, 2
 SHT_FP64, SHT_MIXED = 0, 1
 SHT_SYNTHESIS, SHT_ANALYSIS, SHT_ADJOINT_SYNTHESIS, SHT_ADJOINT_ANALYSIS = 0, 1, 2, 3
+SHT_DERIV_SYNTHESIS = 4  # spin-1 plans: ncomp spin-0 a_lm -> (df/dtheta, df/(sin theta dphi)) per component
 SHT_ADD_OUTPUT, SHT_NO_POLAR_OPT = 1, 2
 SHT_NSTAGES = 6
 STAGE_NAMES = ("legendre_synthesis", "fft_synthesis", "fft_analysis", "legendre_analysis", "analysis_reduce",
@@ -295,9 +296,10 @@ def _devptr(x):
 def sht_execute(plan: Plan, type_, alm, maps, flags=0, stream=None):
     """alm, maps: sequences of device buffers (torch tensors or addresses)."""
     n = plan.narrays
-    if len(alm) != n or len(maps) != n:
-        raise ValueError(f"expected {n} a_lm and {n} map buffers")
-    ap = (_vp * n)(*[_devptr(a) for a in alm])
+    na = plan.ncomp if type_ == SHT_DERIV_SYNTHESIS else n
+    if len(alm) != na or len(maps) != n:
+        raise ValueError(f"expected {na} a_lm and {n} map buffers")
+    ap = (_vp * na)(*[_devptr(a) for a in alm])
     mp = (_vp * n)(*[_devptr(m) for m in maps])
     st = None if stream is None else _vp(_devptr_stream(stream))
     _check(_lib.sht_execute(plan.handle, type_, ap, mp, flags, st), "sht_execute")

@@ -332,3 +332,30 @@ def test_long_rings(sht, nlon):
     # 20010 = 2 3 5 23 29), 20480 = 2^12 5 (plain mixed radix)
     check_pair(sht, sht.sht_geom_gauss(30, nlon), 28, 28, 0, seed=nlon, with_adjoint=True)
     check_pair(sht, sht.sht_geom_gauss(23, nlon), 20, 20, 2, seed=nlon + 1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_deriv_synthesis(sht, precision):
+    # Sect. 4.3: spin-0 a_lm -> df/dtheta, df/(sin theta dphi) through a spin-1 plan
+    l2, mx = (FP64_L2, FP64_MAX) if precision == 0 else (MIX_L2, MIX_MAX)
+    for geom, lmax, ncomp in ((sht.sht_geom_gauss(42, 81), 40, 1), (sht.sht_geom_healpix(16), 47, 2)):
+        rings = rings_of(geom)
+        plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), 1, ncomp, precision)
+        rng = np.random.default_rng(400 + ncomp)
+        alm = [inputs.gaussian_alm(rng, lmax, lmax) for _ in range(ncomp)]
+        a_d = [torch.from_numpy(a).cuda() for a in alm]
+        out = [torch.full((geom.npix,), np.nan, dtype=torch.float64, device="cuda") for _ in range(2 * ncomp)]
+        sht.sht_execute(plan, sht.SHT_DERIV_SYNTHESIS, a_d, out)
+        base = [torch.from_numpy(rng.standard_normal(geom.npix)).cuda() for _ in range(2 * ncomp)]
+        acc = [b.clone() for b in base]
+        sht.sht_execute(plan, sht.SHT_DERIV_SYNTHESIS, a_d, acc, sht.SHT_ADD_OUTPUT)
+        torch.cuda.synchronize()
+        ref = oracle.deriv_synthesis(lmax, lmax, alm, rings)
+        for g, r, b, c in zip(out, ref, base, acc):
+            g = g.cpu().numpy()
+            assert rel_l2(g, r) <= l2 and rel_max(g, r) <= mx, (rel_l2(g, r), rel_max(g, r))
+            assert rel_l2(c.cpu().numpy() - b.cpu().numpy(), r) <= l2
+    p0 = sht.sht_plan_create(sht.sht_geom_gauss(10, 19), sht.sht_alm_create(8, 8), 0, 1, precision)
+    z = torch.zeros(oracle.nalm(8, 8), dtype=torch.complex128, device="cuda")
+    with pytest.raises(sht.ShtError):
+        sht.sht_execute(p0, sht.SHT_DERIV_SYNTHESIS, [z], [torch.zeros(10 * 19, dtype=torch.float64, device="cuda")])

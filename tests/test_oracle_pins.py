@@ -410,3 +410,31 @@ def test_phase_stage_matches_synthesis():
         ms = np.arange(-lmax, lmax + 1)
         p = (F[y][None, :] * np.exp(2j * PI * np.outer(x, ms) / 19)).sum(1)
         np.testing.assert_allclose(p.real, mp[rings.ofs[y]:rings.ofs[y] + 19], atol=1e-13)
+
+
+def test_deriv_synthesis_matches_finite_differences():
+    # Sect. 4.3: the two derivative maps against 4th-order central differences of
+    # the spin-0 synthesis, in theta (rings moved by +-h, +-2h) and in phi
+    # (phi0 moved); pins the reading E = sqrt(l(l+1)) a, B = 0 and its signs
+    lmax = 12
+    rng = np.random.default_rng(21)
+    a = inputs.gaussian_alm(rng, lmax, lmax)
+    theta = np.array([0.3, 0.9, 1.4, 2.0, 2.7])
+    nphi = np.full(len(theta), 27)
+    phi0 = np.array([0.0, 0.1, 0.2, 0.3, 0.4])
+    w = np.ones(len(theta))
+    base = oracle.Rings(theta, nphi, phi0, w)
+    d_th, d_ph = oracle.deriv_synthesis(lmax, lmax, [a], base)
+    h = 1e-3
+
+    def syn(th, p0):
+        return oracle.synthesis(0, lmax, lmax, [a], oracle.Rings(th, nphi, p0, w))[0]
+
+    fd_th = (-syn(theta + 2 * h, phi0) + 8 * syn(theta + h, phi0) - 8 * syn(theta - h, phi0)
+             + syn(theta - 2 * h, phi0)) / (12 * h)
+    fd_ph = (-syn(theta, phi0 + 2 * h) + 8 * syn(theta, phi0 + h) - 8 * syn(theta, phi0 - h)
+             + syn(theta, phi0 - 2 * h)) / (12 * h)
+    fd_ph /= np.repeat(np.sin(theta), nphi)
+    scale = np.max(np.abs(d_th))
+    assert np.max(np.abs(d_th - fd_th)) < 1e-7 * scale
+    assert np.max(np.abs(d_ph - fd_ph)) < 1e-7 * np.max(np.abs(d_ph))
