@@ -82,6 +82,14 @@ extern "C" {
 
 #define SHT_ADD_OUTPUT 1   /* add the result to the output arrays instead of overwriting them */
 #define SHT_NO_POLAR_OPT 2 /* evaluate every (m, ring) term, skipping none (Sect. 3.3) */
+/* a_lm in real-harmonic storage (Sect. 4.5; the paper defers the definition, this
+ * is the reading taken): for m > 0 the two doubles of a coefficient hold
+ * [a_{l,m}, a_{l,-m}] = sqrt(2) (Re a_lm, -Im a_lm), the coefficients of the
+ * orthonormal real basis sqrt(2) Re Y_lm, sqrt(2) Im Y_lm; m = 0 entries are
+ * unchanged.  Inputs are read and outputs written in that storage; with it the
+ * adjoint synthesis is the exact transpose of the synthesis under the plain dot
+ * product of the stored numbers.  sht_execute and sht_execute_noalloc only. */
+#define SHT_REAL_HARMONICS 4
 
 typedef struct sht_geom_s *sht_geom_t;
 typedef struct sht_alm_s *sht_alm_t;
@@ -109,6 +117,17 @@ SHT_API int sht_geom_general(int nrings, const double *theta, const int *nphi, c
  * ring-major map (ofs = y * nlon), weight = Gauss weight * 2 pi / nlon.
  */
 SHT_API int sht_geom_gauss(int nlat, int nlon, sht_geom_t *out);
+
+/*
+ * Reduced Gauss-Legendre grid (Sect. 4.4.2): the nlat Gauss-Legendre rings of
+ * sht_geom_gauss, each thinned to the smallest 2^a 3^b 5^c >= 2 m_y + 1
+ * pixels, where m_y = min(lmax, s cos(theta) + sqrt((T + lmax sin(theta))^2 -
+ * s^2 sin^2(theta))) solves Eq. eq_polaropt for m (T = max(100, 0.01 lmax), s =
+ * |spin|); weight w_GL 2 pi / Nphi_y, phi0 = 0, rings stored one after another.
+ * Not exact in the mathematical sense, exact to the precision the polar
+ * optimisation keeps.  Errors: SHT_ERR_INVALID_ARG, SHT_ERR_OOM.
+ */
+SHT_API int sht_geom_reduced_gauss(int nlat, int lmax, int spin, sht_geom_t *out);
 
 /*
  * ECP grid (Sect. 4.4.1): kind SHT_ECP_FEJER1 / FEJER2 / CC, nlat rings,

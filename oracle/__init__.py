@@ -196,6 +196,28 @@ def synthesis(spin: int, lmax: int, mmax: int, alm, rings: Rings, rings_sel=None
     return maps
 
 
+def _m_of(lmax: int, mmax: int):
+    return np.concatenate([np.full(lmax - m + 1, m) for m in range(mmax + 1)])
+
+
+def real_to_complex(a, lmax: int, mmax: int):
+    """Real-harmonic storage (Sect. 4.5; reading): for m > 0 the two numbers of a
+    slot are [a_{l,m}, a_{l,-m}] = sqrt2 (Re a_lm, -Im a_lm), the coefficients of
+    the real basis sqrt2 Re Y_lm, sqrt2 Im Y_lm; m = 0 slots are unchanged."""
+    a = np.asarray(a, dtype=np.complex128)
+    m = _m_of(lmax, mmax)
+    c = (a.real - 1j * a.imag) / np.sqrt(2.0)
+    return np.where(m > 0, c, a)
+
+
+def complex_to_real(a, lmax: int, mmax: int):
+    """Inverse of real_to_complex."""
+    a = np.asarray(a, dtype=np.complex128)
+    m = _m_of(lmax, mmax)
+    r = np.sqrt(2.0) * (a.real - 1j * a.imag)
+    return np.where(m > 0, r, a)
+
+
 def deriv_synthesis(lmax: int, mmax: int, alm, rings: Rings):
     """Sect. 4.3: maps of df/dtheta and df/(sin(theta) dphi) from spin-0 a_lm.
 

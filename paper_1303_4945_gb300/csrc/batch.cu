@@ -251,6 +251,8 @@ extern "C" int sht_batch_execute(sht_batch_t B, int type, double *const *const *
   using namespace sht;
   if (!B) return set_error(SHT_ERR_INVALID_ARG, "batch is NULL");
   if (type < SHT_SYNTHESIS || type > SHT_ADJOINT_ANALYSIS) return set_error(SHT_ERR_INVALID_ARG, "bad type %d", type);
+  if (flags & SHT_REAL_HARMONICS)
+    return set_error(SHT_ERR_UNSUPPORTED, "real-harmonic storage is not supported in batches");
   if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT)) return set_error(SHT_ERR_INVALID_ARG, "unknown flags");
   if (!alm || !map) return set_error(SHT_ERR_INVALID_ARG, "pointer arrays are NULL");
   const int n = (int)B->plans.size();

@@ -40,6 +40,7 @@ struct LegArgs {
   double *part;
   int ana_tiles, ppt, add;
   int ptr_off;  // batch: first entry of this plan in the pointer table
+  int real;     // real-harmonic storage of the a_lm (spin-0 synthesis reads them directly)
 };
 
 __device__ __forceinline__ int warp_any(bool b) { return __any_sync(0xffffffffu, b); }
@@ -154,6 +155,11 @@ __device__ __forceinline__ void leg_syn_s0_body(const LegArgs &a, double *const 
     double2 fn = make_double2(acc[0][j][0] + acc[1][j][0], acc[0][j][1] + acc[1][j][1]);
     double2 fs = make_double2(acc[0][j][0] - acc[1][j][0], acc[0][j][1] - acc[1][j][1]);
     if (m == 0) fn.y = fs.y = 0.0;  // Im a_l0 is ignored: the field is real
+    if (a.real && m > 0) {  // stored [a_{l,m}, a_{l,-m}] = sqrt2 (Re a_lm, -Im a_lm): same factors for all l
+      const double r = 0.70710678118654752440;
+      fn = make_double2(fn.x * r, -fn.y * r);
+      fs = make_double2(fs.x * r, -fs.y * r);
+    }
     double2 *o = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
     o[0] = fn;
     o[1] = fs;
@@ -660,6 +666,7 @@ __global__ void __launch_bounds__(kAnaThreads) leg_ana_spin_batch(const LegArgs 
 // spin 0: V = 2 njobs values (re, im per job).
 // spin s: V = 4 njobs values (T1, T2 per job): E = -(T1 + sig T2)/2, B = -(i/2)(sig T2 - T1).
 __global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp, int ana_tiles, int astride, int add,
+                           int real,
                            const int *__restrict__ mval, const int64_t *__restrict__ mstart,
                            const int64_t *__restrict__ part_off, const int *__restrict__ tile0,
                            const double *__restrict__ part, DevPtrs alm) {
@@ -694,7 +701,7 @@ __global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp,
     }
     for (int c = 0; c < nout; ++c) {
       double2 *o = reinterpret_cast<double2 *>(alm.p[nout * j + c]) + idx;
-      double2 r = out[c];
+      double2 r = (real && m > 0) ? complex_to_real(out[c]) : out[c];
       if (add) {
         const double2 old = *o;
         r.x += old.x;
@@ -715,8 +722,9 @@ __global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp,
 // P = E + iB, M = E - iB for every (m, l) of a spin plan, indexed like the coefficient table
 __global__ void alm_to_pm(int lmax, int spin, int nm, int astride, const int *__restrict__ mval,
                           const int64_t *__restrict__ mstart, const int64_t *__restrict__ coef_off, int64_t ncoef,
-                          DevPtrs alm, double2 *__restrict__ out, int deriv) {
+                          DevPtrs alm, double2 *__restrict__ out, int mode) {
   const int mi = blockIdx.x, j = blockIdx.y;
+  const int deriv = mode & kAlmDeriv, real = (mode & kAlmReal) && mval[mi] > 0;
   const int m = mval[mi];
   const int as = spin < 0 ? -spin : spin;
   const int l0 = m > as ? m : as;
@@ -727,6 +735,10 @@ __global__ void alm_to_pm(int lmax, int spin, int nm, int astride, const int *__
   double2 *M = out + (int64_t)(2 * j + 1) * ncoef + coef_off[mi] - l0;
   for (int l = l0 + threadIdx.x; l <= lmax; l += blockDim.x) {
     double2 e = E[(int64_t)l * astride], b = B[(int64_t)l * astride];
+    if (real) {
+      e = real_to_complex(e);
+      b = real_to_complex(b);
+    }
     if (deriv) {
       const double f = sqrt((double)l * (double)(l + 1));
       e = make_double2(e.x * f, e.y * f);
@@ -765,15 +777,17 @@ static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar, boo
   a.ana_tiles = P->ana_tiles;
   a.ppt = P->ana_ppt;
   a.add = 0;
+  a.real = 0;
   return a;
 }
 
 // Legendre stage over an explicit work list (stage 0: synthesis items int2, 1:
 // analysis items int4); no a_lm conversion (launch_alm_prepare_fp64 does it)
 cudaError_t launch_leg_fp64_items(const sht_plan_s *P, int stage, const DevPtrs &alm, int polar, const void *items,
-                                  int n, cudaStream_t st) {
+                                  int n, cudaStream_t st, bool real) {
   if (n == 0) return cudaSuccess;
   LegArgs a = make_args(P, alm, polar);
+  a.real = real ? 1 : 0;
   const int nj = P->njobs_pad;
   if (stage == 0) {
     a.syn_items = static_cast<const int2 *>(items);
@@ -807,13 +821,14 @@ cudaError_t launch_leg_fp64_items(const sht_plan_s *P, int stage, const DevPtrs 
   return cudaGetLastError();
 }
 
-cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
+cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo,
+                                int mode) {
   const int n = lo ? P->nsyn_lo[polar] : P->nsyn_items[polar];
   if (n == 0) return cudaSuccess;
-  cudaError_t e = launch_alm_prepare_fp64(P, alm, st);
+  cudaError_t e = launch_alm_prepare_fp64(P, alm, st, mode);
   if (e != cudaSuccess) return e;
   return launch_leg_fp64_items(P, 0, alm, polar, lo ? (const void *)P->d_syn_lo[polar] : P->d_syn_items[polar], n,
-                               st);
+                               st, (mode & kAlmReal) != 0);
 }
 
 cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
@@ -822,9 +837,11 @@ cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int pol
                                st);
 }
 
-cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st) {
+cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st,
+                              bool real) {
   dim3 grid((P->lmax + 1 + 127) / 128, P->nm);
   ana_reduce<<<grid, 128, 0, st>>>(P->lmax, P->spin, P->nm, P->njobs_pad, P->ncomp, P->ana_tiles, P->astride, add,
+                                   real ? 1 : 0,
                                    P->d_mval, P->d_mstart, P->d_ana_part_off[polar], P->d_ana_tile0[polar],
                                    P->d_part, alm);
   return cudaGetLastError();
@@ -847,11 +864,11 @@ void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out, 
   memcpy(out, &a, sizeof(a));
 }
 
-cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, bool deriv) {
+cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, int mode) {
   if (P->spin == 0 || P->nm == 0) return cudaSuccess;
   dim3 g(P->nm, P->njobs_pad);
   alm_to_pm<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->astride, P->d_mval, P->d_mstart, P->d_coef_off,
-                               P->ncoef, alm, P->d_pm64, deriv ? 1 : 0);
+                               P->ncoef, alm, P->d_pm64, mode);
   return cudaGetLastError();
 }
 

@@ -177,8 +177,9 @@ __device__ __forceinline__ void start_s(int m, int s, const PairDev &pd, double2
 // ---------------------------------------------------------------------------
 __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, const int *__restrict__ mval,
                           const int64_t *__restrict__ mstart, const int64_t *__restrict__ coef_off, int64_t ncoef,
-                          DevPtrs alm, float4 *__restrict__ out, int deriv) {
+                          DevPtrs alm, float4 *__restrict__ out, int mode) {
   const int mi = blockIdx.x;
+  const int deriv = mode & kAlmDeriv, real = (mode & kAlmReal) && mval[mi] > 0;
   const int j = blockIdx.y;
   const int m = mval[mi];
   const int as = spin < 0 ? -spin : spin;
@@ -187,7 +188,8 @@ __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, con
     const double2 *src = reinterpret_cast<const double2 *>(alm.p[j]) + mstart[mi];
     float4 *dst = out + (int64_t)j * ncoef + coef_off[mi] - l0;
     for (int l = l0 + threadIdx.x; l <= lmax; l += blockDim.x) {
-      const double2 v = src[(int64_t)l * astride];
+      double2 v = src[(int64_t)l * astride];
+      if (real) v = real_to_complex(v);
       const f2 re = f2_of(v.x), im = f2_of(v.y);
       dst[l] = make_float4(re.h, re.l, im.h, im.l);
     }
@@ -201,6 +203,10 @@ __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, con
   float4 *M = out + (int64_t)(2 * j + 1) * ncoef + coef_off[mi] - l0;
   for (int l = l0 + threadIdx.x; l <= lmax; l += blockDim.x) {
     double2 e = E[(int64_t)l * astride], b = B[(int64_t)l * astride];
+    if (real) {
+      e = real_to_complex(e);
+      b = real_to_complex(b);
+    }
     if (deriv) {
       const double f = sqrt((double)l * (double)(l + 1));
       e = make_double2(e.x * f, e.y * f);
@@ -812,8 +818,8 @@ cudaError_t launch_leg_mixed_items(const sht_plan_s *P, int stage, int polar, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st) {
-  cudaError_t e = launch_alm_prepare_mixed(P, alm, st);
+cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, int mode) {
+  cudaError_t e = launch_alm_prepare_mixed(P, alm, st, mode);
   if (e != cudaSuccess) return e;
   return launch_leg_mixed_items(P, 0, polar, P->d_syn_items[polar], P->nsyn_items[polar], st);
 }
@@ -837,11 +843,11 @@ void leg_mixed_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out)
   memcpy(out, &a, sizeof(a));
 }
 
-cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, bool deriv) {
+cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, int mode) {
   if (P->nm == 0) return cudaSuccess;
   dim3 g(P->nm, P->spin ? P->njobs_pad : P->nmaps_pad);
   alm_to_f2<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->nmaps_pad, P->astride, P->d_mval, P->d_mstart,
-                               P->d_coef_off, P->ncoef, alm, P->d_alm32, deriv ? 1 : 0);
+                               P->d_coef_off, P->ncoef, alm, P->d_alm32, mode);
   return cudaGetLastError();
 }
 

@@ -46,7 +46,10 @@ extern "C" int sht_execute_noalloc(sht_plan_t P, int type, double *const *alm, d
   using namespace sht;
   if (!P) return set_error(SHT_ERR_INVALID_ARG, "plan is NULL");
   if (type < SHT_SYNTHESIS || type > SHT_ADJOINT_ANALYSIS) return set_error(SHT_ERR_INVALID_ARG, "bad type %d", type);
-  if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT)) return set_error(SHT_ERR_INVALID_ARG, "unknown flags");
+  if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT | SHT_REAL_HARMONICS))
+    return set_error(SHT_ERR_INVALID_ARG, "unknown flags");
+  const bool real = (flags & SHT_REAL_HARMONICS) != 0;
+  const int mode = real ? kAlmReal : 0;
   if (!alm || !map) return set_error(SHT_ERR_INVALID_ARG, "pointer arrays are NULL");
   if (P->device < 0 || P->device >= kMaxDevices) return set_error(SHT_ERR_UNSUPPORTED, "device index too large");
   DevPtrs A, M;
@@ -113,10 +116,10 @@ extern "C" int sht_execute_noalloc(sht_plan_t P, int type, double *const *alm, d
   if (synth) {
     if (mixed && P->nsyn_lo[polar])  // FP64 columns beside the mixed kernel
       e = fork_join(
-          st, P->side, P->ev_fork, P->ev_join, [&](cudaStream_t s) { return launch_leg_syn_mixed(P, A, polar, s); },
-          [&](cudaStream_t s) { return launch_leg_syn_fp64(P, A, polar, s, true); });
+          st, P->side, P->ev_fork, P->ev_join, [&](cudaStream_t s) { return launch_leg_syn_mixed(P, A, polar, s, mode); },
+          [&](cudaStream_t s) { return launch_leg_syn_fp64(P, A, polar, s, true, mode); });
     else
-      e = mixed ? launch_leg_syn_mixed(P, A, polar, st) : launch_leg_syn_fp64(P, A, polar, st);
+      e = mixed ? launch_leg_syn_mixed(P, A, polar, st, mode) : launch_leg_syn_fp64(P, A, polar, st, false, mode);
     if (e == cudaSuccess) e = launch_fft_syn(P, M, polar, type == SHT_ADJOINT_ANALYSIS, add, st);
   } else {
     e = launch_fft_ana(P, M, type == SHT_ANALYSIS, st);
@@ -128,7 +131,7 @@ extern "C" int sht_execute_noalloc(sht_plan_t P, int type, double *const *alm, d
       else
         e = mixed ? launch_leg_ana_mixed(P, A, polar, st) : launch_leg_ana_fp64(P, A, polar, st);
     }
-    if (e == cudaSuccess) e = launch_ana_reduce(P, A, polar, add, st);
+    if (e == cudaSuccess) e = launch_ana_reduce(P, A, polar, add, st, real);
   }
   P->d_phase = phase0;
   P->d_part = part0;

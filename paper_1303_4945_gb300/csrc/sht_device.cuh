@@ -134,4 +134,16 @@ inline void ana_shape_spin(int nj, int ppt, F &&f) {
   }
 }
 
+// Real-harmonic storage (Sect. 4.5; reading): for m > 0 the complex slot of a_lm
+// holds [a_{l,m}, a_{l,-m}] = sqrt2 (Re a_lm, -Im a_lm), the coefficients of the
+// real basis sqrt2 Re Y_lm, sqrt2 Im Y_lm; m = 0 entries are unchanged.
+__device__ __forceinline__ double2 real_to_complex(double2 r) {
+  const double h = 0.70710678118654752440;
+  return make_double2(r.x * h, -r.y * h);
+}
+__device__ __forceinline__ double2 complex_to_real(double2 c) {
+  const double q = 1.41421356237309504880;
+  return make_double2(c.x * q, -c.y * q);
+}
+
 }  // namespace sht

@@ -161,6 +161,44 @@ static int make_regular(const std::vector<double> &th, const std::vector<double>
   return sht_geom_general(n, th.data(), nphi.data(), phi0.data(), ofs.data(), nullptr, w.data(), out);
 }
 
+// smallest n' >= n whose prime factors are 2, 3 and 5
+static int smooth235(int n) {
+  for (int k = std::max(n, 1);; ++k) {
+    int r = k;
+    for (int f : {2, 3, 5})
+      while (r % f == 0) r /= f;
+    if (r == 1) return k;
+  }
+}
+
+// Sect. 4.4.2: Gauss-Legendre rings thinned by the polar optimisation.  Eq.
+// eq_polaropt solved for m: sqrt(m^2 + s^2 - 2 m s cos(theta)) = T + lmax sin(theta)
+// gives m_y = s cos(theta) + sqrt((T + lmax sin(theta))^2 - s^2 sin^2(theta)),
+// T = max(100, 0.01 lmax); ring y gets the smallest 2^a 3^b 5^c >= 2 min(m_y, lmax) + 1
+// pixels and the weight w_GL 2 pi / Nphi_y.
+extern "C" int sht_geom_reduced_gauss(int nlat, int lmax, int spin, sht_geom_t *out) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nlat < 1 || lmax < 0) return fail(SHT_ERR_INVALID_ARG, "nlat >= 1 and lmax >= 0 required");
+  std::vector<double> th, wq;
+  gl_nodes(nlat, th, wq);
+  const double T = std::max(100.0, 0.01 * lmax), s = std::abs(spin);
+  std::vector<int> nphi(nlat);
+  std::vector<double> phi0(nlat, 0.0), w(nlat);
+  std::vector<int64_t> ofs(nlat);
+  int64_t o = 0;
+  for (int i = 0; i < nlat; ++i) {
+    const double c = cos(th[i]), sn = sin(th[i]), r = T + lmax * sn;
+    const double m = s * c + sqrt(std::max(0.0, r * r - s * s * sn * sn));
+    const int mm = (int)std::min<double>(lmax, floor(m));
+    nphi[i] = smooth235(2 * mm + 1);
+    ofs[i] = o;
+    o += nphi[i];
+    w[i] = wq[i] * 2.0 * M_PI / nphi[i];
+  }
+  return sht_geom_general(nlat, th.data(), nphi.data(), phi0.data(), ofs.data(), nullptr, w.data(), out);
+}
+
 extern "C" int sht_geom_gauss(int nlat, int nlon, sht_geom_t *out) {
   if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -1111,7 +1149,9 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
   if (type < SHT_SYNTHESIS || type > SHT_DERIV_SYNTHESIS) return fail(SHT_ERR_INVALID_ARG, "bad type %d", type);
   const bool deriv = type == SHT_DERIV_SYNTHESIS;
   if (deriv && P->spin != 1) return fail(SHT_ERR_INVALID_ARG, "SHT_DERIV_SYNTHESIS needs a plan of spin 1");
-  if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT)) return fail(SHT_ERR_INVALID_ARG, "unknown flags");
+  if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT | SHT_REAL_HARMONICS))
+    return fail(SHT_ERR_INVALID_ARG, "unknown flags");
+  const bool real = (flags & SHT_REAL_HARMONICS) != 0;
   if (!alm || !map) return fail(SHT_ERR_INVALID_ARG, "pointer arrays are NULL");
   DevPtrs A, M;
   memset(&A, 0, sizeof(A));
@@ -1157,23 +1197,24 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
   const bool mixed = P->precision == SHT_MIXED;
   auto leg = [&](int stg, const void *items, int n, cudaStream_t s) {
     return mixed ? launch_leg_mixed_items(P, stg, polar, items, n, s)
-                 : launch_leg_fp64_items(P, stg, A, polar, items, n, s);
+                 : launch_leg_fp64_items(P, stg, A, polar, items, n, s, real);
   };
+  const int mode = (deriv ? kAlmDeriv : 0) | (real ? kAlmReal : 0);
   // A mixed plan's FP64 items (small m near the poles) run on the high-priority
   // side stream beside its mixed Legendre kernel; the ring FFT waits for both.
   if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS || deriv) {
     const int weighted = type == SHT_ADJOINT_ANALYSIS;
     const bool lo = mixed && P->nsyn_lo[polar] > 0;
     stage(0, st, [&] {
-      cudaError_t r = mixed ? launch_alm_prepare_mixed(P, A, st, deriv) : launch_alm_prepare_fp64(P, A, st, deriv);
-      if (r == cudaSuccess && lo) r = launch_alm_prepare_fp64(P, A, st, deriv);  // the FP64 items read P/M
+      cudaError_t r = mixed ? launch_alm_prepare_mixed(P, A, st, mode) : launch_alm_prepare_fp64(P, A, st, mode);
+      if (r == cudaSuccess && lo) r = launch_alm_prepare_fp64(P, A, st, mode);  // the FP64 items read P/M
       return r;
     });
     if (lo) {
       record(P->ev_fork, st);
       wait(P->side, P->ev_fork);
       stage(5, P->side, [&] {
-        return launch_leg_fp64_items(P, 0, A, polar, P->d_syn_lo[polar], P->nsyn_lo[polar], P->side);
+        return launch_leg_fp64_items(P, 0, A, polar, P->d_syn_lo[polar], P->nsyn_lo[polar], P->side, real);
       });
       record(P->ev_lo, P->side);
     }
@@ -1194,7 +1235,7 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
     }
     stage(3, st, [&] { return leg(1, P->d_ana_items[polar], P->nana_items[polar], st); });
     if (lo) wait(st, P->ev_lo);
-    stage(4, st, [&] { return launch_ana_reduce(P, A, polar, add, st); });
+    stage(4, st, [&] { return launch_ana_reduce(P, A, polar, add, st, real); });
   }
   if (cur != P->device) cudaSetDevice(cur);
   if (e != cudaSuccess) return fail(SHT_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));

@@ -195,6 +195,8 @@ struct sht_plan_s {
 // Cross-TU launch helpers (all return cudaError_t of the launch).
 // ----------------------------------------------------------------------------
 namespace sht {
+constexpr int kAlmDeriv = 1, kAlmReal = 2;  // a_lm conversion modes (see launch_alm_prepare_fp64)
+
 // Runs side_fn on stream `side` concurrently with main_fn on `st`: `side` waits for
 // the work queued on `st` so far, side_fn is launched first (its CTAs are the
 // long ones), and `st` waits for it before anything queued later.  The pattern
@@ -224,14 +226,15 @@ cudaError_t launch_fft_spectrum(const FftPlanDev *host_plan, const FftPlanDev *d
 // Legendre stage
 // lo: run the mixed plan's FP64 columns (work lists d_syn_lo / d_ana_lo)
 cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st,
-                                bool lo = false);
+                                bool lo = false, int mode = 0);
 cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st,
                                 bool lo = false);
-cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st);
-cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
+cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st,
+                              bool real = false);
+cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, int mode = 0);
 // the Legendre stage over an explicit work list (stage 0 synthesis, 1 analysis), no a_lm conversion
 cudaError_t launch_leg_fp64_items(const sht_plan_s *P, int stage, const DevPtrs &alm, int polar, const void *items,
-                                  int n, cudaStream_t st);
+                                  int n, cudaStream_t st, bool real = false);
 cudaError_t launch_leg_mixed_items(const sht_plan_s *P, int stage, int polar, const void *items, int n,
                                    cudaStream_t st);
 cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
@@ -254,10 +257,11 @@ size_t fft_args_size();
 void leg_fp64_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out, bool lo = false);
 void leg_mixed_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
 void fft_fill_args(const sht_plan_s *P, int polar, int weighted, int add, int ptr_off, void *out);
-// a_lm -> the P = E+iB / M = E-iB tables (FP64 spin) or double-float tables (mixed); deriv: the
-// first-derivative mode of Sect. 4.3 (spin-1 plan, E = sqrt(l(l+1)) a of ncomp spin-0 arrays, B = 0)
-cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, bool deriv = false);
-cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, bool deriv = false);
+// a_lm -> the P = E+iB / M = E-iB tables (FP64 spin) or double-float tables (mixed); mode bits:
+// kAlmDeriv, the first-derivative mode of Sect. 4.3 (spin-1 plan, E = sqrt(l(l+1)) a of ncomp
+// spin-0 arrays, B = 0); kAlmReal, inputs in real-harmonic storage
+cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, int mode = 0);
+cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, int mode = 0);
 // stage 0: synthesis, 1: analysis
 cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, int ppt, const void *args, const int4 *items,
                                   int n, const PtrTable &tbl, cudaStream_t st);

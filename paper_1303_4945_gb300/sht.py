@@ -30,7 +30,7 @@ SHT_ECP_FEJER1, SHT_ECP_FEJER2, SHT_ECP_CC = 0, 1, 2
 SHT_FP64, SHT_MIXED = 0, 1
 SHT_SYNTHESIS, SHT_ANALYSIS, SHT_ADJOINT_SYNTHESIS, SHT_ADJOINT_ANALYSIS = 0, 1, 2, 3
 SHT_DERIV_SYNTHESIS = 4  # spin-1 plans: ncomp spin-0 a_lm -> (df/dtheta, df/(sin theta dphi)) per component
-SHT_ADD_OUTPUT, SHT_NO_POLAR_OPT = 1, 2
+SHT_ADD_OUTPUT, SHT_NO_POLAR_OPT, SHT_REAL_HARMONICS = 1, 2, 4
 SHT_NSTAGES = 6
 STAGE_NAMES = ("legendre_synthesis", "fft_synthesis", "fft_analysis", "legendre_analysis", "analysis_reduce",
                "fp64_polar_items")
@@ -49,6 +49,7 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 _sig = {
     "sht_geom_general": [ctypes.c_int, _dp, _ip, _dp, _i64p, _ip, _dp, ctypes.POINTER(_vp)],
     "sht_geom_gauss": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
+    "sht_geom_reduced_gauss": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
     "sht_geom_ecp": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
     "sht_geom_healpix": [ctypes.c_int, ctypes.POINTER(_vp)],
     "sht_geom_subset": [_vp, ctypes.c_int, _ip, ctypes.POINTER(_vp)],
@@ -247,6 +248,12 @@ def sht_geom_general(theta, nphi, phi0, ofs, stride=None, weight=None) -> Geomet
 def sht_geom_gauss(nlat, nlon) -> Geometry:
     h = _vp()
     _check(_lib.sht_geom_gauss(nlat, nlon, ctypes.byref(h)), "sht_geom_gauss")
+    return Geometry(h.value)
+
+
+def sht_geom_reduced_gauss(nlat, lmax, spin=0) -> Geometry:
+    h = _vp()
+    _check(_lib.sht_geom_reduced_gauss(nlat, lmax, spin, ctypes.byref(h)), "sht_geom_reduced_gauss")
     return Geometry(h.value)
 
 

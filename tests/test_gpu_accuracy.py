@@ -5,9 +5,9 @@ for m = 0) go through synthesis onto a reduced Gauss-Legendre grid and back
 through analysis; the rms and maximum errors of the round trip must stay near
 double precision (the paper reports rms growing roughly linearly and the
 maximum roughly as lmax^(3/2), both close to the IEEE limit).  The reduced
-grid gives ring y the smallest 2^a 3^b 5^c length >= 2 m_y + 1, with m_y the
-largest m the polar optimisation (Sect. 3.3) keeps on that ring; the per-pixel
-weight is the Gauss-Legendre weight times 2 pi / Nphi_y.
+grid is the library's reduced Gauss-Legendre geometry (Sect. 4.4.2): ring y has
+the smallest 2^a 3^b 5^c length >= 2 m_y + 1, with m_y the largest m the polar
+optimisation (Sect. 3.3) keeps on that ring.
 """
 import math
 
@@ -31,32 +31,9 @@ def sht():
     return m
 
 
-def smooth_at_least(n):
-    best = None
-    p2 = 1
-    while p2 < 4 * n:
-        p3 = p2
-        while p3 < 4 * n:
-            p5 = p3
-            while p5 < 4 * n:
-                if p5 >= n and (best is None or p5 < best):
-                    best = p5
-                p5 *= 5
-            p3 *= 3
-        p2 *= 2
-    return best
-
-
 def reduced_gl(sht, lmax):
-    nlat, nlon = lmax + 1, 2 * lmax + 1
-    full = sht.sht_geom_gauss(nlat, nlon).rings()
-    T = max(100.0, 0.01 * lmax)
-    theta = full["theta"]
-    mmax_y = np.minimum(lmax, np.floor(lmax * np.sin(theta) + T)).astype(int)
-    nphi = np.array([smooth_at_least(2 * m + 1) for m in mmax_y])
-    weight = full["weight"] * nlon / nphi  # GL weight x 2 pi / Nphi_y
-    ofs = np.concatenate([[0], np.cumsum(nphi[:-1])]).astype(np.int64)
-    return sht.sht_geom_general(theta, nphi, np.zeros(nlat), ofs, weight=weight), int(nphi.sum()), nlat * nlon
+    geom = sht.sht_geom_reduced_gauss(lmax + 1, lmax, 0)
+    return geom, geom.npix, (lmax + 1) * (2 * lmax + 1)
 
 
 @pytest.mark.parametrize("lmax", [127, 511, 1023])

@@ -359,3 +359,78 @@ def test_deriv_synthesis(sht, precision):
     z = torch.zeros(oracle.nalm(8, 8), dtype=torch.complex128, device="cuda")
     with pytest.raises(sht.ShtError):
         sht.sht_execute(p0, sht.SHT_DERIV_SYNTHESIS, [z], [torch.zeros(10 * 19, dtype=torch.float64, device="cuda")])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("spin", [0, 2])
+def test_real_harmonic_storage(sht, precision, spin):
+    # Sect. 4.5: a_lm stored as real-harmonic coefficients (reading in oracle.real_to_complex)
+    l2, mx = (FP64_L2, FP64_MAX) if precision == 0 else (MIX_L2, MIX_MAX)
+    lmax = 40
+    geom = sht.sht_geom_gauss(42, 81)
+    rings = rings_of(geom)
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), spin, 1, precision)
+    narr = plan.narrays
+    rng = np.random.default_rng(500 + spin)
+    ar = [inputs.gaussian_alm(rng, lmax, lmax, lmin=abs(spin)) for _ in range(narr)]  # real storage
+    ac = [oracle.real_to_complex(a, lmax, lmax) for a in ar]
+    maps = [rng.standard_normal(geom.npix) for _ in range(narr)]
+    R = sht.SHT_REAL_HARMONICS
+    # synthesis reads real storage
+    a_d = [torch.from_numpy(a).cuda() for a in ar]
+    out = [torch.zeros(geom.npix, dtype=torch.float64, device="cuda") for _ in range(narr)]
+    sht.sht_execute(plan, sht.SHT_SYNTHESIS, a_d, out, R)
+    ref = oracle.synthesis(spin, lmax, lmax, ac, rings)
+    # analysis and adjoint synthesis write real storage
+    m_d = [torch.from_numpy(x).cuda() for x in maps]
+    n = oracle.nalm(lmax, lmax)
+    ana = [torch.full((n,), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda") for _ in range(narr)]
+    sht.sht_execute(plan, sht.SHT_ANALYSIS, ana, m_d, R)
+    adj = [torch.full((n,), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda") for _ in range(narr)]
+    sht.sht_execute(plan, sht.SHT_ADJOINT_SYNTHESIS, adj, m_d, R)
+    # accumulation in real storage, and the no-alloc entry
+    acc = [torch.from_numpy(a).cuda() for a in ar]
+    sht.sht_execute(plan, sht.SHT_ANALYSIS, acc, m_d, R | sht.SHT_ADD_OUTPUT)
+    out2 = [torch.zeros(geom.npix, dtype=torch.float64, device="cuda") for _ in range(narr)]
+    sht.sht_execute_noalloc(plan, sht.SHT_SYNTHESIS, a_d, out2, R)
+    torch.cuda.synchronize()
+    ref_a = [oracle.complex_to_real(x, lmax, lmax) for x in oracle.analysis(spin, lmax, lmax, maps, rings)]
+    ref_j = [oracle.complex_to_real(x, lmax, lmax) for x in
+             oracle.analysis(spin, lmax, lmax, maps, rings, adjoint=True)]
+    for g, r in zip(out, ref):
+        assert rel_l2(g.cpu().numpy(), r) <= l2 and rel_max(g.cpu().numpy(), r) <= mx
+    for g, r in zip(out2, ref):
+        assert rel_l2(g.cpu().numpy(), r) <= l2
+    for g, r in zip(ana, ref_a):
+        assert rel_l2(g.cpu().numpy(), r) <= l2
+    for g, r in zip(adj, ref_j):
+        assert rel_l2(g.cpu().numpy(), r) <= l2
+    for g, a0, r in zip(acc, ar, ref_a):
+        assert rel_l2(g.cpu().numpy() - a0, r) <= l2
+    # in real storage the adjoint synthesis is the plain transpose: <S a, p> = <a, S^T p>
+    lhs = sum(float(torch.dot(o, m)) for o, m in zip(out, m_d))
+    _, mm = inputs.lm_arrays(lmax, lmax)
+    rhs = 0.0
+    for a, j in zip(ar, adj):
+        j = j.cpu().numpy()
+        rhs += float(np.sum(a.real * j.real) + np.sum((a.imag * j.imag)[mm > 0]))
+    assert abs(lhs - rhs) <= 1e-11 * max(1.0, abs(lhs))
+
+
+def test_real_harmonic_deriv_and_batch(sht):
+    lmax = 30
+    geom = sht.sht_geom_gauss(32, 61)
+    rings = rings_of(geom)
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), 1, 1, 0)
+    ar = inputs.gaussian_alm(np.random.default_rng(510), lmax, lmax)
+    out = [torch.zeros(geom.npix, dtype=torch.float64, device="cuda") for _ in range(2)]
+    sht.sht_execute(plan, sht.SHT_DERIV_SYNTHESIS, [torch.from_numpy(ar).cuda()], out, sht.SHT_REAL_HARMONICS)
+    torch.cuda.synchronize()
+    ref = oracle.deriv_synthesis(lmax, lmax, [oracle.real_to_complex(ar, lmax, lmax)], rings)
+    for g, r in zip(out, ref):
+        assert rel_l2(g.cpu().numpy(), r) <= FP64_L2
+    batch = sht.sht_batch_create([plan])
+    with pytest.raises(sht.ShtError) as ei:
+        sht.sht_batch_execute(batch, sht.SHT_SYNTHESIS, [[torch.from_numpy(ar).cuda()] * 2], [out],
+                              sht.SHT_REAL_HARMONICS)
+    assert ei.value.code == sht.SHT_ERR_UNSUPPORTED

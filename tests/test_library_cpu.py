@@ -108,3 +108,32 @@ def test_alm_layouts():
                 dict(lmax=3, mmax=3, mval=[4]), dict(lmax=3, mmax=3, stride=0)):
         with pytest.raises(sht.ShtError):
             sht.sht_alm_create(**bad)
+
+
+def _smooth235(n):
+    for f in (2, 3, 5):
+        while n % f == 0:
+            n //= f
+    return n == 1
+
+
+def test_reduced_gauss_geometry():
+    # Sect. 4.4.2: ring y holds the smallest 2^a 3^b 5^c >= 2 m_y + 1 pixels, m_y from
+    # Eq. eq_polaropt solved for m; same nodes as the full grid; sum Nphi w = 4 pi
+    for lmax, spin in ((2047, 0), (1023, 2), (100, 0)):
+        nlat = lmax + 1
+        red = sht.sht_geom_reduced_gauss(nlat, lmax, spin).rings()
+        full = sht.sht_geom_gauss(nlat, 2 * lmax + 1).rings()
+        np.testing.assert_array_equal(red["theta"], full["theta"])
+        T = max(100.0, 0.01 * lmax)
+        th = red["theta"]
+        r = T + lmax * np.sin(th)
+        m = np.minimum(lmax, np.floor(abs(spin) * np.cos(th) + np.sqrt(r * r - spin * spin * np.sin(th) ** 2)))
+        for n, mm in zip(red["nphi"], m):
+            lo = int(2 * mm + 1)
+            assert n >= lo and _smooth235(int(n))
+            assert not any(_smooth235(x) for x in range(lo, int(n)))  # the smallest such length
+        assert abs(np.sum(red["nphi"] * red["weight"]) - 4 * np.pi) < 1e-12
+        assert np.all(np.diff(red["ofs"]) == red["nphi"][:-1])
+    red = sht.sht_geom_reduced_gauss(2048, 2047)
+    assert red.npix < 0.7 * 2048 * 4095  # more than 30% of the pixels saved at lmax > 1000

@@ -438,3 +438,26 @@ def test_deriv_synthesis_matches_finite_differences():
     scale = np.max(np.abs(d_th))
     assert np.max(np.abs(d_th - fd_th)) < 1e-7 * scale
     assert np.max(np.abs(d_ph - fd_ph)) < 1e-7 * np.max(np.abs(d_ph))
+
+
+def test_real_harmonic_basis_is_orthonormal():
+    # Sect. 4.5 reading: the basis functions of real-harmonic storage (one per
+    # stored number: m = 0 real parts, both numbers for m > 0) are orthonormal
+    # under Gauss-Legendre quadrature, which fixes the sqrt2 factors
+    lmax = 4
+    rings = oracle.gauss_rings(lmax + 1, 2 * lmax + 1)
+    n = oracle.nalm(lmax, lmax)
+    m = oracle._m_of(lmax, lmax)
+    coords = [(i, 0) for i in range(n)] + [(i, 1) for i in range(n) if m[i] > 0]
+    assert len(coords) == (lmax + 1) ** 2
+    basis = []
+    for i, part in coords:
+        r = np.zeros(n, dtype=np.complex128)
+        r[i] = 1.0 if part == 0 else 1j
+        basis.append(oracle.synthesis(0, lmax, lmax, [oracle.real_to_complex(r, lmax, lmax)], rings)[0])
+    w = np.repeat(rings.weight, rings.nphi)
+    gram = np.array([[np.sum(w * u * v) for v in basis] for u in basis])
+    np.testing.assert_allclose(gram, np.eye(len(basis)), atol=1e-13)
+    a = inputs.gaussian_alm(np.random.default_rng(3), lmax, lmax)
+    np.testing.assert_allclose(oracle.complex_to_real(oracle.real_to_complex(a, lmax, lmax), lmax, lmax), a,
+                               atol=1e-15)
