@@ -50,6 +50,7 @@ def test_work_counts():
     assert bench.f32_ops_per_triple(0, 1) == 48 and bench.f32_ops_per_triple(2, 1) == 163
     assert bench.launches_per_step(2, "fp64") == 6 and bench.launches_per_step(0, "fp64") == 5
     assert bench.launches_per_step(0, "mixed") == 6
+    assert bench.launches_per_step(2, "mixed", True) == 9 and bench.launches_per_step(0, "mixed", True) == 8
 
 
 class _Plan:

@@ -434,3 +434,26 @@ def test_real_harmonic_deriv_and_batch(sht):
         sht.sht_batch_execute(batch, sht.SHT_SYNTHESIS, [[torch.from_numpy(ar).cuda()] * 2], [out],
                               sht.SHT_REAL_HARMONICS)
     assert ei.value.code == sht.SHT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_high_spin(sht, precision):
+    # Sect. 4.1: spins well above 2 (the paper repeats its accuracy test at s = 37);
+    # plans accept |s| <= 64
+    l2, mx = (FP64_L2, FP64_MAX) if precision == 0 else (MIX_L2, MIX_MAX)
+    check_pair(sht, sht.sht_geom_gauss(72, 141), 70, 70, 37, seed=600, precision=precision, l2=l2, mx=mx)
+    check_pair(sht, sht.sht_geom_gauss(82, 161), 80, 80, 64, seed=601, precision=precision, l2=l2, mx=mx)
+    check_pair(sht, sht.sht_geom_healpix(16), 40, 40, -5, seed=602, precision=precision, l2=l2, mx=mx)
+    # exact Gauss-Legendre round trip at s = 37
+    lmax = 90
+    geom = sht.sht_geom_gauss(lmax + 1, 2 * lmax + 1)
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), 37, 1, precision)
+    rng = np.random.default_rng(603)
+    alm = [torch.from_numpy(inputs.gaussian_alm(rng, lmax, lmax, lmin=37)).cuda() for _ in range(2)]
+    maps = [torch.empty(geom.npix, dtype=torch.float64, device="cuda") for _ in range(2)]
+    back = [torch.empty_like(a) for a in alm]
+    sht.sht_execute(plan, sht.SHT_SYNTHESIS, alm, maps)
+    sht.sht_execute(plan, sht.SHT_ANALYSIS, back, maps)
+    torch.cuda.synchronize()
+    for a, b in zip(alm, back):
+        assert float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) <= 10 * l2
