@@ -99,6 +99,12 @@ __device__ __forceinline__ void acc_mul(f2 &acc, f2 w, float ah, float al) {
   acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, p.l));
 }
 __device__ __forceinline__ void renorm(f2 &a) { a = fast_two_sum(a.h, a.l); }
+// a + b with the low word carried unnormalised (a running sum of a few dozen
+// terms: the low word stays within a few ulps of the high word's last bit)
+__device__ __forceinline__ f2 f2_add_lazy(f2 a, f2 b) {
+  const f2 s = two_sum(a.h, b.h);
+  return {s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l)};
+}
 __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
   const f2 s = two_sum(a.h, b.h);
   return fast_two_sum(s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l));
@@ -731,7 +737,7 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
       const f2 *row = &slot[sl][part * 32];
       f2 t = row[0];
 #pragma unroll 8
-      for (int i = 1; i < 32; ++i) t = f2_add(t, row[i]);
+      for (int i = 1; i < 32; ++i) t = f2_add_lazy(t, row[i]);
       quart[part][sl] = t;
     }
     __syncthreads();
@@ -743,12 +749,19 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
     }
   }
 }
+// one-job shapes of up to two pairs a thread are held to 80 registers: six CTAs
+// per SM instead of five (their shared slot table allows six); measured at one
+// E/B pair, lmax 4095: 84.1 ms against 85.0 (two pairs) and 84.0 against 86.8 (one)
 template <int NJ, int PPT, bool SPIN>
-__global__ void __launch_bounds__(kAnaThreads) mix_ana(MixArgs a) {
+constexpr int mix_ana_min_blocks() {
+  return (NJ == 1 && PPT <= 2) ? 6 : ((!SPIN && NJ == 1 && PPT == 4) ? 5 : 1);  // spin 0, 4 pairs: 96 registers
+}
+template <int NJ, int PPT, bool SPIN>
+__global__ void __launch_bounds__(kAnaThreads, (mix_ana_min_blocks<NJ, PPT, SPIN>())) mix_ana(MixArgs a) {
   mix_ana_body<NJ, PPT, SPIN>(a, nullptr, a.ana_items[blockIdx.x]);
 }
 template <int NJ, int PPT, bool SPIN>
-__global__ void __launch_bounds__(kAnaThreads) mix_ana_batch(const MixArgs *__restrict__ args,
+__global__ void __launch_bounds__(kAnaThreads, (mix_ana_min_blocks<NJ, PPT, SPIN>())) mix_ana_batch(const MixArgs *__restrict__ args,
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const MixArgs &a = args[it.w];

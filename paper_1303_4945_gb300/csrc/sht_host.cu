@@ -1071,9 +1071,9 @@ extern "C" int sht_plan_autotune(sht_plan_t P, void *stream, float *ms_per_candi
     // one untimed and two timed runs of the analysis Legendre stage (polar cut on)
     for (int it = 0; it < 3 && e == cudaSuccess; ++it) {
       if (it == 1) e = cudaEventRecord(ev[0], st);
+      // the tiling's own kernel only (a mixed plan's FP64 items run beside it)
       if (e == cudaSuccess)
         e = P->precision == SHT_MIXED ? launch_leg_ana_mixed(P, none, 1, st) : launch_leg_ana_fp64(P, none, 1, st);
-      if (e == cudaSuccess && P->precision == SHT_MIXED && P->nana_lo[1]) e = launch_leg_ana_fp64(P, none, 1, st, true);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
