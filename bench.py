@@ -277,8 +277,8 @@ MEASURED_TRAFFIC = {
     # profiles/dram_traffic_spin2_lmax4095.md (spin 2, GL 4096 x 8191, lmax 4095, one launch each)
     "fp64:legendre_analysis": {"bytes": 706942720 + 941203200, "sha256": "696b0de9716a2778b0e70b039dd9a4f2e207e96b035236f992fe34830cb5ba3d"},
     "fp64:legendre_synthesis": {"bytes": 554776320 + 323874816, "sha256": "696b0de9716a2778b0e70b039dd9a4f2e207e96b035236f992fe34830cb5ba3d"},
-    "mixed:legendre_analysis": {"bytes": 676905216 + 1784456704, "sha256": "49cee25b8dbd707ece985b4f1375b70da6c574d7c83c49d834ab19422ff25aaf"},
-    "mixed:legendre_synthesis": {"bytes": 545575680 + 323118848, "sha256": "49cee25b8dbd707ece985b4f1375b70da6c574d7c83c49d834ab19422ff25aaf"},
+    "mixed:legendre_analysis": {"bytes": 659847936 + 3475654656, "sha256": "5872d72464d53f5970754b0ca2224a3f26ef3958e07b1b1c731649991f3faeb8"},
+    "mixed:legendre_synthesis": {"bytes": 549097984 + 323081472, "sha256": "5872d72464d53f5970754b0ca2224a3f26ef3958e07b1b1c731649991f3faeb8"},
 }
 
 
