@@ -2,8 +2,10 @@
 //
 // One CTA transforms one north/south ring pair of one map: the two real
 // rings are packed as z = p_north + i p_south into a single complex DFT of
-// length Nphi (pairs always share Nphi).  The whole ring lives in shared
-// memory and is transformed in place: mixed-radix decimation-in-frequency
+// length Nphi (pairs always share Nphi).  The ring lives in shared memory
+// (up to kFftMaxLen points; longer rings in an L2-resident global scratch slot
+// per CTA of a persistent grid) and is transformed in place: mixed-radix
+// decimation-in-frequency
 // passes (radix 2, 4 and odd radices up to 31), each thread running whole
 // butterflies, one barrier per pass; the output comes out digit-reversed and
 // is read back through a position table.  Lengths with a prime factor above

@@ -9,11 +9,12 @@
 // FP64 remains for the recursion-coefficient tables, the start values, the
 // conversion of inputs/outputs and the ring FFTs.
 //
-// Structure, ring pairing, parity split, the coupled (lp, lm) recursion for
-// spin and the analysis reduction follow legendre_fp64.cu exactly; only the
-// arithmetic type differs.  The enhanced exponent uses steps of 2^104: pairs
-// above 2^52 are scaled down every 8 steps; values at scale 0 and -1 are
-// accumulated (the latter times 2^-104), anything smaller is negligible.
+// Structure, ring pairing, parity split, the separate +s / -s recursions for
+// spin and the analysis reduction follow legendre_fp64.cu; only the arithmetic
+// type differs.  The enhanced exponent uses steps of 2^104: pairs above 2^52
+// are scaled down every 8 steps; values at scale 0 and -1 are accumulated (the
+// latter times 2^-104), anything smaller is negligible.  A mixed plan hands the
+// items of small m near the poles to the FP64 kernels (sht_plan_s::fp64_m_below).
 #include "sht_device.cuh"
 
 namespace sht {

@@ -1,6 +1,7 @@
 // tables.cu -- plan-time kernels: recursion coefficients and start-value prefactors.
 //
-// Recursion (Sect. 4.1, quoted from Kostelec & Rockmore) for d^l_{a b} with
+// Recursion of Sect. 4.1 (the Wigner-d recursion it takes from Kostelec &
+// Rockmore), restated for d^l_{a b} with
 // a = -m, b = s:
 //   [cos t + m s / (l (l+1))] d^l = c1_l d^{l-1} + c2_l d^{l+1},
 //   c1_l = sqrt((l^2 - m^2)(l^2 - s^2)) / (l (2l+1)),
