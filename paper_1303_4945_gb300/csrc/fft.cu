@@ -6,10 +6,11 @@
 // (up to kFftMaxLen points; longer rings in an L2-resident global scratch slot
 // per CTA of a persistent grid) and is transformed in place: mixed-radix
 // decimation-in-frequency
-// passes (radix 2, 4 and odd radices up to 31), each thread running whole
-// butterflies, one barrier per pass; the output comes out digit-reversed and
+// passes (radix 2, 4 and odd radices up to 31 with each thread running whole
+// butterflies, one barrier per pass; odd radices up to 127 as sweeps over the
+// ring); the output comes out digit-reversed and
 // is read back through a position table.  Lengths with a prime factor above
-// 31 go through Rader's algorithm (prime n, n-1 smooth: a cyclic convolution
+// 127 go through Rader's algorithm (prime n, n-1 smooth: a cyclic convolution
 // of length n-1) or Bluestein's (chirp convolution of smooth length >= 2n-1);
 // both convolutions run DIF forward and the transposed (DIT) passes back, so
 // the result returns to natural order without a permutation pass.
@@ -134,6 +135,95 @@ __device__ __noinline__ void fft_stage(Ring ring, int len, int L, const double2 
   __syncthreads();
 }
 
+// One in-place pass of an odd radix R in (kMaxRadix, kMaxBigRadix], the same
+// butterflies as fft_stage.  R values no longer fit in one thread's registers, so
+// the symmetric form of dft_small runs as sweeps over the ring:
+//   1. S_j = x_j + x_{R-j} into slot j and D_j = x_j - x_{R-j} into slot R-j
+//      (j = 1..h, after the input twiddles for DIT), one item per (butterfly, j);
+//   2. in rounds of whole butterflies, one item per (butterfly, k), k = 0..h,
+//      computes y_k and y_{R-k} from x_0, S and D into registers; after a barrier
+//      the items write them back in place (DIF: times the output twiddles).
+// Items are k-major so that a warp shares k (its cos/sin loads broadcast) and
+// walks consecutive butterflies (consecutive slots).  cos and sin of 2 pi t / R
+// come from the ring's own table: W[t len / R] = e^{-2 pi i t / R}.
+template <bool DIT, class Ring>
+__device__ __noinline__ void fft_stage_big(Ring ring, int len, int L, int R, const double2 *__restrict__ W) {
+  constexpr int kItems = 4;  // output pairs a thread holds across the barrier
+  const int LR = L / R, nb = len / R, tw = len / L, h = (R - 1) / 2, tr = len / R;
+  for (int i = threadIdx.x; i < nb * h; i += blockDim.x) {
+    const int j = 1 + i / nb, q = i % nb;
+    const int B = q / LR, b = q - B * LR;
+    double2 *p = ring.at(B * L + b);
+    double2 u = p[j * LR], v = p[(R - j) * LR];
+    if (DIT && b != 0) {
+      u = cmul(u, __ldg(W + j * b * tw));
+      v = cmul(v, __ldg(W + (R - j) * b * tw));
+    }
+    p[j * LR] = cadd(u, v);
+    p[(R - j) * LR] = csub(u, v);
+  }
+  __syncthreads();
+  const int per = h + 1;
+  int nround = (int)(blockDim.x * kItems) / per;  // butterflies per round
+  if (nround >= 32) nround &= ~31;
+  for (int q0 = 0; q0 < nb; q0 += nround) {
+    const int nq = min(nround, nb - q0), nit = nq * per;
+    double2 ya[kItems], yb[kItems];
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int i = threadIdx.x + u * blockDim.x;
+      if (i < nit) {
+        const int k = i / nq, q = q0 + i % nq;
+        const int B = q / LR, b = q - B * LR;
+        const double2 *p = ring.at(B * L + b);
+        double2 A = p[0];
+        if (k == 0) {
+          for (int j = 1; j <= h; ++j) A = cadd(A, p[j * LR]);
+          ya[u] = A;
+        } else {
+          double2 Bn = make_double2(0.0, 0.0);  // -(sum_j D_j sin(2 pi j k / R))
+          int t = 0;
+          for (int j = 1; j <= h; ++j) {
+            t += k;
+            if (t >= R) t -= R;
+            const double2 w = __ldg(W + t * tr);
+            const double2 sj = p[j * LR], dj = p[(R - j) * LR];
+            A.x = fma(sj.x, w.x, A.x);
+            A.y = fma(sj.y, w.x, A.y);
+            Bn.x = fma(dj.x, w.y, Bn.x);
+            Bn.y = fma(dj.y, w.y, Bn.y);
+          }
+          ya[u] = make_double2(A.x - Bn.y, A.y + Bn.x);  // y_k = A - i B
+          yb[u] = make_double2(A.x + Bn.y, A.y - Bn.x);  // y_{R-k} = A + i B
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int i = threadIdx.x + u * blockDim.x;
+      if (i < nit) {
+        const int k = i / nq, q = q0 + i % nq;
+        const int B = q / LR, b = q - B * LR;
+        double2 *p = ring.at(B * L + b);
+        double2 y0 = ya[u];
+        if (k == 0) {
+          p[0] = y0;
+        } else {
+          double2 y1 = yb[u];
+          if (!DIT && b != 0) {
+            y0 = cmul(y0, __ldg(W + k * b * tw));
+            y1 = cmul(y1, __ldg(W + (R - k) * b * tw));
+          }
+          p[k * LR] = y0;
+          p[(R - k) * LR] = y1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <bool DIT, class Ring>
 __device__ void fft_stage_any(Ring ring, int len, int L, int R, const double2 *W) {
   switch (R) {
@@ -148,7 +238,8 @@ __device__ void fft_stage_any(Ring ring, int len, int L, int R, const double2 *W
     case 19: fft_stage<19, DIT>(ring, len, L, W); break;
     case 23: fft_stage<23, DIT>(ring, len, L, W); break;
     case 29: fft_stage<29, DIT>(ring, len, L, W); break;
-    default: fft_stage<31, DIT>(ring, len, L, W); break;
+    case 31: fft_stage<31, DIT>(ring, len, L, W); break;
+    default: fft_stage_big<DIT>(ring, len, L, R, W); break;
   }
 }
 

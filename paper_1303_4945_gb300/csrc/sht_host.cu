@@ -461,13 +461,32 @@ static bool factor_small(int n, std::vector<int> &rad) {
     rad.push_back(2);
     n /= 2;
   }
-  for (int p = 3; p <= 31 && n > 1; p += 2) {
+  for (int p = 3; p <= kMaxBigRadix && n > 1; p += 2) {
     while (n % p == 0) {
       rad.push_back(p);
       n /= p;
     }
   }
   return n == 1 && rad.size() <= 24;
+}
+
+// FP64 instructions per point of the passes rad (a model for choosing the
+// Bluestein length): radix 2 and 4 cost 2 and 4 adds a point; an odd radix with
+// h = (R-1)/2 costs 4 h^2 multiply-adds and 10 h adds a butterfly; every pass
+// but the last adds a complex twiddle product (4 instructions) a point.
+static double fft_cost_per_point(const std::vector<int> &rad) {
+  double c = 0.0;
+  for (size_t i = 0; i < rad.size(); ++i) {
+    const int R = rad[i];
+    if (R == 2 || R == 4) {
+      c += R;
+    } else {
+      const double h = (R - 1) / 2;
+      c += (4.0 * h * h + 10.0 * h) / R;
+    }
+    if (i + 1 < rad.size()) c += 4.0;
+  }
+  return c;
 }
 
 static bool is_prime(int n) {
@@ -541,12 +560,24 @@ static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scra
     fp.kind = 1;
     fp.len = n - 1;
   } else {
-    int M = 2 * n - 1;  // smallest smooth convolution length
-    while (M <= kFftMaxGlobalLen && !factor_small(M, rad)) ++M;
-    if (M > kFftMaxGlobalLen)
+    // convolution length >= 2n-1: the cheapest by the pass model among the
+    // smooth lengths up to the first one whose radices are all <= 31
+    int best = 0;
+    double best_cost = 0.0;
+    for (int M = 2 * n - 1; M <= kFftMaxGlobalLen; ++M) {
+      if (!factor_small(M, rad)) continue;
+      const double c = M * fft_cost_per_point(rad);
+      if (best == 0 || c < best_cost) {
+        best = M;
+        best_cost = c;
+      }
+      if (rad.back() <= kMaxRadix) break;
+    }
+    if (best == 0)
       return fail(SHT_ERR_UNSUPPORTED, "ring length %d: no FFT of size <= %d available", n, kFftMaxGlobalLen);
+    factor_small(best, rad);
     fp.kind = 2;
-    fp.len = M;
+    fp.len = best;
   }
   fp.nrad = (int)rad.size();
   for (int i = 0; i < fp.nrad; ++i) fp.rad[i] = rad[i];

@@ -24,6 +24,7 @@ constexpr int kMaxJobs = 16;      // ncomp limit
 constexpr int kSynTile = 128;     // ring pairs per synthesis Legendre CTA (one per thread)
 constexpr int kAnaThreads = 128;  // threads per analysis Legendre CTA
 constexpr int kMaxRadix = 8 * 4;  // generic odd radix limit of the FFT engine (primes <= 31)
+constexpr int kMaxBigRadix = 127;  // odd radices above 31 run as shared-memory sweeps (fft_stage_big)
 constexpr int kFftThreads = 512;
 constexpr int kFftMinBlocks = 512 / kFftThreads;  // launch bound: at most 128 registers a thread
 // longest in-place transform: the ring buffer (16 bytes a point) must fit the
