@@ -48,8 +48,8 @@ struct sht_batch_s {
   std::vector<Group> groups;
   void *d_fft_syn[2][2][2] = {};  // [polar][weighted][add]: FFT argument records
   void *d_fft_ana[2] = {};        // [weighted]
-  int4 *d_fft_items = nullptr;    // (pair, map, -, plan)
-  int nfft_items = 0;
+  int4 *d_fft_items[2] = {};      // (pair, map, -, plan) of FP64 plans [0] and mixed plans [1]
+  int nfft_items[2] = {};
   int fft_smem = 0;
   std::vector<void *> allocs;
   // FP64 groups run beside mixed groups: a side stream forked and joined by events
@@ -178,17 +178,20 @@ int build(sht_batch_s *B) {
     for (int k = 0; k < n; ++k) fft_fill_args(B->plans[k], 1, w, 0, B->ptr_off[k], args.data() + k * rec);
     if (e == cudaSuccess) e = upload_bytes(B, args, &B->d_fft_ana[w]);
   }
-  std::vector<std::pair<int64_t, int4>> fi;
+  std::vector<std::pair<int64_t, int4>> fi[2];  // by engine: FP64, double-float
   for (int k = 0; k < n; ++k) {
     const sht_plan_s *P = B->plans[k];
     B->fft_smem = std::max(B->fft_smem, P->fft_smem);
+    const int df = P->precision == SHT_MIXED;
     for (int p = 0; p < P->npairs; ++p)
-      for (int j = 0; j < P->nmaps; ++j) fi.push_back({(int64_t)P->pair_len[p], make_int4(p, j, 0, k)});
+      for (int j = 0; j < P->nmaps; ++j) fi[df].push_back({(int64_t)P->pair_len[p], make_int4(p, j, 0, k)});
   }
-  sort_by_cost(fi);
-  auto fv = strip(fi);
-  B->nfft_items = (int)fv.size();
-  if (e == cudaSuccess) e = upload(B, fv.data(), fv.size(), &B->d_fft_items);
+  for (int df = 0; df < 2; ++df) {
+    sort_by_cost(fi[df]);
+    auto fv = strip(fi[df]);
+    B->nfft_items[df] = (int)fv.size();
+    if (e == cudaSuccess && !fv.empty()) e = upload(B, fv.data(), fv.size(), &B->d_fft_items[df]);
+  }
   int least = 0, greatest = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&B->side, cudaStreamNonBlocking, greatest);
@@ -317,11 +320,13 @@ extern "C" int sht_batch_execute(sht_batch_t B, int type, double *const *const *
         e = launch_alm_prepare_fp64(P, A[k], st);
     }
     if (e == cudaSuccess) e = legendre(0);
-    if (e == cudaSuccess)
-      e = launch_fft_batch(0, B->d_fft_syn[polar][weighted][add], B->d_fft_items, B->nfft_items, B->fft_smem, TM, st);
+    for (int df = 0; df < 2 && e == cudaSuccess; ++df)
+      e = launch_fft_batch(0, df, B->d_fft_syn[polar][weighted][add], B->d_fft_items[df], B->nfft_items[df],
+                           B->fft_smem, TM, st);
   } else {
     const int weighted = type == SHT_ANALYSIS;
-    e = launch_fft_batch(1, B->d_fft_ana[weighted], B->d_fft_items, B->nfft_items, B->fft_smem, TM, st);
+    for (int df = 0; df < 2 && e == cudaSuccess; ++df)
+      e = launch_fft_batch(1, df, B->d_fft_ana[weighted], B->d_fft_items[df], B->nfft_items[df], B->fft_smem, TM, st);
     if (e == cudaSuccess) e = legendre(1);
     for (int k = 0; k < n && e == cudaSuccess; ++k) e = launch_ana_reduce(B->plans[k], A[k], polar, add, st);
   }

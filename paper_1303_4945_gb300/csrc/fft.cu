@@ -1,4 +1,4 @@
-// fft.cu -- ring FFTs of Eqs. syn1 and ana2 in IEEE double.
+// fft.cu -- ring FFTs of Eqs. syn1 and ana2.
 //
 // One CTA transforms one north/south ring pair of one map: the two real
 // rings are packed as z = p_north + i p_south into a single complex DFT of
@@ -19,10 +19,18 @@
 //   c_m = F_m e^{i m phi0} (m >= 0), c_{-m} = conj(c_m); m is folded modulo N
 //   when N <= 2 mmax (aliasing, Eq. syn1).
 // Analysis, per ring:   G_m = w e^{-i m phi0} sum_x p_x e^{-2 pi i m x / N}  (Eq. ana2).
+//
+// The engine is written once over a number policy: IEEE double (F64, plans of
+// the FP64 form) or double-float pairs on the FP32 pipe (DF, plans of the mixed
+// form: the FP32 pipe issues 64 times the FP64 rate on GB300, and ~46 bits an
+// operation keep the transform's relative error near 1e-14).  Ring pixels and
+// the F_m / G_m arrays stay FP64 in memory; DF converts on the way in and out.
 #include <algorithm>
 #include <mutex>
 #include <set>
+#include <vector>
 
+#include "df.cuh"
 #include "sht_internal.h"
 
 namespace sht {
@@ -36,56 +44,151 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
 // cos(2 pi t / R) and sin(2 pi t / R) for odd radices R <= kMaxRadix, t = 1..(R-1)/2,
-// written once per device (fft_prepare_device).  The butterflies index them with
-// compile-time constants, so they are read as constant-bank operands.
+// in FP64 and as hi/lo float pairs, written once per device (fft_prepare_device).
+// The butterflies index them with compile-time constants, so they are read as
+// constant-bank operands.
 __constant__ double c_cos[kMaxRadix + 1][kMaxRadix / 2 + 1];
 __constant__ double c_sin[kMaxRadix + 1][kMaxRadix / 2 + 1];
+__constant__ float2 c_cos2[kMaxRadix + 1][kMaxRadix / 2 + 1];
+__constant__ float2 c_sin2[kMaxRadix + 1][kMaxRadix / 2 + 1];
+
+// A complex double-float: re = (v.x, v.y), im = (v.z, v.w); 16 bytes like a
+// double2 and moved as one 128-bit access.
+struct cf2 {
+  float4 v;
+};
+
+// Number policies.  C is the complex type the ring holds, S the type of its
+// parts.  acc(s, x) adds x to a running sum and macc(s, x, c) adds x c (c real),
+// both with the low word carried lazily in DF; fin() normalises such a sum.
+// a_mi_b(A, B) = A - i B and a_pi_b(A, B) = A + i B.
+struct F64 {
+  using C = double2;
+  using S = double;
+  static constexpr int kRegRadix = kMaxRadix;  // largest odd radix with a register-resident butterfly
+  static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
+  static __device__ __forceinline__ C sub(C a, C b) { return csub(a, b); }
+  static __device__ __forceinline__ C mul(C a, C b) { return cmul(a, b); }
+  static __device__ __forceinline__ C conj(C a) { return cconj(a); }
+  static __device__ __forceinline__ void acc(C &s, C x) { s = cadd(s, x); }
+  static __device__ __forceinline__ void macc(C &s, C x, S c) {
+    s.x = fma(x.x, c, s.x);
+    s.y = fma(x.y, c, s.y);
+  }
+  static __device__ __forceinline__ void fin(C &) {}
+  static __device__ __forceinline__ C a_mi_b(C A, C B) { return make_double2(A.x + B.y, A.y - B.x); }
+  static __device__ __forceinline__ C a_pi_b(C A, C B) { return make_double2(A.x - B.y, A.y + B.x); }
+  static __device__ __forceinline__ S re(C a) { return a.x; }
+  static __device__ __forceinline__ S im(C a) { return a.y; }
+  static __device__ __forceinline__ S sneg(S a) { return -a; }
+  static __device__ __forceinline__ S kcos(int R, int t) { return c_cos[R][t]; }
+  static __device__ __forceinline__ S ksin(int R, int t) { return c_sin[R][t]; }
+  static __device__ __forceinline__ C ldg(const C *p) { return __ldg(p); }
+  static __device__ __forceinline__ C of(double2 v) { return v; }
+  static __device__ __forceinline__ double2 val(C v) { return v; }
+  static __device__ __forceinline__ const C *tw(const FftPlanDev &fp) { return fp.w; }
+  static __device__ __forceinline__ const C *spec(const FftPlanDev &fp) { return fp.spec; }
+  static __device__ __forceinline__ const C *chirp(const FftPlanDev &fp) { return fp.chirp; }
+};
+
+struct DF {
+  using C = cf2;
+  using S = f2;
+  static constexpr int kRegRadix = 13;  // above, the butterfly's pairs spill: sweeps instead
+  static __device__ __forceinline__ C mk(f2 r, f2 i) { return {make_float4(r.h, r.l, i.h, i.l)}; }
+  static __device__ __forceinline__ S re(C a) { return {a.v.x, a.v.y}; }
+  static __device__ __forceinline__ S im(C a) { return {a.v.z, a.v.w}; }
+  static __device__ __forceinline__ C zero() { return {make_float4(0.f, 0.f, 0.f, 0.f)}; }
+  static __device__ __forceinline__ C add(C a, C b) { return mk(f2_add(re(a), re(b)), f2_add(im(a), im(b))); }
+  static __device__ __forceinline__ C sub(C a, C b) { return mk(f2_sub(re(a), re(b)), f2_sub(im(a), im(b))); }
+  static __device__ __forceinline__ C mul(C a, C b) {
+    return mk(dot2(re(a), re(b), neg(im(a)), im(b)), dot2(re(a), im(b), im(a), re(b)));
+  }
+  static __device__ __forceinline__ C conj(C a) { return {make_float4(a.v.x, a.v.y, -a.v.z, -a.v.w)}; }
+  static __device__ __forceinline__ void acc(C &s, C x) {
+    s = mk(f2_add_lazy(re(s), re(x)), f2_add_lazy(im(s), im(x)));
+  }
+  static __device__ __forceinline__ f2 madd(f2 s, f2 x, f2 c) {
+    const f2 p = sht::mul(x, c);
+    const f2 t = two_sum(s.h, p.h);
+    return {t.h, __fadd_rn(s.l, __fadd_rn(t.l, p.l))};
+  }
+  static __device__ __forceinline__ void macc(C &s, C x, S c) { s = mk(madd(re(s), re(x), c), madd(im(s), im(x), c)); }
+  static __device__ __forceinline__ void fin(C &s) {
+    s = mk(fast_two_sum(s.v.x, s.v.y), fast_two_sum(s.v.z, s.v.w));
+  }
+  static __device__ __forceinline__ C a_mi_b(C A, C B) { return mk(f2_add(re(A), im(B)), f2_sub(im(A), re(B))); }
+  static __device__ __forceinline__ C a_pi_b(C A, C B) { return mk(f2_sub(re(A), im(B)), f2_add(im(A), re(B))); }
+  static __device__ __forceinline__ S sneg(S a) { return neg(a); }
+  static __device__ __forceinline__ S kcos(int R, int t) {
+    const float2 c = c_cos2[R][t];
+    return {c.x, c.y};
+  }
+  static __device__ __forceinline__ S ksin(int R, int t) {
+    const float2 c = c_sin2[R][t];
+    return {c.x, c.y};
+  }
+  static __device__ __forceinline__ C ldg(const C *p) { return {__ldg(&p->v)}; }
+  static __device__ __forceinline__ C of(double2 v) { return mk(f2_of(v.x), f2_of(v.y)); }
+  static __device__ __forceinline__ double2 val(C a) { return make_double2(f2_val(re(a)), f2_val(im(a))); }
+  static __device__ __forceinline__ const C *tw(const FftPlanDev &fp) { return reinterpret_cast<const C *>(fp.wf); }
+  static __device__ __forceinline__ const C *spec(const FftPlanDev &fp) {
+    return reinterpret_cast<const C *>(fp.specf);
+  }
+  static __device__ __forceinline__ const C *chirp(const FftPlanDev &fp) {
+    return reinterpret_cast<const C *>(fp.chirpf);
+  }
+};
 
 // y_s = sum_r x_r e^{-2 pi i r s / R} for s < R; out(s, y_s) receives each output.
 // Odd R uses the symmetric form: with S_j = x_j + x_{R-j}, D_j = x_j - x_{R-j},
 //   y_k = A_k - i B_k,  y_{R-k} = A_k + i B_k,
 //   A_k = x_0 + sum_j S_j cos(2 pi j k / R),  B_k = sum_j D_j sin(2 pi j k / R),
 // i.e. 4 h^2 real multiply-adds for R points (h = (R-1)/2) instead of 4 R^2.
-template <int R, class Out>
-__device__ __forceinline__ void dft_small(double2 (&x)[R], Out &&out) {
+template <int R, class N, class Out>
+__device__ __forceinline__ void dft_small(typename N::C (&x)[R], Out &&out) {
+  using C = typename N::C;
+  using S = typename N::S;
   if constexpr (R == 2) {
-    out(0, cadd(x[0], x[1]));
-    out(1, csub(x[0], x[1]));
+    out(0, N::add(x[0], x[1]));
+    out(1, N::sub(x[0], x[1]));
   } else if constexpr (R == 4) {
-    const double2 s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
-    const double2 s13 = cadd(x[1], x[3]), d13 = csub(x[1], x[3]);
-    out(0, cadd(s02, s13));
-    out(1, make_double2(d02.x + d13.y, d02.y - d13.x));  // d02 - i d13
-    out(2, csub(s02, s13));
-    out(3, make_double2(d02.x - d13.y, d02.y + d13.x));  // d02 + i d13
+    const C s02 = N::add(x[0], x[2]), d02 = N::sub(x[0], x[2]);
+    const C s13 = N::add(x[1], x[3]), d13 = N::sub(x[1], x[3]);
+    out(0, N::add(s02, s13));
+    out(1, N::a_mi_b(d02, d13));
+    out(2, N::sub(s02, s13));
+    out(3, N::a_pi_b(d02, d13));
   } else {
     static_assert(R % 2 == 1 && R <= kMaxRadix, "odd radix");
     constexpr int h = (R - 1) / 2;
-    const double2 x0 = x[0];
-    double2 y0 = x0;
+    const C x0 = x[0];
+    C y0 = x0;
 #pragma unroll
     for (int j = 1; j <= h; ++j) {  // S_j into x[j], D_j into x[R-j]
-      const double2 a = x[j], b = x[R - j];
-      x[j] = cadd(a, b);
-      x[R - j] = csub(a, b);
-      y0 = cadd(y0, x[j]);
+      const C a = x[j], b = x[R - j];
+      x[j] = N::add(a, b);
+      x[R - j] = N::sub(a, b);
+      N::acc(y0, x[j]);
     }
+    N::fin(y0);
     out(0, y0);
 #pragma unroll
     for (int k = 1; k <= h; ++k) {
-      double2 A = x0, B = make_double2(0.0, 0.0);
+      C A = x0, B = N::zero();
 #pragma unroll
       for (int j = 1; j <= h; ++j) {
         const int t = (j * k) % R;
-        const double c = t <= h ? c_cos[R][t] : c_cos[R][R - t];
-        const double sn = t <= h ? c_sin[R][t] : -c_sin[R][R - t];
-        A.x = fma(x[j].x, c, A.x);
-        A.y = fma(x[j].y, c, A.y);
-        B.x = fma(x[R - j].x, sn, B.x);
-        B.y = fma(x[R - j].y, sn, B.y);
+        const S c = N::kcos(R, t <= h ? t : R - t);
+        const S sn = t <= h ? N::ksin(R, t) : N::sneg(N::ksin(R, R - t));
+        N::macc(A, x[j], c);
+        N::macc(B, x[R - j], sn);
       }
-      out(k, make_double2(A.x + B.y, A.y - B.x));
-      out(R - k, make_double2(A.x - B.y, A.y + B.x));
+      N::fin(A);
+      N::fin(B);
+      out(k, N::a_mi_b(A, B));
+      out(R - k, N::a_pi_b(A, B));
     }
   }
 }
@@ -94,16 +197,18 @@ __device__ __forceinline__ void dft_small(double2 (&x)[R], Out &&out) {
 // so the out-of-line passes address it as shared memory.
 extern __shared__ double2 s_ring[];
 
-// Where a ring lives while it is transformed: shared memory (every length up to
-// kFftMaxLen), or a CTA-private slot of global scratch for longer rings, which
-// stays in L2 (the engine is the same; barriers order global accesses within
-// the CTA as they do shared ones).
+// Where a ring of element type C lives while it is transformed: shared memory
+// (every length up to kFftMaxLen), or a CTA-private slot of global scratch for
+// longer rings, which stays in L2 (the engine is the same; barriers order global
+// accesses within the CTA as they do shared ones).
+template <class C>
 struct SharedRing {
-  __device__ __forceinline__ double2 *at(int i) const { return s_ring + i; }
+  __device__ __forceinline__ C *at(int i) const { return reinterpret_cast<C *>(s_ring) + i; }
 };
+template <class C>
 struct GlobalRing {
-  double2 *p;
-  __device__ __forceinline__ double2 *at(int i) const { return p + i; }
+  C *p;
+  __device__ __forceinline__ C *at(int i) const { return p + i; }
 };
 
 // One in-place pass of radix R over the len / L blocks of length L of the ring.
@@ -112,30 +217,31 @@ struct GlobalRing {
 //   its transpose (DIT = true): input r times W_L^{r b}, then DFT_R.
 // Each butterfly touches only its own R slots, so one barrier per pass suffices.
 // W holds e^{-2 pi i k / len}; W_L^e = W[e len / L].
-template <int R, bool DIT, class Ring>
-__device__ __noinline__ void fft_stage(Ring ring, int len, int L, const double2 *__restrict__ W) {
+template <int R, bool DIT, class N, class Ring>
+__device__ __noinline__ void fft_stage(Ring ring, int len, int L, const typename N::C *__restrict__ W) {
+  using C = typename N::C;
   const int LR = L / R;
   const int nb = len / R;
   const int tw = len / L;
   for (int q = threadIdx.x; q < nb; q += blockDim.x) {
     const int B = q / LR, b = q - B * LR;
-    double2 *p = ring.at(B * L + b);
-    double2 x[R];
+    C *p = ring.at(B * L + b);
+    C x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = p[r * LR];
     if (DIT && b != 0) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], __ldg(W + r * b * tw));
+      for (int r = 1; r < R; ++r) x[r] = N::mul(x[r], N::ldg(W + r * b * tw));
     }
-    dft_small<R>(x, [&](int s, double2 y) {
-      if (!DIT && s != 0 && b != 0) y = cmul(y, __ldg(W + s * b * tw));
+    dft_small<R, N>(x, [&](int s, C y) {
+      if (!DIT && s != 0 && b != 0) y = N::mul(y, N::ldg(W + s * b * tw));
       p[s * LR] = y;
     });
   }
   __syncthreads();
 }
 
-// One in-place pass of an odd radix R in (kMaxRadix, kMaxBigRadix], the same
+// One in-place pass of an odd radix R in (N::kRegRadix, kMaxBigRadix], the same
 // butterflies as fft_stage.  R values no longer fit in one thread's registers, so
 // the symmetric form of dft_small runs as sweeps over the ring:
 //   1. S_j = x_j + x_{R-j} into slot j and D_j = x_j - x_{R-j} into slot R-j
@@ -145,22 +251,24 @@ __device__ __noinline__ void fft_stage(Ring ring, int len, int L, const double2 
 //      the items write them back in place (DIF: times the output twiddles).
 // Items are k-major so that a warp shares k (its cos/sin loads broadcast) and
 // walks consecutive butterflies (consecutive slots).  cos and sin of 2 pi t / R
-// come from the ring's own table: W[t len / R] = e^{-2 pi i t / R}.
-template <bool DIT, class Ring>
-__device__ __noinline__ void fft_stage_big(Ring ring, int len, int L, int R, const double2 *__restrict__ W) {
+// come from the ring's own table: W[t len / R] = e^{-2 pi i t / R}.  The DF
+// sums are normalised every 8 terms.
+template <bool DIT, class N, class Ring>
+__device__ __noinline__ void fft_stage_big(Ring ring, int len, int L, int R, const typename N::C *__restrict__ W) {
+  using C = typename N::C;
   constexpr int kItems = 4;  // output pairs a thread holds across the barrier
   const int LR = L / R, nb = len / R, tw = len / L, h = (R - 1) / 2, tr = len / R;
   for (int i = threadIdx.x; i < nb * h; i += blockDim.x) {
     const int j = 1 + i / nb, q = i % nb;
     const int B = q / LR, b = q - B * LR;
-    double2 *p = ring.at(B * L + b);
-    double2 u = p[j * LR], v = p[(R - j) * LR];
+    C *p = ring.at(B * L + b);
+    C u = p[j * LR], v = p[(R - j) * LR];
     if (DIT && b != 0) {
-      u = cmul(u, __ldg(W + j * b * tw));
-      v = cmul(v, __ldg(W + (R - j) * b * tw));
+      u = N::mul(u, N::ldg(W + j * b * tw));
+      v = N::mul(v, N::ldg(W + (R - j) * b * tw));
     }
-    p[j * LR] = cadd(u, v);
-    p[(R - j) * LR] = csub(u, v);
+    p[j * LR] = N::add(u, v);
+    p[(R - j) * LR] = N::sub(u, v);
   }
   __syncthreads();
   const int per = h + 1;
@@ -168,33 +276,40 @@ __device__ __noinline__ void fft_stage_big(Ring ring, int len, int L, int R, con
   if (nround >= 32) nround &= ~31;
   for (int q0 = 0; q0 < nb; q0 += nround) {
     const int nq = min(nround, nb - q0), nit = nq * per;
-    double2 ya[kItems], yb[kItems];
+    C ya[kItems], yb[kItems];
 #pragma unroll
     for (int u = 0; u < kItems; ++u) {
       const int i = threadIdx.x + u * blockDim.x;
       if (i < nit) {
         const int k = i / nq, q = q0 + i % nq;
         const int B = q / LR, b = q - B * LR;
-        const double2 *p = ring.at(B * L + b);
-        double2 A = p[0];
+        const C *p = ring.at(B * L + b);
+        C A = p[0];
         if (k == 0) {
-          for (int j = 1; j <= h; ++j) A = cadd(A, p[j * LR]);
+          for (int j = 1; j <= h; ++j) {
+            N::acc(A, p[j * LR]);
+            if ((j & 7) == 0) N::fin(A);
+          }
+          N::fin(A);
           ya[u] = A;
         } else {
-          double2 Bn = make_double2(0.0, 0.0);  // -(sum_j D_j sin(2 pi j k / R))
+          C Bn = N::zero();  // -(sum_j D_j sin(2 pi j k / R))
           int t = 0;
           for (int j = 1; j <= h; ++j) {
             t += k;
             if (t >= R) t -= R;
-            const double2 w = __ldg(W + t * tr);
-            const double2 sj = p[j * LR], dj = p[(R - j) * LR];
-            A.x = fma(sj.x, w.x, A.x);
-            A.y = fma(sj.y, w.x, A.y);
-            Bn.x = fma(dj.x, w.y, Bn.x);
-            Bn.y = fma(dj.y, w.y, Bn.y);
+            const C w = N::ldg(W + t * tr);
+            N::macc(A, p[j * LR], N::re(w));
+            N::macc(Bn, p[(R - j) * LR], N::im(w));
+            if ((j & 7) == 0) {
+              N::fin(A);
+              N::fin(Bn);
+            }
           }
-          ya[u] = make_double2(A.x - Bn.y, A.y + Bn.x);  // y_k = A - i B
-          yb[u] = make_double2(A.x + Bn.y, A.y - Bn.x);  // y_{R-k} = A + i B
+          N::fin(A);
+          N::fin(Bn);
+          ya[u] = N::a_pi_b(A, Bn);  // y_k = A - i B
+          yb[u] = N::a_mi_b(A, Bn);  // y_{R-k} = A + i B
         }
       }
     }
@@ -205,15 +320,15 @@ __device__ __noinline__ void fft_stage_big(Ring ring, int len, int L, int R, con
       if (i < nit) {
         const int k = i / nq, q = q0 + i % nq;
         const int B = q / LR, b = q - B * LR;
-        double2 *p = ring.at(B * L + b);
-        double2 y0 = ya[u];
+        C *p = ring.at(B * L + b);
+        C y0 = ya[u];
         if (k == 0) {
           p[0] = y0;
         } else {
-          double2 y1 = yb[u];
+          C y1 = yb[u];
           if (!DIT && b != 0) {
-            y0 = cmul(y0, __ldg(W + k * b * tw));
-            y1 = cmul(y1, __ldg(W + (R - k) * b * tw));
+            y0 = N::mul(y0, N::ldg(W + k * b * tw));
+            y1 = N::mul(y1, N::ldg(W + (R - k) * b * tw));
           }
           p[k * LR] = y0;
           p[(R - k) * LR] = y1;
@@ -224,44 +339,53 @@ __device__ __noinline__ void fft_stage_big(Ring ring, int len, int L, int R, con
   }
 }
 
-template <bool DIT, class Ring>
-__device__ void fft_stage_any(Ring ring, int len, int L, int R, const double2 *W) {
+// radix R with its butterflies in registers up to N::kRegRadix, else as sweeps
+template <int R, bool DIT, class N, class Ring>
+__device__ __forceinline__ void fft_stage_r(Ring ring, int len, int L, const typename N::C *W) {
+  if constexpr (R <= N::kRegRadix)
+    fft_stage<R, DIT, N>(ring, len, L, W);
+  else
+    fft_stage_big<DIT, N>(ring, len, L, R, W);
+}
+
+template <bool DIT, class N, class Ring>
+__device__ void fft_stage_any(Ring ring, int len, int L, int R, const typename N::C *W) {
   switch (R) {
-    case 2: fft_stage<2, DIT>(ring, len, L, W); break;
-    case 3: fft_stage<3, DIT>(ring, len, L, W); break;
-    case 4: fft_stage<4, DIT>(ring, len, L, W); break;
-    case 5: fft_stage<5, DIT>(ring, len, L, W); break;
-    case 7: fft_stage<7, DIT>(ring, len, L, W); break;
-    case 11: fft_stage<11, DIT>(ring, len, L, W); break;
-    case 13: fft_stage<13, DIT>(ring, len, L, W); break;
-    case 17: fft_stage<17, DIT>(ring, len, L, W); break;
-    case 19: fft_stage<19, DIT>(ring, len, L, W); break;
-    case 23: fft_stage<23, DIT>(ring, len, L, W); break;
-    case 29: fft_stage<29, DIT>(ring, len, L, W); break;
-    case 31: fft_stage<31, DIT>(ring, len, L, W); break;
-    default: fft_stage_big<DIT>(ring, len, L, R, W); break;
+    case 2: fft_stage<2, DIT, N>(ring, len, L, W); break;
+    case 3: fft_stage<3, DIT, N>(ring, len, L, W); break;
+    case 4: fft_stage<4, DIT, N>(ring, len, L, W); break;
+    case 5: fft_stage<5, DIT, N>(ring, len, L, W); break;
+    case 7: fft_stage<7, DIT, N>(ring, len, L, W); break;
+    case 11: fft_stage_r<11, DIT, N>(ring, len, L, W); break;
+    case 13: fft_stage_r<13, DIT, N>(ring, len, L, W); break;
+    case 17: fft_stage_r<17, DIT, N>(ring, len, L, W); break;
+    case 19: fft_stage_r<19, DIT, N>(ring, len, L, W); break;
+    case 23: fft_stage_r<23, DIT, N>(ring, len, L, W); break;
+    case 29: fft_stage_r<29, DIT, N>(ring, len, L, W); break;
+    case 31: fft_stage_r<31, DIT, N>(ring, len, L, W); break;
+    default: fft_stage_big<DIT, N>(ring, len, L, R, W); break;
   }
 }
 
 // Forward DFT of ring[0..fp.len) by decimation in frequency: natural-order input,
 // output X_k at position fp.pos[k] (mixed-radix digit reversal).
-template <class Ring>
+template <class N, class Ring>
 __device__ void fft_dif(Ring ring, const FftPlanDev &fp) {
   int L = fp.len;
   for (int i = 0; i < fp.nrad; ++i) {
-    fft_stage_any<false>(ring, fp.len, L, fp.rad[i], fp.w);
+    fft_stage_any<false, N>(ring, fp.len, L, fp.rad[i], N::tw(fp));
     L /= fp.rad[i];
   }
 }
 
 // The transpose of fft_dif (its passes transposed, in reverse order): input
 // z_k at position fp.pos[k], output the forward DFT of z in natural order.
-template <class Ring>
+template <class N, class Ring>
 __device__ void fft_dit(Ring ring, const FftPlanDev &fp) {
   int L = 1;
   for (int i = fp.nrad - 1; i >= 0; --i) {
     L *= fp.rad[i];
-    fft_stage_any<true>(ring, fp.len, L, fp.rad[i], fp.w);
+    fft_stage_any<true, N>(ring, fp.len, L, fp.rad[i], N::tw(fp));
   }
 }
 
@@ -273,30 +397,32 @@ __device__ void fft_dit(Ring ring, const FftPlanDev &fp) {
 // a kernel whose spectrum was made by fft_dif (so it is digit-reversed like the
 // data): DIF, pointwise product, then the inverse as conj(DIT(conj)), which
 // returns to natural order with no permutation pass.
-template <class Ring>
-__device__ void dft_run(Ring ring, const FftPlanDev &fp, double2 *sh_x0, double2 *sh_a0) {
-  double2 *const buf = ring.at(0);
-  fft_dif(ring, fp);
+template <class N, class Ring>
+__device__ void dft_run(Ring ring, const FftPlanDev &fp, typename N::C *sh_x0, typename N::C *sh_a0) {
+  typename N::C *const buf = ring.at(0);
+  fft_dif<N>(ring, fp);
   if (fp.kind == 0) return;
   if (fp.kind == 1 && threadIdx.x == 0) *sh_a0 = buf[0];  // X_0 sits at position 0
   __syncthreads();
-  for (int i = threadIdx.x; i < fp.len; i += blockDim.x) buf[i] = cconj(cmul(buf[i], fp.spec[i]));
+  const typename N::C *spec = N::spec(fp);
+  for (int i = threadIdx.x; i < fp.len; i += blockDim.x) buf[i] = N::conj(N::mul(buf[i], N::ldg(spec + i)));
   __syncthreads();
-  fft_dit(ring, fp);
+  fft_dit<N>(ring, fp);
 }
 
-__device__ __forceinline__ double2 dft_at(const double2 *buf, const FftPlanDev &fp, int k, double2 x0,
-                                          double2 a0) {
+template <class N>
+__device__ __forceinline__ typename N::C dft_at(const typename N::C *buf, const FftPlanDev &fp, int k,
+                                                typename N::C x0, typename N::C a0) {
   if (fp.kind == 0) return buf[__ldg(fp.pos + k)];
   if (fp.kind == 1) {
-    if (k == 0) return cadd(x0, a0);
-    return cadd(x0, cconj(buf[fp.inv_out[k]]));
+    if (k == 0) return N::add(x0, a0);
+    return N::add(x0, N::conj(buf[fp.inv_out[k]]));
   }
-  return cmul(fp.chirp[k], cconj(buf[k]));
+  return N::mul(N::ldg(N::chirp(fp) + k), N::conj(buf[k]));
 }
 
 // ---------------------------------------------------------------------------
-// spectrum precomputation (plan time): dst = scale * DFT_len(src)
+// spectrum precomputation (plan time, FP64): dst = scale * DFT_len(src)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFftThreads) spectrum_kernel(const FftPlanDev *fpd, const double2 *src,
                                                               double2 *dst, int len, double scale) {
@@ -304,7 +430,7 @@ __global__ void __launch_bounds__(kFftThreads) spectrum_kernel(const FftPlanDev 
   const FftPlanDev fp = *fpd;
   for (int i = threadIdx.x; i < len; i += blockDim.x) buf[i] = src[i];
   __syncthreads();
-  fft_dif(SharedRing{}, fp);
+  fft_dif<F64>(SharedRing<double2>{}, fp);
   for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = make_double2(buf[i].x * scale, buf[i].y * scale);
 }
 // the same for lengths beyond shared memory: transformed in place in dst
@@ -313,7 +439,7 @@ __global__ void __launch_bounds__(kFftThreads) spectrum_kernel_global(const FftP
   const FftPlanDev fp = *fpd;
   for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
   __syncthreads();
-  fft_dif(GlobalRing{dst}, fp);
+  fft_dif<F64>(GlobalRing<double2>{dst}, fp);
   for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = make_double2(dst[i].x * scale, dst[i].y * scale);
 }
 
@@ -385,37 +511,40 @@ __device__ double2 spectrum_at(const FftArgs &a, int j, int p, int k, int N, dou
   return z;
 }
 
-template <class Ring>
+template <class N, class Ring>
 __device__ __forceinline__ void fft_syn_kernel_body(Ring ring, const FftArgs &a, double *const *ptrs, const int p,
                                      const int j) {
-  double2 *const buf = ring.at(0);
-  __shared__ double2 sh_x0, sh_a0;
+  using C = typename N::C;
+  C *const buf = ring.at(0);
+  __shared__ C sh_x0, sh_a0;
   const FftPlanDev fp = a.plans[a.pair_fft[p]];
   const int2 rr = a.pair_rings[p];
   const RingDev rn = a.rings[rr.x];
   const bool south = rr.y >= 0;
   const RingDev rs = a.rings[south ? rr.y : rr.x];
-  const int N = fp.n;
+  const int Nphi = fp.n;
   // inverse DFT via conj(DFT(conj(Z)))
   if (fp.kind == 0) {
-    for (int k = threadIdx.x; k < N; k += blockDim.x)
-      buf[k] = cconj(spectrum_at(a, j, p, k, N, rn.phi0, rs.phi0, south));
+    for (int k = threadIdx.x; k < Nphi; k += blockDim.x)
+      buf[k] = N::of(cconj(spectrum_at(a, j, p, k, Nphi, rn.phi0, rs.phi0, south)));
   } else if (fp.kind == 1) {
-    for (int q = threadIdx.x; q < N - 1; q += blockDim.x)
-      buf[q] = cconj(spectrum_at(a, j, p, fp.perm_in[q], N, rn.phi0, rs.phi0, south));
-    if (threadIdx.x == 0) sh_x0 = cconj(spectrum_at(a, j, p, 0, N, rn.phi0, rs.phi0, south));
+    for (int q = threadIdx.x; q < Nphi - 1; q += blockDim.x)
+      buf[q] = N::of(cconj(spectrum_at(a, j, p, fp.perm_in[q], Nphi, rn.phi0, rs.phi0, south)));
+    if (threadIdx.x == 0) sh_x0 = N::of(cconj(spectrum_at(a, j, p, 0, Nphi, rn.phi0, rs.phi0, south)));
   } else {
+    const C *chirp = N::chirp(fp);
     for (int k = threadIdx.x; k < fp.len; k += blockDim.x)
-      buf[k] = (k < N) ? cmul(cconj(spectrum_at(a, j, p, k, N, rn.phi0, rs.phi0, south)), fp.chirp[k])
-                       : make_double2(0.0, 0.0);
+      buf[k] = (k < Nphi)
+                   ? N::mul(N::of(cconj(spectrum_at(a, j, p, k, Nphi, rn.phi0, rs.phi0, south))), N::ldg(chirp + k))
+                   : N::zero();
   }
   __syncthreads();
-  dft_run(ring, fp, &sh_x0, &sh_a0);
-  const double2 x0 = sh_x0, a0 = sh_a0;
+  dft_run<N>(ring, fp, &sh_x0, &sh_a0);
+  const C x0 = sh_x0, a0 = sh_a0;
   double *mp = ptrs[j];
   const double wn = a.weighted ? rn.weight : 1.0, ws = a.weighted ? rs.weight : 1.0;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    const double2 X = dft_at(buf, fp, x, x0, a0);
+  for (int x = threadIdx.x; x < Nphi; x += blockDim.x) {
+    const double2 X = N::val(dft_at<N>(buf, fp, x, x0, a0));
     // z = conj(X): north = Re z, south = Im z
     double vn = X.x * wn;
     double *on = mp + rn.ofs + (int64_t)x * rn.stride;
@@ -429,30 +558,33 @@ __device__ __forceinline__ void fft_syn_kernel_body(Ring ring, const FftArgs &a,
     }
   }
 }
+template <class N>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) fft_syn_kernel(FftArgs a) {
-  fft_syn_kernel_body(SharedRing{}, a, a.map.p, a.pair0 + blockIdx.x, blockIdx.y);
+  fft_syn_kernel_body<N>(SharedRing<typename N::C>{}, a, a.map.p, a.pair0 + blockIdx.x, blockIdx.y);
 }
+template <class N>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) fft_syn_kernel_batch(const FftArgs *__restrict__ args,
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const FftArgs &a = args[it.w];
-  fft_syn_kernel_body(SharedRing{}, a, tbl.p + a.ptr_off, it.x, it.y);
+  fft_syn_kernel_body<N>(SharedRing<typename N::C>{}, a, tbl.p + a.ptr_off, it.x, it.y);
 }
 
 // ---------------------------------------------------------------------------
 // analysis: ring pixels -> G (per m)
 // ---------------------------------------------------------------------------
-template <class Ring>
+template <class N, class Ring>
 __device__ __forceinline__ void fft_ana_kernel_body(Ring ring, const FftArgs &a, double *const *ptrs, const int p,
                                      const int j) {
-  double2 *const buf = ring.at(0);
-  __shared__ double2 sh_x0, sh_a0;
+  using C = typename N::C;
+  C *const buf = ring.at(0);
+  __shared__ C sh_x0, sh_a0;
   const FftPlanDev fp = a.plans[a.pair_fft[p]];
   const int2 rr = a.pair_rings[p];
   const RingDev rn = a.rings[rr.x];
   const bool south = rr.y >= 0;
   const RingDev rs = a.rings[south ? rr.y : rr.x];
-  const int N = fp.n;
+  const int Nphi = fp.n;
   const double *mp = ptrs[j];
   auto zin = [&](int x) {
     const double vn = mp[rn.ofs + (int64_t)x * rn.stride];
@@ -460,22 +592,23 @@ __device__ __forceinline__ void fft_ana_kernel_body(Ring ring, const FftArgs &a,
     return make_double2(vn, vs);
   };
   if (fp.kind == 0) {
-    for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = zin(k);
+    for (int k = threadIdx.x; k < Nphi; k += blockDim.x) buf[k] = N::of(zin(k));
   } else if (fp.kind == 1) {
-    for (int q = threadIdx.x; q < N - 1; q += blockDim.x) buf[q] = zin(fp.perm_in[q]);
-    if (threadIdx.x == 0) sh_x0 = zin(0);
+    for (int q = threadIdx.x; q < Nphi - 1; q += blockDim.x) buf[q] = N::of(zin(fp.perm_in[q]));
+    if (threadIdx.x == 0) sh_x0 = N::of(zin(0));
   } else {
+    const C *chirp = N::chirp(fp);
     for (int k = threadIdx.x; k < fp.len; k += blockDim.x)
-      buf[k] = (k < N) ? cmul(zin(k), fp.chirp[k]) : make_double2(0.0, 0.0);
+      buf[k] = (k < Nphi) ? N::mul(N::of(zin(k)), N::ldg(chirp + k)) : N::zero();
   }
   __syncthreads();
-  dft_run(ring, fp, &sh_x0, &sh_a0);
-  const double2 x0 = sh_x0, a0 = sh_a0;
+  dft_run<N>(ring, fp, &sh_x0, &sh_a0);
+  const C x0 = sh_x0, a0 = sh_a0;
   const double wn = a.weighted ? rn.weight : 1.0, ws = a.weighted ? rs.weight : 1.0;
   for (int mi = threadIdx.x; mi < a.nm; mi += blockDim.x) {
     const int m = a.mval[mi];
-    const int k = m % N, kn = (N - k) % N;
-    const double2 Zk = dft_at(buf, fp, k, x0, a0), Zn = cconj(dft_at(buf, fp, kn, x0, a0));
+    const int k = m % Nphi, kn = (Nphi - k) % Nphi;
+    const double2 Zk = N::val(dft_at<N>(buf, fp, k, x0, a0)), Zn = cconj(N::val(dft_at<N>(buf, fp, kn, x0, a0)));
     // P_N = (Zk + conj Zn)/2,  P_S = (Zk - conj Zn)/(2i)
     const double2 pn = make_double2(0.5 * (Zk.x + Zn.x), 0.5 * (Zk.y + Zn.y));
     const double2 d = make_double2(Zk.x - Zn.x, Zk.y - Zn.y);
@@ -492,33 +625,39 @@ __device__ __forceinline__ void fft_ana_kernel_body(Ring ring, const FftArgs &a,
     g[1] = gs;
   }
 }
+template <class N>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) fft_ana_kernel(FftArgs a) {
-  fft_ana_kernel_body(SharedRing{}, a, a.map.p, a.pair0 + blockIdx.x, blockIdx.y);
+  fft_ana_kernel_body<N>(SharedRing<typename N::C>{}, a, a.map.p, a.pair0 + blockIdx.x, blockIdx.y);
 }
+template <class N>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) fft_ana_kernel_batch(const FftArgs *__restrict__ args,
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const FftArgs &a = args[it.w];
-  fft_ana_kernel_body(SharedRing{}, a, tbl.p + a.ptr_off, it.x, it.y);
+  fft_ana_kernel_body<N>(SharedRing<typename N::C>{}, a, tbl.p + a.ptr_off, it.x, it.y);
 }
 
 // Rings longer than shared memory holds: a persistent grid, each CTA owning one
 // scratch slot of slot_len points, walks the (pair, map) items in turn.
+template <class N>
 __global__ void __launch_bounds__(kFftThreads) fft_syn_kernel_global(FftArgs a, double2 *scratch,
                                                                      int slot_len) {
-  const GlobalRing ring{scratch + (size_t)blockIdx.x * slot_len};
+  using C = typename N::C;
+  const GlobalRing<C> ring{reinterpret_cast<C *>(scratch + (size_t)blockIdx.x * slot_len)};
   const int n = a.npairs_run * a.nmaps_run;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    fft_syn_kernel_body(ring, a, a.map.p, a.pair0 + it % a.npairs_run, it / a.npairs_run);
+    fft_syn_kernel_body<N>(ring, a, a.map.p, a.pair0 + it % a.npairs_run, it / a.npairs_run);
     __syncthreads();  // the slot is rewritten by the next item
   }
 }
+template <class N>
 __global__ void __launch_bounds__(kFftThreads) fft_ana_kernel_global(FftArgs a, double2 *scratch,
                                                                      int slot_len) {
-  const GlobalRing ring{scratch + (size_t)blockIdx.x * slot_len};
+  using C = typename N::C;
+  const GlobalRing<C> ring{reinterpret_cast<C *>(scratch + (size_t)blockIdx.x * slot_len)};
   const int n = a.npairs_run * a.nmaps_run;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    fft_ana_kernel_body(ring, a, a.map.p, a.pair0 + it % a.npairs_run, it / a.npairs_run);
+    fft_ana_kernel_body<N>(ring, a, a.map.p, a.pair0 + it % a.npairs_run, it / a.npairs_run);
     __syncthreads();
   }
 }
@@ -555,13 +694,20 @@ cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, i
   a.add = add;
   a.pair0 = p0;
   a.npairs_run = p1 - p0;
+  const bool df = P->precision == SHT_MIXED;
   if (P->d_fft_scratch) {
     const int g = (int)std::min<int64_t>((int64_t)a.npairs_run * P->nmaps, P->fft_slots);
-    fft_syn_kernel_global<<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
+    if (df)
+      fft_syn_kernel_global<DF><<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
+    else
+      fft_syn_kernel_global<F64><<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
     return cudaGetLastError();
   }
   dim3 grid(a.npairs_run, P->nmaps);
-  fft_syn_kernel<<<grid, kFftThreads, P->fft_smem, st>>>(a);
+  if (df)
+    fft_syn_kernel<DF><<<grid, kFftThreads, P->fft_smem, st>>>(a);
+  else
+    fft_syn_kernel<F64><<<grid, kFftThreads, P->fft_smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -573,13 +719,20 @@ cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted
   a.weighted = weighted;
   a.pair0 = p0;
   a.npairs_run = p1 - p0;
+  const bool df = P->precision == SHT_MIXED;
   if (P->d_fft_scratch) {
     const int g = (int)std::min<int64_t>((int64_t)a.npairs_run * P->nmaps, P->fft_slots);
-    fft_ana_kernel_global<<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
+    if (df)
+      fft_ana_kernel_global<DF><<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
+    else
+      fft_ana_kernel_global<F64><<<g, kFftThreads, 0, st>>>(a, P->d_fft_scratch, P->fft_slot_len);
     return cudaGetLastError();
   }
   dim3 grid(a.npairs_run, P->nmaps);
-  fft_ana_kernel<<<grid, kFftThreads, P->fft_smem, st>>>(a);
+  if (df)
+    fft_ana_kernel<DF><<<grid, kFftThreads, P->fft_smem, st>>>(a);
+  else
+    fft_ana_kernel<F64><<<grid, kFftThreads, P->fft_smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -611,19 +764,27 @@ cudaError_t fft_prepare_device(int device) {
   cudaError_t e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e == cudaSuccess) {  // radix constants, from long double
     static double hc[kMaxRadix + 1][kMaxRadix / 2 + 1], hs[kMaxRadix + 1][kMaxRadix / 2 + 1];
+    static float2 hc2[kMaxRadix + 1][kMaxRadix / 2 + 1], hs2[kMaxRadix + 1][kMaxRadix / 2 + 1];
     const long double pi = 3.141592653589793238462643383279502884L;
     for (int R = 3; R <= kMaxRadix; R += 2)
       for (int t = 1; t <= R / 2; ++t) {
-        hc[R][t] = (double)cosl(2.0L * pi * t / R);
-        hs[R][t] = (double)sinl(2.0L * pi * t / R);
+        const long double c = cosl(2.0L * pi * t / R), s = sinl(2.0L * pi * t / R);
+        hc[R][t] = (double)c;
+        hs[R][t] = (double)s;
+        hc2[R][t] = make_float2((float)c, (float)(c - (float)c));
+        hs2[R][t] = make_float2((float)s, (float)(s - (float)s));
       }
     e = cudaMemcpyToSymbol(c_cos, hc, sizeof(hc));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sin, hs, sizeof(hs));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cos2, hc2, sizeof(hc2));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sin2, hs2, sizeof(hs2));
   }
-  const void *fns[5] = {(const void *)fft_syn_kernel, (const void *)fft_ana_kernel,
-                        (const void *)fft_syn_kernel_batch, (const void *)fft_ana_kernel_batch,
+  const void *fns[9] = {(const void *)fft_syn_kernel<F64>,       (const void *)fft_ana_kernel<F64>,
+                        (const void *)fft_syn_kernel_batch<F64>, (const void *)fft_ana_kernel_batch<F64>,
+                        (const void *)fft_syn_kernel<DF>,        (const void *)fft_ana_kernel<DF>,
+                        (const void *)fft_syn_kernel_batch<DF>,  (const void *)fft_ana_kernel_batch<DF>,
                         (const void *)spectrum_kernel};
-  for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
     // static + dynamic shared memory may not exceed the opt-in size
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, fns[i]);
@@ -634,15 +795,23 @@ cudaError_t fft_prepare_device(int device) {
   return e;
 }
 
-// synthesis (stage 0) or analysis (stage 1) ring FFTs of every item (pair, map, -, args index)
-cudaError_t launch_fft_batch(int stage, const void *args, const int4 *items, int n, int smem, const PtrTable &tbl,
-                             cudaStream_t st) {
+// synthesis (stage 0) or analysis (stage 1) ring FFTs of every item (pair, map, -, args index),
+// in double-float (df: items of mixed plans) or FP64
+cudaError_t launch_fft_batch(int stage, bool df, const void *args, const int4 *items, int n, int smem,
+                             const PtrTable &tbl, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const FftArgs *a = static_cast<const FftArgs *>(args);
-  if (stage == 0)
-    fft_syn_kernel_batch<<<n, kFftThreads, smem, st>>>(a, items, tbl);
-  else
-    fft_ana_kernel_batch<<<n, kFftThreads, smem, st>>>(a, items, tbl);
+  if (stage == 0) {
+    if (df)
+      fft_syn_kernel_batch<DF><<<n, kFftThreads, smem, st>>>(a, items, tbl);
+    else
+      fft_syn_kernel_batch<F64><<<n, kFftThreads, smem, st>>>(a, items, tbl);
+  } else {
+    if (df)
+      fft_ana_kernel_batch<DF><<<n, kFftThreads, smem, st>>>(a, items, tbl);
+    else
+      fft_ana_kernel_batch<F64><<<n, kFftThreads, smem, st>>>(a, items, tbl);
+  }
   return cudaGetLastError();
 }
 

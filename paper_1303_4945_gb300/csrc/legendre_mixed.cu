@@ -6,8 +6,9 @@
 // (value = hi + lo, two FP32 numbers).  Products use the exact FMA split
 // (Dekker / Kahan two-product), sums Knuth's two-sum; about 46 significant
 // bits survive per operation, enough for ~1e-12 after thousands of steps.
-// FP64 remains for the recursion-coefficient tables, the start values, the
-// conversion of inputs/outputs and the ring FFTs.
+// FP64 remains for the recursion-coefficient tables, the start values and the
+// conversion of inputs/outputs (the ring FFTs of mixed plans run the same
+// double-float arithmetic, in fft.cu).
 //
 // Structure, ring pairing, parity split, the separate +s / -s recursions for
 // spin and the analysis reduction follow legendre_fp64.cu; only the arithmetic
@@ -15,6 +16,7 @@
 // are scaled down every 8 steps; values at scale 0 and -1 are accumulated (the
 // latter times 2^-104), anything smaller is negligible.  A mixed plan hands the
 // items of small m near the poles to the FP64 kernels (sht_plan_s::fp64_m_below).
+#include "df.cuh"
 #include "sht_device.cuh"
 
 namespace sht {
@@ -22,37 +24,6 @@ namespace sht {
 constexpr int kScaleStep32 = 104;
 constexpr float kScaleUp32 = 0x1p+52f;
 constexpr float kScaleFactor32 = 0x1p-104f;
-
-// ---- double-float arithmetic (no contraction: *_rn intrinsics) -------------
-struct f2 {
-  float h, l;
-};
-
-__device__ __forceinline__ f2 f2_of(double v) {
-  const float h = __double2float_rn(v);
-  return {h, __double2float_rn(v - (double)h)};
-}
-__device__ __forceinline__ double f2_val(f2 a) { return (double)a.h + (double)a.l; }
-
-__device__ __forceinline__ f2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // needs |a| >= |b| (or a = 0)
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-// a * b as an unevaluated pair
-__device__ __forceinline__ f2 mul(f2 a, f2 b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  return {p, e};
-}
-__device__ __forceinline__ f2 neg(f2 a) { return {-a.h, -a.l}; }
 
 // cos(theta) as three floats summing exactly to the FP64 value.  Next to the
 // poles x = 1 - O(theta^2) and a two-float x would carry a fixed error of
@@ -76,15 +47,6 @@ __device__ __forceinline__ f2 mul(f2 a, f3 x) {
   e = __fmaf_rn(a.h, x.m, e);
   return {p, e};
 }
-// a b + c d, normalised.  The final fast two-sum is needed: when the
-// recursion's terms cancel (oscillatory regime) the low word of the raw sum
-// can be as large as the high word, and the next product would then drop
-// bits at FP32 precision.
-__device__ __forceinline__ f2 dot2(f2 a, f2 b, f2 c, f2 d) {
-  const f2 p = mul(a, b), q = mul(c, d);
-  const f2 s = two_sum(p.h, q.h);
-  return fast_two_sum(s.h, __fadd_rn(__fadd_rn(p.l, q.l), s.l));
-}
 // a b + c d + e f, normalised (see dot2)
 __device__ __forceinline__ f2 dot3(f2 a, f2 b, f2 c, f2 d, f2 e, f2 f) {
   const f2 p = mul(a, b), q = mul(c, d), r = mul(e, f);
@@ -98,17 +60,6 @@ __device__ __forceinline__ void acc_mul(f2 &acc, f2 w, float ah, float al) {
   const f2 s = two_sum(acc.h, p.h);
   acc.h = s.h;
   acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, p.l));
-}
-__device__ __forceinline__ void renorm(f2 &a) { a = fast_two_sum(a.h, a.l); }
-// a + b with the low word carried unnormalised (a running sum of a few dozen
-// terms: the low word stays within a few ulps of the high word's last bit)
-__device__ __forceinline__ f2 f2_add_lazy(f2 a, f2 b) {
-  const f2 s = two_sum(a.h, b.h);
-  return {s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l)};
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-  const f2 s = two_sum(a.h, b.h);
-  return fast_two_sum(s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l));
 }
 // Accumulation weight of a recursion value y held at the given scale.  The
 // exponent is checked every 8 steps, so a value still labelled scale -1 may

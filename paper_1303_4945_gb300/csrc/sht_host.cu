@@ -548,6 +548,28 @@ static std::vector<double2> twiddles(int len) {
   return w;
 }
 
+// e^{-2 pi i k / len} as hi/lo float pairs, from long double
+static std::vector<float4> twiddles_f(int len) {
+  std::vector<float4> w(len);
+  for (int k = 0; k < len; ++k) {
+    const long double a = -2.0L * kPiL * k / len, c = cosl(a), s = sinl(a);
+    w[k] = make_float4((float)c, (float)(c - (float)c), (float)s, (float)(s - (float)s));
+  }
+  return w;
+}
+
+// an FP64 table on the device as hi/lo float pairs (the double-float engine's copy)
+static int upload_pairs(sht_plan_s *P, const double2 *d, int len, const float4 **out) {
+  std::vector<double2> h(len);
+  CUDA_TRY(cudaMemcpy(h.data(), d, len * sizeof(double2), cudaMemcpyDeviceToHost));
+  std::vector<float4> f(len);
+  for (int i = 0; i < len; ++i) {
+    const float rh = (float)h[i].x, ih = (float)h[i].y;
+    f[i] = make_float4(rh, (float)(h[i].x - (double)rh), ih, (float)(h[i].y - (double)ih));
+  }
+  return dev_upload(P, f, out);
+}
+
 static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scratch_dev) {
   memset(&fp, 0, sizeof(fp));
   fp.n = n;
@@ -643,6 +665,11 @@ static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scra
     CUDA_TRY(cudaMemcpy(scratch_dev, &fp, sizeof(fp), cudaMemcpyHostToDevice));
     CUDA_TRY(launch_fft_spectrum(&fp, scratch_dev, dh, (double2 *)ds, M, 1.0 / M, 0));
     CUDA_TRY(cudaDeviceSynchronize());
+  }
+  if (P->precision == SHT_MIXED) {  // the double-float engine's tables
+    if ((rc = dev_upload(P, twiddles_f(fp.len), &fp.wf)) != SHT_OK) return rc;
+    if (fp.kind != 0 && (rc = upload_pairs(P, fp.spec, fp.len, &fp.specf)) != SHT_OK) return rc;
+    if (fp.kind == 2 && (rc = upload_pairs(P, fp.chirp, n, &fp.chirpf)) != SHT_OK) return rc;
   }
   return SHT_OK;
 }

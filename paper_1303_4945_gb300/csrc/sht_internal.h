@@ -72,6 +72,9 @@ struct FftPlanDev {
   const int *inv_out;    // Rader: index p with g^{-p} = k, for k = 1..n-1
   const double2 *spec;   // Rader / Bluestein kernel spectrum (1/len folded in)
   const double2 *chirp;  // Bluestein: e^{-pi i k^2 / n}
+  // the same three tables as hi/lo float pairs (re.h, re.l, im.h, im.l) for the
+  // double-float engine of mixed plans (null in FP64 plans)
+  const float4 *wf, *specf, *chirpf;
 };
 
 struct DevPtrs {
@@ -268,6 +271,6 @@ cudaError_t launch_leg_fp64_batch(int stage, int spin, int nj, int ppt, const vo
                                   int n, const PtrTable &tbl, cudaStream_t st);
 cudaError_t launch_leg_mixed_batch(int stage, int spin, int nj, int ppt, const void *args, const int4 *items,
                                    int n, const PtrTable &tbl, cudaStream_t st);
-cudaError_t launch_fft_batch(int stage, const void *args, const int4 *items, int n, int smem, const PtrTable &tbl,
-                             cudaStream_t st);
+cudaError_t launch_fft_batch(int stage, bool df, const void *args, const int4 *items, int n, int smem,
+                             const PtrTable &tbl, cudaStream_t st);
 }  // namespace sht

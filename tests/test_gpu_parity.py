@@ -122,16 +122,20 @@ def test_healpix_aliasing(sht, spin):
     check_pair(sht, sht.sht_geom_healpix(8), 28, 28, spin, seed=10 + abs(spin), with_adjoint=True)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("nlon,spin", [(37, 0), (53, 2), (94, 0), (94, 2), (255, 1), (1517, 0), (131, 0), (149, 2),
-                                       (3527, 0), (262, 0), (2367, 2)])
-def test_fft_lengths(sht, nlon, spin):
+                                       (3527, 0), (262, 0), (2367, 2), (4199, 0)])
+def test_fft_lengths(sht, nlon, spin, precision):
     # direct: 37, 53 (one radix above 31), 94 = 2 47, 255 = 3 5 17, 1517 = 37 41 (a
     # twiddled large-radix pass); Rader: 131 (130 = 2 5 13), 149 (148 = 4 37),
     # 3527 (3526 = 2 41 43: a twiddled large-radix pass in the transposed passes);
     # Bluestein: 262 = 2 131 (convolution of 525), 2367 = 3 3 263 (convolution of
-    # 4736 = 4^3 2 37)
+    # 4736 = 4^3 2 37); 4199 = 13 17 19 (radices the double-float engine runs as
+    # sweeps).  Both engines: FP64 (precision 0) and double-float (mixed plans).
     lmax = min(30, (nlon - 1) // 2)
-    check_pair(sht, sht.sht_geom_gauss(lmax + 1 + (nlon % 2), nlon), lmax, lmax, spin, seed=nlon)
+    tol = dict(l2=MIX_L2, mx=MIX_MAX) if precision else {}
+    check_pair(sht, sht.sht_geom_gauss(lmax + 1 + (nlon % 2), nlon), lmax, lmax, spin, seed=nlon,
+               precision=precision, **tol)
 
 
 @pytest.mark.parametrize("nlat", [1, 3, 33])
@@ -330,13 +334,15 @@ def test_mixed_config1_round_trip(sht):
     assert rel_l2(back, alm[0]) < MIX_L2
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("nlon", [14803, 16383, 20011, 20480])
-def test_long_rings(sht, nlon):
+def test_long_rings(sht, nlon, precision):
     # rings longer than one CTA's shared memory holds run from a global scratch
     # slot: 14803 = 113 131 (Bluestein at 29624), 16383 = 3 43 127 (radices 43
     # and 127), 20011 prime (Rader over 20010 = 2 3 5 23 29), 20480 = 2^12 5
-    check_pair(sht, sht.sht_geom_gauss(30, nlon), 28, 28, 0, seed=nlon, with_adjoint=True)
-    check_pair(sht, sht.sht_geom_gauss(23, nlon), 20, 20, 2, seed=nlon + 1)
+    tol = dict(l2=MIX_L2, mx=MIX_MAX) if precision else {}
+    check_pair(sht, sht.sht_geom_gauss(30, nlon), 28, 28, 0, seed=nlon, with_adjoint=True, precision=precision, **tol)
+    check_pair(sht, sht.sht_geom_gauss(23, nlon), 20, 20, 2, seed=nlon + 1, precision=precision, **tol)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
