@@ -40,10 +40,12 @@ LMAX = NLAT = NLON = METRIC = CONFIG = None
 SMS = 152
 
 
-def set_workload(lmax):
-    """GL nlat = lmax + 1, nlon = 2 lmax + 1; lmax 4095 is the headline configuration."""
+def set_workload(lmax, nlat=None):
+    """GL nlat = lmax + 1, nlon = 2 lmax + 1; lmax 4095 is the headline configuration.
+    A smaller nlat (profiling captures: the same rings, fewer of them) is not exact
+    quadrature and not a headline configuration."""
     global LMAX, NLAT, NLON, METRIC, CONFIG
-    LMAX, NLAT, NLON = lmax, lmax + 1, 2 * lmax + 1
+    LMAX, NLAT, NLON = lmax, nlat or lmax + 1, 2 * lmax + 1
     METRIC = f"ms per synth+analysis at lmax {LMAX} (spin 2, GL {NLAT}x{NLON})"
     nalm = (LMAX + 1) * (LMAX + 2) // 2
     big = 16 * 2 * nalm > 129e6 and 8 * 2 * NLAT * NLON > 129e6
@@ -506,11 +508,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--lmax", type=int, default=4095, help="smaller sizes for profiling captures")
+    ap.add_argument("--nlat", type=int, default=None,
+                    help="fewer rings of the same length for profiling captures (default lmax + 1)")
     ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad"],
                     help="spin2: the headline (spin-2 lmax 4095 pair); batch: 64 uneven scalar problems + "
                          "8 maps at lmax 2047 in one batch; grad: loss + gradient at lmax 8191")
     args = ap.parse_args()
-    set_workload(args.lmax)
+    set_workload(args.lmax, args.nlat)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -87,6 +87,12 @@ struct F64 {
   static __device__ __forceinline__ C ldg(const C *p) { return __ldg(p); }
   static __device__ __forceinline__ C of(double2 v) { return v; }
   static __device__ __forceinline__ double2 val(C v) { return v; }
+  static __device__ __forceinline__ S scalar(double v) { return v; }
+  static __device__ __forceinline__ C half(C a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+  static __device__ __forceinline__ C times_minus_i(C a) { return make_double2(a.y, -a.x); }
+  static __device__ __forceinline__ C times_i(C a) { return make_double2(-a.y, a.x); }
+  static __device__ __forceinline__ C scale(C a, S w) { return make_double2(a.x * w, a.y * w); }
+  static __device__ __forceinline__ C scale2(C a, S wr, S wi) { return make_double2(a.x * wr, a.y * wi); }
   static __device__ __forceinline__ const C *tw(const FftPlanDev &fp) { return fp.w; }
   static __device__ __forceinline__ const C *spec(const FftPlanDev &fp) { return fp.spec; }
   static __device__ __forceinline__ const C *chirp(const FftPlanDev &fp) { return fp.chirp; }
@@ -130,8 +136,19 @@ struct DF {
     return {c.x, c.y};
   }
   static __device__ __forceinline__ C ldg(const C *p) { return {__ldg(&p->v)}; }
-  static __device__ __forceinline__ C of(double2 v) { return mk(f2_of(v.x), f2_of(v.y)); }
-  static __device__ __forceinline__ double2 val(C a) { return make_double2(f2_val(re(a)), f2_val(im(a))); }
+  static __device__ __forceinline__ C of(double2 v) { return mk(f2_split(v.x), f2_split(v.y)); }
+  static __device__ __forceinline__ double2 val(C a) { return make_double2(f2_join(re(a)), f2_join(im(a))); }
+  static __device__ __forceinline__ S scalar(double v) { return f2_of(v); }
+  static __device__ __forceinline__ C half(C a) {  // exact (outside FP32's subnormal range)
+    return {make_float4(0.5f * a.v.x, 0.5f * a.v.y, 0.5f * a.v.z, 0.5f * a.v.w)};
+  }
+  static __device__ __forceinline__ C times_minus_i(C a) { return {make_float4(a.v.z, a.v.w, -a.v.x, -a.v.y)}; }
+  static __device__ __forceinline__ C times_i(C a) { return {make_float4(-a.v.z, -a.v.w, a.v.x, a.v.y)}; }
+  static __device__ __forceinline__ C scale(C a, S w) { return scale2(a, w, w); }
+  static __device__ __forceinline__ C scale2(C a, S wr, S wi) {  // real part times wr, imaginary part times wi
+    const f2 r = sht::mul(re(a), wr), i = sht::mul(im(a), wi);
+    return mk(fast_two_sum(r.h, r.l), fast_two_sum(i.h, i.l));
+  }
   static __device__ __forceinline__ const C *tw(const FftPlanDev &fp) { return reinterpret_cast<const C *>(fp.wf); }
   static __device__ __forceinline__ const C *spec(const FftPlanDev &fp) {
     return reinterpret_cast<const C *>(fp.specf);
@@ -455,8 +472,10 @@ cudaError_t launch_fft_spectrum(const FftPlanDev *hp, const FftPlanDev *dp, cons
 }
 
 // e^{i m phi0} with the product m*phi0 carried to ~1e-32 before the sincos
+// (callers skip rings with phi0 = 0; no FP64 compare here, which the compiler
+// would hoist ahead of their test and issue for every coefficient)
 __device__ __forceinline__ double2 phase_of(int m, double phi0) {
-  if (phi0 == 0.0 || m == 0) return make_double2(1.0, 0.0);
+  if (m == 0) return make_double2(1.0, 0.0);
   const double dm = (double)m;
   const double hi = dm * phi0;
   const double lo = fma(dm, phi0, -hi);
@@ -485,29 +504,50 @@ struct FftArgs {
 // ---------------------------------------------------------------------------
 // synthesis: F (per m) -> ring pixels
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double2 synth_coef(const FftArgs &a, int j, int p, int m, double phi_n, double phi_s,
-                                              bool south, bool conj_) {
-  // cN + i cS for coefficient m of the two rings (conj_: conj(cN) + i conj(cS));
-  // F below the first pair the Legendre stage processed for this m is zero.
+// The term of coefficient m for one ring pair, conj?(cN) + i conj?(cS) (conj_ for
+// the m < 0 half of the sum), in the engine's arithmetic; F below the first pair
+// the Legendre stage processed for this m is zero.  (ph_n, ph_s: the rings' phi0
+// are nonzero; rings with phi0 = 0 skip the phase products.)
+template <class N>
+__device__ __forceinline__ typename N::C synth_term(const FftArgs &a, int j, int p, int m, double phi_n,
+                                                    double phi_s, bool south, bool conj_, bool ph_n, bool ph_s) {
+  using C = typename N::C;
   const int mi = a.minv[m];
-  if (mi < 0 || p < a.syn_first[mi]) return make_double2(0.0, 0.0);
+  if (mi < 0 || p < a.syn_first[mi]) return N::zero();
   const double2 *f = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
-  double2 cn = cmul(f[0], phase_of(m, phi_n));
-  double2 cs = south ? cmul(f[1], phase_of(m, phi_s)) : make_double2(0.0, 0.0);
-  if (conj_) {
-    cn = cconj(cn);
-    cs = cconj(cs);
+  double2 cn = f[0];
+  if (ph_n) cn = cmul(cn, phase_of(m, phi_n));
+  C z = N::of(cn);
+  if (conj_) z = N::conj(z);
+  if (south) {
+    double2 cs = f[1];
+    if (ph_s) cs = cmul(cs, phase_of(m, phi_s));
+    C zs = N::of(cs);
+    if (conj_) zs = N::conj(zs);
+    z = N::add(z, N::times_i(zs));
   }
-  return make_double2(cn.x - cs.y, cn.y + cs.x);
+  return z;
 }
 
-// Z_k = sum_{m >= 0, m = k mod N} (cN_m + i cS_m) + sum_{m >= 1, -m = k mod N} (conj cN_m + i conj cS_m)
-__device__ double2 spectrum_at(const FftArgs &a, int j, int p, int k, int N, double phi_n, double phi_s,
-                               bool south) {
-  double2 z = make_double2(0.0, 0.0);
-  for (int m = k; m <= a.mmax; m += N) z = cadd(z, synth_coef(a, j, p, m, phi_n, phi_s, south, false));
-  for (int m = (k == 0 ? N : N - k); m <= a.mmax; m += N)
-    z = cadd(z, synth_coef(a, j, p, m, phi_n, phi_s, south, true));
+// Z_k = sum_{m >= 0, m = k mod N} (cN_m + i cS_m) + sum_{m >= 1, -m = k mod N} (conj cN_m + i conj cS_m);
+// the first term starts the sum (without aliasing, N > 2 mmax, it is the only one)
+template <class N>
+__device__ typename N::C spectrum_at(const FftArgs &a, int j, int p, int k, int Nr, double phi_n, double phi_s,
+                                     bool south, bool ph_n, bool ph_s) {
+  using C = typename N::C;
+  const int mc = k == 0 ? Nr : Nr - k;  // first m of the conjugate terms
+  if (k <= a.mmax) {
+    C z = synth_term<N>(a, j, p, k, phi_n, phi_s, south, false, ph_n, ph_s);
+    for (int m = k + Nr; m <= a.mmax; m += Nr)
+      z = N::add(z, synth_term<N>(a, j, p, m, phi_n, phi_s, south, false, ph_n, ph_s));
+    for (int m = mc; m <= a.mmax; m += Nr)
+      z = N::add(z, synth_term<N>(a, j, p, m, phi_n, phi_s, south, true, ph_n, ph_s));
+    return z;
+  }
+  if (mc > a.mmax) return N::zero();
+  C z = synth_term<N>(a, j, p, mc, phi_n, phi_s, south, true, ph_n, ph_s);
+  for (int m = mc + Nr; m <= a.mmax; m += Nr)
+    z = N::add(z, synth_term<N>(a, j, p, m, phi_n, phi_s, south, true, ph_n, ph_s));
   return z;
 }
 
@@ -523,35 +563,38 @@ __device__ __forceinline__ void fft_syn_kernel_body(Ring ring, const FftArgs &a,
   const bool south = rr.y >= 0;
   const RingDev rs = a.rings[south ? rr.y : rr.x];
   const int Nphi = fp.n;
+  const bool ph_n = rn.phi0 != 0.0, ph_s = south && rs.phi0 != 0.0;
   // inverse DFT via conj(DFT(conj(Z)))
   if (fp.kind == 0) {
     for (int k = threadIdx.x; k < Nphi; k += blockDim.x)
-      buf[k] = N::of(cconj(spectrum_at(a, j, p, k, Nphi, rn.phi0, rs.phi0, south)));
+      buf[k] = N::conj(spectrum_at<N>(a, j, p, k, Nphi, rn.phi0, rs.phi0, south, ph_n, ph_s));
   } else if (fp.kind == 1) {
     for (int q = threadIdx.x; q < Nphi - 1; q += blockDim.x)
-      buf[q] = N::of(cconj(spectrum_at(a, j, p, fp.perm_in[q], Nphi, rn.phi0, rs.phi0, south)));
-    if (threadIdx.x == 0) sh_x0 = N::of(cconj(spectrum_at(a, j, p, 0, Nphi, rn.phi0, rs.phi0, south)));
+      buf[q] = N::conj(spectrum_at<N>(a, j, p, fp.perm_in[q], Nphi, rn.phi0, rs.phi0, south, ph_n, ph_s));
+    if (threadIdx.x == 0) sh_x0 = N::conj(spectrum_at<N>(a, j, p, 0, Nphi, rn.phi0, rs.phi0, south, ph_n, ph_s));
   } else {
     const C *chirp = N::chirp(fp);
     for (int k = threadIdx.x; k < fp.len; k += blockDim.x)
       buf[k] = (k < Nphi)
-                   ? N::mul(N::of(cconj(spectrum_at(a, j, p, k, Nphi, rn.phi0, rs.phi0, south))), N::ldg(chirp + k))
+                   ? N::mul(N::conj(spectrum_at<N>(a, j, p, k, Nphi, rn.phi0, rs.phi0, south, ph_n, ph_s)), N::ldg(chirp + k))
                    : N::zero();
   }
   __syncthreads();
   dft_run<N>(ring, fp, &sh_x0, &sh_a0);
   const C x0 = sh_x0, a0 = sh_a0;
   double *mp = ptrs[j];
-  const double wn = a.weighted ? rn.weight : 1.0, ws = a.weighted ? rs.weight : 1.0;
+  const int weighted = a.weighted;
+  const typename N::S wn = N::scalar(rn.weight), ws = N::scalar(rs.weight);
   for (int x = threadIdx.x; x < Nphi; x += blockDim.x) {
-    const double2 X = N::val(dft_at<N>(buf, fp, x, x0, a0));
-    // z = conj(X): north = Re z, south = Im z
-    double vn = X.x * wn;
+    C zc = N::conj(dft_at<N>(buf, fp, x, x0, a0));  // north = Re z, south = Im z
+    if (weighted) zc = N::scale2(zc, wn, ws);
+    const double2 z = N::val(zc);
+    double vn = z.x;
     double *on = mp + rn.ofs + (int64_t)x * rn.stride;
     if (a.add) vn += *on;
     *on = vn;
     if (south) {
-      double vs = -X.y * ws;
+      double vs = z.y;
       double *os = mp + rs.ofs + (int64_t)x * rs.stride;
       if (a.add) vs += *os;
       *os = vs;
@@ -604,21 +647,22 @@ __device__ __forceinline__ void fft_ana_kernel_body(Ring ring, const FftArgs &a,
   __syncthreads();
   dft_run<N>(ring, fp, &sh_x0, &sh_a0);
   const C x0 = sh_x0, a0 = sh_a0;
-  const double wn = a.weighted ? rn.weight : 1.0, ws = a.weighted ? rs.weight : 1.0;
+  const int weighted = a.weighted;
+  const typename N::S wn = N::scalar(rn.weight), ws = N::scalar(rs.weight);
+  const bool ph_n = rn.phi0 != 0.0, ph_s = south && rs.phi0 != 0.0;
   for (int mi = threadIdx.x; mi < a.nm; mi += blockDim.x) {
     const int m = a.mval[mi];
     const int k = m % Nphi, kn = (Nphi - k) % Nphi;
-    const double2 Zk = N::val(dft_at<N>(buf, fp, k, x0, a0)), Zn = cconj(N::val(dft_at<N>(buf, fp, kn, x0, a0)));
-    // P_N = (Zk + conj Zn)/2,  P_S = (Zk - conj Zn)/(2i)
-    const double2 pn = make_double2(0.5 * (Zk.x + Zn.x), 0.5 * (Zk.y + Zn.y));
-    const double2 d = make_double2(Zk.x - Zn.x, Zk.y - Zn.y);
-    const double2 ps = make_double2(0.5 * d.y, -0.5 * d.x);
-    const double2 en = cconj(phase_of(m, rn.phi0)), es = cconj(phase_of(m, rs.phi0));
-    double2 gn = cmul(pn, en), gs = cmul(ps, es);
-    gn.x *= wn;
-    gn.y *= wn;
-    gs.x *= ws;
-    gs.y *= ws;
+    const C Zk = dft_at<N>(buf, fp, k, x0, a0), Zn = N::conj(dft_at<N>(buf, fp, kn, x0, a0));
+    // P_N = (Zk + conj Zn)/2,  P_S = (Zk - conj Zn)/(2i), in the engine's arithmetic
+    C pn = N::half(N::add(Zk, Zn)), ps = N::half(N::times_minus_i(N::sub(Zk, Zn)));
+    if (weighted) {
+      pn = N::scale(pn, wn);
+      ps = N::scale(ps, ws);
+    }
+    double2 gn = N::val(pn), gs = N::val(ps);
+    if (ph_n) gn = cmul(gn, cconj(phase_of(m, rn.phi0)));
+    if (ph_s) gs = cmul(gs, cconj(phase_of(m, rs.phi0)));
     if (!south) gs = make_double2(0.0, 0.0);
     double2 *g = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
     g[0] = gn;
