@@ -273,26 +273,36 @@ def f32_ops_per_triple(spin, ncomp):
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernels, from the ncu captures summarised under profiles/, with the
-# SHA-256 of the kernel's source file when they were taken: a changed source
-# makes the figure stale and the bench reports null.
+# SHA-256 of the kernel's source file and device headers when they were taken:
+# a changed source makes the figure stale and the bench reports null.
 MEASURED_TRAFFIC = {
-    # profiles/dram_traffic_spin2_lmax4095.md (spin 2, GL 4096 x 8191, lmax 4095, one launch each)
-    "fp64:legendre_analysis": {"bytes": 706942720 + 941203200, "sha256": "696b0de9716a2778b0e70b039dd9a4f2e207e96b035236f992fe34830cb5ba3d"},
-    "fp64:legendre_synthesis": {"bytes": 554776320 + 323874816, "sha256": "696b0de9716a2778b0e70b039dd9a4f2e207e96b035236f992fe34830cb5ba3d"},
-    "mixed:legendre_analysis": {"bytes": 659847936 + 3475654656, "sha256": "5872d72464d53f5970754b0ca2224a3f26ef3958e07b1b1c731649991f3faeb8"},
-    "mixed:legendre_synthesis": {"bytes": 549097984 + 323081472, "sha256": "5872d72464d53f5970754b0ca2224a3f26ef3958e07b1b1c731649991f3faeb8"},
+    # profiles/dram_traffic_spin2_lmax4095.md (spin 2, GL 4096 x 8191, lmax 4095, one launch each);
+    # sha256 over the kernel file and its device headers (_kernel_digest)
+    "fp64:legendre_analysis": {"bytes": 706942720 + 941203200, "sha256": "51bcb216600e775f1f443ee0f293700420ed109bdb18207f7f532cafeff32dfc"},
+    "fp64:legendre_synthesis": {"bytes": 554776320 + 323874816, "sha256": "51bcb216600e775f1f443ee0f293700420ed109bdb18207f7f532cafeff32dfc"},
+    "mixed:legendre_analysis": {"bytes": 659456256 + 3472259840, "sha256": "ec8c0715aba66b858b5c51dc8c10c80c9637772dfd1a38ee6e9c3f00a23cbf62"},
+    "mixed:legendre_synthesis": {"bytes": 545406208 + 321486080, "sha256": "ec8c0715aba66b858b5c51dc8c10c80c9637772dfd1a38ee6e9c3f00a23cbf62"},
 }
 
 
-def _traffic(kernel_file, key):
+KERNEL_HEADERS = {"legendre_fp64.cu": ("sht_device.cuh",), "legendre_mixed.cu": ("df.cuh", "sht_device.cuh")}
+
+
+def _kernel_digest(kernel_file):
+    """SHA-256 over the kernel's source file and the device headers it includes."""
     import hashlib
+    h = hashlib.sha256()
+    for name in (kernel_file,) + KERNEL_HEADERS.get(kernel_file, ()):
+        with open(os.path.join(ROOT, "paper_1303_4945_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic(kernel_file, key):
     rec = MEASURED_TRAFFIC.get(key)
     if not rec:
         return None
-    path = os.path.join(ROOT, "paper_1303_4945_gb300", "csrc", kernel_file)
-    with open(path, "rb") as f:
-        digest = hashlib.sha256(f.read()).hexdigest()
-    return rec["bytes"] if rec["sha256"] == digest else None
+    return rec["bytes"] if rec["sha256"] == _kernel_digest(kernel_file) else None
 
 
 def launches_per_step(spin, form, fp64_items=False):

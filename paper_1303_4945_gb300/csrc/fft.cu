@@ -471,10 +471,10 @@ cudaError_t launch_fft_spectrum(const FftPlanDev *hp, const FftPlanDev *dp, cons
   return cudaGetLastError();
 }
 
-// e^{i m phi0} with the product m*phi0 carried to ~1e-32 before the sincos
-// (callers skip rings with phi0 = 0; no FP64 compare here, which the compiler
-// would hoist ahead of their test and issue for every coefficient)
-__device__ __forceinline__ double2 phase_of(int m, double phi0) {
+// e^{i m phi0} with the product m*phi0 carried to ~1e-32 before the sincos.
+// Callers skip rings with phi0 = 0; out of line so that no part of the sincos
+// (its FP64 range tests) is predicated into their loops for every coefficient.
+__device__ __noinline__ double2 phase_of(int m, double phi0) {
   if (m == 0) return make_double2(1.0, 0.0);
   const double dm = (double)m;
   const double hi = dm * phi0;

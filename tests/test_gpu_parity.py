@@ -334,6 +334,28 @@ def test_mixed_config1_round_trip(sht):
     assert rel_l2(back, alm[0]) < MIX_L2
 
 
+@pytest.mark.parametrize("scale", [1e-25, 1e-12, 1e20])
+def test_mixed_scale_range(sht, scale):
+    # The mixed form converts between FP64 and FP32 pairs from the numbers' bit
+    # fields; a transform of scaled inputs must equal the scaled transform over
+    # FP32's range (1e-25: low words below 2^-64, the two-step scaling path).
+    # 1517 = 37 41 (large-radix passes), 131 (Rader), 262 (Bluestein).
+    for nlon in (1517, 131, 262):
+        lmax = min(30, (nlon - 1) // 2)
+        geom = sht.sht_geom_gauss(lmax + 1 + (nlon % 2), nlon)
+        rings = rings_of(geom)
+        rng = np.random.default_rng(nlon)
+        alm = [inputs.gaussian_alm(rng, lmax, lmax) * scale]
+        plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), 0, 1, sht.SHT_MIXED)
+        got = gpu_synthesis(sht, plan, alm, geom.npix)[0]
+        ref = oracle.synthesis(0, lmax, lmax, alm, rings)[0]
+        assert rel_l2(got, ref) <= MIX_L2, (nlon, scale, rel_l2(got, ref))
+        maps = [rng.standard_normal(geom.npix) * scale]
+        got_a = gpu_analysis(sht, plan, maps, oracle.nalm(lmax, lmax))[0]
+        ref_a = oracle.analysis(0, lmax, lmax, maps, rings)[0]
+        assert rel_l2(got_a, ref_a) <= MIX_L2, (nlon, scale, rel_l2(got_a, ref_a))
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("nlon", [14803, 16383, 20011, 20480])
 def test_long_rings(sht, nlon, precision):
