@@ -574,6 +574,12 @@ def main():
                          "tiling": {"analysis_pairs_per_thread": plan.tiling()[0],
                                     "autotune_ms_per_candidate": {str(k): v for k, v in tune.items()}}}
         outputs[name] = {"maps": [m.cpu().numpy() for m in maps_d], "alm": [a.cpu().numpy() for a in out_d]}
+        if prec == sht.SHT_MIXED:  # the same plan with the FP64 ring-FFT engine (not the headline)
+            plan.fft_precision = sht.SHT_FP64
+            ms64, st64 = time_form(sht, torch, plan, alm_d, maps_d, out_d, args.steps, args.warmup, world, stream)
+            results[name]["with_fp64_fft"] = {
+                "ms_per_step": ms64,
+                "fft_ms_per_step": {k: st64[k][0] / args.steps for k in ("fft_synthesis", "fft_analysis")}}
         del plan
     head = "mixed" if "mixed" in forms else "fp64"
     # mixed vs FP64 on the full output

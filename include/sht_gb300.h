@@ -255,6 +255,20 @@ SHT_API int sht_plan_autotune(sht_plan_t plan, void *cuda_stream, float *ms_per_
 SHT_API int sht_plan_set_fp64_columns(sht_plan_t plan, int m_below);
 SHT_API int sht_plan_get_fp64_columns(sht_plan_t plan, int *m_below);
 
+/* Ring FFT arithmetic of a mixed plan (Eqs. syn1, ana2).  By default a mixed plan
+ * runs its ring FFTs in the same double-float arithmetic as its Legendre stage
+ * (FP32 pairs, ~46 bits an operation: relative errors near 1e-14, far inside the
+ * mixed form's 1e-10; values within FP32's normal range, magnitudes below 2^-126
+ * entering as zero); on GB300 the FP32 pipe issues 64 times the FP64 rate.
+ * sht_plan_set_fft_precision(plan, SHT_FP64) selects the IEEE-double engine the
+ * FP64 plans use, SHT_MIXED the double-float one; sht_plan_get_fft_precision
+ * reads the setting.  FP64 plans always use the FP64 engine.
+ * Errors: SHT_ERR_INVALID_ARG (NULL, an FP64 plan asked for SHT_MIXED, a value
+ * other than SHT_FP64 / SHT_MIXED, a plan in a batch).
+ */
+SHT_API int sht_plan_set_fft_precision(sht_plan_t plan, int precision);
+SHT_API int sht_plan_get_fft_precision(sht_plan_t plan, int *precision);
+
 /* ---- measurement ----------------------------------------------------------
  * Sect. 5.2 times whole transforms by wall clock; these two calls report the
  * device time of each kernel stage instead.  While profiling is on,

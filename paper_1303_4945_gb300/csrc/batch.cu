@@ -48,7 +48,7 @@ struct sht_batch_s {
   std::vector<Group> groups;
   void *d_fft_syn[2][2][2] = {};  // [polar][weighted][add]: FFT argument records
   void *d_fft_ana[2] = {};        // [weighted]
-  int4 *d_fft_items[2] = {};      // (pair, map, -, plan) of FP64 plans [0] and mixed plans [1]
+  int4 *d_fft_items[2] = {};      // (pair, map, -, plan) by FFT engine: FP64 [0], double-float [1]
   int nfft_items[2] = {};
   int fft_smem = 0;
   std::vector<void *> allocs;
@@ -182,7 +182,7 @@ int build(sht_batch_s *B) {
   for (int k = 0; k < n; ++k) {
     const sht_plan_s *P = B->plans[k];
     B->fft_smem = std::max(B->fft_smem, P->fft_smem);
-    const int df = P->precision == SHT_MIXED;
+    const int df = P->fft_df ? 1 : 0;
     for (int p = 0; p < P->npairs; ++p)
       for (int j = 0; j < P->nmaps; ++j) fi[df].push_back({(int64_t)P->pair_len[p], make_int4(p, j, 0, k)});
   }

@@ -738,7 +738,7 @@ cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, i
   a.add = add;
   a.pair0 = p0;
   a.npairs_run = p1 - p0;
-  const bool df = P->precision == SHT_MIXED;
+  const bool df = P->fft_df;
   if (P->d_fft_scratch) {
     const int g = (int)std::min<int64_t>((int64_t)a.npairs_run * P->nmaps, P->fft_slots);
     if (df)
@@ -763,7 +763,7 @@ cudaError_t launch_fft_ana(const sht_plan_s *P, const DevPtrs &map, int weighted
   a.weighted = weighted;
   a.pair0 = p0;
   a.npairs_run = p1 - p0;
-  const bool df = P->precision == SHT_MIXED;
+  const bool df = P->fft_df;
   if (P->d_fft_scratch) {
     const int g = (int)std::min<int64_t>((int64_t)a.npairs_run * P->nmaps, P->fft_slots);
     if (df)

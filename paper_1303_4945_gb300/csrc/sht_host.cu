@@ -1029,6 +1029,7 @@ extern "C" int sht_plan_create(sht_geom_t geom, sht_alm_t alm, int spin, int nco
   P->spin = spin;
   P->ncomp = ncomp;
   P->precision = precision;
+  P->fft_df = precision == SHT_MIXED;
   P->nmaps = spin ? 2 * ncomp : ncomp;
   P->njobs_pad = 1;
   while (P->njobs_pad < ncomp) P->njobs_pad *= 2;
@@ -1103,6 +1104,23 @@ extern "C" int sht_plan_set_fp64_columns(sht_plan_t P, int m_below) {
 extern "C" int sht_plan_get_fp64_columns(sht_plan_t P, int *m_below) {
   if (!P || !m_below) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
   *m_below = P->fp64_m_below;
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_set_fft_precision(sht_plan_t P, int precision) {
+  if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  if (precision != SHT_FP64 && precision != SHT_MIXED) return fail(SHT_ERR_INVALID_ARG, "bad FFT precision");
+  if (precision == SHT_MIXED && P->precision != SHT_MIXED)
+    return fail(SHT_ERR_INVALID_ARG, "FP64 plans have no double-float FFT tables");
+  if (P->batch_refs)
+    return fail(SHT_ERR_INVALID_ARG, "the plan belongs to %d batch(es); destroy them first", P->batch_refs);
+  P->fft_df = precision == SHT_MIXED;
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_get_fft_precision(sht_plan_t P, int *precision) {
+  if (!P || !precision) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  *precision = P->fft_df ? SHT_MIXED : SHT_FP64;
   return SHT_OK;
 }
 

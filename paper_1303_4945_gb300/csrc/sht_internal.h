@@ -160,6 +160,7 @@ struct sht_plan_s {
   // the small-m recursion is non-oscillatory for l < ~1/theta and amplifies its
   // per-step rounding by a power of l
   int fp64_m_below = 0;
+  bool fft_df = false;  // ring FFTs in double-float (mixed plans, by default)
   // the FP64 columns run beside the mixed kernels: a side stream forked and joined by events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

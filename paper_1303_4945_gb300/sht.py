@@ -71,6 +71,8 @@ _sig = {
     "sht_plan_autotune": [_vp, _vp, ctypes.POINTER(ctypes.c_float)],
     "sht_plan_set_fp64_columns": [_vp, ctypes.c_int],
     "sht_plan_get_fp64_columns": [_vp, _ip],
+    "sht_plan_set_fft_precision": [_vp, ctypes.c_int],
+    "sht_plan_get_fft_precision": [_vp, _ip],
     "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
                           ctypes.c_int, _vp],
@@ -226,6 +228,17 @@ class Plan(_Handle):
     @fp64_columns.setter
     def fp64_columns(self, m_below):
         _check(_lib.sht_plan_set_fp64_columns(self._h, m_below), "sht_plan_set_fp64_columns")
+
+    @property
+    def fft_precision(self):
+        """Ring FFT engine: SHT_MIXED (double-float, mixed plans' default) or SHT_FP64."""
+        n = ctypes.c_int()
+        _check(_lib.sht_plan_get_fft_precision(self._h, ctypes.byref(n)), "sht_plan_get_fft_precision")
+        return n.value
+
+    @fft_precision.setter
+    def fft_precision(self, precision):
+        _check(_lib.sht_plan_set_fft_precision(self._h, precision), "sht_plan_set_fft_precision")
 
     def triples(self, flags=0):
         n = ctypes.c_int64()

@@ -155,3 +155,67 @@ def test_fp64_items_under_graph_capture(sht):
         torch.cuda.synchronize()
         for x, y in zip(maps + out, m_ref + o_ref):
             assert torch.equal(x, y), rep
+
+
+def test_fft_precision_setting(sht):
+    """A mixed plan's ring FFTs run in double-float by default; the FP64 engine is
+    selectable per plan.  Both match the oracle, agree with each other far inside
+    the mixed tolerance, and run side by side in one batch."""
+    lmax = 30
+    rng = np.random.default_rng(77)
+    cases = []
+    for nlon in (1517, 131, 262):  # large radices, Rader, Bluestein
+        geom = sht.sht_geom_gauss(lmax + 2, nlon)
+        alm = [inputs.gaussian_alm(rng, lmax, lmax, lmin=2) for _ in range(2)]
+        maps = [rng.standard_normal(geom.npix) for _ in range(2)]
+        cases.append((geom, alm, maps))
+    n = oracle.nalm(lmax, lmax)
+    results = {}
+    for fftp in (sht.SHT_MIXED, sht.SHT_FP64):
+        plans = []
+        for geom, alm, maps in cases:
+            plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), 2, 1, sht.SHT_MIXED)
+            assert plan.fft_precision == sht.SHT_MIXED
+            plan.fft_precision = fftp
+            assert plan.fft_precision == fftp
+            m_d = [torch.zeros(geom.npix, dtype=torch.float64, device="cuda") for _ in range(2)]
+            sht.sht_execute(plan, sht.SHT_SYNTHESIS, [torch.from_numpy(a).cuda() for a in alm], m_d)
+            a_d = [torch.zeros(n, dtype=torch.complex128, device="cuda") for _ in range(2)]
+            sht.sht_execute(plan, sht.SHT_ANALYSIS, a_d, [torch.from_numpy(m).cuda() for m in maps])
+            torch.cuda.synchronize()
+            ref_s = oracle.synthesis(2, lmax, lmax, alm, rings_of(geom))
+            ref_a = oracle.analysis(2, lmax, lmax, maps, rings_of(geom))
+            got_s = [x.cpu().numpy() for x in m_d]
+            got_a = [x.cpu().numpy() for x in a_d]
+            for g, r in zip(got_s + got_a, ref_s + ref_a):
+                assert rel_l2(g, r) <= 1e-10
+            results.setdefault(fftp, []).append((got_s, got_a))
+            plans.append(plan)
+        if fftp == sht.SHT_FP64:
+            fp64_plans = plans
+        else:
+            df_plans = plans
+    for (s1, a1), (s2, a2) in zip(results[sht.SHT_MIXED], results[sht.SHT_FP64]):
+        for g, r in zip(s1 + a1, s2 + a2):
+            assert rel_l2(g, r) <= 1e-12
+    # one batch holding plans of both engines: two FFT launches per stage
+    mixed = [df_plans[0], fp64_plans[1], df_plans[2]]
+    batch = sht.sht_batch_create(mixed)
+    with pytest.raises(sht.ShtError):
+        mixed[1].fft_precision = sht.SHT_MIXED  # locked while in a batch
+    alms = [[torch.from_numpy(a).cuda() for a in c[1]] for c in cases]
+    outs = [[torch.zeros(c[0].npix, dtype=torch.float64, device="cuda") for _ in range(2)] for c in cases]
+    sht.sht_batch_execute(batch, sht.SHT_SYNTHESIS, alms, outs)
+    torch.cuda.synchronize()
+    for (geom, alm, _), o in zip(cases, outs):
+        ref = oracle.synthesis(2, lmax, lmax, alm, rings_of(geom))
+        for g, r in zip(o, ref):
+            assert rel_l2(g.cpu().numpy(), r) <= 1e-10
+    del batch
+    # errors: FP64 plans have no double-float engine; only the two precisions exist
+    p64 = sht.sht_plan_create(cases[0][0], sht.sht_alm_create(lmax, lmax), 0, 1, sht.SHT_FP64)
+    assert p64.fft_precision == sht.SHT_FP64
+    with pytest.raises(sht.ShtError):
+        p64.fft_precision = sht.SHT_MIXED
+    with pytest.raises(sht.ShtError):
+        df_plans[0].fft_precision = 7
