@@ -608,6 +608,7 @@ def main():
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
     used = [False, False]
+    t_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for it in range(args.warmup + args.steps):
         b = it % 2
@@ -627,8 +628,12 @@ def main():
         stream.wait_event(ev_in[b])
         if used[b]:
             stream.wait_event(ev_out[b])  # res_d[b] of two steps back has been downloaded
+        if it >= args.warmup:
+            t_ev[it - args.warmup][0].record(stream)
         sht.sht_execute(plan, sht.SHT_SYNTHESIS, in_d[b], maps_d, 0, stream)
         sht.sht_execute(plan, sht.SHT_ANALYSIS, res_d[b], maps_d, 0, stream)
+        if it >= args.warmup:
+            t_ev[it - args.warmup][1].record(stream)
         ev_done[b].record(stream)
         with torch.cuda.stream(down):
             down.wait_event(ev_done[b])
@@ -641,6 +646,9 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    e2e_transform_ms = sum(a.elapsed_time(b) for a, b in t_ev) / args.steps  # device time of the transforms
+    e2e_gaps = [t_ev[i][1].elapsed_time(t_ev[i + 1][0]) for i in range(args.steps - 1)]  # idle between them
+    e2e_edges = (e0.elapsed_time(t_ev[0][0]), t_ev[-1][1].elapsed_time(e1))  # first upload, last download
     e2e_ok = all(torch.equal(h.cpu() if h.is_cuda else h, r.cpu()) for h, r in
                  zip(host_out[(args.warmup + args.steps - 1) % 2], res_d[(args.warmup + args.steps - 1) % 2]))
     nbytes = sum(a.nbytes for a in alm_h)
@@ -653,6 +661,8 @@ def main():
             "form": head, "roofline": results[head]["roofline"], "clocks": clocks,
             "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "overlap": "uploads and downloads on their own streams, double-buffered",
+                    "transform_ms_per_step": e2e_transform_ms,
+                    "gap_ms_between_transforms": e2e_gaps, "first_upload_last_download_ms": e2e_edges,
                     "result_copied": e2e_ok},
             "gpu_launches": launches_per_step(SPIN, head, results[head].get("fp64_columns", 0) > 0) * args.steps,
             "forms": results}
