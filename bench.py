@@ -509,6 +509,72 @@ def run_grad_workload(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_healpix_workload(args, world, rank, local):
+    """HEALPix Nside 512, lmax 1535, spin 0, a_lm with C_l = 1/(l+1)^2 from rng(1): p = S a
+    once (the data), then per step the weighted analysis with 3 Jacobi refinement
+    iterations: a_0 = A p, a_{k+1} = a_k + A (p - S a_k) (4 analyses, 3 syntheses; the
+    residual is one torch subtraction, the accumulation the ADD_OUTPUT flag)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1303_4945_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1303_4945_gb300 import inputs, sht
+
+    stream = torch.cuda.current_stream()
+    lmax, nside = 1535, 512
+    geom = sht.sht_geom_healpix(nside)
+    lay = sht.sht_alm_create(lmax, lmax)
+    a = torch.from_numpy(inputs.gaussian_alm(np.random.default_rng(1), lmax, lmax,
+                                             cl=inputs.cl_inverse_square)).cuda()
+    l, _ = inputs.lm_arrays(lmax, lmax)
+    low = torch.from_numpy(l < 512).cuda()
+    forms, results = {}, {}
+    sampler = ClockSampler(local)
+    for name, prec in (("fp64", sht.SHT_FP64), ("mixed", sht.SHT_MIXED)):
+        plan = sht.sht_plan_create(geom, lay, 0, 1, prec)
+        plan.autotune(stream)
+        p = torch.empty(geom.npix, dtype=torch.float64, device="cuda")
+        sht.sht_execute(plan, sht.SHT_SYNTHESIS, [a], [p], 0, stream)
+        ak = torch.zeros_like(a)
+        r = torch.empty_like(p)
+
+        def step():
+            sht.sht_execute(plan, sht.SHT_ANALYSIS, [ak], [p], 0, stream)
+            for _ in range(3):
+                sht.sht_execute(plan, sht.SHT_SYNTHESIS, [ak], [r], 0, stream)
+                torch.sub(p, r, out=r)
+                sht.sht_execute(plan, sht.SHT_ANALYSIS, [ak], [r], sht.SHT_ADD_OUTPUT, stream)
+
+        if name == "mixed":
+            sampler.start()
+        ms = _events_ms(torch, stream, step, args.steps, args.warmup, world)
+        if name == "mixed":
+            clocks = sampler.stop()
+        results[name] = ak.clone()
+        syn_l = 2 + (prec == sht.SHT_MIXED)  # (conversion) Legendre, FFT; no FP64 items below lmax 2700
+        forms[name] = {"ms_per_step": ms, "triples": plan.triples(0),
+                       "rel_l2_vs_truth": float(torch.linalg.norm(ak - a) / torch.linalg.norm(a)),
+                       "rel_l2_vs_truth_l_below_512": float(torch.linalg.norm((ak - a)[low])
+                                                            / torch.linalg.norm(a[low])),
+                       "gpu_launches_per_step": 3 * syn_l + 4 * 3}
+        del plan
+        torch.cuda.empty_cache()
+    forms["mixed"]["vs_fp64_rel_l2"] = float(torch.linalg.norm(results["mixed"] - results["fp64"])
+                                             / torch.linalg.norm(a))
+    config = {"workload": "weighted analysis with 3 Jacobi iterations (4 analyses, 3 syntheses) of a "
+                          "HEALPix Nside 512 map, lmax=mmax=1535, spin 0, a_lm C_l=1/(l+1)^2 rng(1)",
+              "parallelism": "replicas"}
+    line = _line("ms per Jacobi-refined analysis at lmax 1535 (HEALPix Nside 512)", forms["mixed"]["ms_per_step"],
+                 args, world, config, "f32x2",
+                 {"form": "mixed", "forms": forms, "clocks": clocks,
+                  "gpu_launches": forms["mixed"]["gpu_launches_per_step"] * args.steps})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -520,9 +586,10 @@ def main():
     ap.add_argument("--lmax", type=int, default=4095, help="smaller sizes for profiling captures")
     ap.add_argument("--nlat", type=int, default=None,
                     help="fewer rings of the same length for profiling captures (default lmax + 1)")
-    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad"],
+    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad", "healpix"],
                     help="spin2: the headline (spin-2 lmax 4095 pair); batch: 64 uneven scalar problems + "
-                         "8 maps at lmax 2047 in one batch; grad: loss + gradient at lmax 8191")
+                         "8 maps at lmax 2047 in one batch; grad: loss + gradient at lmax 8191; healpix: "
+                         "Jacobi-refined analysis on HEALPix Nside 512, lmax 1535")
     args = ap.parse_args()
     set_workload(args.lmax, args.nlat)
     world, rank, local = dist_setup()
@@ -530,7 +597,8 @@ def main():
         run_reference(args, world, rank)
         return
     if args.workload != "spin2":
-        (run_batch_workload if args.workload == "batch" else run_grad_workload)(args, world, rank, local)
+        runners = {"batch": run_batch_workload, "grad": run_grad_workload, "healpix": run_healpix_workload}
+        runners[args.workload](args, world, rank, local)
         return
     import numpy as np
     import torch
