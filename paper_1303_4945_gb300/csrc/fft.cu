@@ -499,55 +499,81 @@ struct FftArgs {
   int ptr_off;
   int nmaps_run;  // maps per side (global-ring kernels walk npairs_run x nmaps_run items)
   int pair0, npairs_run;  // the ring pairs [pair0, pair0 + npairs_run) one launch transforms
+  int m_identity;         // mval[mi] = mi for every mi (the phases can be walked along m)
 };
 
 // ---------------------------------------------------------------------------
 // synthesis: F (per m) -> ring pixels
 // ---------------------------------------------------------------------------
-// The term of coefficient m for one ring pair, conj?(cN) + i conj?(cS) (conj_ for
-// the m < 0 half of the sum), in the engine's arithmetic; F below the first pair
-// the Legendre stage processed for this m is zero.  (ph_n, ph_s: the rings' phi0
-// are nonzero; rings with phi0 = 0 skip the phase products.)
+// e^{i m phi} for m = m0, m0 + step, m0 + 2 step, ... in the engine's arithmetic:
+// one sincos for the first value and one for the step, then one product a step
+// (its rounding adds up over at most a ring's length / blockDim steps)
 template <class N>
-__device__ __forceinline__ typename N::C synth_term(const FftArgs &a, int j, int p, int m, double phi_n,
-                                                    double phi_s, bool south, bool conj_, bool ph_n, bool ph_s) {
+struct PhaseWalk {
+  typename N::C e, s;
+  __device__ __forceinline__ void init(int m0, int step, double phi) {
+    e = N::of(phase_of(m0, phi));
+    s = N::of(phase_of(step, phi));
+  }
+  __device__ __forceinline__ void next() { e = N::mul(e, s); }
+};
+
+// The term of coefficient m for one ring pair, conj?(cN e^{i m phiN}) + i conj?(cS e^{i m phiS})
+// (conj_ for the m < 0 half of the sum), in the engine's arithmetic; pn, ps are the
+// phases e^{i m phi} of rings with phi0 != 0 (ph_n, ph_s).  F below the first pair
+// the Legendre stage processed for this m is zero.
+template <class N>
+__device__ __forceinline__ typename N::C synth_term(const FftArgs &a, int j, int p, int m, bool south, bool conj_,
+                                                    bool ph_n, bool ph_s, typename N::C pn, typename N::C ps) {
   using C = typename N::C;
   const int mi = a.minv[m];
   if (mi < 0 || p < a.syn_first[mi]) return N::zero();
   const double2 *f = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
-  double2 cn = f[0];
-  if (ph_n) cn = cmul(cn, phase_of(m, phi_n));
-  C z = N::of(cn);
+  C z = N::of(f[0]);
+  if (ph_n) z = N::mul(z, pn);
   if (conj_) z = N::conj(z);
   if (south) {
-    double2 cs = f[1];
-    if (ph_s) cs = cmul(cs, phase_of(m, phi_s));
-    C zs = N::of(cs);
+    C zs = N::of(f[1]);
+    if (ph_s) zs = N::mul(zs, ps);
     if (conj_) zs = N::conj(zs);
     z = N::add(z, N::times_i(zs));
   }
   return z;
 }
 
-// Z_k = sum_{m >= 0, m = k mod N} (cN_m + i cS_m) + sum_{m >= 1, -m = k mod N} (conj cN_m + i conj cS_m);
-// the first term starts the sum (without aliasing, N > 2 mmax, it is the only one)
+// Z_k = sum_{m >= 0, m = k mod N} (cN_m + i cS_m) + sum_{m >= 1, -m = k mod N} (conj cN_m + i conj cS_m),
+// c_m = F_m e^{i m phi0}.  The first term starts the sum (without aliasing, N > 2 mmax,
+// it is the only one).  en, es = e^{i k phi}, bn, bs = e^{i N phi} of the two rings:
+// the term m = k + N i has phase e^{i k phi} (e^{i N phi})^i, the conjugate term
+// m = N (i + 1) - k has e^{-i k phi} (e^{i N phi})^(i + 1).
 template <class N>
-__device__ typename N::C spectrum_at(const FftArgs &a, int j, int p, int k, int Nr, double phi_n, double phi_s,
-                                     bool south, bool ph_n, bool ph_s) {
+__device__ typename N::C spectrum_at(const FftArgs &a, int j, int p, int k, int Nr, bool south, bool ph_n, bool ph_s,
+                                     typename N::C en, typename N::C es, typename N::C bn, typename N::C bs) {
   using C = typename N::C;
   const int mc = k == 0 ? Nr : Nr - k;  // first m of the conjugate terms
-  if (k <= a.mmax) {
-    C z = synth_term<N>(a, j, p, k, phi_n, phi_s, south, false, ph_n, ph_s);
-    for (int m = k + Nr; m <= a.mmax; m += Nr)
-      z = N::add(z, synth_term<N>(a, j, p, m, phi_n, phi_s, south, false, ph_n, ph_s));
-    for (int m = mc; m <= a.mmax; m += Nr)
-      z = N::add(z, synth_term<N>(a, j, p, m, phi_n, phi_s, south, true, ph_n, ph_s));
-    return z;
+  C z = N::zero();
+  bool first = true;
+  auto add = [&](int m, bool cj, C pn, C ps) {
+    const C t = synth_term<N>(a, j, p, m, south, cj, ph_n, ph_s, pn, ps);
+    z = first ? t : N::add(z, t);
+    first = false;
+  };
+  C pn = en, ps = es;
+  for (int m = k; m <= a.mmax; m += Nr) {
+    add(m, false, pn, ps);
+    if (ph_n) pn = N::mul(pn, bn);
+    if (ph_s) ps = N::mul(ps, bs);
   }
-  if (mc > a.mmax) return N::zero();
-  C z = synth_term<N>(a, j, p, mc, phi_n, phi_s, south, true, ph_n, ph_s);
-  for (int m = mc + Nr; m <= a.mmax; m += Nr)
-    z = N::add(z, synth_term<N>(a, j, p, m, phi_n, phi_s, south, true, ph_n, ph_s));
+  if (mc <= a.mmax) {
+    C qn = N::conj(en), qs = N::conj(es);
+    if (ph_n) qn = N::mul(qn, bn);
+    if (ph_s) qs = N::mul(qs, bs);
+    for (int m = mc; m <= a.mmax; m += Nr) {
+      add(m, true, qn, qs);
+      if (ph_n) qn = N::mul(qn, bn);
+      if (ph_s) qs = N::mul(qs, bs);
+    }
+  }
   return z;
 }
 
@@ -564,21 +590,37 @@ __device__ __forceinline__ void fft_syn_kernel_body(Ring ring, const FftArgs &a,
   const RingDev rs = a.rings[south ? rr.y : rr.x];
   const int Nphi = fp.n;
   const bool ph_n = rn.phi0 != 0.0, ph_s = south && rs.phi0 != 0.0;
-  // inverse DFT via conj(DFT(conj(Z)))
-  if (fp.kind == 0) {
-    for (int k = threadIdx.x; k < Nphi; k += blockDim.x)
-      buf[k] = N::conj(spectrum_at<N>(a, j, p, k, Nphi, rn.phi0, rs.phi0, south, ph_n, ph_s));
-  } else if (fp.kind == 1) {
-    for (int q = threadIdx.x; q < Nphi - 1; q += blockDim.x)
-      buf[q] = N::conj(spectrum_at<N>(a, j, p, fp.perm_in[q], Nphi, rn.phi0, rs.phi0, south, ph_n, ph_s));
-    if (threadIdx.x == 0) sh_x0 = N::conj(spectrum_at<N>(a, j, p, 0, Nphi, rn.phi0, rs.phi0, south, ph_n, ph_s));
-  } else {
-    const C *chirp = N::chirp(fp);
-    for (int k = threadIdx.x; k < fp.len; k += blockDim.x)
-      buf[k] = (k < Nphi)
-                   ? N::mul(N::conj(spectrum_at<N>(a, j, p, k, Nphi, rn.phi0, rs.phi0, south, ph_n, ph_s)), N::ldg(chirp + k))
-                   : N::zero();
+  // the spectrum in natural order k = tid, tid + blockDim, ..., with the rings'
+  // phases walked along; inverse DFT via conj(DFT(conj(Z))).  Rader's input order
+  // is q with g^q = k: q = (N-1 - inv_out[k]) mod (N-1), as g^{-inv_out[k]} = k.
+  PhaseWalk<N> phn, phs;
+  C bn = N::zero(), bs = N::zero();
+  if (ph_n) {
+    phn.init(threadIdx.x, blockDim.x, rn.phi0);
+    bn = N::of(phase_of(Nphi, rn.phi0));
   }
+  if (ph_s) {
+    phs.init(threadIdx.x, blockDim.x, rs.phi0);
+    bs = N::of(phase_of(Nphi, rs.phi0));
+  }
+  const C *chirp = N::chirp(fp);
+  for (int k = threadIdx.x; k < Nphi; k += blockDim.x) {
+    const C z = N::conj(spectrum_at<N>(a, j, p, k, Nphi, south, ph_n, ph_s, phn.e, phs.e, bn, bs));
+    if (fp.kind == 0) {
+      buf[k] = z;
+    } else if (fp.kind == 1) {
+      if (k == 0)
+        sh_x0 = z;
+      else
+        buf[(Nphi - 1 - fp.inv_out[k]) % (Nphi - 1)] = z;
+    } else {
+      buf[k] = N::mul(z, N::ldg(chirp + k));
+    }
+    if (ph_n) phn.next();
+    if (ph_s) phs.next();
+  }
+  if (fp.kind == 2)
+    for (int k = Nphi + threadIdx.x; k < fp.len; k += blockDim.x) buf[k] = N::zero();
   __syncthreads();
   dft_run<N>(ring, fp, &sh_x0, &sh_a0);
   const C x0 = sh_x0, a0 = sh_a0;
@@ -650,6 +692,11 @@ __device__ __forceinline__ void fft_ana_kernel_body(Ring ring, const FftArgs &a,
   const int weighted = a.weighted;
   const typename N::S wn = N::scalar(rn.weight), ws = N::scalar(rs.weight);
   const bool ph_n = rn.phi0 != 0.0, ph_s = south && rs.phi0 != 0.0;
+  // phases e^{i m phi}: walked along m = mi when the m list is 0, 1, 2, ...
+  const bool walk = a.m_identity;
+  PhaseWalk<N> wpn, wps;
+  if (ph_n && walk) wpn.init(threadIdx.x, blockDim.x, rn.phi0);
+  if (ph_s && walk) wps.init(threadIdx.x, blockDim.x, rs.phi0);
   for (int mi = threadIdx.x; mi < a.nm; mi += blockDim.x) {
     const int m = a.mval[mi];
     const int k = m % Nphi, kn = (Nphi - k) % Nphi;
@@ -660,10 +707,16 @@ __device__ __forceinline__ void fft_ana_kernel_body(Ring ring, const FftArgs &a,
       pn = N::scale(pn, wn);
       ps = N::scale(ps, ws);
     }
-    double2 gn = N::val(pn), gs = N::val(ps);
-    if (ph_n) gn = cmul(gn, cconj(phase_of(m, rn.phi0)));
-    if (ph_s) gs = cmul(gs, cconj(phase_of(m, rs.phi0)));
-    if (!south) gs = make_double2(0.0, 0.0);
+    if (ph_n) {
+      pn = N::mul(pn, N::conj(walk ? wpn.e : N::of(phase_of(m, rn.phi0))));
+      if (walk) wpn.next();
+    }
+    if (ph_s) {
+      ps = N::mul(ps, N::conj(walk ? wps.e : N::of(phase_of(m, rs.phi0))));
+      if (walk) wps.next();
+    }
+    const double2 gn = N::val(pn);
+    const double2 gs = south ? N::val(ps) : make_double2(0.0, 0.0);
     double2 *g = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
     g[0] = gn;
     g[1] = gs;
@@ -726,6 +779,7 @@ static FftArgs make_fft_args(const sht_plan_s *P, const DevPtrs &map, int polar)
   a.nmaps_run = P->nmaps;
   a.pair0 = 0;
   a.npairs_run = P->npairs;
+  a.m_identity = P->m_identity;
   return a;
 }
 

@@ -906,6 +906,8 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   P->ncoef = nco;
   std::vector<int> minv(P->mmax + 1, -1);
   for (int i = 0; i < P->nm; ++i) minv[P->mval[i]] = i;
+  P->m_identity = 1;
+  for (int i = 0; i < P->nm; ++i) P->m_identity &= P->mval[i] == i;
   if ((rc = upload(P, P->mval, &P->d_mval)) != SHT_OK) return rc;
   if ((rc = upload(P, P->mstart, &P->d_mstart)) != SHT_OK) return rc;
   if ((rc = upload(P, coff, &P->d_coef_off)) != SHT_OK) return rc;

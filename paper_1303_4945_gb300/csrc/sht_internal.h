@@ -161,6 +161,7 @@ struct sht_plan_s {
   // per-step rounding by a power of l
   int fp64_m_below = 0;
   bool fft_df = false;  // ring FFTs in double-float (mixed plans, by default)
+  int m_identity = 0;   // the m list is 0, 1, ..., nm - 1
   // the FP64 columns run beside the mixed kernels: a side stream forked and joined by events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
