@@ -68,7 +68,7 @@ extern "C" {
 #define SHT_ECP_CC 2     /* theta_n = n pi / (nlat - 1),  n = 0..nlat-1 (Clenshaw-Curtis) */
 
 #define SHT_FP64 0  /* recursion and accumulation in IEEE double */
-#define SHT_MIXED 1 /* recursion and accumulation in compensated FP32 pairs; FP64 kept for tables, start values and FFT */
+#define SHT_MIXED 1 /* recursion, accumulation and (by default) ring FFTs in compensated FP32 pairs; FP64 kept for tables and start values */
 
 #define SHT_SYNTHESIS 0         /* a_lm -> map, Eq. syn_used */
 #define SHT_ANALYSIS 1          /* map -> a_lm, Eq. ana_used (with the ring weights) */

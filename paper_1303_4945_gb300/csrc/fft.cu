@@ -5,11 +5,10 @@
 // length Nphi (pairs always share Nphi).  The ring lives in shared memory
 // (up to kFftMaxLen points; longer rings in an L2-resident global scratch slot
 // per CTA of a persistent grid) and is transformed in place: mixed-radix
-// decimation-in-frequency
-// passes (radix 2, 4 and odd radices up to 31 with each thread running whole
-// butterflies, one barrier per pass; odd radices up to 127 as sweeps over the
-// ring); the output comes out digit-reversed and
-// is read back through a position table.  Lengths with a prime factor above
+// decimation-in-frequency passes (radix 2, 4 and small odd radices with each
+// thread running whole butterflies, one barrier per pass; larger odd radices up
+// to 127 as sweeps over the ring); the output comes out digit-reversed and is
+// read back through a position table.  Lengths with a prime factor above
 // 127 go through Rader's algorithm (prime n, n-1 smooth: a cyclic convolution
 // of length n-1) or Bluestein's (chirp convolution of smooth length >= 2n-1);
 // both convolutions run DIF forward and the transposed (DIT) passes back, so
@@ -22,9 +21,11 @@
 //
 // The engine is written once over a number policy: IEEE double (F64, plans of
 // the FP64 form) or double-float pairs on the FP32 pipe (DF, plans of the mixed
-// form: the FP32 pipe issues 64 times the FP64 rate on GB300, and ~46 bits an
-// operation keep the transform's relative error near 1e-14).  Ring pixels and
-// the F_m / G_m arrays stay FP64 in memory; DF converts on the way in and out.
+// form by default, see sht_plan_set_fft_precision: the FP32 pipe issues 64
+// times the FP64 rate on GB300, and ~46 bits an operation keep the transform's
+// relative error near 1e-14).  Ring pixels and the F_m / G_m arrays stay FP64 in
+// memory; DF converts on the way in and out.  Phases e^{i m phi0} are walked
+// along m (PhaseWalk) rather than evaluated per term.
 #include <algorithm>
 #include <mutex>
 #include <set>

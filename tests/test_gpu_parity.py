@@ -238,7 +238,7 @@ def test_polar_cut_matches_full_sum(sht):
                 assert rel_l2(c[o:o + n], r[o:o + n]) < FP64_L2 * 10, y
 
 
-def test_config1_round_trip(sht):
+def test_gl127_scalar_round_trip(sht):
     # GL 128 x 255, lmax = mmax = 127, spin 0, a_lm N(0,1) with a_l0 real, seed 0
     geom = sht.sht_geom_gauss(128, 255)
     lay = sht.sht_alm_create(127, 127)
@@ -324,7 +324,7 @@ def test_mixed_large_lmax_against_fp64(sht):
             assert rel_l2(g_[idx], r_[idx]) < MIX_L2
 
 
-def test_mixed_config1_round_trip(sht):
+def test_mixed_gl127_scalar_round_trip(sht):
     geom = sht.sht_geom_gauss(128, 255)
     lay = sht.sht_alm_create(127, 127)
     plan = sht.sht_plan_create(geom, lay, 0, 1, sht.SHT_MIXED)
