@@ -350,6 +350,12 @@ def roofline_for(stages, plan, spin, precision, peaks, steps):
                "algorithmic_fp32_ops_per_launch": ops,
                "fp64_equivalent_tflops": fp64_flops / sec / 1e12}
     out["frac"] = out["achieved"] / out["peak"]
+    measured = peaks.get("pipes_measured")  # this box's own microbenchmark (sht_measure_pipe_peaks)
+    if measured:
+        pm = measured["fp64_fma_tflops"] if precision == "fp64" else measured["fp32_fma_tops"]
+        out.update({"peak_measured": pm, "frac_of_measured": out["achieved"] / pm,
+                    "peak_measured_source": "sht_measure_pipe_peaks: independent FMA chains, "
+                                            + ("FP64 TFLOP/s" if precision == "fp64" else "FP32 T op/s")})
     key = ("fp64:" if precision == "fp64" else "mixed:") + name
     out["traffic"] = _traffic(kfile, key)
     out.update({"ms_per_launch": per_launch_ms, "triples_per_launch": triples})
@@ -610,6 +616,7 @@ def main():
     from paper_1303_4945_gb300 import inputs, sht
 
     peaks = _peaks()
+    peaks["pipes_measured"] = sht.sht_measure_pipe_peaks(local)
     geom = sht.sht_geom_gauss(NLAT, NLON)
     lay = sht.sht_alm_create(LMAX, LMAX)
     forms = {"fp64": sht.SHT_FP64}

@@ -286,6 +286,17 @@ SHT_API int sht_plan_get_fft_precision(sht_plan_t plan, int *precision);
 SHT_API int sht_plan_profile(sht_plan_t plan, int enable);
 SHT_API int sht_plan_profile_read(sht_plan_t plan, double *ms, int64_t *count);
 
+/* Measured throughput of the pipes the transforms run on (the denominators of
+ * their rooflines), on device (-1: the current one): every thread of a grid of 8
+ * CTAs x 256 threads per SM runs 8 independent chains of one operation; the
+ * best of three timed launches after an untimed one.  out[0] FP64 FMA in
+ * TFLOP/s (an FMA counted as 2 flops), out[1] FP32 FMA and out[2] FP32 add in
+ * T op/s (one per lane operation, as the mixed form's roofline counts them).
+ * Runs on a stream of its own and synchronises it (about 40 ms on a GB300).
+ * Errors: SHT_ERR_INVALID_ARG (NULL out, bad device), SHT_ERR_CUDA.
+ */
+SHT_API int sht_measure_pipe_peaks(int device, double *out);
+
 /* ---- transforms without allocation -------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that must
  * not allocate device memory while they run transforms -- code recorded under

@@ -72,6 +72,7 @@ _sig = {
     "sht_plan_set_fp64_columns": [_vp, ctypes.c_int],
     "sht_plan_get_fp64_columns": [_vp, _ip],
     "sht_plan_set_fft_precision": [_vp, ctypes.c_int],
+    "sht_measure_pipe_peaks": [ctypes.c_int, _dp],
     "sht_plan_get_fft_precision": [_vp, _ip],
     "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
@@ -348,6 +349,13 @@ class Batch(_Handle):
 
     def __len__(self):
         return _lib.sht_batch_size(self._h)
+
+
+def sht_measure_pipe_peaks(device=-1):
+    """Measured pipe throughput (see include/sht_gb300.h): FP64 FMA TFLOP/s, FP32 FMA and add T op/s."""
+    out = (ctypes.c_double * 3)()
+    _check(_lib.sht_measure_pipe_peaks(device, out), "sht_measure_pipe_peaks")
+    return {"fp64_fma_tflops": out[0], "fp32_fma_tops": out[1], "fp32_add_tops": out[2]}
 
 
 def sht_batch_create(plans) -> Batch:
