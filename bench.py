@@ -560,7 +560,7 @@ def run_healpix_workload(args, world, rank, local):
         if name == "mixed":
             clocks = sampler.stop()
         results[name] = ak.clone()
-        syn_l = 2 + (prec == sht.SHT_MIXED)  # (conversion) Legendre, FFT; no FP64 items below lmax 2700
+        syn_l = 2 + (prec == sht.SHT_MIXED)  # (conversion) Legendre, FFT; no FP64 items below lmax 2000
         forms[name] = {"ms_per_step": ms, "triples": plan.triples(0),
                        "rel_l2_vs_truth": float(torch.linalg.norm(ak - a) / torch.linalg.norm(a)),
                        "rel_l2_vs_truth_l_below_512": float(torch.linalg.norm((ak - a)[low])

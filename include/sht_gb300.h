@@ -244,9 +244,11 @@ SHT_API int sht_plan_autotune(sht_plan_t plan, void *cuda_stream, float *ms_per_
  * values lose accuracy first as lmax grows.  A mixed plan therefore runs the work
  * items of the columns m < m_below that touch a ring within 0.05 rad of a pole in
  * the FP64 kernels (same results as an FP64 plan there), on a high-priority side
- * stream beside the mixed kernels.  The default is floor((lmax / 2700)^3): 0
- * below lmax 2700, 3 at lmax 4095, 27 at 8191 (white-noise adjoint synthesis at
- * lmax 8191: 1.3e-11 relative to the FP64 form).  sht_plan_set_fp64_columns
+ * stream beside the mixed kernels.  The default is lmax / 170 from lmax 2000 on
+ * (12 at lmax 2047, 24 at 4095, 48 at 8191), 0 below: every ring's own error
+ * stays near or below 5e-11 (spin-2 synthesis against the FP64 form, ring by
+ * ring; the rings nearest the poles need the most columns), and the FP64 items
+ * stay hidden beside the mixed kernels.  sht_plan_set_fp64_columns
  * changes it (any m_below >= 0; it rebuilds the work lists and may allocate a
  * P/M table of ncoef x arrays x 16 bytes); sht_plan_get_fp64_columns reads it.
  * Errors: SHT_ERR_INVALID_ARG (NULL, an FP64 plan, a plan in a batch,

@@ -735,15 +735,15 @@ static std::vector<int> ana_ppt_candidates(int spin, int nj) {
 // array and its first tile; sizes the tile-sum array for this tiling.
 // Mixed form: columns m below this run in FP64 on the rings near the poles.  The
 // double-float recursion keeps ~48 bits; for small m near the poles it is
-// non-oscillatory over l < ~1/theta, where its per-step rounding grows like a
-// power of l, and the measured error of a column grows like lmax^2.4 (m+1)^-0.85
-// (white-noise inputs, against the FP64 form and the oracle).  (lmax / 2700)^3
-// keeps every column near or below 1e-10: 3 columns at lmax 4095, 27 at 8191,
-// none below lmax 2700.
-static int default_fp64_columns(int lmax) {
-  const double r = lmax / 2700.0;
-  return (int)std::floor(r * r * r);
-}
+// non-oscillatory over l < ~m/theta, where its per-step rounding grows like a
+// power of l.  On the rings nearest a pole the columns m > |s| still carry
+// weight theta^(m-|s|), so enough of them must run in FP64 for each ring's own
+// error (not only the map's) to stay below 1e-10: lmax / 170 columns (12 at
+// lmax 2047, 24 at 4095, 48 at 8191) keep every ring near or below 5e-11 in
+// spin-2 synthesis (measured against the FP64 form ring by ring), and their
+// FP64 items stay hidden on the side stream.  Below lmax 2000 the rings' errors
+// are below 3e-11 without them, and the items would no longer be hidden.
+static int default_fp64_columns(int lmax) { return lmax < 2000 ? 0 : lmax / 170; }
 
 // an item of column mi over ring pairs [p0, p1) runs in FP64 (mixed plans only)
 static bool lo_item(const sht_plan_s *P, int mi, int p0, int p1) {

@@ -1,6 +1,6 @@
 """Mixed-form plans whose small-m columns run in the FP64 kernels.
 
-The default threshold is 0 below lmax 2700, so these tests force one on small
+The default threshold is 0 below lmax 2000, so these tests force one on small
 plans: results must match the oracle for every transform type (those columns
 to the FP64 tolerance, the plan as a whole to the mixed one), inside a batch
 and through the no-alloc entry point; the threshold's default and its error
@@ -122,7 +122,9 @@ def test_default_and_errors(sht):
     with pytest.raises(sht.ShtError):
         mx.fp64_columns = -1
     big = sht.sht_plan_create(sht.sht_geom_gauss(4097, 5), sht.sht_alm_create(4095, 2), 0, 1, sht.SHT_MIXED)
-    assert big.fp64_columns == 3  # floor((4095 / 2700)^3)
+    assert big.fp64_columns == 24  # lmax / 170 from lmax 2000 on
+    small = sht.sht_plan_create(sht.sht_geom_gauss(1025, 5), sht.sht_alm_create(1023, 2), 0, 1, sht.SHT_MIXED)
+    assert small.fp64_columns == 0
 
 
 def test_fp64_items_under_graph_capture(sht):
