@@ -642,14 +642,16 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
   };
   const f2 zero[V] = {};
 
-  int since = 0;  // steps since the last exponent check
+  int since = 0;         // steps since the last exponent check
+  bool settled = false;  // every lane's values at scale 0: they stay there (warp-uniform)
   for (int lb = l0; lb <= lmax; lb += LC) {
     if (LC >= 2) {
 #pragma unroll 1
       for (int q = 0; q < LC; q += 2) {
         const int l = lb + q;
         if (l > lmax) break;
-        const int md = mode();
+        const int md = settled ? 0 : mode();
+        settled = md == 0;
         if (md == 2) {
           recur(l);
           recur(l + 1);
@@ -668,7 +670,7 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
           put(q + 1, c1);
         }
         since += 2;
-        if (since >= 8) {
+        if (!settled && since >= 8) {
           rescale_all();
           since = 0;
         }
@@ -676,9 +678,10 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
     } else {  // one degree per chunk: parity alternates between chunks
       f2 c0[V];
       const bool odd = ((lb - l0) & 1) != 0;
-      if (mode() == 0) step(lb, odd, true, c0); else step(lb, odd, false, c0);
+      settled = settled || mode() == 0;
+      if (settled) step(lb, odd, true, c0); else step(lb, odd, false, c0);
       put(0, c0);
-      if (++since >= 8) {
+      if (!settled && ++since >= 8) {
         rescale_all();
         since = 0;
       }
