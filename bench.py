@@ -280,8 +280,8 @@ MEASURED_TRAFFIC = {
     # sha256 over the kernel file and its device headers (_kernel_digest)
     "fp64:legendre_analysis": {"bytes": 706942720 + 941203200, "sha256": "51bcb216600e775f1f443ee0f293700420ed109bdb18207f7f532cafeff32dfc"},
     "fp64:legendre_synthesis": {"bytes": 554776320 + 323874816, "sha256": "51bcb216600e775f1f443ee0f293700420ed109bdb18207f7f532cafeff32dfc"},
-    "mixed:legendre_analysis": {"bytes": 659456256 + 3472259840, "sha256": "ec8c0715aba66b858b5c51dc8c10c80c9637772dfd1a38ee6e9c3f00a23cbf62"},
-    "mixed:legendre_synthesis": {"bytes": 545406208 + 321486080, "sha256": "ec8c0715aba66b858b5c51dc8c10c80c9637772dfd1a38ee6e9c3f00a23cbf62"},
+    "mixed:legendre_analysis": {"bytes": 656024320 + 3468856832, "sha256": "ea9f20645ae07514fcb5f42e7deb811cee55d6eed60c1317f38d6e7e20ba634f"},
+    "mixed:legendre_synthesis": {"bytes": 549227008 + 321439232, "sha256": "ea9f20645ae07514fcb5f42e7deb811cee55d6eed60c1317f38d6e7e20ba634f"},
 }
 
 
