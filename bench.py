@@ -581,6 +581,85 @@ def run_healpix_workload(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_variants_workload(args, world, rank, local):
+    """The transforms beyond the headline pair, each in both forms: derivative
+    synthesis at lmax 4095 (GL 4096 x 8191, Sect. 4.3), a spin-2 pair on the
+    reduced Gauss-Legendre grid at lmax 4095 (Sect. 4.4.2), a scalar pair on the
+    Clenshaw-Curtis grid (2049 x 4096) and one in real-harmonic storage (GL 2048 x
+    4095) at lmax 2047 (Sect. 4.4, 4.5), and a spin-37 pair at lmax 2047 (Sect.
+    4.1).  Each is timed with CUDA events; the line's value sums the mixed times."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1303_4945_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1303_4945_gb300 import inputs, sht
+
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(5)
+    cl = inputs.cl_inverse_square
+    items = [
+        ("deriv_synthesis_lmax4095", 4095, 1, lambda: sht.sht_geom_gauss(4096, 8191), "deriv", 0),
+        ("reduced_gl_spin2_pair_lmax4095", 4095, 2, lambda: sht.sht_geom_reduced_gauss(4096, 4095, 2), "pair", 0),
+        ("clenshaw_curtis_pair_lmax2047", 2047, 0, lambda: sht.sht_geom_ecp(sht.SHT_ECP_CC, 2049, 4096), "pair", 0),
+        ("real_harmonics_pair_lmax2047", 2047, 0, lambda: sht.sht_geom_gauss(2048, 4095), "pair",
+         sht.SHT_REAL_HARMONICS),
+        ("spin37_pair_lmax2047", 2047, 37, lambda: sht.sht_geom_gauss(2048, 4095), "pair", 0),
+    ]
+    results, total, launches = {}, 0.0, 0
+    sampler = ClockSampler(local)
+    sampler.start()
+    for name, lmax, spin, make, kind, flags in items:
+        geom = make()
+        lay = sht.sht_alm_create(lmax, lmax)
+        narr = 1 if (spin == 0 or kind == "deriv") else 2
+        alm = [torch.from_numpy(inputs.gaussian_alm(rng, lmax, lmax, cl=cl, lmin=0 if kind == "deriv" else spin)).cuda()
+               for _ in range(narr)]
+        nmaps = 2 if spin else 1
+        rec = {"npix": geom.npix}
+        outs = {}
+        for form, prec in (("fp64", sht.SHT_FP64), ("mixed", sht.SHT_MIXED)):
+            plan = sht.sht_plan_create(geom, lay, spin, 1, prec)
+            plan.autotune(stream)
+            maps = [torch.empty(geom.npix, dtype=torch.float64, device="cuda") for _ in range(nmaps)]
+            back = [torch.empty_like(a) for a in alm]
+
+            def step():
+                if kind == "deriv":
+                    sht.sht_execute(plan, sht.SHT_DERIV_SYNTHESIS, alm, maps, flags, stream)
+                else:
+                    sht.sht_execute(plan, sht.SHT_SYNTHESIS, alm, maps, flags, stream)
+                    sht.sht_execute(plan, sht.SHT_ANALYSIS, back, maps, flags, stream)
+
+            ms = _events_ms(torch, stream, step, args.steps, args.warmup, world)
+            plan.profile(True)
+            step()
+            counts = plan.profile_read()
+            plan.profile(False)
+            n_launch = int(sum(c for _, c in counts.values()))
+            rec[form] = {"ms": ms, "launches": n_launch}
+            outs[form] = [x.cpu().numpy() for x in maps] + ([] if kind == "deriv" else [x.cpu().numpy() for x in back])
+            if form == "mixed":
+                total += ms
+                launches += n_launch
+            del plan
+            torch.cuda.empty_cache()
+        rec["mixed_vs_fp64_rel_l2"] = max(float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                                          for a, b in zip(outs["mixed"], outs["fp64"]))
+        results[name] = rec
+    clocks = sampler.stop()
+    config = {"workload": "derivative synthesis (lmax 4095, GL 4096x8191), spin-2 pair on the reduced GL grid "
+                          "(lmax 4095), scalar pairs on Clenshaw-Curtis 2049x4096 and in real-harmonic storage "
+                          "(GL 2048x4095) at lmax 2047, spin-37 pair (lmax 2047); a_lm C_l=1/(l+1)^2 rng(5)",
+              "parallelism": "replicas"}
+    line = _line("ms per pass over the derivative / grid-variant / high-spin transforms", total, args, world, config,
+                 "f32x2", {"form": "mixed", "items": results, "clocks": clocks, "gpu_launches": launches * args.steps})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -592,10 +671,11 @@ def main():
     ap.add_argument("--lmax", type=int, default=4095, help="smaller sizes for profiling captures")
     ap.add_argument("--nlat", type=int, default=None,
                     help="fewer rings of the same length for profiling captures (default lmax + 1)")
-    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad", "healpix"],
+    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad", "healpix", "variants"],
                     help="spin2: the headline (spin-2 lmax 4095 pair); batch: 64 uneven scalar problems + "
                          "8 maps at lmax 2047 in one batch; grad: loss + gradient at lmax 8191; healpix: "
-                         "Jacobi-refined analysis on HEALPix Nside 512, lmax 1535")
+                         "Jacobi-refined analysis on HEALPix Nside 512, lmax 1535; variants: derivative "
+                         "synthesis, grid variants, real harmonics, spin 37")
     args = ap.parse_args()
     set_workload(args.lmax, args.nlat)
     world, rank, local = dist_setup()
@@ -603,7 +683,8 @@ def main():
         run_reference(args, world, rank)
         return
     if args.workload != "spin2":
-        runners = {"batch": run_batch_workload, "grad": run_grad_workload, "healpix": run_healpix_workload}
+        runners = {"batch": run_batch_workload, "grad": run_grad_workload, "healpix": run_healpix_workload,
+                   "variants": run_variants_workload}
         runners[args.workload](args, world, rank, local)
         return
     import numpy as np

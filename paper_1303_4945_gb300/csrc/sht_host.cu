@@ -172,9 +172,12 @@ static int smooth235(int n) {
 }
 
 // Sect. 4.4.2: Gauss-Legendre rings thinned by the polar optimisation.  Eq.
-// eq_polaropt solved for m: sqrt(m^2 + s^2 - 2 m s cos(theta)) = T + lmax sin(theta)
-// gives m_y = s cos(theta) + sqrt((T + lmax sin(theta))^2 - s^2 sin^2(theta)),
-// T = max(100, 0.01 lmax); ring y gets the smallest 2^a 3^b 5^c >= 2 min(m_y, lmax) + 1
+// eq_polaropt solved for m: sqrt(m^2 + s^2 - 2 m s cos(theta)) = T + lmax sin(theta).
+// A ring carries the terms of both m and -m, for which the sign of m s cos(theta)
+// differs, so its band limit is the larger root:
+//   m_y = |s| |cos(theta)| + sqrt((T + lmax sin(theta))^2 - s^2 sin^2(theta)),
+// T = max(100, 0.01 lmax), the same on mirrored rings (which thus keep sharing one
+// Legendre evaluation); ring y gets the smallest 2^a 3^b 5^c >= 2 min(m_y, lmax) + 1
 // pixels and the weight w_GL 2 pi / Nphi_y.
 extern "C" int sht_geom_reduced_gauss(int nlat, int lmax, int spin, sht_geom_t *out) {
   if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
@@ -189,7 +192,7 @@ extern "C" int sht_geom_reduced_gauss(int nlat, int lmax, int spin, sht_geom_t *
   int64_t o = 0;
   for (int i = 0; i < nlat; ++i) {
     const double c = cos(th[i]), sn = sin(th[i]), r = T + lmax * sn;
-    const double m = s * c + sqrt(std::max(0.0, r * r - s * s * sn * sn));
+    const double m = s * fabs(c) + sqrt(std::max(0.0, r * r - s * s * sn * sn));
     const int mm = (int)std::min<double>(lmax, floor(m));
     nphi[i] = smooth235(2 * mm + 1);
     ofs[i] = o;

@@ -128,12 +128,14 @@ def test_reduced_gauss_geometry():
         T = max(100.0, 0.01 * lmax)
         th = red["theta"]
         r = T + lmax * np.sin(th)
-        m = np.minimum(lmax, np.floor(abs(spin) * np.cos(th) + np.sqrt(r * r - spin * spin * np.sin(th) ** 2)))
+        # the larger root (the terms of m and -m): the same on mirrored rings
+        m = np.minimum(lmax, np.floor(abs(spin) * np.abs(np.cos(th)) + np.sqrt(r * r - spin * spin * np.sin(th) ** 2)))
         for n, mm in zip(red["nphi"], m):
             lo = int(2 * mm + 1)
             assert n >= lo and _smooth235(int(n))
             assert not any(_smooth235(x) for x in range(lo, int(n)))  # the smallest such length
         assert abs(np.sum(red["nphi"] * red["weight"]) - 4 * np.pi) < 1e-12
         assert np.all(np.diff(red["ofs"]) == red["nphi"][:-1])
+        np.testing.assert_array_equal(red["nphi"], red["nphi"][::-1])  # mirrored rings pair up
     red = sht.sht_geom_reduced_gauss(2048, 2047)
     assert red.npix < 0.7 * 2048 * 4095  # more than 30% of the pixels saved at lmax > 1000
