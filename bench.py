@@ -259,6 +259,26 @@ def time_form(sht, torch, plan, alm_d, maps_d, out_d, steps, warmup, world, stre
     return max_over_ranks(ms, world), stages
 
 
+def paper_rule_times(sht, torch, plan, alm_d, maps_d, out_d, stream, budget_s=2.0, max_pairs=60):
+    """The paper's timing rule (Sect. 5.2): repeat the pair until at least 2 s have
+    accumulated and take the minimum per direction; the median beside it."""
+    import statistics
+
+    syn, ana = [], []
+    while sum(syn) + sum(ana) < 1e3 * budget_s and len(syn) < max_pairs:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        sht.sht_execute(plan, sht.SHT_SYNTHESIS, alm_d, maps_d, 0, stream)
+        ev[1].record(stream)
+        sht.sht_execute(plan, sht.SHT_ANALYSIS, out_d, maps_d, 0, stream)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        syn.append(ev[0].elapsed_time(ev[1]))
+        ana.append(ev[1].elapsed_time(ev[2]))
+    return {"pairs": len(syn), "synthesis_ms_min": min(syn), "synthesis_ms_median": statistics.median(syn),
+            "analysis_ms_min": min(ana), "analysis_ms_median": statistics.median(ana)}
+
+
 # FP32-pipe operations (FADD, FMUL and FFMA count one each: the pipe issues one
 # of them per lane per clock) of the double-float arithmetic per (m, l,
 # ring-pair) step, counted from the kernel source: a compensated multiply-add
@@ -730,6 +750,8 @@ def main():
                          "tiling": {"analysis_pairs_per_thread": plan.tiling()[0],
                                     "autotune_ms_per_candidate": {str(k): v for k, v in tune.items()}}}
         outputs[name] = {"maps": [m.cpu().numpy() for m in maps_d], "alm": [a.cpu().numpy() for a in out_d]}
+        if world == 1:
+            results[name]["paper_rule"] = paper_rule_times(sht, torch, plan, alm_d, maps_d, out_d, stream)
         if prec == sht.SHT_MIXED:  # the same plan with the FP64 ring-FFT engine (not the headline)
             plan.fft_precision = sht.SHT_FP64
             ms64, st64 = time_form(sht, torch, plan, alm_d, maps_d, out_d, args.steps, args.warmup, world, stream)
