@@ -735,9 +735,14 @@ def main():
     results = {}
     outputs = {}
     sampler = ClockSampler(local)
+    data_bytes = sum(a.nbytes for a in alm_h) + 8 * 2 * geom.npix  # a_lm and maps of one pair
     for name, prec in forms.items():
+        t0 = time.perf_counter()
         plan = sht.sht_plan_create(geom, lay, SPIN, 1, prec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         tune = plan.autotune(stream)  # analysis tiling, chosen by timing (outside the timed region)
+        t2 = time.perf_counter()
         if name == list(forms)[-1]:
             sampler.start()
         ms, stages = time_form(sht, torch, plan, alm_d, maps_d, out_d, args.steps, args.warmup, world, stream)
@@ -746,6 +751,8 @@ def main():
         results[name] = {"ms_per_step": ms, "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
                          "roofline": roofline_for(stages, plan, SPIN, name, peaks, args.steps),
                          "triples": plan.triples(0), "workspace_bytes": plan.workspace(),
+                         "setup": {"plan_create_ms": 1e3 * (t1 - t0), "autotune_ms": 1e3 * (t2 - t1),
+                                   "workspace_over_data": plan.workspace() / data_bytes},
                          "fp64_columns": plan.fp64_columns if prec == sht.SHT_MIXED else 0,
                          "tiling": {"analysis_pairs_per_thread": plan.tiling()[0],
                                     "autotune_ms_per_candidate": {str(k): v for k, v in tune.items()}}}
