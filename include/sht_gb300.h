@@ -299,6 +299,16 @@ SHT_API int sht_plan_profile_read(sht_plan_t plan, double *ms, int64_t *count);
  */
 SHT_API int sht_measure_pipe_peaks(int device, double *out);
 
+/* How the ring FFTs (Eqs. syn1, ana2) transform a ring of n points; host logic
+ * only, no device needed.  kind: 0 mixed radix of length n, 1 Rader (n prime,
+ * n - 1 smooth) of length n - 1, 2 Bluestein (a chirp convolution) of length
+ * len >= 2n - 1.  radices[0..nrad) (caller-owned, room for 24) are the passes of
+ * the length-len transform in order: 4s, a 2, then odd radices up to 127
+ * ascending; their product is len.  Errors: SHT_ERR_INVALID_ARG (NULL, n < 1),
+ * SHT_ERR_UNSUPPORTED (no transform of at most 65536 points fits).
+ */
+SHT_API int sht_fft_plan_info(int n, int *kind, int *len, int *nrad, int *radices);
+
 /* ---- transforms without allocation -------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that must
  * not allocate device memory while they run transforms -- code recorded under

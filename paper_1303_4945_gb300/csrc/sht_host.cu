@@ -573,37 +573,58 @@ static int upload_pairs(sht_plan_s *P, const double2 *d, int len, const float4 *
   return dev_upload(P, f, out);
 }
 
+// How a ring of n points is transformed (host logic only): kind 0 mixed radix
+// of length n, 1 Rader (n prime, n-1 smooth) of length n-1, 2 Bluestein of the
+// convolution length >= 2n-1 that the pass model rates cheapest among the
+// smooth lengths up to the first one whose radices are all <= 31.  Returns
+// false when no length up to kFftMaxGlobalLen fits.
+static bool fft_choose(int n, int &kind, int &len, std::vector<int> &rad) {
+  if (n <= kFftMaxGlobalLen && factor_small(n, rad)) {
+    kind = 0;
+    len = n;
+    return true;
+  }
+  if (is_prime(n) && n - 1 <= kFftMaxGlobalLen && factor_small(n - 1, rad)) {
+    kind = 1;
+    len = n - 1;
+    return true;
+  }
+  int best = 0;
+  double best_cost = 0.0;
+  for (int M = 2 * n - 1; M <= kFftMaxGlobalLen; ++M) {
+    if (!factor_small(M, rad)) continue;
+    const double c = M * fft_cost_per_point(rad);
+    if (best == 0 || c < best_cost) {
+      best = M;
+      best_cost = c;
+    }
+    if (rad.back() <= kMaxRadix) break;
+  }
+  if (best == 0) return false;
+  factor_small(best, rad);
+  kind = 2;
+  len = best;
+  return true;
+}
+
+extern "C" int sht_fft_plan_info(int n, int *kind, int *len, int *nrad, int *radices) {
+  if (!kind || !len || !nrad || !radices) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(SHT_ERR_INVALID_ARG, "ring length must be >= 1");
+  std::vector<int> rad;
+  if (!fft_choose(n, *kind, *len, rad))
+    return fail(SHT_ERR_UNSUPPORTED, "ring length %d: no FFT of size <= %d available", n, kFftMaxGlobalLen);
+  *nrad = (int)rad.size();
+  for (int i = 0; i < *nrad; ++i) radices[i] = rad[i];
+  return SHT_OK;
+}
+
 static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scratch_dev) {
   memset(&fp, 0, sizeof(fp));
   fp.n = n;
   std::vector<int> rad;
   int rc;
-  if (n <= kFftMaxGlobalLen && factor_small(n, rad)) {
-    fp.kind = 0;
-    fp.len = n;
-  } else if (is_prime(n) && n - 1 <= kFftMaxGlobalLen && factor_small(n - 1, rad)) {
-    fp.kind = 1;
-    fp.len = n - 1;
-  } else {
-    // convolution length >= 2n-1: the cheapest by the pass model among the
-    // smooth lengths up to the first one whose radices are all <= 31
-    int best = 0;
-    double best_cost = 0.0;
-    for (int M = 2 * n - 1; M <= kFftMaxGlobalLen; ++M) {
-      if (!factor_small(M, rad)) continue;
-      const double c = M * fft_cost_per_point(rad);
-      if (best == 0 || c < best_cost) {
-        best = M;
-        best_cost = c;
-      }
-      if (rad.back() <= kMaxRadix) break;
-    }
-    if (best == 0)
-      return fail(SHT_ERR_UNSUPPORTED, "ring length %d: no FFT of size <= %d available", n, kFftMaxGlobalLen);
-    factor_small(best, rad);
-    fp.kind = 2;
-    fp.len = best;
-  }
+  if (!fft_choose(n, fp.kind, fp.len, rad))
+    return fail(SHT_ERR_UNSUPPORTED, "ring length %d: no FFT of size <= %d available", n, kFftMaxGlobalLen);
   fp.nrad = (int)rad.size();
   for (int i = 0; i < fp.nrad; ++i) fp.rad[i] = rad[i];
   if ((rc = dev_upload(P, twiddles(fp.len), &fp.w)) != SHT_OK) return rc;

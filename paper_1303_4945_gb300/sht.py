@@ -73,6 +73,7 @@ _sig = {
     "sht_plan_get_fp64_columns": [_vp, _ip],
     "sht_plan_set_fft_precision": [_vp, ctypes.c_int],
     "sht_measure_pipe_peaks": [ctypes.c_int, _dp],
+    "sht_fft_plan_info": [ctypes.c_int, _ip, _ip, _ip, _ip],
     "sht_plan_get_fft_precision": [_vp, _ip],
     "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
@@ -356,6 +357,14 @@ def sht_measure_pipe_peaks(device=-1):
     out = (ctypes.c_double * 3)()
     _check(_lib.sht_measure_pipe_peaks(device, out), "sht_measure_pipe_peaks")
     return {"fp64_fma_tflops": out[0], "fp32_fma_tops": out[1], "fp32_add_tops": out[2]}
+
+
+def sht_fft_plan_info(n):
+    """(kind, transform length, radices) for a ring of n points: kind 0 mixed radix, 1 Rader, 2 Bluestein."""
+    kind, ln, nrad = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rad = (ctypes.c_int * 24)()
+    _check(_lib.sht_fft_plan_info(n, ctypes.byref(kind), ctypes.byref(ln), ctypes.byref(nrad), rad), "sht_fft_plan_info")
+    return kind.value, ln.value, [rad[i] for i in range(nrad.value)]
 
 
 def sht_batch_create(plans) -> Batch:

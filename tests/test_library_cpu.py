@@ -139,3 +139,48 @@ def test_reduced_gauss_geometry():
         np.testing.assert_array_equal(red["nphi"], red["nphi"][::-1])  # mirrored rings pair up
     red = sht.sht_geom_reduced_gauss(2048, 2047)
     assert red.npix < 0.7 * 2048 * 4095  # more than 30% of the pixels saved at lmax > 1000
+
+
+def _is_prime(n):
+    return n > 1 and all(n % d for d in range(2, int(n ** 0.5) + 1))
+
+
+def test_fft_plan_choice():
+    # the ring-FFT planner (host logic): kind 0 direct mixed radix, 1 Rader, 2 Bluestein
+    known = {
+        8191: (1, 8190, [2, 3, 3, 5, 7, 13]),     # the bench's rings: prime, Rader over 8190
+        4095: (0, 4095, [3, 3, 5, 7, 13]),
+        37: (0, 37, [37]),                        # one large radix
+        16383: (0, 16383, [3, 43, 127]),          # 3 43 127: the largest radix
+        131: (1, 130, [2, 5, 13]),
+        149: (1, 148, [4, 37]),
+        20011: (1, 20010, [2, 3, 5, 23, 29]),
+        20480: (0, 20480, [4, 4, 4, 4, 4, 4, 5]),
+        262: (2, 525, [3, 5, 5, 7]),              # 2 131: Bluestein, convolution >= 523
+        2367: (2, 4736, [4, 4, 4, 2, 37]),
+        14803: (2, 29624, [4, 2, 7, 23, 23]),
+        1: (0, 1, []),
+    }
+    for n, want in known.items():
+        assert sht.sht_fft_plan_info(n) == want, n
+    allowed = {2, 4} | {p for p in range(3, 128, 2) if _is_prime(p)}
+    for n in range(1, 3001):
+        kind, ln, rad = sht.sht_fft_plan_info(n)
+        assert int(np.prod(rad)) == ln and set(rad) <= allowed, n
+        assert rad == sorted(rad, key=lambda r: (r not in (2, 4), r == 2, r)), n  # 4s, a 2, odd ascending
+        assert rad.count(2) <= 1
+        if kind == 0:
+            assert ln == n
+        elif kind == 1:
+            assert _is_prime(n) and ln == n - 1
+            assert any(p > 127 for p in range(2, n + 1) if n % p == 0 and _is_prime(p))  # not direct
+        else:
+            assert kind == 2 and ln >= 2 * n - 1
+            assert not _is_prime(n) or any(p > 127 for p in range(2, n) if (n - 1) % p == 0 and _is_prime(p))
+    for bad in (0, -5):
+        with pytest.raises(sht.ShtError) as ei:
+            sht.sht_fft_plan_info(bad)
+        assert ei.value.code == sht.SHT_ERR_INVALID_ARG
+    with pytest.raises(sht.ShtError) as ei:  # 2 20011: Bluestein would need more than 65536 points
+        sht.sht_fft_plan_info(40022)
+    assert ei.value.code == sht.SHT_ERR_UNSUPPORTED
