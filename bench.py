@@ -298,8 +298,8 @@ def f32_ops_per_triple(spin, ncomp):
 MEASURED_TRAFFIC = {
     # profiles/dram_traffic_spin2_lmax4095.md (spin 2, GL 4096 x 8191, lmax 4095, one launch each);
     # sha256 over the kernel file and its device headers (_kernel_digest)
-    "fp64:legendre_analysis": {"bytes": 706942720 + 941203200, "sha256": "51bcb216600e775f1f443ee0f293700420ed109bdb18207f7f532cafeff32dfc"},
-    "fp64:legendre_synthesis": {"bytes": 554776320 + 323874816, "sha256": "51bcb216600e775f1f443ee0f293700420ed109bdb18207f7f532cafeff32dfc"},
+    "fp64:legendre_analysis": {"bytes": 708601344 + 941840384, "sha256": "cd3970788aed5e416475654291e228e1996a18a954c89025fa9634f97ca50d43"},
+    "fp64:legendre_synthesis": {"bytes": 552622848 + 323180544, "sha256": "cd3970788aed5e416475654291e228e1996a18a954c89025fa9634f97ca50d43"},
     "mixed:legendre_analysis": {"bytes": 656024320 + 3468856832, "sha256": "ea9f20645ae07514fcb5f42e7deb811cee55d6eed60c1317f38d6e7e20ba634f"},
     "mixed:legendre_synthesis": {"bytes": 549227008 + 321439232, "sha256": "ea9f20645ae07514fcb5f42e7deb811cee55d6eed60c1317f38d6e7e20ba634f"},
 }

@@ -228,8 +228,7 @@ __device__ __forceinline__ void leg_syn_spin_body(const LegArgs &a, double *cons
       s4[j][1] = fma(M.y, sp, s4[j][1]);
     }
     const Coef c = ldg_coef(cf + l);
-    const double t = c.a * x;
-    const double u = t + c.ak, v = t - c.ak;
+    const double u = fma(c.a, x, c.ak), v = fma(c.a, x, -c.ak);  // A x +- AK, one rounding each
     const double np_ = fma(u, lpc, -c.c * lpp);
     const double nm_ = fma(v, lmc, -c.c * lmp);
     lpp = lpc;
@@ -245,9 +244,8 @@ __device__ __forceinline__ void leg_syn_spin_body(const LegArgs &a, double *cons
       for (int k = 0; k < 8; ++k) {
         if (l <= lmax) {
           const Coef c = ldg_coef(cf + l);
-          const double t = c.a * x;
-          const double np_ = fma(t + c.ak, lpc, -c.c * lpp);
-          const double nm_ = fma(t - c.ak, lmc, -c.c * lmp);
+          const double np_ = fma(fma(c.a, x, c.ak), lpc, -c.c * lpp);
+          const double nm_ = fma(fma(c.a, x, -c.ak), lmc, -c.c * lmp);
           lpp = lpc;
           lpc = np_;
           lmp = lmc;
@@ -565,9 +563,8 @@ __device__ __forceinline__ void leg_ana_spin_body(const LegArgs &a, double *cons
           const Coef c = ldg_coef(cf + l);
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            const double t = c.a * x[k];
-            const double np_ = fma(t + c.ak, lpc[k], -c.c * lpp[k]);
-            const double nm_ = fma(t - c.ak, lmc[k], -c.c * lmp[k]);
+            const double np_ = fma(fma(c.a, x[k], c.ak), lpc[k], -c.c * lpp[k]);
+            const double nm_ = fma(fma(c.a, x[k], -c.ak), lmc[k], -c.c * lmp[k]);
             lpp[k] = lpc[k];
             lpc[k] = np_;
             lmp[k] = lmc[k];
@@ -613,8 +610,7 @@ __device__ __forceinline__ void leg_ana_spin_body(const LegArgs &a, double *cons
             v[o + 2] = fma(wm, wmn[k][j][0], fma(sp, wms[k][j][0], v[o + 2]));
             v[o + 3] = fma(wm, wmn[k][j][1], fma(sp, wms[k][j][1], v[o + 3]));
           }
-          const double t = c.a * x[k];
-          const double u = t + c.ak, w = t - c.ak;
+          const double u = fma(c.a, x[k], c.ak), w = fma(c.a, x[k], -c.ak);  // A x +- AK, one rounding each
           const double np_ = fma(u, lpc[k], -c.c * lpp[k]);
           const double nm_ = fma(w, lmc[k], -c.c * lmp[k]);
           lpp[k] = lpc[k];
