@@ -309,6 +309,20 @@ SHT_API int sht_measure_pipe_peaks(int device, double *out);
  */
 SHT_API int sht_fft_plan_info(int n, int *kind, int *len, int *nrad, int *radices);
 
+/* The polar optimisation (Sect. 3.3, Eq. eq_polaropt, T = max(100, 0.01 lmax)) as
+ * a plan of this geometry, lmax and spin applies it; host logic only, no device
+ * needed.  Ring pairs (sht_geom_info's npairs) are ordered from the poles towards
+ * the equator; for each of the nm values mval[i] (0 <= m <= lmax) first_pair[i]
+ * is the first pair kept (npairs: none), the cut being a prefix.  pair_theta, if
+ * not NULL, receives the northern ring's theta of every pair in that order
+ * (npairs doubles).  *triples = sum over m of (npairs - first_pair) (lmax -
+ * max(m, |spin|) + 1), the (m, l, ring-pair) steps of one Legendre stage.
+ * Arrays are caller-owned.  Errors: SHT_ERR_INVALID_ARG (NULL, lmax < 0, nm < 1,
+ * m outside 0..lmax).
+ */
+SHT_API int sht_geom_polar_cut(sht_geom_t geom, int lmax, int spin, int nm, const int *mval, int *first_pair,
+                               double *pair_theta, int64_t *triples);
+
 /* ---- transforms without allocation -------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that must
  * not allocate device memory while they run transforms -- code recorded under

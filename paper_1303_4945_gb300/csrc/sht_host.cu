@@ -698,6 +698,54 @@ static int build_fft_plan(sht_plan_s *P, int n, FftPlanDev &fp, FftPlanDev *scra
   return SHT_OK;
 }
 
+// Polar cut (Sect. 3.3): skip (m, pair) when
+//   sqrt(m^2 + s^2 - 2 m s cos theta) - lmax sin theta > T,  T = max(100, 0.01 lmax),
+// for both rings of the pair (cos theta and -cos theta: the smaller root, |m s| |cos theta|).
+// Pairs run from the poles towards the equator, so for each m the cut is a
+// prefix: the result is the index of the first pair kept (npairs if none).
+static std::vector<int> polar_first_pairs(const sht_geom_s *g, const std::vector<int> &pair_n, int lmax, int spin,
+                                          const std::vector<int> &mval) {
+  const double T = std::max(100.0, 0.01 * lmax), s = spin;
+  const int npairs = (int)pair_n.size();
+  std::vector<int> first(mval.size(), npairs);
+  for (size_t i = 0; i < mval.size(); ++i) {
+    const double m = mval[i];
+    for (int p = 0; p < npairs; ++p) {
+      const double th = g->theta[pair_n[p]];
+      const double c = fabs(cos(th)), sn = sin(th);
+      const double v = sqrt(std::max(0.0, m * m + s * s - 2.0 * fabs(m * s) * c)) - lmax * sn;
+      if (!(v > T)) {
+        first[i] = p;
+        break;
+      }
+    }
+  }
+  return first;
+}
+
+extern "C" int sht_geom_polar_cut(sht_geom_t g, int lmax, int spin, int nm, const int *mval, int *first_pair,
+                                  double *pair_theta, int64_t *triples) {
+  if (!g || !mval || !first_pair || !triples) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  if (lmax < 0 || nm < 1) return fail(SHT_ERR_INVALID_ARG, "lmax >= 0 and nm >= 1 required");
+  std::vector<int> pn, ps;
+  pair_rings(g, pn, ps);
+  std::vector<int> mv(mval, mval + nm);
+  for (int m : mv)
+    if (m < 0 || m > lmax) return fail(SHT_ERR_INVALID_ARG, "m = %d outside 0..lmax", m);
+  const std::vector<int> first = polar_first_pairs(g, pn, lmax, spin, mv);
+  const int as = spin < 0 ? -spin : spin;
+  int64_t trip = 0;
+  for (int i = 0; i < nm; ++i) {
+    first_pair[i] = first[i];
+    const int nl = lmax - std::max(mv[i], as) + 1;
+    if (nl > 0) trip += (int64_t)(pn.size() - first[i]) * nl;
+  }
+  if (pair_theta)
+    for (size_t p = 0; p < pn.size(); ++p) pair_theta[p] = g->theta[pn[p]];
+  *triples = trip;
+  return SHT_OK;
+}
+
 // ----------------------------------------------------------------------------
 // Plans
 // ----------------------------------------------------------------------------
@@ -952,25 +1000,7 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   CUDA_TRY(launch_coef_tables(P, 0));
   CUDA_TRY(cudaDeviceSynchronize());
 
-  // ---- polar cut (Sect. 3.3): skip (m, pair) when
-  //      sqrt(m^2 + s^2 - 2 m s cos theta) - lmax sin theta > T,  T = max(100, 0.01 lmax),
-  //      for both rings of the pair (cos theta and -cos theta).
-  const double T = std::max(100.0, 0.01 * P->lmax);
-  P->first_pair.assign(P->nm, 0);
-  for (int i = 0; i < P->nm; ++i) {
-    double m = P->mval[i], s = P->spin;
-    int first = P->npairs;
-    for (int p = 0; p < P->npairs; ++p) {
-      double th = g->theta[P->pair_n[p]];
-      double c = fabs(cos(th)), sn = sin(th);
-      double v = sqrt(std::max(0.0, m * m + s * s - 2.0 * fabs(m * s) * c)) - P->lmax * sn;
-      if (!(v > T)) {
-        first = p;
-        break;
-      }
-    }
-    P->first_pair[i] = first;
-  }
+  P->first_pair = polar_first_pairs(g, P->pair_n, P->lmax, P->spin, P->mval);
 
   // ---- work lists ----
   P->fp64_m_below = P->precision == SHT_MIXED ? default_fp64_columns(P->lmax) : 0;

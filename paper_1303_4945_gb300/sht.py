@@ -74,6 +74,7 @@ _sig = {
     "sht_plan_set_fft_precision": [_vp, ctypes.c_int],
     "sht_measure_pipe_peaks": [ctypes.c_int, _dp],
     "sht_fft_plan_info": [ctypes.c_int, _ip, _ip, _ip, _ip],
+    "sht_geom_polar_cut": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, _i64p],
     "sht_plan_get_fft_precision": [_vp, _ip],
     "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
@@ -365,6 +366,17 @@ def sht_fft_plan_info(n):
     rad = (ctypes.c_int * 24)()
     _check(_lib.sht_fft_plan_info(n, ctypes.byref(kind), ctypes.byref(ln), ctypes.byref(nrad), rad), "sht_fft_plan_info")
     return kind.value, ln.value, [rad[i] for i in range(nrad.value)]
+
+
+def sht_geom_polar_cut(geom: Geometry, lmax, spin, mval):
+    """(first kept ring pair per m, each pair's northern theta, triples) of the polar optimisation."""
+    mv = np.ascontiguousarray(mval, dtype=np.int32)
+    first = np.empty(len(mv), np.int32)
+    th = np.empty(geom.info()[2], np.float64)
+    trip = ctypes.c_int64()
+    _check(_lib.sht_geom_polar_cut(geom.handle, lmax, spin, len(mv), _ptr(mv, _ip), _ptr(first, _ip), _ptr(th, _dp),
+                                   ctypes.byref(trip)), "sht_geom_polar_cut")
+    return first, th, trip.value
 
 
 def sht_batch_create(plans) -> Batch:

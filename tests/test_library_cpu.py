@@ -184,3 +184,32 @@ def test_fft_plan_choice():
     with pytest.raises(sht.ShtError) as ei:  # 2 20011: Bluestein would need more than 65536 points
         sht.sht_fft_plan_info(40022)
     assert ei.value.code == sht.SHT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("spin", [0, 2, -3])
+def test_polar_cut(spin):
+    # Sect. 3.3: (m, pair) is skipped when sqrt(m^2 + s^2 - 2 |m s| |cos theta|) - lmax sin theta > T,
+    # T = max(100, 0.01 lmax); pairs run pole -> equator, so the kept pairs of each m are a suffix
+    lmax = 1023
+    geom = sht.sht_geom_gauss(lmax + 1, 2 * lmax + 1)
+    mval = np.arange(lmax + 1)
+    first, th, trip = sht.sht_geom_polar_cut(geom, lmax, spin, mval)
+    npairs = geom.info()[2]
+    assert len(th) == npairs == (lmax + 1) // 2
+    gl = np.sort(geom.rings()["theta"])[:npairs]
+    np.testing.assert_array_equal(th, gl)  # GL: pair p holds the p-th ring from the north pole
+    T = max(100.0, 0.01 * lmax)
+    s = abs(spin)
+    for m in (0, 1, 7, 300, 600, 800, 1023):
+        v = np.sqrt(np.maximum(0.0, m * m + s * s - 2.0 * m * s * np.abs(np.cos(th)))) - lmax * np.sin(th)
+        skipped = v > T
+        assert first[m] == (np.argmin(skipped) if not skipped.all() else npairs), m
+        assert skipped[:first[m]].all() and not skipped[first[m]:].any(), m  # a prefix
+    assert first[0] == 0 and np.all(np.diff(first) >= 0)  # more of the cap skipped as m grows
+    l0 = np.maximum(mval, s)
+    assert trip == int(np.sum((npairs - first) * (lmax - l0 + 1)))
+    full = int(np.sum(npairs * (lmax - l0 + 1)))
+    assert 0.6 * full < trip < full  # the cut removes a fifth or so of the steps on GL
+    for bad in ([lmax + 1], [-1]):
+        with pytest.raises(sht.ShtError):
+            sht.sht_geom_polar_cut(geom, lmax, spin, bad)
