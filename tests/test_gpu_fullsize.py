@@ -51,6 +51,8 @@ def test_headline_workload_against_oracle(setup, precision):
     sht, rings, alm, maps_in, ref_syn, ref_ana = setup
     geom = sht.sht_geom_gauss(NLAT, NLON)
     plan = sht.sht_plan_create(geom, sht.sht_alm_create(LMAX, LMAX), SPIN, 1, precision)
+    # the plan's work (the bench's roofline counts it) is the polar cut's host count
+    assert plan.triples(0) == sht.sht_geom_polar_cut(geom, LMAX, SPIN, np.arange(LMAX + 1))[2]
     stream = torch.cuda.current_stream()
     plan.autotune(stream)
     a_d = [torch.from_numpy(a).cuda() for a in alm]
