@@ -23,7 +23,7 @@ constexpr int kMaxPtr = 32;       // max device pointers per execute (maps or a_
 constexpr int kMaxJobs = 16;      // ncomp limit
 constexpr int kSynTile = 128;     // ring pairs per synthesis Legendre CTA (one per thread)
 constexpr int kAnaThreads = 128;  // threads per analysis Legendre CTA
-constexpr int kMaxRadix = 8 * 4;  // generic odd radix limit of the FFT engine (primes <= 31)
+constexpr int kMaxRadix = 8 * 4;  // odd radices with register butterflies and constant cos/sin tables (primes <= 31)
 constexpr int kMaxBigRadix = 127;  // odd radices above 31 run as shared-memory sweeps (fft_stage_big)
 constexpr int kFftThreads = 512;
 constexpr int kFftMinBlocks = 512 / kFftThreads;  // launch bound: at most 128 registers a thread
