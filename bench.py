@@ -145,6 +145,30 @@ def max_over_ranks(x, world):
 
 
 # ------------------------------------------------------------------ oracle ---
+_SMALL_ORACLE = """
+import time, numpy as np, oracle
+from paper_1303_4945_gb300 import inputs
+lmax = 127
+th, w = oracle.gauss_nodes(lmax + 1)
+rings = oracle.Rings(th, np.full(lmax + 1, 2 * lmax + 1), np.zeros(lmax + 1), w * 2 * np.pi / (2 * lmax + 1))
+alm = inputs.scalar_gl_small(0, lmax)
+oracle.synthesis(0, lmax, lmax, alm, rings)  # loads and warms the library
+t = time.perf_counter()
+maps = oracle.synthesis(0, lmax, lmax, alm, rings)
+oracle.analysis(0, lmax, lmax, maps, rings)
+print(1e3 * (time.perf_counter() - t))
+"""
+
+
+def oracle_single_thread_small():
+    """The oracle on one host core (OMP_NUM_THREADS=1, its own process) on the small
+    scalar workload: GL 128 x 255, lmax 127, one synthesis + analysis (ms)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", _SMALL_ORACLE], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+
+
 def oracle_sample(target_s=15.0, gpu_out=None, others=None):
     """Time the FP64 CPU oracle on a bounded sample of the workload and
     extrapolate to one full synthesis + analysis pair (ms).
@@ -854,6 +878,7 @@ def main():
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         others = {k: v for k, v in outputs.items() if k != head}
         cb, acc = oracle_sample(args.cpu_seconds, gpu_out=outputs[head], others=others)
+        cb["single_core_scalar_gl128_lmax127_ms"] = oracle_single_thread_small()
         line["cpu_baseline"] = cb
         line["accuracy_vs_oracle_sample"] = acc
     if rank == 0:
