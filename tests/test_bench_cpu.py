@@ -78,3 +78,8 @@ def test_headline_config_exceeds_l2():
     bench.set_workload(4095)
     assert bench.CONFIG["lmax"] == 4095 and bench.CONFIG["nlon"] == 8191
     assert bench.CONFIG["l2_policy"].startswith("inputs larger than L2")
+
+
+def test_oracle_single_core_leg():
+    # the cpu_baseline leg times the oracle on one core in a process of its own
+    assert bench.oracle_single_thread_small() > 0
