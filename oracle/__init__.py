@@ -15,7 +15,7 @@ Parity status per function (see the tests under ``tests/test_oracle_*.py``):
   synthesis    pinned: brute-force direct summation at lmax <= 8, GL round trip.
   analysis     pinned: GL and ECP round trips, adjoint identity.
   gauss/ecp    pinned: exact integration of polynomials.
-  healpix      pinned: pixel count, equal area, symmetry.
+  healpix      pinned: pixel count, equal area, symmetry, every pixel centre (Gorski et al. 2005).
 """
 from __future__ import annotations
 

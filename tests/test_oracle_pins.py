@@ -252,6 +252,52 @@ def test_healpix_rings(nside):
         np.testing.assert_allclose(z, [2 / 3, 0, -2 / 3], atol=1e-15)
 
 
+def _healpix_pixel_centre(nside, p):
+    """(z, phi) of RING-scheme pixel p from the pixel-centre formulas of Gorski et al.
+    2005 (written out here, independently of the oracle's ring builder).  North polar
+    cap: ring i (1 <= i < nside) holds 4i pixels after 2i(i-1) earlier ones, pixel j
+    (1-based) at z = 1 - i^2/(3 nside^2), phi = pi/(2i) (j - 1/2).  Equatorial belt:
+    ring i (nside <= i <= 3 nside) holds 4 nside pixels, z = 4/3 - 2i/(3 nside),
+    phi = pi/(2 nside) (j - f) with f = 1 when i + nside is odd, 1/2 when even.
+    South polar cap: the mirror image of the north one."""
+    ncap = 2 * nside * (nside - 1)
+    npix = 12 * nside * nside
+    if p < ncap:
+        i = 1
+        while 2 * i * (i + 1) <= p:
+            i += 1
+        j = p - 2 * i * (i - 1) + 1
+        return 1.0 - i * i / (3.0 * nside * nside), PI / (2 * i) * (j - 0.5)
+    if p < npix - ncap:
+        q = p - ncap
+        i = nside + q // (4 * nside)
+        j = q % (4 * nside) + 1
+        f = 1.0 if (i + nside) % 2 else 0.5
+        return 4.0 / 3.0 - 2.0 * i / (3.0 * nside), PI / (2 * nside) * (j - f)
+    q = npix - 1 - p  # counted back from the last pixel: ring i from the south pole
+    i = 1
+    while 2 * i * (i + 1) <= q:
+        i += 1
+    j = 4 * i - (q - 2 * i * (i - 1))  # position within the ring, 1-based, in increasing phi
+    return -(1.0 - i * i / (3.0 * nside * nside)), PI / (2 * i) * (j - 0.5)
+
+
+@pytest.mark.parametrize("nside", [4, 8])
+def test_healpix_pixel_centres(nside):
+    """Every pixel centre of the ring description (theta_y, phi0_y + 2 pi x / Nphi_y at
+    map index ofs_y + x) equals the Gorski et al. pixel-centre formula: pins the polar
+    rings' phi0 = pi/(4i) and the equatorial alternation (reading R6), which a wrong
+    shift or pixel order in the ring builder would break."""
+    r = oracle.healpix_rings(nside)
+    z_ring = np.cos(r.theta)
+    for y in range(r.nrings):
+        for x in range(r.nphi[y]):
+            p = int(r.ofs[y]) + x
+            z, phi = _healpix_pixel_centre(nside, p)
+            assert abs(z_ring[y] - z) < 1e-14, (nside, y, x)
+            assert abs(r.phi0[y] + 2 * PI * x / r.nphi[y] - phi) < 1e-13, (nside, y, x)
+
+
 # -------------------------------------------------------------- transforms ---
 def _brute_synthesis(s, lmax, alm, rings):
     """Eq. syn_used summed term by term with explicit-sum lambdas (lmax tiny)."""
