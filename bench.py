@@ -11,8 +11,10 @@ of maps) are larger than L2 (129 MB), so no flush is needed between steps.
 Reported:
   value / ms_per_step  device time per pair (CUDA events, max over ranks)
   forms                both the mixed form and the plain FP64 form
-  roofline             dominant Legendre kernel: algorithmic flops / its
-                       event-timed duration against the pipe it runs on
+  roofline             dominant Legendre kernel: the method's algorithmic flops
+                       (26 per triple at spin 2) / its event-timed duration,
+                       against the FMA-flop peak of the pipe it runs on; the
+                       double-float issue fraction beside it (issue_frac)
   e2e                  same pair through the public API from pinned host a_lm,
                        host<->device copies inside the timed region
   cpu_baseline         the FP64 CPU oracle on a bounded sample, host cores
@@ -360,49 +362,67 @@ def launches_per_step(spin, form, fp64_items=False):
     return n
 
 
-def roofline_for(stages, plan, spin, precision, peaks, steps):
-    """Dominant Legendre kernel against the pipe it runs on.
+def roofline_for(stages, plan, spin, precision, peaks, steps, ncomp=1):
+    """Dominant Legendre kernel against the pipe it runs on, in the method's own work.
 
-    FP64 form: algorithmic FP64 flops (flops_per_triple, FMA = 2) against the
-    FP64 pipe (152 SMs x 2 DFMA lanes x 2 flops x clock).  Mixed form: the
-    FP32-pipe operations of the double-float algorithm (f32_ops_per_triple)
-    against the FP32 pipe's issue rate (152 SMs x 128 lanes x clock); the same
-    work as FMA-counted flops and the FP64-equivalent rate are given beside it.
+    achieved = algorithmic flops of the method per launch (flops_per_triple x the
+    plan's exact triple count; an FMA counts 2) / the kernel's CUDA-event time.
+    peak = the FMA-counted flop rate of the pipe the kernel runs on: the FP64 pipe
+    for the FP64 form, the FP32 pipe for the mixed form (whose double-float
+    arithmetic issues several FP32 operations per method flop).  The peak is the
+    rate this box's own microbenchmark measured (sht_measure_pipe_peaks: FMA
+    chains, 2 flops each) when it ran, else the figure derived from unit counts
+    and the clock.  frac = achieved / peak.
+
+    Beside it, for the mixed form: issue_frac, the FP32-pipe operations the
+    double-float algorithm issues per triple (f32_ops_per_triple, FADD / FMUL /
+    FFMA one each) over the pipe's issue rate -- how busy the emulation keeps the
+    pipe, not the method's work -- and fp64_equivalent_tflops, the method's rate
+    against which the FP64 pipe (fp64_pipe_tflops) compares.
     """
-    # per transform: the stage's launches (one per ring-pair range, plus the a_lm
-    # conversion in the synthesis stage) summed, divided by the timed steps
+    # per transform: the stage's launches summed, divided by the timed steps
     syn_ms, _ = stages["legendre_synthesis"]
     ana_ms, _ = stages["legendre_analysis"]
     name, t_ms = ("legendre_synthesis", syn_ms) if syn_ms >= ana_ms else ("legendre_analysis", ana_ms)
     per_launch_ms = t_ms / max(steps, 1)
     triples = plan.triples(0)
     clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    fp64_flops = triples * flops_per_triple(spin, 1)
+    flops = triples * flops_per_triple(spin, ncomp)
     sec = per_launch_ms * 1e-3
+    achieved = flops / sec / 1e12
+    measured = peaks.get("pipes_measured")  # this box's own microbenchmark (sht_measure_pipe_peaks)
     if precision == "fp64":
         kfile = "legendre_fp64.cu"
-        out = {"bound": "alu", "kernel": name, "achieved": fp64_flops / sec / 1e12,
-               "peak": SMS * 4 * clock / 1e12, "unit": "TFLOP/s",
-               "peak_source": "FP64 pipe: 152 SMs x 2 DFMA lanes/clk x 2 flop x sm_max clock (of nominal clock)",
-               "algorithmic_flops_per_launch": fp64_flops}
+        derived = SMS * 2 * 2 * clock / 1e12  # 2 DFMA lanes per SM per clock, 2 flops each
+        peak = measured["fp64_fma_tflops"] if measured else derived
+        out = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "peak_source": ("FP64 pipe, measured on this GPU by sht_measure_pipe_peaks (FMA = 2 flops)"
+                               if measured else
+                               "FP64 pipe derived: 152 SMs x 2 DFMA lanes/clk x 2 flops x sm_max clock"),
+               "peak_derived": derived}
     else:
         kfile = "legendre_mixed.cu"
-        ops = triples * f32_ops_per_triple(spin, 1)
-        out = {"bound": "alu", "kernel": name, "achieved": ops / sec / 1e12,
-               "peak": SMS * 128 * clock / 1e12, "unit": "T FP32-pipe ops/s",
-               "peak_source": "FP32 pipe issue: 152 SMs x 128 lanes/clk x sm_max clock (FADD/FMUL/FFMA one op each)",
-               "algorithmic_fp32_ops_per_launch": ops,
-               "fp64_equivalent_tflops": fp64_flops / sec / 1e12}
-    out["frac"] = out["achieved"] / out["peak"]
-    measured = peaks.get("pipes_measured")  # this box's own microbenchmark (sht_measure_pipe_peaks)
-    if measured:
-        pm = measured["fp64_fma_tflops"] if precision == "fp64" else measured["fp32_fma_tops"]
-        out.update({"peak_measured": pm, "frac_of_measured": out["achieved"] / pm,
-                    "peak_measured_source": "sht_measure_pipe_peaks: independent FMA chains, "
-                                            + ("FP64 TFLOP/s" if precision == "fp64" else "FP32 T op/s")})
+        derived = SMS * 128 * 2 * clock / 1e12  # 128 FFMA lanes per SM per clock, 2 flops each
+        peak = 2 * measured["fp32_fma_tops"] if measured else derived
+        ops = triples * f32_ops_per_triple(spin, ncomp)
+        issue_peak = measured["fp32_fma_tops"] if measured else derived / 2
+        fp64_pipe = measured["fp64_fma_tflops"] if measured else SMS * 4 * clock / 1e12
+        out = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "peak_source": ("FP32 pipe FMA-flop rate, 2 x the FFMA rate measured on this GPU by "
+                               "sht_measure_pipe_peaks" if measured else
+                               "FP32 pipe derived: 152 SMs x 128 FFMA lanes/clk x 2 flops x sm_max clock"),
+               "peak_derived": derived,
+               "issue_frac": ops / sec / 1e12 / issue_peak,
+               "issue_frac_note": "double-float FP32-pipe operations issued per second over the FP32 issue rate "
+                                  "(emulation work included; not the method's work)",
+               "fp32_ops_per_triple": f32_ops_per_triple(spin, ncomp),
+               "fp64_equivalent_tflops": achieved, "fp64_pipe_tflops": fp64_pipe}
+    out["frac"] = achieved / peak
+    out["flops_per_triple"] = flops_per_triple(spin, ncomp)
     key = ("fp64:" if precision == "fp64" else "mixed:") + name
     out["traffic"] = _traffic(kfile, key)
-    out.update({"ms_per_launch": per_launch_ms, "triples_per_launch": triples})
+    out.update({"ms_per_launch": per_launch_ms, "triples_per_launch": triples,
+                "algorithmic_flops_per_launch": flops})
     return out
 
 

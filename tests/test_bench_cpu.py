@@ -66,9 +66,18 @@ def test_roofline_arithmetic(monkeypatch):
     assert r["achieved"] == pytest.approx(26e10 / 0.150 / 1e12)
     assert r["peak"] == pytest.approx(152 * 4 * 2e9 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    # mixed form: the method's 26 flops per triple against the FP32 pipe's FMA-flop
+    # rate; the double-float issue rate is a separate field
     m = bench.roofline_for(stages, _Plan(), 2, "mixed", peaks, 3)
-    assert m["achieved"] == pytest.approx(163e10 / 0.150 / 1e12)
-    assert m["peak"] == pytest.approx(152 * 128 * 2e9 / 1e12)
+    assert m["achieved"] == pytest.approx(26e10 / 0.150 / 1e12)
+    assert m["peak"] == pytest.approx(152 * 128 * 2 * 2e9 / 1e12)
+    assert m["frac"] == pytest.approx(m["achieved"] / m["peak"])
+    assert m["issue_frac"] == pytest.approx(163e10 / 0.150 / 1e12 / (152 * 128 * 2e9 / 1e12))
+    # with the box's measured pipe rates the peak is 2 x the measured FFMA rate
+    peaks["pipes_measured"] = {"fp64_fma_tflops": 1.25, "fp32_fma_tops": 38.3, "fp32_add_tops": 38.3}
+    m = bench.roofline_for(stages, _Plan(), 2, "mixed", peaks, 3)
+    assert m["peak"] == pytest.approx(76.6) and m["frac"] == pytest.approx(26e10 / 0.150 / 1e12 / 76.6)
+    assert bench.roofline_for(stages, _Plan(), 2, "fp64", peaks, 3)["peak"] == pytest.approx(1.25)
     # traffic: only while the kernel source still hashes as recorded
     monkeypatch.setattr(bench, "MEASURED_TRAFFIC", {"mixed:legendre_analysis": {"bytes": 123, "sha256": "0" * 64}})
     assert bench.roofline_for(stages, _Plan(), 2, "mixed", peaks, 3)["traffic"] is None
