@@ -332,20 +332,28 @@ SHT_API int sht_geom_polar_cut(sht_geom_t geom, int lmax, int spin, int nm, cons
  * device synchronisation of an allocation.
  *
  * sht_execute_noalloc runs the same transform as sht_execute on a plan made
- * beforehand, with the same arguments and results, but its per-call working
- * memory (the phase array, the analysis partial sums and the converted a_lm
- * tables) comes from a fixed 64 MiB area compiled into the library, and the
- * call allocates nothing, on the device or the host.  Every GPU that loads
- * the library holds the area until the process exits.  Limit: transforms
- * whose working memory exceeds 64 MiB (about nmaps * nm * npairs * 32 bytes
- * for the phase array, plus the analysis partials) are rejected with
- * SHT_ERR_UNSUPPORTED, the message giving the size needed.  The first call
- * on each device looks up the area's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture begins.  All calls on a
- * device share the one area and it keeps the last call's contents (nothing
- * in it needs to start at zero): calls that overlap on the GPU -- on
- * different streams or from different threads -- race.  No profiling events
- * are recorded.  Errors: as sht_execute, plus SHT_ERR_UNSUPPORTED for the size.
+ * beforehand, with the same arguments and results, for the types
+ * SHT_SYNTHESIS, SHT_ANALYSIS, SHT_ADJOINT_SYNTHESIS and SHT_ADJOINT_ANALYSIS
+ * (SHT_DERIV_SYNTHESIS is rejected with SHT_ERR_INVALID_ARG) and the flags
+ * SHT_ADD_OUTPUT, SHT_NO_POLAR_OPT and SHT_REAL_HARMONICS.  Its per-call
+ * working memory (the phase array, the analysis partial sums and the converted
+ * a_lm tables) comes from a fixed 64 MiB area compiled into the library, and
+ * the call allocates nothing, on the device or the host.  What the plan
+ * allocated when it was made is still used: its read-only tables and, for
+ * rings longer than 14336 points, its FFT scratch slots.  Every GPU that
+ * loads the library holds the area until the process exits.  Limit:
+ * transforms whose working memory exceeds 64 MiB (about nmaps * nm * npairs *
+ * 32 bytes for the phase array, plus the analysis partials) are rejected with
+ * SHT_ERR_UNSUPPORTED, the message giving the size needed.  The first call on
+ * each device looks up the area's device address (cudaGetSymbolAddress) and
+ * keeps it: make that first call before any stream capture begins, and do not
+ * call cudaDeviceReset afterwards (the kept address would be stale).  All
+ * calls on a device share the one area and it keeps the last call's contents
+ * (nothing in it needs to start at zero): calls that overlap on the GPU -- on
+ * different streams or from different threads -- race.  The plan's workspace
+ * pointers point at the area while the call runs, so no other call on the same
+ * plan, sht_execute included, may run concurrently.  No profiling events are
+ * recorded.  Errors: as sht_execute, plus SHT_ERR_UNSUPPORTED for the size.
  */
 SHT_API int sht_execute_noalloc(sht_plan_t plan, int type, double *const *alm, double *const *map, int flags,
                                 void *cuda_stream);

@@ -6,18 +6,26 @@
 // reserved by another allocator's pool, or latency-bound loops that cannot
 // afford the implicit device synchronisation of cudaMalloc / cudaFree.
 // This entry point runs the transform of an existing plan exactly like
-// sht_execute, but takes all of its per-call working memory -- the phase
-// array F/G, the analysis tile sums and the converted a_lm tables (both, for a
-// mixed plan with FP64 columns) -- from
-// one fixed area compiled into the library (kNoallocBytes below), so the
-// call itself makes no allocation of any kind and does not use the plan's
-// own workspace.  Every GPU that loads the library holds this area until the
-// process exits.
+// sht_execute, but takes its per-call working memory -- the phase array F/G,
+// the analysis tile sums and the converted a_lm tables (both, for a mixed plan
+// with FP64 columns) -- from one fixed area compiled into the library
+// (kNoallocBytes below), so the call itself makes no allocation of any kind.
+// Two things still come from the plan, both allocated once when the plan was
+// made: its read-only tables (recursion coefficients, ring pairs, work lists,
+// FFT twiddles) and, for rings longer than the in-shared-memory limit
+// (kFftMaxLen points), its FFT scratch slots.  The plan's workspace pointers
+// are swapped to the area for the length of the call and restored on return,
+// so no other call on the same plan (sht_execute included) may run
+// concurrently from another thread.  Every GPU that loads the library holds
+// the area until the process exits.
 //
 // The area is shared by every call on a device and keeps whatever the last
 // call left in it; the kernels write every element they later read (no part
 // of it has to start at zero).  Calls that overlap on the GPU -- on
 // different streams, or from different threads -- race on the area.
+// The area's device address is looked up once per device and kept:
+// cudaDeviceReset is not supported once the call has been used on a device
+// (a reset can move the area, and the kept address would then be stale).
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
