@@ -90,6 +90,16 @@ extern "C" {
  * adjoint synthesis is the exact transpose of the synthesis under the plain dot
  * product of the stored numbers.  sht_execute and sht_execute_noalloc only. */
 #define SHT_REAL_HARMONICS 4
+/* The gradient factors of the adjoint transforms (Sect. 4.5), for a real loss L
+ * of real maps with the a_lm stored for m >= 0 only: the synthesis counts every
+ * stored m > 0 coefficient twice (once for -m), so with D = diag(2 - delta_m0)
+ *   SHT_ADJOINT_SYNTHESIS | SHT_GRADIENT writes D Y^H g = dL/da for g = dL/dp
+ *     (dL/da = dL/dRe a + i dL/dIm a; the m = 0 entries' imaginary part is 0),
+ *   SHT_ADJOINT_ANALYSIS | SHT_GRADIENT reads g = dL/da of an analysis a = A p
+ *     and writes W S D^-1 g = dL/dp (the m > 0 entries count half).
+ * Only these two types and complex storage (not with SHT_REAL_HARMONICS, whose
+ * adjoint already is the gradient); sht_execute only. */
+#define SHT_GRADIENT 8
 
 typedef struct sht_geom_s *sht_geom_t;
 typedef struct sht_alm_s *sht_alm_t;

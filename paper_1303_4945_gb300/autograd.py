@@ -17,35 +17,19 @@ m < 0 coefficients implied by the reality of the maps.  With D = diag(2 - delta_
 where Y^H is the adjoint synthesis (analysis with unit weights) and W S the
 adjoint analysis (synthesis times the ring weights).  Both follow from the real
 inner product sum Re(conj(x) y) over the stored entries, for which the
-synthesis counts every m > 0 coefficient twice (once for -m).
+synthesis counts every m > 0 coefficient twice (once for -m).  The factors D
+and D^-1 are applied inside the library (the SHT_GRADIENT flag of the two
+adjoint types); this module only allocates the outputs and passes pointers.
 
 Inputs are CUDA tensors: a_lm as complex128 of shape (narrays, nalm), maps as
 float64 of shape (narrays, npix), narrays = ncomp (spin 0) or 2 ncomp (spin:
-E, B / Q, U interleaved).  The plan must use the default triangular a_lm layout.
+E, B / Q, U interleaved).
 """
-import numpy as np
 import torch
 
 from . import sht as _sht
 
 __all__ = ["synthesis", "analysis"]
-
-
-def _m_weights(plan, device):
-    """(2 - delta_m0) per stored a_lm entry, and the m = 0 mask."""
-    cache = getattr(plan, "_autograd_m", None)
-    if cache is None or cache[0].device != device:
-        lay = plan.alm
-        if getattr(lay, "custom", False):
-            raise ValueError("autograd wrappers need the default triangular a_lm layout")
-        lmax, mmax = lay.lmax, lay.mmax
-        m = np.concatenate([np.full(lmax - mm + 1, mm) for mm in range(mmax + 1)])
-        if len(m) != lay.size():
-            raise ValueError("autograd wrappers need the default triangular a_lm layout")
-        mt = torch.from_numpy(m).to(device)
-        cache = (torch.where(mt == 0, 1.0, 2.0).to(torch.float64), mt == 0)
-        plan._autograd_m = cache
-    return cache
 
 
 def _rows(t):
@@ -75,10 +59,7 @@ class _Synthesis(torch.autograd.Function):
         g = g.contiguous()
         grad = torch.empty((plan.narrays, plan.alm.size()), dtype=torch.complex128, device=g.device)
         st = torch.cuda.current_stream(g.device)
-        _sht.sht_execute(plan, _sht.SHT_ADJOINT_SYNTHESIS, _rows(grad), _rows(g), 0, st)
-        w, m0 = _m_weights(plan, g.device)
-        grad = grad * w
-        grad = torch.where(m0, torch.complex(grad.real, torch.zeros_like(grad.real)), grad)
+        _sht.sht_execute(plan, _sht.SHT_ADJOINT_SYNTHESIS, _rows(grad), _rows(g), _sht.SHT_GRADIENT, st)
         return grad, None
 
 
@@ -96,11 +77,10 @@ class _Analysis(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         plan = ctx.plan
-        w, _ = _m_weights(plan, g.device)
-        gh = (g / w).contiguous()
+        g = g.contiguous()
         grad = torch.empty((plan.narrays, plan.geom.npix), dtype=torch.float64, device=g.device)
         st = torch.cuda.current_stream(g.device)
-        _sht.sht_execute(plan, _sht.SHT_ADJOINT_ANALYSIS, _rows(gh), _rows(grad), 0, st)
+        _sht.sht_execute(plan, _sht.SHT_ADJOINT_ANALYSIS, _rows(g), _rows(grad), _sht.SHT_GRADIENT, st)
         return grad, None
 
 

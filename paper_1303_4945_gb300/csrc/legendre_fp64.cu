@@ -41,6 +41,7 @@ struct LegArgs {
   int ana_tiles, ppt, add;
   int ptr_off;  // batch: first entry of this plan in the pointer table
   int real;     // real-harmonic storage of the a_lm (spin-0 synthesis reads them directly)
+  int half;     // m > 0 coefficients count half (SHT_GRADIENT with the adjoint analysis)
 };
 
 __device__ __forceinline__ int warp_any(bool b) { return __any_sync(0xffffffffu, b); }
@@ -159,6 +160,10 @@ __device__ __forceinline__ void leg_syn_s0_body(const LegArgs &a, double *const 
       const double r = 0.70710678118654752440;
       fn = make_double2(fn.x * r, -fn.y * r);
       fs = make_double2(fs.x * r, -fs.y * r);
+    }
+    if (a.half && m > 0) {  // the sum is linear in the a_lm: halving them halves F_m
+      fn = make_double2(0.5 * fn.x, 0.5 * fn.y);
+      fs = make_double2(0.5 * fs.x, 0.5 * fs.y);
     }
     double2 *o = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
     o[0] = fn;
@@ -662,7 +667,7 @@ __global__ void __launch_bounds__(kAnaThreads) leg_ana_spin_batch(const LegArgs 
 // spin 0: V = 2 njobs values (re, im per job).
 // spin s: V = 4 njobs values (T1, T2 per job): E = -(T1 + sig T2)/2, B = -(i/2)(sig T2 - T1).
 __global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp, int ana_tiles, int astride, int add,
-                           int real,
+                           int real, int grad,
                            const int *__restrict__ mval, const int64_t *__restrict__ mstart,
                            const int64_t *__restrict__ part_off, const int *__restrict__ tile0,
                            const double *__restrict__ part, DevPtrs alm) {
@@ -698,6 +703,7 @@ __global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp,
     for (int c = 0; c < nout; ++c) {
       double2 *o = reinterpret_cast<double2 *>(alm.p[nout * j + c]) + idx;
       double2 r = (real && m > 0) ? complex_to_real(out[c]) : out[c];
+      if (grad && m > 0) r = make_double2(2.0 * r.x, 2.0 * r.y);  // the stored a_lm also stands for a_{l,-m}
       if (add) {
         const double2 old = *o;
         r.x += old.x;
@@ -722,6 +728,7 @@ __global__ void alm_to_pm(int lmax, int spin, int nm, int astride, const int *__
   const int mi = blockIdx.x, j = blockIdx.y;
   const int deriv = mode & kAlmDeriv, real = (mode & kAlmReal) && mval[mi] > 0;
   const int m = mval[mi];
+  const double hf = ((mode & kAlmHalf) && m > 0) ? 0.5 : 1.0;
   const int as = spin < 0 ? -spin : spin;
   const int l0 = m > as ? m : as;
   // deriv (Sect. 4.3): E = sqrt(l(l+1)) a_lm of the spin-0 array j, B = 0
@@ -741,6 +748,8 @@ __global__ void alm_to_pm(int lmax, int spin, int nm, int astride, const int *__
       b = make_double2(0.0, 0.0);
     }
     if (m == 0) e.y = b.y = 0.0;  // Im of m = 0 coefficients is ignored
+    e = make_double2(hf * e.x, hf * e.y);
+    b = make_double2(hf * b.x, hf * b.y);
     P[l] = make_double2(e.x - b.y, e.y + b.x);
     M[l] = make_double2(e.x + b.y, e.y - b.x);
   }
@@ -774,16 +783,18 @@ static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar, boo
   a.ppt = P->ana_ppt;
   a.add = 0;
   a.real = 0;
+  a.half = 0;
   return a;
 }
 
 // Legendre stage over an explicit work list (stage 0: synthesis items int2, 1:
 // analysis items int4); no a_lm conversion (launch_alm_prepare_fp64 does it)
 cudaError_t launch_leg_fp64_items(const sht_plan_s *P, int stage, const DevPtrs &alm, int polar, const void *items,
-                                  int n, cudaStream_t st, bool real) {
+                                  int n, cudaStream_t st, int amode) {
   if (n == 0) return cudaSuccess;
   LegArgs a = make_args(P, alm, polar);
-  a.real = real ? 1 : 0;
+  a.real = (amode & kAlmReal) ? 1 : 0;
+  a.half = (amode & kAlmHalf) ? 1 : 0;
   const int nj = P->njobs_pad;
   if (stage == 0) {
     a.syn_items = static_cast<const int2 *>(items);
@@ -824,7 +835,7 @@ cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int pol
   cudaError_t e = launch_alm_prepare_fp64(P, alm, st, mode);
   if (e != cudaSuccess) return e;
   return launch_leg_fp64_items(P, 0, alm, polar, lo ? (const void *)P->d_syn_lo[polar] : P->d_syn_items[polar], n,
-                               st, (mode & kAlmReal) != 0);
+                               st, mode);
 }
 
 cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, bool lo) {
@@ -834,10 +845,10 @@ cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int pol
 }
 
 cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st,
-                              bool real) {
+                              bool real, bool grad) {
   dim3 grid((P->lmax + 1 + 127) / 128, P->nm);
   ana_reduce<<<grid, 128, 0, st>>>(P->lmax, P->spin, P->nm, P->njobs_pad, P->ncomp, P->ana_tiles, P->astride, add,
-                                   real ? 1 : 0,
+                                   real ? 1 : 0, grad ? 1 : 0,
                                    P->d_mval, P->d_mstart, P->d_ana_part_off[polar], P->d_ana_tile0[polar],
                                    P->d_part, alm);
   return cudaGetLastError();

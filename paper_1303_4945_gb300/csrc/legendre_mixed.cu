@@ -140,6 +140,7 @@ __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, con
   const int deriv = mode & kAlmDeriv, real = (mode & kAlmReal) && mval[mi] > 0;
   const int j = blockIdx.y;
   const int m = mval[mi];
+  const double hf = ((mode & kAlmHalf) && m > 0) ? 0.5 : 1.0;
   const int as = spin < 0 ? -spin : spin;
   const int l0 = m > as ? m : as;
   if (spin == 0) {
@@ -148,7 +149,7 @@ __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, con
     for (int l = l0 + threadIdx.x; l <= lmax; l += blockDim.x) {
       double2 v = src[(int64_t)l * astride];
       if (real) v = real_to_complex(v);
-      const f2 re = f2_of(v.x), im = f2_of(v.y);
+      const f2 re = f2_of(hf * v.x), im = f2_of(hf * v.y);
       dst[l] = make_float4(re.h, re.l, im.h, im.l);
     }
     return;
@@ -171,6 +172,8 @@ __global__ void alm_to_f2(int lmax, int spin, int nm, int narr, int astride, con
       b = make_double2(0.0, 0.0);
     }
     if (m == 0) e.y = b.y = 0.0;
+    e = make_double2(hf * e.x, hf * e.y);
+    b = make_double2(hf * b.x, hf * b.y);
     const f2 pr = f2_of(e.x - b.y), pi = f2_of(e.y + b.x), mr = f2_of(e.x + b.y), mi_ = f2_of(e.y - b.x);
     P[l] = make_float4(pr.h, pr.l, pi.h, pi.l);
     M[l] = make_float4(mr.h, mr.l, mi_.h, mi_.l);

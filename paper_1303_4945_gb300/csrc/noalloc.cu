@@ -139,7 +139,7 @@ extern "C" int sht_execute_noalloc(sht_plan_t P, int type, double *const *alm, d
       else
         e = mixed ? launch_leg_ana_mixed(P, A, polar, st) : launch_leg_ana_fp64(P, A, polar, st);
     }
-    if (e == cudaSuccess) e = launch_ana_reduce(P, A, polar, add, st, real);
+    if (e == cudaSuccess) e = launch_ana_reduce(P, A, polar, add, st, real, false);
   }
   P->d_phase = phase0;
   P->d_part = part0;

@@ -1281,9 +1281,12 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
   if (type < SHT_SYNTHESIS || type > SHT_DERIV_SYNTHESIS) return fail(SHT_ERR_INVALID_ARG, "bad type %d", type);
   const bool deriv = type == SHT_DERIV_SYNTHESIS;
   if (deriv && P->spin != 1) return fail(SHT_ERR_INVALID_ARG, "SHT_DERIV_SYNTHESIS needs a plan of spin 1");
-  if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT | SHT_REAL_HARMONICS))
+  if (flags & ~(SHT_ADD_OUTPUT | SHT_NO_POLAR_OPT | SHT_REAL_HARMONICS | SHT_GRADIENT))
     return fail(SHT_ERR_INVALID_ARG, "unknown flags");
   const bool real = (flags & SHT_REAL_HARMONICS) != 0;
+  const bool grad = (flags & SHT_GRADIENT) != 0;
+  if (grad && ((type != SHT_ADJOINT_SYNTHESIS && type != SHT_ADJOINT_ANALYSIS) || real))
+    return fail(SHT_ERR_INVALID_ARG, "SHT_GRADIENT applies to the two adjoint types in complex storage only");
   if (!alm || !map) return fail(SHT_ERR_INVALID_ARG, "pointer arrays are NULL");
   DevPtrs A, M;
   memset(&A, 0, sizeof(A));
@@ -1327,11 +1330,14 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
   };
   const bool mixed = P->precision == SHT_MIXED;
+  // a_lm read by a synthesis: derivative mode, real storage, or (the adjoint
+  // analysis of a gradient) the m > 0 entries halved
+  const int mode = (deriv ? kAlmDeriv : 0) | (real ? kAlmReal : 0) | (grad ? kAlmHalf : 0);
+  const int amode = mode & (kAlmReal | kAlmHalf);
   auto leg = [&](int stg, const void *items, int n, cudaStream_t s) {
     return mixed ? launch_leg_mixed_items(P, stg, polar, items, n, s)
-                 : launch_leg_fp64_items(P, stg, A, polar, items, n, s, real);
+                 : launch_leg_fp64_items(P, stg, A, polar, items, n, s, amode);
   };
-  const int mode = (deriv ? kAlmDeriv : 0) | (real ? kAlmReal : 0);
   // A mixed plan's FP64 items (small m near the poles) run on the high-priority
   // side stream beside its mixed Legendre kernel; the ring FFT waits for both.
   if (type == SHT_SYNTHESIS || type == SHT_ADJOINT_ANALYSIS || deriv) {
@@ -1346,7 +1352,7 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
       record(P->ev_fork, st);
       wait(P->side, P->ev_fork);
       stage(5, P->side, [&] {
-        return launch_leg_fp64_items(P, 0, A, polar, P->d_syn_lo[polar], P->nsyn_lo[polar], P->side, real);
+        return launch_leg_fp64_items(P, 0, A, polar, P->d_syn_lo[polar], P->nsyn_lo[polar], P->side, amode);
       });
       record(P->ev_lo, P->side);
     }
@@ -1367,7 +1373,7 @@ extern "C" int sht_execute(sht_plan_t P, int type, double *const *alm, double *c
     }
     stage(3, st, [&] { return leg(1, P->d_ana_items[polar], P->nana_items[polar], st); });
     if (lo) wait(st, P->ev_lo);
-    stage(4, st, [&] { return launch_ana_reduce(P, A, polar, add, st, real); });
+    stage(4, st, [&] { return launch_ana_reduce(P, A, polar, add, st, real, grad); });
   }
   if (cur != P->device) cudaSetDevice(cur);
   if (e != cudaSuccess) return fail(SHT_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));

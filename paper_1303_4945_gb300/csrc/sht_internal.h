@@ -201,7 +201,7 @@ struct sht_plan_s {
 // Cross-TU launch helpers (all return cudaError_t of the launch).
 // ----------------------------------------------------------------------------
 namespace sht {
-constexpr int kAlmDeriv = 1, kAlmReal = 2;  // a_lm conversion modes (see launch_alm_prepare_fp64)
+constexpr int kAlmDeriv = 1, kAlmReal = 2, kAlmHalf = 4;  // a_lm conversion modes (see launch_alm_prepare_fp64)
 
 // Runs side_fn on stream `side` concurrently with main_fn on `st`: `side` waits for
 // the work queued on `st` so far, side_fn is launched first (its CTAs are the
@@ -235,12 +235,14 @@ cudaError_t launch_leg_syn_fp64(const sht_plan_s *P, const DevPtrs &alm, int pol
                                 bool lo = false, int mode = 0);
 cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st,
                                 bool lo = false);
+// grad: the gradient factor of Sect. 4.5's adjoint for the stored m >= 0 a_lm (m > 0 doubled)
 cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st,
-                              bool real = false);
+                              bool real = false, bool grad = false);
 cudaError_t launch_leg_syn_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st, int mode = 0);
 // the Legendre stage over an explicit work list (stage 0 synthesis, 1 analysis), no a_lm conversion
+// amode: kAlmReal / kAlmHalf bits for the spin-0 synthesis, which reads the a_lm directly
 cudaError_t launch_leg_fp64_items(const sht_plan_s *P, int stage, const DevPtrs &alm, int polar, const void *items,
-                                  int n, cudaStream_t st, bool real = false);
+                                  int n, cudaStream_t st, int amode = 0);
 cudaError_t launch_leg_mixed_items(const sht_plan_s *P, int stage, int polar, const void *items, int n,
                                    cudaStream_t st);
 cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
@@ -265,7 +267,8 @@ void leg_mixed_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out)
 void fft_fill_args(const sht_plan_s *P, int polar, int weighted, int add, int ptr_off, void *out);
 // a_lm -> the P = E+iB / M = E-iB tables (FP64 spin) or double-float tables (mixed); mode bits:
 // kAlmDeriv, the first-derivative mode of Sect. 4.3 (spin-1 plan, E = sqrt(l(l+1)) a of ncomp
-// spin-0 arrays, B = 0); kAlmReal, inputs in real-harmonic storage
+// spin-0 arrays, B = 0); kAlmReal, inputs in real-harmonic storage; kAlmHalf, the m > 0
+// coefficients halved (the adjoint analysis of a gradient, see SHT_GRADIENT)
 cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, int mode = 0);
 cudaError_t launch_alm_prepare_mixed(const sht_plan_s *P, const DevPtrs &alm, cudaStream_t st, int mode = 0);
 // stage 0: synthesis, 1: analysis

@@ -30,7 +30,7 @@ SHT_ECP_FEJER1, SHT_ECP_FEJER2, SHT_ECP_CC = 0, 1, 2
 SHT_FP64, SHT_MIXED = 0, 1
 SHT_SYNTHESIS, SHT_ANALYSIS, SHT_ADJOINT_SYNTHESIS, SHT_ADJOINT_ANALYSIS = 0, 1, 2, 3
 SHT_DERIV_SYNTHESIS = 4  # spin-1 plans: ncomp spin-0 a_lm -> (df/dtheta, df/(sin theta dphi)) per component
-SHT_ADD_OUTPUT, SHT_NO_POLAR_OPT, SHT_REAL_HARMONICS = 1, 2, 4
+SHT_ADD_OUTPUT, SHT_NO_POLAR_OPT, SHT_REAL_HARMONICS, SHT_GRADIENT = 1, 2, 4, 8
 SHT_NSTAGES = 6
 STAGE_NAMES = ("legendre_synthesis", "fft_synthesis", "fft_analysis", "legendre_analysis", "analysis_reduce",
                "fp64_polar_items")

@@ -8,12 +8,17 @@ maximum roughly as lmax^(3/2), both close to the IEEE limit).  The reduced
 grid is the library's reduced Gauss-Legendre geometry (Sect. 4.4.2): ring y has
 the smallest 2^a 3^b 5^c length >= 2 m_y + 1, with m_y the largest m the polar
 optimisation (Sect. 3.3) keeps on that ring.
+
+The HEALPix workload (Nside 512, lmax 1535, C_l = 1/(l+1)^2, seed 1) runs the
+weighted analysis with Jacobi refinement at full size; its first synthesis and
+analysis are also checked against the oracle on sampled rings and m values.
 """
 import math
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1303_4945_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -71,6 +76,31 @@ def test_healpix_jacobi_full_size(sht):
     assert geom.npix == 12 * 512 ** 2
     lay = sht.sht_alm_create(lmax, lmax)
     a = inputs.gaussian_alm(np.random.default_rng(1), lmax, lmax, cl=inputs.cl_inverse_square)
+    # the first synthesis on sampled rings (both polar caps with their aliased short
+    # rings, the equatorial belt) and the first analysis at sampled m, against the
+    # oracle on the same inputs; per-ring and per-sample bounds as at full size
+    r = geom.rings()
+    rings = oracle.Rings(r["theta"], r["nphi"], r["phi0"], r["weight"], ofs=r["ofs"])
+    ring_sel = [0, 1, 7, 300, 511, 1023, 1535, 2040, 2046]
+    m_sel = [0, 1, 5, 600, 1535]
+    ref_p = oracle.synthesis(0, lmax, lmax, [a], rings, rings_sel=ring_sel)[0]
+    _, mm = inputs.lm_arrays(lmax, lmax)
+    msk = np.isin(mm, m_sel)
+
+    def sampled_against_oracle(p, a0, prec):
+        ring_tol, tol = (1e-11, 1e-12) if prec == 0 else (1e-10, 1e-10)
+        idx = np.concatenate([np.arange(rings.ofs[y], rings.ofs[y] + rings.nphi[y]) for y in ring_sel])
+        for y in ring_sel:
+            s = slice(rings.ofs[y], rings.ofs[y] + rings.nphi[y])
+            e = np.linalg.norm(p[s] - ref_p[s]) / np.linalg.norm(ref_p[s])
+            assert e <= ring_tol, (prec, y, e)
+        e = np.linalg.norm(p[idx] - ref_p[idx]) / np.linalg.norm(ref_p[idx])
+        assert e <= tol, (prec, e)
+        ref_a = oracle.analysis(0, lmax, lmax, [p], rings, m_sel=m_sel)[0][msk]
+        ea = np.linalg.norm(a0[msk] - ref_a) / np.linalg.norm(ref_a)
+        print("precision", prec, "sampled rings", f"{e:.2e}", "sampled m", f"{ea:.2e}")
+        assert ea <= tol, (prec, ea)
+
     a_d = torch.from_numpy(a).cuda()
     l, _ = inputs.lm_arrays(lmax, lmax)
     low = torch.from_numpy(l < 512).cuda()
@@ -81,6 +111,7 @@ def test_healpix_jacobi_full_size(sht):
         sht.sht_execute(plan, sht.SHT_SYNTHESIS, [a_d], [p])
         ak = torch.zeros_like(a_d)
         sht.sht_execute(plan, sht.SHT_ANALYSIS, [ak], [p])
+        sampled_against_oracle(p.cpu().numpy(), ak.cpu().numpy(), prec)
         seq = [ak.clone()]
         r = torch.empty_like(p)
         for _ in range(3):

@@ -116,7 +116,13 @@ def test_gradcheck_synthesis_and_analysis(mods, spin):
 
 
 def test_full_size_forward_backward(mods):
-    # lmax 8191 on Gauss-Legendre 8192 x 16383 (rings beyond shared memory)
+    # lmax 8191 on Gauss-Legendre 8192 x 16383 (rings beyond shared memory): both
+    # forms forward and backward; the forward maps on sampled rings (both poles, the
+    # equator) and the gradient at sampled m against the oracle on the same inputs,
+    # a directional finite difference, and the mixed gradient against the FP64 one.
+    # The FP64 bounds are the full-size test's at lmax 4095 with the sample as a
+    # whole at 2e-12: the oracle's own recursion error grows linearly with lmax
+    # (Sect. 5.1.2), about 1e-12 after 4500 steps.
     sht, ag = mods
     lmax = 8191
     geom = sht.sht_geom_gauss(lmax + 1, 2 * lmax + 1)
@@ -124,13 +130,35 @@ def test_full_size_forward_backward(mods):
     rng = np.random.default_rng(4)
     a, d = workload(lmax, geom, rng)
     dt = torch.from_numpy(d).cuda().reshape(1, -1)
+    r = geom.rings()
+    rings = oracle.Rings(r["theta"], r["nphi"], r["phi0"], r["weight"], ofs=r["ofs"])
+    ring_sel = [0, 1, 2048, 4095, 6000, 8190, 8191]
+    m_sel = [0, 1, 47, 3000, 8191]
+    ref_p = oracle.synthesis(0, lmax, lmax, [a], rings, rings_sel=ring_sel)[0]
+    idx = np.concatenate([np.arange(rings.ofs[y], rings.ofs[y] + rings.nphi[y]) for y in ring_sel])
+    _, m = inputs.lm_arrays(lmax, lmax)
+    msk = np.isin(m, m_sel)
+    tol = {0: (1e-11, 2e-12), 1: (1e-10, 1e-10)}  # (each ring, the sample)
     grads = {}
     for prec in (0, 1):
         plan = sht.sht_plan_create(geom, lay, 0, 1, prec)
         at = torch.from_numpy(a).cuda().reshape(1, -1).requires_grad_(True)
-        loss = ((ag.synthesis(plan, at) - dt) ** 2).sum()
+        pt = ag.synthesis(plan, at)
+        loss = ((pt - dt) ** 2).sum()
         loss.backward()
         grads[prec] = at.grad.detach()
+        p = pt.detach()[0].cpu().numpy()
+        for y in ring_sel:
+            s = slice(rings.ofs[y], rings.ofs[y] + rings.nphi[y])
+            assert rel_l2(p[s], ref_p[s]) <= tol[prec][0], (prec, y, rel_l2(p[s], ref_p[s]))
+        assert rel_l2(p[idx], ref_p[idx]) <= tol[prec][1], (prec, rel_l2(p[idx], ref_p[idx]))
+        # the backward pass of this form on its own residual: D Y^H 2 (p - d) at the sampled m
+        yh = oracle.analysis(0, lmax, lmax, [2.0 * (p - d)], rings, m_sel=m_sel, adjoint=True)[0]
+        ref_g = np.where(m == 0, yh.real + 0j, 2.0 * yh)[msk]
+        got_g = grads[prec][0].cpu().numpy()[msk]
+        print("precision", prec, "sampled rings", f"{rel_l2(p[idx], ref_p[idx]):.2e}",
+              "gradient at sampled m", f"{rel_l2(got_g, ref_g):.2e}")
+        assert rel_l2(got_g, ref_g) <= tol[prec][1], (prec, rel_l2(got_g, ref_g))
         if prec == 0:
             v = torch.from_numpy(inputs.gaussian_alm(rng, lmax, lmax, cl=inputs.cl_inverse_square)).cuda()
             v = v.reshape(1, -1)
@@ -142,7 +170,46 @@ def test_full_size_forward_backward(mods):
             fd = (L(at.detach() + h * v) - L(at.detach() - h * v)) / (2 * h)
             an = float(torch.sum((grads[0].conj() * v).real))
             assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
-        del plan
+        del plan, pt
         torch.cuda.empty_cache()
     err = float(torch.linalg.norm(grads[1] - grads[0]) / torch.linalg.norm(grads[0]))
     assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("spin,precision", [(0, 0), (0, 1), (2, 0), (2, 1)])
+def test_gradient_flag_against_oracle(mods, spin, precision):
+    """SHT_GRADIENT through the C ABI: the adjoint synthesis times D = diag(2 - delta_m0),
+    and the adjoint analysis of D^-1 g, against the oracle (HEALPix: aliased rings,
+    phi0 != 0); the flag is refused where it has no meaning."""
+    sht, _ = mods
+    lmax = 40
+    geom = sht.sht_geom_healpix(16)
+    r = geom.rings()
+    rings = oracle.Rings(r["theta"], r["nphi"], r["phi0"], r["weight"], ofs=r["ofs"])
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), spin, 1, precision)
+    narr = plan.narrays
+    rng = np.random.default_rng(40 + spin)
+    g_map = [rng.standard_normal(geom.npix) for _ in range(narr)]
+    g_alm = [inputs.gaussian_alm(rng, lmax, lmax, lmin=abs(spin)) for _ in range(narr)]
+    _, m = inputs.lm_arrays(lmax, lmax)
+    D = np.where(m == 0, 1.0, 2.0)
+    tol = 1e-12 if precision == 0 else 1e-10
+    out = [torch.full((len(m),), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda") for _ in range(narr)]
+    sht.sht_execute(plan, sht.SHT_ADJOINT_SYNTHESIS, out, [torch.from_numpy(x).cuda() for x in g_map],
+                    sht.SHT_GRADIENT)
+    ref = oracle.analysis(spin, lmax, lmax, g_map, rings, adjoint=True)
+    for o, rr in zip(out, ref):
+        o = o.cpu().numpy()
+        assert rel_l2(o, D * rr) <= tol
+        assert np.all(o[m == 0].imag == 0)
+    maps = [torch.full((geom.npix,), np.nan, dtype=torch.float64, device="cuda") for _ in range(narr)]
+    sht.sht_execute(plan, sht.SHT_ADJOINT_ANALYSIS, [torch.from_numpy(x).cuda() for x in g_alm], maps,
+                    sht.SHT_GRADIENT)
+    ref = oracle.synthesis(spin, lmax, lmax, [x / D for x in g_alm], rings, weighted=True)
+    for o, rr in zip(maps, ref):
+        assert rel_l2(o.cpu().numpy(), rr) <= tol
+    for type_, flags in ((sht.SHT_SYNTHESIS, sht.SHT_GRADIENT),
+                         (sht.SHT_ADJOINT_SYNTHESIS, sht.SHT_GRADIENT | sht.SHT_REAL_HARMONICS)):
+        with pytest.raises(sht.ShtError) as e:
+            sht.sht_execute(plan, type_, out, maps, flags)
+        assert e.value.code == sht.SHT_ERR_INVALID_ARG
