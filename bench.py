@@ -162,25 +162,63 @@ print(1e3 * (time.perf_counter() - t))
 """
 
 
-def oracle_single_thread_small():
-    """The oracle on one host core (OMP_NUM_THREADS=1, its own process) on the small
-    scalar workload: GL 128 x 255, lmax 127, one synthesis + analysis (ms)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1")
+def oracle_small_full(threads=None):
+    """The oracle on the small scalar workload in full (GL 128 x 255, lmax 127, one
+    synthesis + analysis), in a process of its own: threads=1 pins it to one host
+    core (OMP_NUM_THREADS=1), None lets it use every core (ms, measured)."""
+    env = dict(os.environ)
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
+    else:
+        env.pop("OMP_NUM_THREADS", None)
     r = subprocess.run([sys.executable, "-c", _SMALL_ORACLE], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
 
 
-def oracle_sample(target_s=15.0, gpu_out=None, others=None):
-    """Time the FP64 CPU oracle on a bounded sample of the workload and
-    extrapolate to one full synthesis + analysis pair (ms).
+def oracle_single_thread_small():
+    """The oracle on one host core for the small scalar workload (ms)."""
+    return oracle_small_full(1)
 
-    Synthesis: every ring costs the same (all m, all l, one DFT), so the
-    sample is a set of rings spread over latitude, scaled by nrings / sample.
-    Analysis: per-m cost varies with lmax - m; the sample is m values evenly
-    spaced over 0..mmax, scaled by (mmax + 1) / sample.  The sample size is
-    grown from a probe so the whole leg takes about target_s seconds.
-    If gpu_out is given, the sampled outputs are compared with it.
+
+def _warm_oracle():
+    """Load the oracle library and start its thread pool outside any timed region."""
+    import numpy as np
+
+    import oracle
+
+    th, w = oracle.gauss_nodes(9)
+    r = oracle.Rings(th, np.full(9, 17), np.zeros(9), w * 2 * np.pi / 17)
+    a = np.zeros(oracle.nalm(8, 8), dtype=np.complex128)
+    maps = oracle.synthesis(0, 8, 8, [a], r)
+    oracle.analysis(0, 8, 8, maps, r)
+
+
+def oracle_sample_sizes(cores):
+    """The fixed sample both arms time: 2 rings and 2 m values per host core, so
+    that every core has work in both legs (the oracle runs its synthesis in
+    parallel over rings and its analysis over m); rings evenly spaced from pole to
+    pole, m evenly spaced from 0 to mmax (most costly first, as the loop hands
+    them out)."""
+    import numpy as np
+
+    nr = min(NLAT, 2 * cores)
+    nm = min(LMAX + 1, 2 * cores)
+    rsel = np.unique(np.linspace(0, NLAT - 1, nr).round().astype(int))
+    msel = np.unique(np.linspace(0, LMAX, nm).round().astype(int))
+    return rsel, msel
+
+
+def oracle_sample(gpu_out=None, others=None):
+    """Time the FP64 CPU oracle on the fixed sample of oracle_sample_sizes and
+    extrapolate to one full synthesis + analysis pair (ms):
+
+        T_pair = t_syn * nlat / n_rings + t_ana * (mmax + 1) / n_m
+
+    (every ring of the synthesis costs the same; the evenly spaced m values
+    average the analysis's cost over m).  The library is loaded and its thread
+    pool started before the timer.  If gpu_out is given, the sampled outputs are
+    compared with it.
     """
     import numpy as np
 
@@ -191,34 +229,27 @@ def oracle_sample(target_s=15.0, gpu_out=None, others=None):
     rings = oracle.Rings(th, np.full(NLAT, NLON), np.zeros(NLAT), w * 2 * np.pi / NLON)
     alm = inputs.spin2_eb(SEED, LMAX)
     cores = os.cpu_count() or 1
-
     if gpu_out is not None:
         ana_in = gpu_out["maps"]  # a GPU synthesis output: the analyses are compared on equal input
     else:
         rng = np.random.default_rng(7)
         ana_in = [rng.standard_normal(rings.npix) for _ in range(2)]
-
-    def run(nr, nmv):
-        rsel = np.unique(np.linspace(0, NLAT - 1, nr).round().astype(int))
-        msel = np.unique(np.linspace(0, LMAX, nmv).round().astype(int))
-        t0 = time.perf_counter()
-        maps = oracle.synthesis(SPIN, LMAX, LMAX, alm, rings, rings_sel=rsel)
-        t1 = time.perf_counter()
-        back = oracle.analysis(SPIN, LMAX, LMAX, ana_in, rings, m_sel=msel)
-        t2 = time.perf_counter()
-        return rsel, msel, maps, back, t1 - t0, t2 - t1
-
-    # probe with a tiny sample, then size the real one
-    rsel, msel, _, _, ts, ta = run(max(2, cores // 4), 2)
-    per_ring = ts / len(rsel)
-    per_m = ta / len(msel)
-    nr = int(max(len(rsel), min(NLAT, 0.5 * target_s / max(per_ring, 1e-6))))
-    nm = int(max(2, min(LMAX + 1, 0.5 * target_s / max(per_m, 1e-6))))
-    rsel, msel, maps, back, ts, ta = run(nr, nm)
-    full_ms = 1e3 * (ts * NLAT / len(rsel) + ta * (LMAX + 1) / len(msel))
+    _warm_oracle()
+    rsel, msel = oracle_sample_sizes(cores)
+    t0 = time.perf_counter()
+    maps = oracle.synthesis(SPIN, LMAX, LMAX, alm, rings, rings_sel=rsel)
+    t1 = time.perf_counter()
+    back = oracle.analysis(SPIN, LMAX, LMAX, ana_in, rings, m_sel=msel)
+    t2 = time.perf_counter()
+    ts, ta = t1 - t0, t2 - t1
+    per_ring, per_m = 1e3 * ts / len(rsel), 1e3 * ta / len(msel)
+    full_ms = per_ring * NLAT + per_m * (LMAX + 1)
     res = {"value": full_ms, "unit": "ms", "cores": cores, "kind": "oracle",
-           "sample": f"synthesis of {len(rsel)} of {NLAT} rings ({ts:.1f} s) and analysis of {len(msel)} of "
-                     f"{LMAX + 1} m values ({ta:.1f} s), evenly spaced, extrapolated to one full pair"}
+           "sample": f"synthesis of {len(rsel)} of {NLAT} rings ({ts:.2f} s) and analysis of {len(msel)} of "
+                     f"{LMAX + 1} m values ({ta:.2f} s), evenly spaced, 2 of each per core, library loaded and "
+                     f"threads started before the timer",
+           "ms_per_ring_synthesis": per_ring, "ms_per_m_analysis": per_m,
+           "extrapolation": f"T_pair = ms_per_ring_synthesis x {NLAT} + ms_per_m_analysis x {LMAX + 1}"}
     acc = None
     if gpu_out is not None:
         acc = {}
@@ -239,14 +270,15 @@ def oracle_sample(target_s=15.0, gpu_out=None, others=None):
 
 
 def run_reference(args, world, rank):
-    """--impl reference: the oracle itself, timed on host cores (rank 0 only)."""
+    """--impl reference: the oracle itself, timed on host cores (rank 0 only): every
+    step times the same fixed sample as the bench's cpu_baseline leg."""
     if rank != 0:
         return
     t0 = time.perf_counter()
     per_step = []
     base = None
     for i in range(args.warmup + args.steps):
-        res, _ = oracle_sample(target_s=max(5.0, 60.0 / max(1, args.warmup + args.steps)))
+        res, _ = oracle_sample()
         if i >= args.warmup:
             per_step.append(res["value"])
             base = res
@@ -255,7 +287,11 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": base["cores"], "kind": "oracle",
-                             "sample": base["sample"]},
+                             "sample": base["sample"] + "; median over the timed steps",
+                             "ms_per_ring_synthesis": base["ms_per_ring_synthesis"],
+                             "ms_per_m_analysis": base["ms_per_m_analysis"],
+                             "extrapolation": base["extrapolation"],
+                             "step_values_ms": per_step},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
@@ -731,7 +767,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--lmax", type=int, default=4095, help="smaller sizes for profiling captures")
     ap.add_argument("--nlat", type=int, default=None,
                     help="fewer rings of the same length for profiling captures (default lmax + 1)")
@@ -897,8 +932,10 @@ def main():
             "forms": results}
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         others = {k: v for k, v in outputs.items() if k != head}
-        cb, acc = oracle_sample(args.cpu_seconds, gpu_out=outputs[head], others=others)
-        cb["single_core_scalar_gl128_lmax127_ms"] = oracle_single_thread_small()
+        cb, acc = oracle_sample(gpu_out=outputs[head], others=others)
+        cb["scalar_gl128_lmax127_full_ms"] = {"one_core": oracle_small_full(1), "all_cores": oracle_small_full(None),
+                                              "note": "the small scalar workload (GL 128 x 255, lmax 127, one "
+                                                      "synthesis + analysis) in full, measured, not extrapolated"}
         line["cpu_baseline"] = cb
         line["accuracy_vs_oracle_sample"] = acc
     if rank == 0:

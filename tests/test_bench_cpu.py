@@ -92,3 +92,27 @@ def test_headline_config_exceeds_l2():
 def test_oracle_single_core_leg():
     # the cpu_baseline leg times the oracle on one core in a process of its own
     assert bench.oracle_single_thread_small() > 0
+
+
+def test_fixed_oracle_sample_and_reference_line():
+    # both arms time the same sample: 2 rings and 2 m values per core, poles and
+    # both ends of the m range included; the reference arm prints its line with
+    # the per-unit costs and the extrapolation formula
+    import json
+    import subprocess
+    import sys
+
+    bench.set_workload(4095)
+    rsel, msel = bench.oracle_sample_sizes(16)
+    assert len(rsel) == 32 and rsel[0] == 0 and rsel[-1] == 4095
+    assert len(msel) == 32 and msel[0] == 0 and msel[-1] == 4095
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--lmax", "31", "--steps", "2",
+                        "--warmup", "1"], cwd=bench.ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    cb = line["cpu_baseline"]
+    assert line["impl"] == "reference" and line["value"] > 0 and len(cb["step_values_ms"]) == 2
+    assert cb["value"] == line["value"]
+    # the last step's value is the formula applied to its per-unit costs (32 rings, 32 m at lmax 31)
+    t = cb["ms_per_ring_synthesis"] * 32 + cb["ms_per_m_analysis"] * 32
+    assert abs(t - cb["step_values_ms"][-1]) <= 1e-9 * t
