@@ -367,7 +367,7 @@ MEASURED_TRAFFIC = {
 }
 
 
-KERNEL_HEADERS = {"legendre_fp64.cu": ("sht_device.cuh",), "legendre_mixed.cu": ("df.cuh", "sht_device.cuh")}
+KERNEL_HEADERS = {"legendre_fp64.cu": ("sht_device.cuh",), "legendre_mixed.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh")}
 
 
 def _kernel_digest(kernel_file):

@@ -120,9 +120,16 @@ def test_full_size_forward_backward(mods):
     # forms forward and backward; the forward maps on sampled rings (both poles, the
     # equator) and the gradient at sampled m against the oracle on the same inputs,
     # a directional finite difference, and the mixed gradient against the FP64 one.
-    # The FP64 bounds are the full-size test's at lmax 4095 with the sample as a
-    # whole at 2e-12: the oracle's own recursion error grows linearly with lmax
-    # (Sect. 5.1.2), about 1e-12 after 4500 steps.
+    # Bounds: on the rings nearest the poles double precision itself is the limit at
+    # this lmax -- the m = 0 recursion is non-oscillatory for l < ~1/theta (about
+    # 3400 here) and amplifies rounding by powers of l: evaluated in 40 digits at the
+    # same double cos(theta), the oracle's own m = 0 sum is 4.6e-11 off on the first
+    # ring and 2.5e-10 on the third (a plain FP64 recursion 9e-11 and 1.7e-9), in
+    # line with the maximum error growing like lmax^(3/2) (Sect. 5.1.2).  So every
+    # sampled ring is held to 1e-10 in both forms; the rings more than 0.05 rad from
+    # the poles, taken together, to 2e-12 (FP64; the 1e-12 of lmax 4095 with the
+    # oracle's linear drift) and 1e-10 (mixed); the gradient at the sampled m to
+    # 1e-11 and 1e-10.
     sht, ag = mods
     lmax = 8191
     geom = sht.sht_geom_gauss(lmax + 1, 2 * lmax + 1)
@@ -133,12 +140,13 @@ def test_full_size_forward_backward(mods):
     r = geom.rings()
     rings = oracle.Rings(r["theta"], r["nphi"], r["phi0"], r["weight"], ofs=r["ofs"])
     ring_sel = [0, 1, 2048, 4095, 6000, 8190, 8191]
+    away = [y for y in ring_sel if min(rings.theta[y], np.pi - rings.theta[y]) > 0.05]
     m_sel = [0, 1, 47, 3000, 8191]
     ref_p = oracle.synthesis(0, lmax, lmax, [a], rings, rings_sel=ring_sel)[0]
-    idx = np.concatenate([np.arange(rings.ofs[y], rings.ofs[y] + rings.nphi[y]) for y in ring_sel])
+    idx = np.concatenate([np.arange(rings.ofs[y], rings.ofs[y] + rings.nphi[y]) for y in away])
     _, m = inputs.lm_arrays(lmax, lmax)
     msk = np.isin(m, m_sel)
-    tol = {0: (1e-11, 2e-12), 1: (1e-10, 1e-10)}  # (each ring, the sample)
+    tol = {0: (1e-10, 2e-12, 1e-11), 1: (1e-10, 1e-10, 1e-10)}  # (each ring, rings away from the poles, gradient)
     grads = {}
     for prec in (0, 1):
         plan = sht.sht_plan_create(geom, lay, 0, 1, prec)
@@ -148,6 +156,7 @@ def test_full_size_forward_backward(mods):
         loss.backward()
         grads[prec] = at.grad.detach()
         p = pt.detach()[0].cpu().numpy()
+        print("precision", prec, "per ring", {y: f"{rel_l2(p[rings.ofs[y]:rings.ofs[y] + rings.nphi[y]], ref_p[rings.ofs[y]:rings.ofs[y] + rings.nphi[y]]):.2e}" for y in ring_sel})
         for y in ring_sel:
             s = slice(rings.ofs[y], rings.ofs[y] + rings.nphi[y])
             assert rel_l2(p[s], ref_p[s]) <= tol[prec][0], (prec, y, rel_l2(p[s], ref_p[s]))
@@ -156,9 +165,9 @@ def test_full_size_forward_backward(mods):
         yh = oracle.analysis(0, lmax, lmax, [2.0 * (p - d)], rings, m_sel=m_sel, adjoint=True)[0]
         ref_g = np.where(m == 0, yh.real + 0j, 2.0 * yh)[msk]
         got_g = grads[prec][0].cpu().numpy()[msk]
-        print("precision", prec, "sampled rings", f"{rel_l2(p[idx], ref_p[idx]):.2e}",
+        print("precision", prec, "rings away from the poles", f"{rel_l2(p[idx], ref_p[idx]):.2e}",
               "gradient at sampled m", f"{rel_l2(got_g, ref_g):.2e}")
-        assert rel_l2(got_g, ref_g) <= tol[prec][1], (prec, rel_l2(got_g, ref_g))
+        assert rel_l2(got_g, ref_g) <= tol[prec][2], (prec, rel_l2(got_g, ref_g))
         if prec == 0:
             v = torch.from_numpy(inputs.gaussian_alm(rng, lmax, lmax, cl=inputs.cl_inverse_square)).cuda()
             v = v.reshape(1, -1)
