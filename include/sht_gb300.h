@@ -281,6 +281,33 @@ SHT_API int sht_plan_get_fp64_columns(sht_plan_t plan, int *m_below);
 SHT_API int sht_plan_set_fft_precision(sht_plan_t plan, int precision);
 SHT_API int sht_plan_get_fft_precision(sht_plan_t plan, int *precision);
 
+/* ---- the synthesis contraction on the tensor cores ---------------------------
+ * The paper's synthesis (Eq. syn2; the inner loop of Sect. 3.2, Fig. 1) is, for
+ * one m, a product F = Lambda^T a over the degrees l.  A mixed plan can run that
+ * product on the tensor cores: the double-float recursion of Sect. 4.1 still
+ * generates Lambda, which is split exactly into three bf16 digits on a fixed grid
+ * plus an FP32 remainder (contracted on the CUDA cores); the a_lm are split into
+ * five bf16 digits on a grid per 256 degrees; the digit products are summed in
+ * FP32 accumulators where no rounding can occur, and the sums are added in
+ * double-float.  Results agree with the double-float contraction to ~1e-13
+ * relative (a term's error is below 2^-40 of the bound of its operands).
+ * Shapes: spin 0 with ncomp <= 8, spin s with ncomp <= 4 (SHT_ERR_UNSUPPORTED
+ * otherwise).  sht_plan_set_tensor_cores(plan, 1) selects it for SHT_SYNTHESIS,
+ * SHT_ADJOINT_ANALYSIS and SHT_DERIV_SYNTHESIS through sht_execute and
+ * sht_execute_noalloc; 0 selects the double-float contraction (the default).
+ * Batches keep the double-float kernels.  Errors: SHT_ERR_INVALID_ARG (NULL, an
+ * FP64 plan, a plan in a batch), SHT_ERR_UNSUPPORTED.
+ *
+ * The tensor-core kernel waits on its own matrix products with a bounded number
+ * of tries; if a wait gives up it stops, records bit 0 in the plan's device
+ * status word and leaves its outputs undefined.  sht_plan_device_status
+ * synchronises the device, writes the word to *status, clears it and returns
+ * SHT_ERR_TIMEOUT if it was set (SHT_OK otherwise).
+ */
+SHT_API int sht_plan_set_tensor_cores(sht_plan_t plan, int on);
+SHT_API int sht_plan_get_tensor_cores(sht_plan_t plan, int *on);
+SHT_API int sht_plan_device_status(sht_plan_t plan, int *status);
+
 /* ---- measurement ----------------------------------------------------------
  * Sect. 5.2 times whole transforms by wall clock; these two calls report the
  * device time of each kernel stage instead.  While profiling is on,

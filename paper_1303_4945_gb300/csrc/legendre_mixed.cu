@@ -649,6 +649,7 @@ cudaError_t launch_leg_mixed_items(const sht_plan_s *P, int stage, int polar, co
   const int nj = P->njobs_pad;
   if (stage == 0) {
     a.syn_items = static_cast<const int2 *>(items);
+    if (P->tc_syn) return launch_leg_tc_syn(P, &a, n, st);
     if (P->spin == 0) {
       switch (nj) {
         case 1: mix_syn_s0<1><<<n, kSynTile, 0, st>>>(a); break;

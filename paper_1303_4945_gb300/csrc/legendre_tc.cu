@@ -1,0 +1,620 @@
+// legendre_tc.cu -- the mixed form's Legendre synthesis (Eq. syn2) with the
+// contraction of a_lm against Lambda_lm on the tensor cores (tcgen05).
+//
+// For one m and the 128 ring pairs of a CTA the synthesis is a product
+// F[pair][col] = sum_l Lambda[pair][l] B[l][col] (Sect. 3.2's inner loop over l,
+// Fig. 1), with B the a_lm values arranged by column (real and imaginary parts,
+// the even/odd-l split of the ring-pair parity, the +s / -s spin combinations).
+// Lambda is still generated on the fly by the double-float recursion of Sect. 4.1
+// (one thread per ring pair, as in legendre_mixed.cu); the product runs as bf16
+// matrix products with FP32 accumulation, made exact by splitting both operands
+// into digits on a common grid (an Ozaki-style error-free split):
+//
+//  * Lambda = L0 + L1 + L2 + r.  The digits Lj are multiples of qj = u 2^(-7-8j)
+//    with |Lj| <= 128 qj, where u is a power of two bounding |Lambda_lm| for the
+//    whole plan (|sLambda_lm| <= sqrt((2l+1)/(4 pi)) since |d^l| <= 1); each fits
+//    a bf16 exactly.  The FP32 remainder r (|r| <= q2/2) is contracted on the
+//    CUDA cores (one FFMA per output column), so Lambda enters to ~2^-43 u.
+//  * B = B0 + ... + B4 with digits on the grid u_c 2^(-7-8j), u_c a power of two
+//    bounding column c of B over a window of 256 degrees.
+//  * The products Li Bj with i + j = k are accumulated in TMEM level k (k <= 5;
+//    the dropped products are below 2^-48 of the bounds).  Every product is a
+//    multiple of the level's quantum and a level's sum over one window stays
+//    below 2^24 quanta, so the FP32 accumulation is exact whatever its rounding.
+//  * After each window the six levels are read from TMEM and added in
+//    double-float, together with the CUDA-core remainder sums.
+//
+// MMA shape: M = 128 ring pairs (one TMEM lane per pair: thread t reads lane t),
+// N = 16 or 32 columns, K = 16 degrees per instruction; A (the Lambda digits)
+// and B (the a_lm digits) are K-major in shared memory without swizzle, 8x16-byte
+// core matrices 128 bytes apart along K and 256 bytes apart along M / N.  A is
+// double-buffered (the recursion writes K-step s + 1 while the MMAs of s run),
+// B is rebuilt per K-step once the previous K-step's MMAs have completed.
+#include "mixed_common.cuh"
+
+namespace sht {
+namespace tc {
+
+constexpr int kRows = 128;          // ring pairs per CTA = MMA M = TMEM lanes
+constexpr int kK = 16;              // degrees per MMA (bf16 K)
+constexpr int kWin = 16;            // K-steps per TMEM window (256 degrees)
+constexpr int kLamDigits = 3;       // bf16 digits of Lambda (plus an FP32 remainder)
+constexpr int kAlmDigits = 5;       // bf16 digits of the a_lm columns
+constexpr int kLevels = 6;          // TMEM accumulators: digit products with i + j <= 5
+constexpr int kATile = kRows * kK * 2;  // bytes of one 128 x 16 bf16 tile
+constexpr unsigned long long kWaitNs = 100000000ull;  // bounded mbarrier waits: 100 ms of global time
+
+// ---- PTX wrappers -------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// shared-memory matrix descriptor, no swizzle: LBO = byte stride between core
+// matrices along K, SBO = along M / N (checked on the device against CPU products)
+__device__ __forceinline__ uint64_t mat_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+// instruction descriptor: D FP32, A and B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// waits for the completion of the barrier phase of the given parity; false once
+// kWaitNs have passed (the matrix products take microseconds)
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done = 0;
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (!done && (it & 63) == 63 && global_ns() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 8 consecutive 32-bit TMEM columns of this thread's lane (warp w reads lanes 32w..32w+31)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- exact digits ---------------------------------------------------------------
+// round x to a multiple of the quantum q whose magic constant is s = 1.5 * 2^23 * q
+// (|x| < 2^22 q): the sum's rounding does it, the subtraction is exact
+__device__ __forceinline__ float round_to(float x, float s) { return __fsub_rn(__fadd_rn(x, s), s); }
+// two digits (each with at most 8 significant bits, so their FP32 patterns end in
+// 16 zero bits) packed as bf16 in one word: lo at the lower address
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+// the bf16 bits of one digit
+__device__ __forceinline__ uint16_t bf16_of(float d) { return (uint16_t)(__float_as_uint(d) >> 16); }
+// the power of two 2^(e+1) above a non-negative x in [2^e, 2^(e+1)) (2^-126 for 0)
+__device__ __forceinline__ float pow2_above(float x) {
+  return __int_as_float((__float_as_int(x) & 0x7f800000) + 0x00800000);
+}
+
+// Shapes: NCOL output columns per pair (spin: N1, S4, N2, S3 as re/im per job;
+// spin 0: even-l and odd-l sums as re/im per job), MMA width N >= 16, NV a_lm
+// values per degree (spin: P = E + iB and M = E - iB, re and im; spin 0: re, im).
+template <int NJ, bool SPIN>
+struct Shape {
+  static constexpr int NL = SPIN ? 2 : 1;
+  static constexpr int NCOL = SPIN ? 8 * NJ : 4 * NJ;
+  static constexpr int N = NCOL < 16 ? 16 : NCOL;
+  static constexpr int NV = SPIN ? 4 * NJ : 2 * NJ;
+  static constexpr int TCOLS = kLevels * N <= 128 ? 128 : 256;  // TMEM allocation (a power of two)
+  static constexpr int BTILE = N * kK * 2;                      // bytes of one B digit tile
+  static constexpr int A_BYTES = 2 * NL * kLamDigits * kATile;  // two buffers
+  static constexpr int B_BYTES = NL * kAlmDigits * BTILE;
+  static constexpr int SMEM = A_BYTES + B_BYTES + 2 * NV * 4;
+  // dynamic shared memory requested: enough that at most 512 / TCOLS CTAs fit on an
+  // SM, so their TMEM allocations never wait for one another
+  static constexpr int SMEM_LAUNCH = TCOLS == 128 ? (SMEM > 46 * 1024 ? SMEM : 46 * 1024)
+                                                  : (SMEM > 77 * 1024 ? SMEM : 77 * 1024);
+  static_assert(NCOL <= 32, "tensor-core synthesis: at most 32 output columns");
+  static_assert(128 % NV == 0, "a_lm values per degree must divide the CTA");
+};
+
+}  // namespace tc
+
+struct TcArgs {
+  MixArgs m;        // tables, work items and phase array of the mixed form
+  float lam_bound;  // power of two bounding |Lambda_lm| over the plan
+  int *err;         // device status word: bit 0 set when a bounded wait gave up
+};
+
+namespace tc {
+
+// the double-float a_lm value v (Shape::NV of them per degree) at table index ci
+template <int NJ, bool SPIN>
+__device__ __forceinline__ f2 alm_value(const MixArgs &a, int64_t ci, int v) {
+  if (SPIN) {
+    const float4 q = __ldg(a.alm32 + (int64_t)(2 * (v / 4) + ((v & 2) ? 1 : 0)) * a.ncoef + ci);
+    return (v & 1) ? f2{q.z, q.w} : f2{q.x, q.y};
+  }
+  const float4 q = __ldg(a.alm32 + (int64_t)(v / 2) * a.ncoef + ci);
+  return (v & 1) ? f2{q.z, q.w} : f2{q.x, q.y};
+}
+
+// Column bounds of one window (degrees lw0..lw1): umax[v] = max |value v| over
+// the window (atomically, as FP32 bit patterns of non-negative numbers).  The
+// caller synchronises before the bounds are read.
+template <int NJ, bool SPIN>
+__device__ __forceinline__ void window_bounds(const MixArgs &a, int64_t co, int lw0, int lw1, float *umax) {
+  using S = Shape<NJ, SPIN>;
+  const int v = threadIdx.x % S::NV;
+  float mx = 0.f;
+  for (int l = lw0 + (int)threadIdx.x / S::NV; l <= lw1; l += kRows / S::NV)
+    mx = fmaxf(mx, fabsf(alm_value<NJ, SPIN>(a, co + l, v).h));
+  // lanes holding the same v differ in the bits above log2(NV): reduce over them
+#pragma unroll
+  for (int o = S::NV; o < 32; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) < S::NV) atomicMax(reinterpret_cast<int *>(umax) + v, __float_as_int(mx));
+}
+
+// The B digit tiles of K-step degrees lb..lb+15 (zero past lmax): value v of degree
+// lb + k split into kAlmDigits digits on its window's grid and written, with the
+// parity sign s = (-1)^(l - l0) where the column needs it, into the rows of the
+// columns that read it (see the column layout in tc_syn_body).  Rows no value
+// writes stay zero from the kernel's start.
+template <int NJ, bool SPIN>
+__device__ __forceinline__ void build_b(const MixArgs &a, int64_t co, int lb, int lmax, const float *umax,
+                                        unsigned char *Bt) {
+  using S = Shape<NJ, SPIN>;
+  for (int t = threadIdx.x; t < kK * S::NV; t += kRows) {
+    const int k = t % kK, v = t / kK, l = lb + k;
+    const f2 x = l <= lmax ? alm_value<NJ, SPIN>(a, co + l, v) : f2{0.f, 0.f};
+    const float s0 = pow2_above(umax[v]) * 98304.0f;  // 1.5 * 2^23 * (bound * 2^-7)
+    float d[kAlmDigits];
+    float r = x.h;
+    d[0] = round_to(r, s0);
+    r = __fsub_rn(r, d[0]);
+    d[1] = round_to(r, s0 * 0x1p-8f);
+    r = __fsub_rn(r, d[1]);
+    d[2] = round_to(r, s0 * 0x1p-16f);
+    r = __fadd_rn(__fsub_rn(r, d[2]), x.l);
+    d[3] = round_to(r, s0 * 0x1p-24f);
+    r = __fsub_rn(r, d[3]);
+    d[4] = round_to(r, s0 * 0x1p-32f);
+    const bool odd = k & 1;
+    // (tile, row) pairs of this value; spin: P.re -> (+, 8j) and (-, 8j+6) signed,
+    // P.im -> (+, 8j+1) and (-, 8j+7) signed, M.re -> (+, 8j+2) signed and (-, 8j+4),
+    // M.im -> (+, 8j+3) signed and (-, 8j+5); spin 0: the even- or odd-l row of its job
+    int lam0, row0, lam1 = -1, row1 = 0, neg0 = 0, neg1 = 0;
+    int zrow = -1;
+    if (SPIN) {
+      const int j = v / 4, c = v % 4;
+      lam0 = 0;
+      lam1 = 1;
+      row0 = 8 * j + c;
+      row1 = 8 * j + (c < 2 ? 6 + c : 2 + c);
+      neg0 = (c >= 2) && odd;
+      neg1 = (c < 2) && odd;
+    } else {
+      const int j = v / 2, c = v % 2;
+      lam0 = 0;
+      row0 = 4 * j + (odd ? 2 : 0) + c;
+      zrow = 4 * j + (odd ? 0 : 2) + c;
+    }
+    const int off = (k / 8) * 128 + (k % 8) * 2;
+#pragma unroll
+    for (int dj = 0; dj < kAlmDigits; ++dj) {
+      unsigned char *tile0 = Bt + (lam0 * kAlmDigits + dj) * S::BTILE + off;
+      *reinterpret_cast<uint16_t *>(tile0 + (row0 / 8) * 256 + (row0 % 8) * 16) = bf16_of(neg0 ? -d[dj] : d[dj]);
+      if (SPIN) {
+        unsigned char *tile1 = Bt + (lam1 * kAlmDigits + dj) * S::BTILE + off;
+        *reinterpret_cast<uint16_t *>(tile1 + (row1 / 8) * 256 + (row1 % 8) * 16) = bf16_of(neg1 ? -d[dj] : d[dj]);
+      } else {
+        *reinterpret_cast<uint16_t *>(tile0 + (zrow / 8) * 256 + (zrow % 8) * 16) = 0;
+      }
+    }
+  }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// synthesis, spin 0 and spin s
+//
+// Columns of the product (per job j): spin, 8j + {0,1} N1 = sum P l+, {2,3}
+// S4 = sum s M l+, {4,5} N2 = sum M l-, {6,7} S3 = sum s P l- (re, im; s =
+// (-1)^(l - l0), P = E + iB, M = E - iB); spin 0, 4j + {0,1} the even-l and
+// 4j + {2,3} the odd-l sums of a_lm lambda.  The +s digits (A set 0) meet B rows
+// holding P, s M; the -s digits (A set 1) rows holding M, s P.
+// ---------------------------------------------------------------------------
+template <int NJ, bool SPIN>
+__device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, unsigned char *smem) {
+  using S = tc::Shape<NJ, SPIN>;
+  constexpr int NL = S::NL, NCOL = S::NCOL, N = S::N;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const MixArgs &a = ta.m;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int mi = item.x;
+  const int p = item.y + tid;
+  const bool valid = p < a.npairs;
+  const int m = a.mval[mi];
+  const int s = a.spin, as = s < 0 ? -s : s;
+  const int l0 = m > as ? m : as, lmax = a.lmax;
+  const int nks = (lmax - l0 + tc::kK) / tc::kK;
+  const int64_t co = a.coef_off[mi] - l0;
+  const float4 *__restrict__ cf = a.coef32 + 2 * co;
+  unsigned char *const Abuf = smem;
+  unsigned char *const Bt = smem + S::A_BYTES;
+  float *const umax = reinterpret_cast<float *>(Bt + S::B_BYTES);
+
+  if (warp == 0) tc::tmem_alloc(&tslot, S::TCOLS);
+  if (tid == 0) tc::bar_init(&mbar);
+  for (int i = tid; i < S::B_BYTES / 16; i += tc::kRows) reinterpret_cast<uint4 *>(Bt)[i] = make_uint4(0, 0, 0, 0);
+  if (tid < 2 * S::NV) umax[tid] = 0.f;
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = tslot;
+
+  // recursion state (as in the double-float synthesis): +s values lpc/lpp, -s lmc/lmp
+  const PairDev pd = a.pairs[valid ? p : 0];
+  const f3 x = f3_of(pd.x);
+  f2 lpc, lmc = {0.f, 0.f}, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
+  int scp, scm = 0;
+  if (SPIN) {
+    start_s(m, s, pd, a.mpre[mi], &lpc, &scp);
+    start_s(m, -s, pd, a.mpre[mi], &lmc, &scm);
+  } else {
+    start_s0(m, pd, a.mpre[mi], &lpc, &scp);
+  }
+  if (!valid) {
+    lpc = lmc = f2{0.f, 0.f};
+    scp = scm = 0;
+  }
+  // digit grid of Lambda: magic constants of the quanta u 2^-7, u 2^-15, u 2^-23
+  const float ls0 = ta.lam_bound * 98304.0f, ls1 = ls0 * 0x1p-8f, ls2 = ls0 * 0x1p-16f;
+  f2 acc[NCOL];
+  float racc[NCOL];
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c) {
+    acc[c] = f2{0.f, 0.f};
+    racc[c] = 0.f;
+  }
+
+  // eight degrees lb..lb+7 (lb - l0 even; SETTLED: every lane's values at scale 0,
+  // passed as a literal so that each call inlines its own variant): digits packed per pair of degrees into
+  // pk[set][digit][q / 2], remainders contracted into racc, recursion advanced
+  auto half = [&](int lb, const bool SETTLED, uint32_t (&pk)[NL][tc::kLamDigits][4]) {
+    float dlo[NL][tc::kLamDigits];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int l = lb + q;
+      const bool in = l <= lmax;  // uniform over the CTA
+      const bool odd = q & 1;
+      f2 w[NL];
+      w[0] = SETTLED ? lpc : weight(lpc, scp);
+      if (SPIN) w[1] = SETTLED ? lmc : weight(lmc, scm);
+      float rr[NL];
+#pragma unroll
+      for (int t = 0; t < NL; ++t) {
+        if (!in) w[t] = f2{0.f, 0.f};
+        const float d0 = tc::round_to(w[t].h, ls0);
+        float r = __fsub_rn(w[t].h, d0);
+        const float d1 = tc::round_to(r, ls1);
+        r = __fsub_rn(r, d1);
+        const float d2 = tc::round_to(r, ls2);
+        rr[t] = __fadd_rn(__fsub_rn(r, d2), w[t].l);
+        if (!odd) {
+          dlo[t][0] = d0;
+          dlo[t][1] = d1;
+          dlo[t][2] = d2;
+        } else {
+          pk[t][0][q / 2] = tc::pack_bf16(dlo[t][0], d0);
+          pk[t][1][q / 2] = tc::pack_bf16(dlo[t][1], d1);
+          pk[t][2][q / 2] = tc::pack_bf16(dlo[t][2], d2);
+        }
+      }
+      if (in) {
+        const int64_t ci = co + l;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          if (SPIN) {
+            const float4 P = __ldg(a.alm32 + (int64_t)(2 * j) * a.ncoef + ci);
+            const float4 M = __ldg(a.alm32 + (int64_t)(2 * j + 1) * a.ncoef + ci);
+            const float rp = rr[0], rm = rr[1], sp = odd ? -rr[0] : rr[0], sm = odd ? -rr[1] : rr[1];
+            racc[8 * j + 0] = __fmaf_rn(rp, P.x, racc[8 * j + 0]);
+            racc[8 * j + 1] = __fmaf_rn(rp, P.z, racc[8 * j + 1]);
+            racc[8 * j + 2] = __fmaf_rn(sp, M.x, racc[8 * j + 2]);
+            racc[8 * j + 3] = __fmaf_rn(sp, M.z, racc[8 * j + 3]);
+            racc[8 * j + 4] = __fmaf_rn(rm, M.x, racc[8 * j + 4]);
+            racc[8 * j + 5] = __fmaf_rn(rm, M.z, racc[8 * j + 5]);
+            racc[8 * j + 6] = __fmaf_rn(sm, P.x, racc[8 * j + 6]);
+            racc[8 * j + 7] = __fmaf_rn(sm, P.z, racc[8 * j + 7]);
+          } else {
+            const float4 v = __ldg(a.alm32 + (int64_t)j * a.ncoef + ci);
+            const int c = 4 * j + (odd ? 2 : 0);
+            racc[c] = __fmaf_rn(rr[0], v.x, racc[c]);
+            racc[c + 1] = __fmaf_rn(rr[0], v.z, racc[c + 1]);
+          }
+        }
+        const Coef32 cc = ld_coef32(cf + 2 * l);
+        const f2 t = mul(cc.a, x);
+        const f2 nc = neg(cc.c);
+        if (SPIN) {
+          const f2 np_ = dot3(t, lpc, cc.ak, lpc, nc, lpp);
+          const f2 nm_ = dot3(t, lmc, neg(cc.ak), lmc, nc, lmp);
+          lpp = lpc;
+          lpc = np_;
+          lmp = lmc;
+          lmc = nm_;
+        } else {
+          const f2 ln = dot2(t, lpc, nc, lpp);
+          lpp = lpc;
+          lpc = ln;
+        }
+      }
+    }
+    if (!SETTLED) {  // enhanced exponent: rescale every eight degrees (see mixed_common.cuh)
+      if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
+        lpc = {lpc.h * kScaleFactor32, lpc.l * kScaleFactor32};
+        lpp = {lpp.h * kScaleFactor32, lpp.l * kScaleFactor32};
+        ++scp;
+      }
+      if (SPIN && scm < 0 && fabsf(lmc.h) > kScaleUp32) {
+        lmc = {lmc.h * kScaleFactor32, lmc.l * kScaleFactor32};
+        lmp = {lmp.h * kScaleFactor32, lmp.l * kScaleFactor32};
+        ++scm;
+      }
+    }
+  };
+
+  // the MMAs of one K-step (thread 0): every digit product Li Bj with i + j <= 5 into
+  // level i + j, the first product of a level in a window overwriting it
+  auto issue = [&](int ks) {
+    tc::fence_after();
+    constexpr uint32_t idesc = tc::instr_desc(tc::kRows, N);
+    const uint32_t abase = tc::smem_u32(Abuf + (ks & 1) * (NL * tc::kLamDigits * tc::kATile));
+    const uint32_t bbase = tc::smem_u32(Bt);
+    const bool first = (ks % tc::kWin) == 0;
+    uint32_t inited = 0;
+#pragma unroll
+    for (int t = 0; t < NL; ++t)
+#pragma unroll
+      for (int i = 0; i < tc::kLamDigits; ++i)
+#pragma unroll
+        for (int j = 0; j < tc::kAlmDigits; ++j) {
+          const int k = i + j;
+          if (k >= tc::kLevels) continue;
+          const uint64_t ad = tc::mat_desc(abase + (t * tc::kLamDigits + i) * tc::kATile, 128, 256);
+          const uint64_t bd = tc::mat_desc(bbase + (t * tc::kAlmDigits + j) * S::BTILE, 128, 256);
+          const uint32_t accum = (!first || ((inited >> k) & 1u)) ? 1u : 0u;
+          inited |= 1u << k;
+          tc::mma_bf16(tbase + k * N, ad, bd, idesc, accum);
+        }
+    tc::mma_commit(&mbar);
+  };
+
+  // after a window: the six levels of this thread's lane plus the remainder sums,
+  // added to the double-float column sums
+  auto readout = [&]() {
+    const uint32_t lane = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int c0 = 0; c0 < NCOL; c0 += 8) {
+      float dv[tc::kLevels][8];
+#pragma unroll
+      for (int k = 0; k < tc::kLevels; ++k) tc::tmem_ld8(lane + k * N + c0, dv[k]);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c0 + c >= NCOL) break;
+        f2 t = {dv[0][c], 0.f};
+#pragma unroll
+        for (int k = 1; k < tc::kLevels; ++k) t = f2_add_lazy(t, f2{dv[k][c], 0.f});
+        t = f2_add_lazy(t, f2{racc[c0 + c], 0.f});
+        racc[c0 + c] = 0.f;
+        acc[c0 + c] = f2_add(acc[c0 + c], t);
+      }
+    }
+  };
+
+  int ncommit = 0, nwaited = 0;
+  bool ok = true, settled = false;
+  for (int ks = 0; ks < nks; ++ks) {
+    const int lb = l0 + ks * tc::kK;
+    if (ks % tc::kWin == 0) {  // column bounds of this window's a_lm
+      float *um = umax + ((ks / tc::kWin) & 1) * S::NV;
+      if (tid < S::NV) umax[(((ks / tc::kWin) & 1) ^ 1) * S::NV + tid] = 0.f;  // the other window's, for later
+      const int lw1 = lb + tc::kWin * tc::kK - 1;
+      tc::window_bounds<NJ, SPIN>(a, co, lb, lw1 < lmax ? lw1 : lmax, um);
+      __syncthreads();
+    }
+    unsigned char *Aw = Abuf + (ks & 1) * (NL * tc::kLamDigits * tc::kATile);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      uint32_t pk[NL][tc::kLamDigits][4];
+      if (settled)
+        half(lb + 8 * h, true, pk);
+      else
+        half(lb + 8 * h, false, pk);
+      settled = settled || __all_sync(0xffffffffu, scp == 0 && scm == 0);
+#pragma unroll
+      for (int t = 0; t < NL; ++t)
+#pragma unroll
+        for (int i = 0; i < tc::kLamDigits; ++i)
+          *reinterpret_cast<uint4 *>(Aw + (t * tc::kLamDigits + i) * tc::kATile + (tid / 8) * 256 + h * 128 +
+                                     (tid % 8) * 16) = make_uint4(pk[t][i][0], pk[t][i][1], pk[t][i][2], pk[t][i][3]);
+    }
+    // the previous K-step's MMAs read the B tiles: wait for them before rebuilding
+    bool fail = false;
+    if (ncommit > nwaited) {
+      fail = !tc::bar_wait(&mbar, (uint32_t)(ncommit - 1) & 1u);
+      nwaited = ncommit;
+    }
+    if (!fail) tc::build_b<NJ, SPIN>(a, co, lb, lmax, umax + ((ks / tc::kWin) & 1) * S::NV, Bt);
+    tc::fence_async_smem();
+    if (__syncthreads_or(fail)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) issue(ks);
+    ++ncommit;
+    if (ks % tc::kWin == tc::kWin - 1 || ks == nks - 1) {
+      fail = !tc::bar_wait(&mbar, (uint32_t)(ncommit - 1) & 1u);
+      nwaited = ncommit;
+      if (__syncthreads_or(fail)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
+      readout();
+      tc::fence_before();
+    }
+  }
+  if (!ok) {  // a wait gave up: flag it, give the MMAs in flight a bounded wait, release TMEM
+    if (tid == 0) atomicOr(ta.err, 1);
+    if (ncommit > nwaited) tc::bar_wait(&mbar, (uint32_t)(ncommit - 1) & 1u);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tbase, S::TCOLS);
+  if (!ok || !valid) return;
+
+  if (SPIN) {
+    const double sig = (as & 1) ? -1.0 : 1.0;
+    const double h0 = ((l0 + m) & 1) ? -0.5 : 0.5;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const double n1r = f2_val(acc[8 * j + 0]), n1i = f2_val(acc[8 * j + 1]);
+      const double s4r = f2_val(acc[8 * j + 2]), s4i = f2_val(acc[8 * j + 3]);
+      const double n2r = f2_val(acc[8 * j + 4]), n2i = f2_val(acc[8 * j + 5]);
+      const double s3r = f2_val(acc[8 * j + 6]), s3i = f2_val(acc[8 * j + 7]);
+      const double ar = n1r + sig * n2r, ai = n1i + sig * n2i;
+      const double br = sig * n2r - n1r, bi = sig * n2i - n1i;
+      const double cr = s3r + sig * s4r, ci = s3i + sig * s4i;
+      const double dr = sig * s4r - s3r, di = sig * s4i - s3i;
+      double2 qn = make_double2(-0.5 * ar, -0.5 * ai);
+      double2 un = make_double2(0.5 * bi, -0.5 * br);
+      double2 qs = make_double2(-h0 * cr, -h0 * ci);
+      double2 us = make_double2(h0 * di, -h0 * dr);
+      if (m == 0) qn.y = qs.y = un.y = us.y = 0.0;
+      double2 *oq = a.phase + (((size_t)(2 * j) * a.nm + mi) * a.npairs + p) * 2;
+      double2 *ou = a.phase + (((size_t)(2 * j + 1) * a.nm + mi) * a.npairs + p) * 2;
+      oq[0] = qn;
+      oq[1] = qs;
+      ou[0] = un;
+      ou[1] = us;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const double e0 = f2_val(acc[4 * j + 0]), e1 = f2_val(acc[4 * j + 1]);
+      const double o0 = f2_val(acc[4 * j + 2]), o1 = f2_val(acc[4 * j + 3]);
+      double2 fn = make_double2(e0 + o0, e1 + o1), fs = make_double2(e0 - o0, e1 - o1);
+      if (m == 0) fn.y = fs.y = 0.0;
+      double2 *o = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
+      o[0] = fn;
+      o[1] = fs;
+    }
+  }
+}
+
+}  // namespace sht
+
+namespace sht {
+
+template <int NJ, bool SPIN>
+__global__ void __launch_bounds__(tc::kRows, (tc::Shape<NJ, SPIN>::TCOLS == 128 ? 4 : 2))
+    tc_syn(TcArgs ta) {
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  tc_syn_body<NJ, SPIN>(ta, ta.m.syn_items[blockIdx.x], tc_smem);
+}
+
+template <int NJ, bool SPIN>
+static cudaError_t tc_set_smem() {
+  return cudaFuncSetAttribute(tc_syn<NJ, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc::Shape<NJ, SPIN>::SMEM_LAUNCH);
+}
+
+// dynamic shared memory above 48 KB for every instance (once per device, at plan time)
+cudaError_t tc_prepare_device() {
+  cudaError_t e = tc_set_smem<1, false>();
+  if (e == cudaSuccess) e = tc_set_smem<2, false>();
+  if (e == cudaSuccess) e = tc_set_smem<4, false>();
+  if (e == cudaSuccess) e = tc_set_smem<8, false>();
+  if (e == cudaSuccess) e = tc_set_smem<1, true>();
+  if (e == cudaSuccess) e = tc_set_smem<2, true>();
+  if (e == cudaSuccess) e = tc_set_smem<4, true>();
+  return e;
+}
+
+bool tc_supported(int spin, int njobs_pad) {
+  return spin == 0 ? njobs_pad <= 8 : njobs_pad <= 4;
+}
+
+float tc_lambda_bound(int lmax) {
+  // |sLambda_lm| <= sqrt((2l + 1) / (4 pi)) (|d^l| <= 1); the next power of two
+  // above it, with room for the recursion's rounding
+  const double b = sqrt((2.0 * lmax + 1.0) / (4.0 * M_PI)) * (1.0 + 1e-6);
+  return (float)exp2(ceil(log2(b)));
+}
+
+cudaError_t launch_leg_tc_syn(const sht_plan_s *P, const void *mixargs, int n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  TcArgs ta;
+  memcpy(&ta.m, mixargs, sizeof(MixArgs));
+  ta.lam_bound = P->tc_lam_bound;
+  ta.err = P->d_err;
+  const int nj = P->njobs_pad;
+  if (P->spin == 0) {
+    switch (nj) {
+      case 1: tc_syn<1, false><<<n, tc::kRows, tc::Shape<1, false>::SMEM_LAUNCH, st>>>(ta); break;
+      case 2: tc_syn<2, false><<<n, tc::kRows, tc::Shape<2, false>::SMEM_LAUNCH, st>>>(ta); break;
+      case 4: tc_syn<4, false><<<n, tc::kRows, tc::Shape<4, false>::SMEM_LAUNCH, st>>>(ta); break;
+      case 8: tc_syn<8, false><<<n, tc::kRows, tc::Shape<8, false>::SMEM_LAUNCH, st>>>(ta); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (nj) {
+      case 1: tc_syn<1, true><<<n, tc::kRows, tc::Shape<1, true>::SMEM_LAUNCH, st>>>(ta); break;
+      case 2: tc_syn<2, true><<<n, tc::kRows, tc::Shape<2, true>::SMEM_LAUNCH, st>>>(ta); break;
+      case 4: tc_syn<4, true><<<n, tc::kRows, tc::Shape<4, true>::SMEM_LAUNCH, st>>>(ta); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sht

@@ -756,7 +756,7 @@ static void free_plan(sht_plan_s *P) {
   cudaSetDevice(P->device);
   void *ptrs[] = {P->d_pairs, P->d_pair_rings, P->d_rings, P->d_mval, P->d_mstart, P->d_coef_off,
                   P->d_coef, P->d_coef32, P->d_alm32, P->d_pm64, P->d_mpre, P->d_minv, P->d_phase, P->d_part, P->d_fft,
-                  P->d_pair_fft, P->d_fft_scratch};
+                  P->d_pair_fft, P->d_fft_scratch, P->d_err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 2; ++k) {
@@ -997,6 +997,12 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
     P->workspace += nco * P->nmaps_pad * sizeof(double2);
   }
   CUDA_TRY(cudaMalloc(&P->d_mpre, P->nm * sizeof(double2)));
+  CUDA_TRY(cudaMalloc(&P->d_err, sizeof(int)));
+  CUDA_TRY(cudaMemset(P->d_err, 0, sizeof(int)));
+  if (P->precision == SHT_MIXED) {
+    P->tc_lam_bound = tc_lambda_bound(P->lmax);
+    CUDA_TRY(tc_prepare_device());
+  }
   CUDA_TRY(launch_coef_tables(P, 0));
   CUDA_TRY(cudaDeviceSynchronize());
 
@@ -1178,6 +1184,37 @@ extern "C" int sht_plan_get_fft_precision(sht_plan_t P, int *precision) {
   if (!P || !precision) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
   *precision = P->fft_df ? SHT_MIXED : SHT_FP64;
   return SHT_OK;
+}
+
+extern "C" int sht_plan_set_tensor_cores(sht_plan_t P, int on) {
+  if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  if (on && P->precision != SHT_MIXED) return fail(SHT_ERR_INVALID_ARG, "FP64 plans have no tensor-core form");
+  if (on && !tc_supported(P->spin, P->njobs_pad))
+    return fail(SHT_ERR_UNSUPPORTED, "tensor-core synthesis holds at most 32 columns (spin 0: ncomp <= 8, spin: ncomp <= 4)");
+  if (P->batch_refs)
+    return fail(SHT_ERR_INVALID_ARG, "the plan belongs to %d batch(es); destroy them first", P->batch_refs);
+  P->tc_syn = on ? 1 : 0;
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_get_tensor_cores(sht_plan_t P, int *on) {
+  if (!P || !on) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  *on = P->tc_syn;
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_device_status(sht_plan_t P, int *status) {
+  if (!P || !status) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, P->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) e = cudaMemset(P->d_err, 0, sizeof(int));
+  if (cur != P->device) cudaSetDevice(cur);
+  if (e != cudaSuccess) return fail(SHT_ERR_CUDA, "device status: %s", cudaGetErrorString(e));
+  *status = v;
+  return v ? fail(SHT_ERR_TIMEOUT, "a bounded device-side wait gave up (status %d)", v) : SHT_OK;
 }
 
 extern "C" int sht_plan_autotune(sht_plan_t P, void *stream, float *ms_per_candidate) {

@@ -161,6 +161,10 @@ struct sht_plan_s {
   // per-step rounding by a power of l
   int fp64_m_below = 0;
   bool fft_df = false;  // ring FFTs in double-float (mixed plans, by default)
+  // mixed plans: the synthesis contraction on the tensor cores (legendre_tc.cu)
+  int tc_syn = 0;
+  float tc_lam_bound = 0.f;  // power of two bounding |Lambda_lm| for lmax
+  int *d_err = nullptr;      // device status word written by kernels with bounded waits
   int m_identity = 0;   // the m list is 0, 1, ..., nm - 1
   // the FP64 columns run beside the mixed kernels: a side stream forked and joined by events
   cudaStream_t side = nullptr;
@@ -246,6 +250,12 @@ cudaError_t launch_leg_fp64_items(const sht_plan_s *P, int stage, const DevPtrs 
 cudaError_t launch_leg_mixed_items(const sht_plan_s *P, int stage, int polar, const void *items, int n,
                                    cudaStream_t st);
 cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int polar, cudaStream_t st);
+// tensor-core synthesis (legendre_tc.cu): mixargs is the mixed kernels' argument
+// record (MixArgs) with its synthesis work list set; n work items
+cudaError_t launch_leg_tc_syn(const sht_plan_s *P, const void *mixargs, int n, cudaStream_t st);
+cudaError_t tc_prepare_device();
+bool tc_supported(int spin, int njobs_pad);
+float tc_lambda_bound(int lmax);
 // ring FFTs
 // ring pairs [p0, p1) (p1 < 0: to the last pair)
 cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, int weighted, int add,

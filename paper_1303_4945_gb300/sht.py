@@ -76,6 +76,9 @@ _sig = {
     "sht_fft_plan_info": [ctypes.c_int, _ip, _ip, _ip, _ip],
     "sht_geom_polar_cut": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, _i64p],
     "sht_plan_get_fft_precision": [_vp, _ip],
+    "sht_plan_set_tensor_cores": [_vp, ctypes.c_int],
+    "sht_plan_get_tensor_cores": [_vp, _ip],
+    "sht_plan_device_status": [_vp, _ip],
     "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
                           ctypes.c_int, _vp],
@@ -242,6 +245,23 @@ class Plan(_Handle):
     @fft_precision.setter
     def fft_precision(self, precision):
         _check(_lib.sht_plan_set_fft_precision(self._h, precision), "sht_plan_set_fft_precision")
+
+    @property
+    def tensor_cores(self):
+        """Mixed plans: True when the synthesis contraction runs on the tensor cores."""
+        n = ctypes.c_int()
+        _check(_lib.sht_plan_get_tensor_cores(self._h, ctypes.byref(n)), "sht_plan_get_tensor_cores")
+        return bool(n.value)
+
+    @tensor_cores.setter
+    def tensor_cores(self, on):
+        _check(_lib.sht_plan_set_tensor_cores(self._h, 1 if on else 0), "sht_plan_set_tensor_cores")
+
+    def device_status(self):
+        """Synchronises; raises ShtError (SHT_ERR_TIMEOUT) if a bounded device-side wait gave up."""
+        n = ctypes.c_int()
+        _check(_lib.sht_plan_device_status(self._h, ctypes.byref(n)), "sht_plan_device_status")
+        return n.value
 
     def triples(self, flags=0):
         n = ctypes.c_int64()
