@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <map>
 #include <numeric>
 
@@ -211,8 +212,83 @@ extern "C" int sht_geom_gauss(int nlat, int nlon, sht_geom_t *out) {
   return make_regular(th, w, nlon, out);
 }
 
+// ---- DFT of any length on the host, in long double ------------------------------
+// X_i = sum_k x_k e^{+2 pi i k i / n}.  Bluestein's chirp identity turns it into a
+// cyclic convolution, done with radix-2 transforms of a power-of-two length >= 2n - 1.
+typedef std::complex<long double> cld;
+
+static void fft2_ld(std::vector<cld> &a, bool inverse) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {  // bit reversal
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const long double ang = (inverse ? 2.0L : -2.0L) * kPiL / (long double)len;
+    for (size_t k = 0; k < len / 2; ++k) {
+      const cld w(cosl(ang * k), sinl(ang * k));
+      for (size_t i = k; i < n; i += len) {
+        const cld u = a[i], v = a[i + len / 2] * w;
+        a[i] = u + v;
+        a[i + len / 2] = u - v;
+      }
+    }
+  }
+}
+
+static std::vector<cld> dft_pos_ld(const std::vector<cld> &x) {
+  const int64_t n = (int64_t)x.size();
+  if (n <= 64) {  // short: the sum itself
+    std::vector<cld> X(n);
+    for (int64_t i = 0; i < n; ++i) {
+      cld s = 0;
+      for (int64_t k = 0; k < n; ++k) {
+        const long double ang = 2.0L * kPiL * (long double)((i * k) % n) / (long double)n;
+        s += x[k] * cld(cosl(ang), sinl(ang));
+      }
+      X[i] = s;
+    }
+    return X;
+  }
+  // e^{2 pi i k i / n} = w_i w_k conj(w_{i-k}), w_j = e^{pi i j^2 / n} (j^2 reduced mod 2n)
+  auto chirp = [&](int64_t j) {
+    const int64_t q = (j * j) % (2 * n);
+    const long double ang = kPiL * (long double)q / (long double)n;
+    return cld(cosl(ang), sinl(ang));
+  };
+  size_t M = 1;
+  while ((int64_t)M < 2 * n - 1) M <<= 1;
+  std::vector<cld> a(M, 0), b(M, 0);
+  for (int64_t k = 0; k < n; ++k) a[k] = x[k] * chirp(k);
+  for (int64_t j = 0; j < n; ++j) {
+    b[j] = std::conj(chirp(j));
+    if (j) b[M - j] = b[j];
+  }
+  fft2_ld(a, false);
+  fft2_ld(b, false);
+  for (size_t i = 0; i < M; ++i) a[i] *= b[i];
+  fft2_ld(a, true);
+  std::vector<cld> X(n);
+  for (int64_t i = 0; i < n; ++i) X[i] = chirp(i) * a[i] / (long double)M;
+  return X;
+}
+
 // ECP colatitudes and quadrature weights on [-1, 1] (Fejer 1, Fejer 2,
-// Clenshaw-Curtis), by the cosine sums of the respective rules.
+// Clenshaw-Curtis; Sect. 4.4.1).  Each rule's weights are one DFT of the rule's
+// moment sequence (Waldvogel 2006), so they cost O(n log n) instead of O(n^2):
+//  CC, N = nlat - 1, theta_i = i pi / N:
+//    w_i = (c_i / N) Re sum_k A_k e^{2 pi i k i / N}, A_0 = 1,
+//    A_k = -b_k / (4k^2 - 1) for 1 <= k <= N/2 (b_k = 1 at k = N/2, else 2),
+//    c_0 = c_N = 1, else 2 (w_N = w_0);
+//  Fejer 1, N = nlat, theta_i = (i + 1/2) pi / N:
+//    w_i = (2 / N) Re sum_k A_k e^{i pi k / N} e^{2 pi i k i / N}, A_0 = 1,
+//    A_k = -2 / (4k^2 - 1) for 1 <= k <= N/2;
+//  Fejer 2, N = nlat + 1, theta_i = i pi / N, i = 1..N-1:
+//    w_i = (4 sin(theta_i) / N) Im[e^{-i pi i / N} sum_k S_k e^{2 pi i k i / N}],
+//    S_k = 1 / (2k - 1) for 1 <= k <= N/2, since sin((2k-1) theta_i) is the
+//    imaginary part of e^{-i pi i / N} e^{2 pi i k i / N}.
 extern "C" int sht_geom_ecp(int kind, int nlat, int nlon, sht_geom_t *out) {
   if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -220,28 +296,38 @@ extern "C" int sht_geom_ecp(int kind, int nlat, int nlon, sht_geom_t *out) {
   std::vector<double> th(nlat), w(nlat);
   if (kind == SHT_ECP_FEJER1) {
     const int N = nlat;
+    std::vector<cld> A(N, 0);
+    A[0] = 1;
+    for (int k = 1; 2 * k <= N; ++k) {
+      const long double ang = kPiL * k / N;
+      A[k] = cld(cosl(ang), sinl(ang)) * (-2.0L / (4.0L * k * k - 1.0L));
+    }
+    const std::vector<cld> X = dft_pos_ld(A);
     for (int i = 0; i < N; ++i) {
-      long double t = kPiL * (2 * i + 1) / (2 * N), acc = 0.0L;
-      for (int k = 1; 2 * k <= N; ++k) acc += cosl(2 * k * t) / (4.0L * k * k - 1.0L);
-      th[i] = (double)t;
-      w[i] = (double)((1.0L - 2.0L * acc) * 2.0L / N);
+      th[i] = (double)(kPiL * (2 * i + 1) / (2 * N));
+      w[i] = (double)(X[i].real() * 2.0L / N);
     }
   } else if (kind == SHT_ECP_FEJER2) {
     const int N = nlat + 1;
+    std::vector<cld> S(N, 0);
+    for (int k = 1; 2 * k <= N; ++k) S[k] = 1.0L / (2 * k - 1);
+    const std::vector<cld> X = dft_pos_ld(S);
     for (int i = 1; i < N; ++i) {
-      long double t = kPiL * i / N, acc = 0.0L;
-      for (int k = 1; 2 * k <= N; ++k) acc += sinl((2 * k - 1) * t) / (2 * k - 1);
+      const long double t = kPiL * i / N;
+      const cld z = cld(cosl(t), -sinl(t)) * X[i];
       th[i - 1] = (double)t;
-      w[i - 1] = (double)(4.0L * sinl(t) * acc / N);
+      w[i - 1] = (double)(4.0L * sinl(t) * z.imag() / N);
     }
   } else if (kind == SHT_ECP_CC) {
     if (nlat < 2) return fail(SHT_ERR_INVALID_ARG, "Clenshaw-Curtis needs nlat >= 2");
     const int N = nlat - 1;
+    std::vector<cld> A(N, 0);
+    A[0] = 1;
+    for (int k = 1; 2 * k <= N; ++k) A[k] = -((2 * k == N) ? 1.0L : 2.0L) / (4.0L * k * k - 1.0L);
+    const std::vector<cld> X = dft_pos_ld(A);
     for (int i = 0; i <= N; ++i) {
-      long double t = kPiL * i / N, acc = 0.0L;
-      for (int k = 1; 2 * k <= N; ++k) acc += ((2 * k == N) ? 1.0L : 2.0L) * cosl(2 * k * t) / (4.0L * k * k - 1.0L);
-      th[i] = (double)t;
-      w[i] = (double)(((i == 0 || i == N) ? 1.0L : 2.0L) * (1.0L - acc) / N);
+      th[i] = (double)(kPiL * i / N);
+      w[i] = (double)(((i == 0 || i == N) ? 1.0L : 2.0L) * X[i % N].real() / N);
     }
   } else {
     return fail(SHT_ERR_INVALID_ARG, "unknown ECP kind %d", kind);

@@ -213,3 +213,51 @@ def test_polar_cut(spin):
     for bad in ([lmax + 1], [-1]):
         with pytest.raises(sht.ShtError):
             sht.sht_geom_polar_cut(geom, lmax, spin, bad)
+
+
+def _ecp_weights_longdouble(kind, nlat, nodes):
+    """The defining cosine / sine sums of the three ECP rules (Sect. 4.4.1), evaluated
+    term by term in numpy's long double at the given node indices (weights on [-1, 1])."""
+    pi = np.longdouble("3.14159265358979323846264338327950288")
+    out = []
+    for i in nodes:
+        if kind == 0:
+            N = nlat
+            t = pi * (2 * i + 1) / (2 * N)
+            k = np.arange(1, N // 2 + 1, dtype=np.longdouble)
+            out.append(2 / N * (1 - 2 * np.sum(np.cos(2 * k * t) / (4 * k * k - 1))))
+        elif kind == 1:
+            N = nlat + 1
+            t = pi * (i + 1) / N
+            k = np.arange(1, N // 2 + 1, dtype=np.longdouble)
+            out.append(4 * np.sin(t) / N * np.sum(np.sin((2 * k - 1) * t) / (2 * k - 1)))
+        else:
+            N = nlat - 1
+            t = pi * i / N
+            k = np.arange(1, N // 2 + 1, dtype=np.longdouble)
+            b = np.where(2 * k == N, 1, 2)
+            c = 1 if i in (0, N) else 2
+            out.append(c / N * (1 - np.sum(b * np.cos(2 * k * t) / (4 * k * k - 1))))
+    return np.array(out, dtype=np.longdouble)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("nlat", [2, 3, 17, 128, 1001, 4096, 8192])
+def test_ecp_weights_by_fft(kind, nlat):
+    # the product builds the weights as one DFT of each rule's moment sequence
+    # (Waldvogel 2006); against the rule's sum in long double to 1e-14 of the
+    # largest weight (every node up to nlat 1001, a spread sample above), and against
+    # the oracle's direct double sums to their own accuracy (~1e-16 per term, so
+    # up to ~1e-13 of the largest weight at nlat 8192)
+    w = sht.sht_geom_ecp(kind, nlat, 1).rings()["weight"] / (2 * np.pi)
+    nodes = np.arange(nlat) if nlat <= 1001 else np.unique(np.r_[0:8, nlat - 8:nlat, np.linspace(0, nlat - 1, 48).astype(int)])
+    ref = _ecp_weights_longdouble(kind, nlat, nodes)
+    wmax = float(np.max(np.abs(ref)))
+    assert float(np.max(np.abs(w[nodes] - ref))) <= 1e-14 * wmax
+    _, wo = oracle.ecp_nodes(kind, nlat)
+    assert np.max(np.abs(w - wo)) <= 2e-13 * np.max(np.abs(wo))
+    # exact integration of x^k, k below the rule's degree of exactness (nlat - 1 here)
+    x = np.cos(sht.sht_geom_ecp(kind, nlat, 1).rings()["theta"])
+    for k in range(0, min(nlat, 40)):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.sum(w * x ** k) - exact) < 1e-13, (k, np.sum(w * x ** k), exact)
