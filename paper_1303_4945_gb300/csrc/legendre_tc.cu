@@ -71,8 +71,9 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+constexpr int kIssuers = 3;  // threads issuing a K-step's MMAs (lane 0 of warps 0-2), one commit each
 __device__ __forceinline__ void bar_init(uint64_t *bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1));
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(kIssuers));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -143,7 +144,14 @@ struct Shape {
   static constexpr int BTILE = N * kK * 2;                      // bytes of one B digit tile
   static constexpr int A_BYTES = 2 * NL * kLamDigits * kATile;  // two buffers
   static constexpr int B_BYTES = NL * kAlmDigits * BTILE;
-  static constexpr int SMEM = A_BYTES + B_BYTES + 2 * NV * 4;
+  // per degree of a K-step, staged in shared memory one K-step ahead: the two
+  // float4 of its recursion coefficients and one float4 per a_lm table row read
+  static constexpr int NARR = SPIN ? 2 * NJ : NJ;
+  static constexpr int ROW = 2 + NARR;
+  static constexpr int STG = kK * ROW;                 // float4 per K-step
+  static constexpr int PF = (STG + kRows - 1) / kRows;  // of them per thread
+  static constexpr int ST_BYTES = 2 * STG * 16;        // two buffers
+  static constexpr int SMEM = A_BYTES + ST_BYTES + B_BYTES + 2 * NV * 4;
   // dynamic shared memory requested: enough that at most 512 / TCOLS CTAs fit on an
   // SM, so their TMEM allocations never wait for one another
   static constexpr int SMEM_LAUNCH = TCOLS == 128 ? (SMEM > 46 * 1024 ? SMEM : 46 * 1024)
@@ -173,6 +181,13 @@ __device__ __forceinline__ f2 alm_value(const MixArgs &a, int64_t ci, int v) {
   return (v & 1) ? f2{q.z, q.w} : f2{q.x, q.y};
 }
 
+// the double-float a_lm value v from a staged degree row (coefficients, then the tables)
+template <int NJ, bool SPIN>
+__device__ __forceinline__ f2 staged_value(const float4 *row, int v) {
+  const float4 q = SPIN ? row[2 + 2 * (v / 4) + ((v & 2) ? 1 : 0)] : row[2 + v / 2];
+  return (v & 1) ? f2{q.z, q.w} : f2{q.x, q.y};
+}
+
 // Column bounds of one window (degrees lw0..lw1): umax[v] = max |value v| over
 // the window (atomically, as FP32 bit patterns of non-negative numbers).  The
 // caller synchronises before the bounds are read.
@@ -189,18 +204,17 @@ __device__ __forceinline__ void window_bounds(const MixArgs &a, int64_t co, int 
   if ((threadIdx.x & 31) < S::NV) atomicMax(reinterpret_cast<int *>(umax) + v, __float_as_int(mx));
 }
 
-// The B digit tiles of K-step degrees lb..lb+15 (zero past lmax): value v of degree
+// The B digit tiles of a K-step from its staged rows (zero past lmax): value v of degree
 // lb + k split into kAlmDigits digits on its window's grid and written, with the
 // parity sign s = (-1)^(l - l0) where the column needs it, into the rows of the
 // columns that read it (see the column layout in tc_syn_body).  Rows no value
 // writes stay zero from the kernel's start.
 template <int NJ, bool SPIN>
-__device__ __forceinline__ void build_b(const MixArgs &a, int64_t co, int lb, int lmax, const float *umax,
-                                        unsigned char *Bt) {
+__device__ __forceinline__ void build_b(const float4 *stg, const float *umax, unsigned char *Bt) {
   using S = Shape<NJ, SPIN>;
   for (int t = threadIdx.x; t < kK * S::NV; t += kRows) {
-    const int k = t % kK, v = t / kK, l = lb + k;
-    const f2 x = l <= lmax ? alm_value<NJ, SPIN>(a, co + l, v) : f2{0.f, 0.f};
+    const int k = t % kK, v = t / kK;
+    const f2 x = staged_value<NJ, SPIN>(stg + k * S::ROW, v);  // zero past lmax
     const float s0 = pow2_above(umax[v]) * 98304.0f;  // 1.5 * 2^23 * (bound * 2^-7)
     float d[kAlmDigits];
     float r = x.h;
@@ -277,11 +291,36 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   const int64_t co = a.coef_off[mi] - l0;
   const float4 *__restrict__ cf = a.coef32 + 2 * co;
   unsigned char *const Abuf = smem;
-  unsigned char *const Bt = smem + S::A_BYTES;
+  float4 *const stage = reinterpret_cast<float4 *>(smem + S::A_BYTES);
+  unsigned char *const Bt = smem + S::A_BYTES + S::ST_BYTES;
   float *const umax = reinterpret_cast<float *>(Bt + S::B_BYTES);
 
+  // the staged rows of K-step ks: thread t loads entries t, t + 128, ... (zero past lmax)
+  float4 pf[S::PF];
+  auto prefetch = [&](int ks) {
+    const int lb = l0 + ks * tc::kK;
+#pragma unroll
+    for (int i = 0; i < S::PF; ++i) {
+      const int e = tid + i * tc::kRows;
+      pf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < S::STG) {
+        const int k = e / S::ROW, c = e % S::ROW, l = lb + k;
+        if (l <= lmax) pf[i] = c < 2 ? __ldg(cf + 2 * l + c) : __ldg(a.alm32 + (int64_t)(c - 2) * a.ncoef + co + l);
+      }
+    }
+  };
+  auto stage_store = [&](int ks) {
+    float4 *dst = stage + (ks & 1) * S::STG;
+#pragma unroll
+    for (int i = 0; i < S::PF; ++i) {
+      const int e = tid + i * tc::kRows;
+      if (e < S::STG) dst[e] = pf[i];
+    }
+  };
   if (warp == 0) tc::tmem_alloc(&tslot, S::TCOLS);
   if (tid == 0) tc::bar_init(&mbar);
+  prefetch(0);
+  stage_store(0);
   for (int i = tid; i < S::B_BYTES / 16; i += tc::kRows) reinterpret_cast<uint4 *>(Bt)[i] = make_uint4(0, 0, 0, 0);
   if (tid < 2 * S::NV) umax[tid] = 0.f;
   tc::fence_before();
@@ -314,46 +353,55 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
     racc[c] = 0.f;
   }
 
-  // eight degrees lb..lb+7 (lb - l0 even; SETTLED: every lane's values at scale 0,
-  // passed as a literal so that each call inlines its own variant): digits packed per pair of degrees into
-  // pk[set][digit][q / 2], remainders contracted into racc, recursion advanced
-  auto half = [&](int lb, const bool SETTLED, uint32_t (&pk)[NL][tc::kLamDigits][4]) {
+  // accumulation weight of the +s / -s values (see weight() in mixed_common.cuh): 1 at
+  // scale 0, 2^-104 at scale -1, 0 below; scales change only at the rescale checks
+  auto wfac = [](int sc) { return sc == 0 ? 1.f : (sc == -1 ? kScaleFactor32 : 0.f); };
+  float wfp = wfac(scp), wfm = wfac(scm);
+  bool settled = false;  // every lane of the warp at scale 0 (warp-uniform; scales only rise)
+
+  // eight degrees lb..lb+7 (lb - l0 even): digits packed per pair of degrees into
+  // pk[set][digit][q / 2], remainders contracted into racc, recursion advanced.
+  // Every second degree the warp votes: if every lane's values are negligible for
+  // the next two steps (as in the double-float kernels) the digits are zero and
+  // only the recursion runs.
+  auto half = [&](const int lb, const float4 *rows, uint32_t (&pk)[NL][tc::kLamDigits][4]) {
     float dlo[NL][tc::kLamDigits];
+    bool dead = false;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int l = lb + q;
       const bool in = l <= lmax;  // uniform over the CTA
       const bool odd = q & 1;
-      f2 w[NL];
-      w[0] = SETTLED ? lpc : weight(lpc, scp);
-      if (SPIN) w[1] = SETTLED ? lmc : weight(lmc, scm);
-      float rr[NL];
+      if (!odd) dead = !settled && __all_sync(0xffffffffu, negligible(lpc, scp) && (!SPIN || negligible(lmc, scm)));
+      const float4 *row = rows + q * S::ROW;  // this degree's staged coefficients and a_lm
+      if (in && !dead) {
+        f2 w[NL];
+        w[0] = f2{lpc.h * wfp, lpc.l * wfp};
+        if (SPIN) w[1] = f2{lmc.h * wfm, lmc.l * wfm};
+        float rr[NL];
 #pragma unroll
-      for (int t = 0; t < NL; ++t) {
-        if (!in) w[t] = f2{0.f, 0.f};
-        const float d0 = tc::round_to(w[t].h, ls0);
-        float r = __fsub_rn(w[t].h, d0);
-        const float d1 = tc::round_to(r, ls1);
-        r = __fsub_rn(r, d1);
-        const float d2 = tc::round_to(r, ls2);
-        rr[t] = __fadd_rn(__fsub_rn(r, d2), w[t].l);
-        if (!odd) {
-          dlo[t][0] = d0;
-          dlo[t][1] = d1;
-          dlo[t][2] = d2;
-        } else {
-          pk[t][0][q / 2] = tc::pack_bf16(dlo[t][0], d0);
-          pk[t][1][q / 2] = tc::pack_bf16(dlo[t][1], d1);
-          pk[t][2][q / 2] = tc::pack_bf16(dlo[t][2], d2);
+        for (int t = 0; t < NL; ++t) {
+          const float d0 = tc::round_to(w[t].h, ls0);
+          float r = __fsub_rn(w[t].h, d0);
+          const float d1 = tc::round_to(r, ls1);
+          r = __fsub_rn(r, d1);
+          const float d2 = tc::round_to(r, ls2);
+          rr[t] = __fadd_rn(__fsub_rn(r, d2), w[t].l);
+          if (!odd) {
+            dlo[t][0] = d0;
+            dlo[t][1] = d1;
+            dlo[t][2] = d2;
+          } else {
+            pk[t][0][q / 2] = tc::pack_bf16(dlo[t][0], d0);
+            pk[t][1][q / 2] = tc::pack_bf16(dlo[t][1], d1);
+            pk[t][2][q / 2] = tc::pack_bf16(dlo[t][2], d2);
+          }
         }
-      }
-      if (in) {
-        const int64_t ci = co + l;
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
           if (SPIN) {
-            const float4 P = __ldg(a.alm32 + (int64_t)(2 * j) * a.ncoef + ci);
-            const float4 M = __ldg(a.alm32 + (int64_t)(2 * j + 1) * a.ncoef + ci);
+            const float4 P = row[2 + 2 * j];
+            const float4 M = row[3 + 2 * j];
             const float rp = rr[0], rm = rr[1], sp = odd ? -rr[0] : rr[0], sm = odd ? -rr[1] : rr[1];
             racc[8 * j + 0] = __fmaf_rn(rp, P.x, racc[8 * j + 0]);
             racc[8 * j + 1] = __fmaf_rn(rp, P.z, racc[8 * j + 1]);
@@ -364,13 +412,27 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
             racc[8 * j + 6] = __fmaf_rn(sm, P.x, racc[8 * j + 6]);
             racc[8 * j + 7] = __fmaf_rn(sm, P.z, racc[8 * j + 7]);
           } else {
-            const float4 v = __ldg(a.alm32 + (int64_t)j * a.ncoef + ci);
+            const float4 v = row[2 + j];
             const int c = 4 * j + (odd ? 2 : 0);
             racc[c] = __fmaf_rn(rr[0], v.x, racc[c]);
             racc[c + 1] = __fmaf_rn(rr[0], v.z, racc[c + 1]);
           }
         }
-        const Coef32 cc = ld_coef32(cf + 2 * l);
+      } else {  // zero digits (past lmax, or negligible values)
+#pragma unroll
+        for (int t = 0; t < NL; ++t) {
+          if (!odd) {
+            dlo[t][0] = dlo[t][1] = dlo[t][2] = 0.f;
+          } else {
+            pk[t][0][q / 2] = tc::pack_bf16(dlo[t][0], 0.f);
+            pk[t][1][q / 2] = tc::pack_bf16(dlo[t][1], 0.f);
+            pk[t][2][q / 2] = tc::pack_bf16(dlo[t][2], 0.f);
+          }
+        }
+      }
+      if (in) {
+        const float4 u = row[0], v = row[1];
+        const Coef32 cc = {{u.x, u.y}, {u.z, u.w}, {v.x, v.y}};
         const f2 t = mul(cc.a, x);
         const f2 nc = neg(cc.c);
         if (SPIN) {
@@ -387,7 +449,7 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
         }
       }
     }
-    if (!SETTLED) {  // enhanced exponent: rescale every eight degrees (see mixed_common.cuh)
+    if (!settled) {  // enhanced exponent: rescale every eight degrees (see mixed_common.cuh)
       if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
         lpc = {lpc.h * kScaleFactor32, lpc.l * kScaleFactor32};
         lpp = {lpp.h * kScaleFactor32, lpp.l * kScaleFactor32};
@@ -398,32 +460,39 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
         lmp = {lmp.h * kScaleFactor32, lmp.l * kScaleFactor32};
         ++scm;
       }
+      wfp = wfac(scp);
+      wfm = wfac(scm);
+      settled = __all_sync(0xffffffffu, scp == 0 && scm == 0);
     }
   };
 
-  // the MMAs of one K-step (thread 0): every digit product Li Bj with i + j <= 5 into
-  // level i + j, the first product of a level in a window overwriting it
-  auto issue = [&](int ks) {
+  // the MMAs of one K-step, issued by lane 0 of warps 0-2: issuer w takes the levels
+  // k = w, w + 3 (every digit product Li Bj with i + j = k; the first product of a
+  // level in a window overwrites it) and commits them to the barrier
+  // descriptors of the first A and B tiles; a tile's descriptor adds its byte offset / 16
+  const uint64_t adesc0 = tc::mat_desc(tc::smem_u32(Abuf), 128, 256);
+  const uint64_t bdesc0 = tc::mat_desc(tc::smem_u32(Bt), 128, 256);
+  auto issue = [&](int ks, int w) {
     tc::fence_after();
     constexpr uint32_t idesc = tc::instr_desc(tc::kRows, N);
-    const uint32_t abase = tc::smem_u32(Abuf + (ks & 1) * (NL * tc::kLamDigits * tc::kATile));
-    const uint32_t bbase = tc::smem_u32(Bt);
+    const uint64_t abuf = adesc0 + (uint64_t)(((ks & 1) * (NL * tc::kLamDigits * tc::kATile)) >> 4);
     const bool first = (ks % tc::kWin) == 0;
-    uint32_t inited = 0;
 #pragma unroll
-    for (int t = 0; t < NL; ++t)
+    for (int k = 0; k < tc::kLevels; ++k) {
+      if (k % tc::kIssuers != w) continue;
+      bool init = first;
 #pragma unroll
-      for (int i = 0; i < tc::kLamDigits; ++i)
+      for (int t = 0; t < NL; ++t)
 #pragma unroll
-        for (int j = 0; j < tc::kAlmDigits; ++j) {
-          const int k = i + j;
-          if (k >= tc::kLevels) continue;
-          const uint64_t ad = tc::mat_desc(abase + (t * tc::kLamDigits + i) * tc::kATile, 128, 256);
-          const uint64_t bd = tc::mat_desc(bbase + (t * tc::kAlmDigits + j) * S::BTILE, 128, 256);
-          const uint32_t accum = (!first || ((inited >> k) & 1u)) ? 1u : 0u;
-          inited |= 1u << k;
-          tc::mma_bf16(tbase + k * N, ad, bd, idesc, accum);
+        for (int i = 0; i < tc::kLamDigits; ++i) {
+          const int j = k - i;
+          if (j < 0 || j >= tc::kAlmDigits) continue;
+          const uint64_t ad = abuf + (uint64_t)(((t * tc::kLamDigits + i) * tc::kATile) >> 4);
+          const uint64_t bd = bdesc0 + (uint64_t)(((t * tc::kAlmDigits + j) * S::BTILE) >> 4);
+          tc::mma_bf16(tbase + k * N, ad, bd, idesc, init ? 0u : 1u);
+          init = false;
         }
+    }
     tc::mma_commit(&mbar);
   };
 
@@ -450,7 +519,7 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   };
 
   int ncommit = 0, nwaited = 0;
-  bool ok = true, settled = false;
+  bool ok = true;
   for (int ks = 0; ks < nks; ++ks) {
     const int lb = l0 + ks * tc::kK;
     if (ks % tc::kWin == 0) {  // column bounds of this window's a_lm
@@ -461,14 +530,12 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
       __syncthreads();
     }
     unsigned char *Aw = Abuf + (ks & 1) * (NL * tc::kLamDigits * tc::kATile);
+    const float4 *rows = stage + (ks & 1) * S::STG;
+    if (ks + 1 < nks) prefetch(ks + 1);  // its latency hides behind this K-step's work
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       uint32_t pk[NL][tc::kLamDigits][4];
-      if (settled)
-        half(lb + 8 * h, true, pk);
-      else
-        half(lb + 8 * h, false, pk);
-      settled = settled || __all_sync(0xffffffffu, scp == 0 && scm == 0);
+      half(lb + 8 * h, rows + 8 * h * S::ROW, pk);
 #pragma unroll
       for (int t = 0; t < NL; ++t)
 #pragma unroll
@@ -482,13 +549,14 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
       fail = !tc::bar_wait(&mbar, (uint32_t)(ncommit - 1) & 1u);
       nwaited = ncommit;
     }
-    if (!fail) tc::build_b<NJ, SPIN>(a, co, lb, lmax, umax + ((ks / tc::kWin) & 1) * S::NV, Bt);
+    if (!fail) tc::build_b<NJ, SPIN>(rows, umax + ((ks / tc::kWin) & 1) * S::NV, Bt);
+    if (ks + 1 < nks) stage_store(ks + 1);  // its buffer's last readers finished before the previous barrier
     tc::fence_async_smem();
     if (__syncthreads_or(fail)) {
       ok = false;
       break;
     }
-    if (tid == 0) issue(ks);
+    if ((tid & 31) == 0 && warp < tc::kIssuers) issue(ks, warp);
     ++ncommit;
     if (ks % tc::kWin == tc::kWin - 1 || ks == nks - 1) {
       fail = !tc::bar_wait(&mbar, (uint32_t)(ncommit - 1) & 1u);
