@@ -462,6 +462,26 @@ def roofline_for(stages, plan, spin, precision, peaks, steps, ncomp=1):
     return out
 
 
+def stage_rooflines(stages, plan, spin, precision, peaks, steps, ncomp=1):
+    """Both Legendre stages in the method's work (flops_per_triple x triples per
+    launch / the stage's CUDA-event time) against the FMA-flop peak of the pipe the
+    form runs on (measured on this GPU when available)."""
+    measured = peaks.get("pipes_measured")
+    clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    if precision == "fp64":
+        peak = measured["fp64_fma_tflops"] if measured else SMS * 4 * clock / 1e12
+    else:
+        peak = 2 * measured["fp32_fma_tops"] if measured else SMS * 256 * clock / 1e12
+    flops = plan.triples(0) * flops_per_triple(spin, ncomp)
+    out = {}
+    for st in ("legendre_synthesis", "legendre_analysis"):
+        ms = stages[st][0] / max(steps, 1)
+        if ms > 0:
+            out[st] = {"ms_per_launch": ms, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
+                       "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_tflops": peak}
+    return out
+
+
 def _line(metric, ms, args, world, config, dtype, extra):
     line = {"metric": metric, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -681,6 +701,66 @@ def run_healpix_workload(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_maps8_workload(args, world, rank, local):
+    """Eight scalar maps through one plan (ncomp 8): synthesis + analysis at lmax 4095 on
+    Gauss-Legendre 4096 x 8191, a_lm with C_l = 1/(l+1)^2 from rng(6); the FP64 form,
+    the mixed form with the double-float contraction, and the mixed form with the
+    synthesis contraction on the tensor cores (the multi-map case where the product
+    has 32 columns)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1303_4945_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1303_4945_gb300 import inputs, sht
+
+    peaks = _peaks()
+    peaks["pipes_measured"] = sht.sht_measure_pipe_peaks(local)
+    stream = torch.cuda.current_stream()
+    lmax, ncomp = 4095, 8
+    geom = sht.sht_geom_gauss(lmax + 1, 2 * lmax + 1)
+    lay = sht.sht_alm_create(lmax, lmax)
+    rng = np.random.default_rng(6)
+    alm_d = [torch.from_numpy(inputs.gaussian_alm(rng, lmax, lmax, cl=inputs.cl_inverse_square)).cuda()
+             for _ in range(ncomp)]
+    maps_d = [torch.empty(geom.npix, dtype=torch.float64, device="cuda") for _ in range(ncomp)]
+    out_d = [torch.empty_like(a) for a in alm_d]
+    forms, outs = {}, {}
+    sampler = ClockSampler(local)
+    clocks = None
+    for name, prec, tc in (("fp64", sht.SHT_FP64, False), ("mixed", sht.SHT_MIXED, False),
+                           ("mixed_tc", sht.SHT_MIXED, True)):
+        plan = sht.sht_plan_create(geom, lay, 0, ncomp, prec)
+        if tc:
+            plan.tensor_cores = True
+        plan.autotune(stream)
+        if name == "mixed_tc":
+            sampler.start()
+        ms, stages = time_form(sht, torch, plan, alm_d, maps_d, out_d, args.steps, args.warmup, world, stream)
+        if name == "mixed_tc":
+            clocks = sampler.stop()
+        kind = "fp64" if prec == sht.SHT_FP64 else "mixed"
+        forms[name] = {"ms_per_step": ms, "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+                       "stage_rooflines": stage_rooflines(stages, plan, 0, kind, peaks, args.steps, ncomp),
+                       "triples": plan.triples(0), "device_status": plan.device_status()}
+        outs[name] = ([m.cpu().numpy() for m in maps_d], [a.cpu().numpy() for a in out_d])
+        del plan
+        torch.cuda.empty_cache()
+    for name in ("mixed", "mixed_tc"):
+        forms[name]["vs_fp64_rel_l2"] = {
+            "maps": max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(outs[name][0], outs["fp64"][0])),
+            "alm": max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(outs[name][1], outs["fp64"][1]))}
+    config = {"workload": "8 scalar maps in one plan (ncomp 8): synthesis + analysis, Gauss-Legendre nlat=4096 "
+                          "nlon=8191, lmax=mmax=4095, a_lm C_l=1/(l+1)^2 rng(6)", "parallelism": "replicas"}
+    line = _line("ms per synth+analysis of 8 maps at lmax 4095 (GL 4096x8191)", forms["mixed_tc"]["ms_per_step"],
+                 args, world, config, "f32x2", {"form": "mixed_tc", "forms": forms, "clocks": clocks,
+                                                "gpu_launches": 6 * args.steps})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_variants_workload(args, world, rank, local):
     """The transforms beyond the headline pair, each in both forms: derivative
     synthesis at lmax 4095 (GL 4096 x 8191, Sect. 4.3), a spin-2 pair on the
@@ -770,11 +850,12 @@ def main():
     ap.add_argument("--lmax", type=int, default=4095, help="smaller sizes for profiling captures")
     ap.add_argument("--nlat", type=int, default=None,
                     help="fewer rings of the same length for profiling captures (default lmax + 1)")
-    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad", "healpix", "variants"],
+    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad", "healpix", "variants", "maps8"],
                     help="spin2: the headline (spin-2 lmax 4095 pair); batch: 64 uneven scalar problems + "
                          "8 maps at lmax 2047 in one batch; grad: loss + gradient at lmax 8191; healpix: "
                          "Jacobi-refined analysis on HEALPix Nside 512, lmax 1535; variants: derivative "
-                         "synthesis, grid variants, real harmonics, spin 37")
+                         "synthesis, grid variants, real harmonics, spin 37; maps8: 8 scalar maps at lmax 4095 "
+                         "with the tensor-core synthesis")
     args = ap.parse_args()
     set_workload(args.lmax, args.nlat)
     world, rank, local = dist_setup()
@@ -783,7 +864,7 @@ def main():
         return
     if args.workload != "spin2":
         runners = {"batch": run_batch_workload, "grad": run_grad_workload, "healpix": run_healpix_workload,
-                   "variants": run_variants_workload}
+                   "variants": run_variants_workload, "maps8": run_maps8_workload}
         runners[args.workload](args, world, rank, local)
         return
     import numpy as np
@@ -799,10 +880,12 @@ def main():
     peaks["pipes_measured"] = sht.sht_measure_pipe_peaks(local)
     geom = sht.sht_geom_gauss(NLAT, NLON)
     lay = sht.sht_alm_create(LMAX, LMAX)
-    forms = {"fp64": sht.SHT_FP64}
+    # form name -> (precision, synthesis contraction on the tensor cores)
+    forms = {"fp64": (sht.SHT_FP64, False)}
     try:
         sht.sht_plan_create(sht.sht_geom_gauss(8, 15), sht.sht_alm_create(7, 7), 2, 1, sht.SHT_MIXED)
-        forms["mixed"] = sht.SHT_MIXED
+        forms["mixed"] = (sht.SHT_MIXED, False)
+        forms["mixed_tc"] = (sht.SHT_MIXED, True)
     except sht.ShtError:
         pass
     alm_h = inputs.spin2_eb(SEED, LMAX)
@@ -815,20 +898,27 @@ def main():
     outputs = {}
     sampler = ClockSampler(local)
     data_bytes = sum(a.nbytes for a in alm_h) + 8 * 2 * geom.npix  # a_lm and maps of one pair
-    for name, prec in forms.items():
+    clocks = None
+    for name, (prec, tc) in forms.items():
         t0 = time.perf_counter()
         plan = sht.sht_plan_create(geom, lay, SPIN, 1, prec)
+        if prec == sht.SHT_MIXED:
+            plan.tensor_cores = tc
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         tune = plan.autotune(stream)  # analysis tiling, chosen by timing (outside the timed region)
         t2 = time.perf_counter()
-        if name == list(forms)[-1]:
+        if name == "mixed" or (name == "fp64" and "mixed" not in forms):
             sampler.start()
         ms, stages = time_form(sht, torch, plan, alm_d, maps_d, out_d, args.steps, args.warmup, world, stream)
-        if name == list(forms)[-1]:
+        if name == "mixed" or (name == "fp64" and "mixed" not in forms):
             clocks = sampler.stop()
+        form_kind = "fp64" if prec == sht.SHT_FP64 else "mixed"
         results[name] = {"ms_per_step": ms, "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-                         "roofline": roofline_for(stages, plan, SPIN, name, peaks, args.steps),
+                         "roofline": roofline_for(stages, plan, SPIN, form_kind, peaks, args.steps),
+                         "stage_rooflines": stage_rooflines(stages, plan, SPIN, form_kind, peaks, args.steps),
+                         "synthesis_contraction": "tensor cores (tcgen05, exact bf16 digit split)" if tc
+                         else ("FP64" if prec == sht.SHT_FP64 else "double-float FP32"),
                          "triples": plan.triples(0), "workspace_bytes": plan.workspace(),
                          "setup": {"plan_create_ms": 1e3 * (t1 - t0), "autotune_ms": 1e3 * (t2 - t1),
                                    "workspace_over_data": plan.workspace() / data_bytes},
@@ -838,7 +928,7 @@ def main():
         outputs[name] = {"maps": [m.cpu().numpy() for m in maps_d], "alm": [a.cpu().numpy() for a in out_d]}
         if world == 1:
             results[name]["paper_rule"] = paper_rule_times(sht, torch, plan, alm_d, maps_d, out_d, stream)
-        if prec == sht.SHT_MIXED:  # the same plan with the FP64 ring-FFT engine (not the headline)
+        if name == "mixed":  # the same plan with the FP64 ring-FFT engine (not the headline)
             plan.fft_precision = sht.SHT_FP64
             ms64, st64 = time_form(sht, torch, plan, alm_d, maps_d, out_d, args.steps, args.warmup, world, stream)
             results[name]["with_fp64_fft"] = {
@@ -846,22 +936,25 @@ def main():
                 "fft_ms_per_step": {k: st64[k][0] / args.steps for k in ("fft_synthesis", "fft_analysis")}}
         del plan
     head = "mixed" if "mixed" in forms else "fp64"
-    # mixed vs FP64 on the full output
-    if "mixed" in forms:
-        def rl2(a, b):
-            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
-        results["mixed"]["vs_fp64_rel_l2"] = {
-            "Q": rl2(outputs["mixed"]["maps"][0], outputs["fp64"]["maps"][0]),
-            "U": rl2(outputs["mixed"]["maps"][1], outputs["fp64"]["maps"][1]),
-            "E": rl2(outputs["mixed"]["alm"][0], outputs["fp64"]["alm"][0]),
-            "B": rl2(outputs["mixed"]["alm"][1], outputs["fp64"]["alm"][1])}
+    # mixed forms vs FP64 on the full output
+    def rl2(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    for name in ("mixed", "mixed_tc"):
+        if name in forms:
+            results[name]["vs_fp64_rel_l2"] = {
+                "Q": rl2(outputs[name]["maps"][0], outputs["fp64"]["maps"][0]),
+                "U": rl2(outputs[name]["maps"][1], outputs["fp64"]["maps"][1]),
+                "E": rl2(outputs[name]["alm"][0], outputs["fp64"]["alm"][0]),
+                "B": rl2(outputs[name]["alm"][1], outputs["fp64"]["alm"][1])}
 
     # end to end through the public API from pinned host memory: every step copies
     # its a_lm in and its result out.  As a serving loop would, the copies run on
     # streams of their own with double-buffered device arrays, overlapping the
     # neighbouring steps' transforms; the timed region starts before the first
     # step's upload and ends after the last step's download.
-    plan = sht.sht_plan_create(geom, lay, SPIN, 1, forms[head])
+    plan = sht.sht_plan_create(geom, lay, SPIN, 1, forms[head][0])
+    if forms[head][0] == sht.SHT_MIXED:
+        plan.tensor_cores = forms[head][1]
     plan.set_tiling(results[head]["tiling"]["analysis_pairs_per_thread"])
     host_in = [torch.from_numpy(a).pin_memory() for a in alm_h]
     host_out = [[torch.empty(a.shape, dtype=torch.complex128).pin_memory() for a in alm_h] for _ in range(2)]

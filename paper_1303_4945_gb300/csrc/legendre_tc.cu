@@ -364,17 +364,18 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   // Every second degree the warp votes: if every lane's values are negligible for
   // the next two steps (as in the double-float kernels) the digits are zero and
   // only the recursion runs.
-  auto half = [&](const int lb, const float4 *rows, uint32_t (&pk)[NL][tc::kLamDigits][4]) {
+  auto half = [&](const float4 *rows, uint32_t (&pk)[NL][tc::kLamDigits][4]) {
     float dlo[NL][tc::kLamDigits];
     bool dead = false;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int l = lb + q;
-      const bool in = l <= lmax;  // uniform over the CTA
+      // past lmax the staged rows are zero: the recursion runs on zero coefficients
+      // (its values become zero one degree later) and meets zero a_lm, so those
+      // degrees add nothing and need no test
       const bool odd = q & 1;
       if (!odd) dead = !settled && __all_sync(0xffffffffu, negligible(lpc, scp) && (!SPIN || negligible(lmc, scm)));
       const float4 *row = rows + q * S::ROW;  // this degree's staged coefficients and a_lm
-      if (in && !dead) {
+      if (!dead) {
         f2 w[NL];
         w[0] = f2{lpc.h * wfp, lpc.l * wfp};
         if (SPIN) w[1] = f2{lmc.h * wfm, lmc.l * wfm};
@@ -418,7 +419,7 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
             racc[c + 1] = __fmaf_rn(rr[0], v.z, racc[c + 1]);
           }
         }
-      } else {  // zero digits (past lmax, or negligible values)
+      } else {  // zero digits (negligible values)
 #pragma unroll
         for (int t = 0; t < NL; ++t) {
           if (!odd) {
@@ -430,7 +431,7 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
           }
         }
       }
-      if (in) {
+      {
         const float4 u = row[0], v = row[1];
         const Coef32 cc = {{u.x, u.y}, {u.z, u.w}, {v.x, v.y}};
         const f2 t = mul(cc.a, x);
@@ -535,7 +536,7 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       uint32_t pk[NL][tc::kLamDigits][4];
-      half(lb + 8 * h, rows + 8 * h * S::ROW, pk);
+      half(rows + 8 * h * S::ROW, pk);
 #pragma unroll
       for (int t = 0; t < NL; ++t)
 #pragma unroll
@@ -653,9 +654,10 @@ bool tc_supported(int spin, int njobs_pad) {
 }
 
 float tc_lambda_bound(int lmax) {
-  // |sLambda_lm| <= sqrt((2l + 1) / (4 pi)) (|d^l| <= 1); the next power of two
-  // above it, with room for the recursion's rounding
-  const double b = sqrt((2.0 * lmax + 1.0) / (4.0 * M_PI)) * (1.0 + 1e-6);
+  // |sLambda_lm| <= sqrt((2l + 1) / (4 pi)) (|d^l| <= 1) up to l = lmax + 1 (the
+  // kernel computes one value past lmax); the next power of two above it, with
+  // room for the recursion's rounding
+  const double b = sqrt((2.0 * lmax + 3.0) / (4.0 * M_PI)) * (1.0 + 1e-6);
   return (float)exp2(ceil(log2(b)));
 }
 
