@@ -497,8 +497,8 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
     tc::mma_commit(&mbar);
   };
 
-  // after a window: the six levels of this thread's lane plus the remainder sums,
-  // added to the double-float column sums
+  // after a window: the six levels of this thread's lane, added to the double-float
+  // column sums (the remainder sums are folded in after every K-step)
   auto readout = [&]() {
     const uint32_t lane = tbase + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
@@ -512,8 +512,6 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
         f2 t = {dv[0][c], 0.f};
 #pragma unroll
         for (int k = 1; k < tc::kLevels; ++k) t = f2_add_lazy(t, f2{dv[k][c], 0.f});
-        t = f2_add_lazy(t, f2{racc[c0 + c], 0.f});
-        racc[c0 + c] = 0.f;
         acc[c0 + c] = f2_add(acc[c0 + c], t);
       }
     }
@@ -552,6 +550,13 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
     }
     if (!fail) tc::build_b<NJ, SPIN>(rows, umax + ((ks / tc::kWin) & 1) * S::NV, Bt);
     if (ks + 1 < nks) stage_store(ks + 1);  // its buffer's last readers finished before the previous barrier
+    // the K-step's FP32 remainder sums (16 terms each) into the double-float column
+    // sums: summed in FP32 over a whole window their rounding reached ~1e-11
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+      acc[c] = f2_add_lazy(acc[c], f2{racc[c], 0.f});
+      racc[c] = 0.f;
+    }
     tc::fence_async_smem();
     if (__syncthreads_or(fail)) {
       ok = false;
@@ -631,8 +636,20 @@ __global__ void __launch_bounds__(tc::kRows, (tc::Shape<NJ, SPIN>::TCOLS == 128 
   tc_syn_body<NJ, SPIN>(ta, ta.m.syn_items[blockIdx.x], tc_smem);
 }
 
+// batches: item (mi, first pair, -, record); the record holds the plan's arguments
+template <int NJ, bool SPIN>
+__global__ void __launch_bounds__(tc::kRows, (tc::Shape<NJ, SPIN>::TCOLS == 128 ? 4 : 2))
+    tc_syn_batch(const TcArgs *__restrict__ args, const int4 *__restrict__ items) {
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  const int4 it = items[blockIdx.x];
+  tc_syn_body<NJ, SPIN>(args[it.w], make_int2(it.x, it.y), tc_smem);
+}
+
 template <int NJ, bool SPIN>
 static cudaError_t tc_set_smem() {
+  cudaError_t e = cudaFuncSetAttribute(tc_syn_batch<NJ, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tc::Shape<NJ, SPIN>::SMEM_LAUNCH);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(tc_syn<NJ, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               tc::Shape<NJ, SPIN>::SMEM_LAUNCH);
 }
@@ -659,6 +676,38 @@ float tc_lambda_bound(int lmax) {
   // room for the recursion's rounding
   const double b = sqrt((2.0 * lmax + 3.0) / (4.0 * M_PI)) * (1.0 + 1e-6);
   return (float)exp2(ceil(log2(b)));
+}
+
+size_t tc_args_size() { return sizeof(TcArgs); }
+
+void leg_tc_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out) {
+  TcArgs ta;
+  leg_mixed_fill_args(P, polar, ptr_off, &ta.m);
+  ta.lam_bound = P->tc_lam_bound;
+  ta.err = P->d_err;
+  memcpy(out, &ta, sizeof(ta));
+}
+
+cudaError_t launch_leg_tc_batch(int spin, int nj, const void *targs, const int4 *items, int n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const TcArgs *a = static_cast<const TcArgs *>(targs);
+  if (spin == 0) {
+    switch (nj) {
+      case 1: tc_syn_batch<1, false><<<n, tc::kRows, tc::Shape<1, false>::SMEM_LAUNCH, st>>>(a, items); break;
+      case 2: tc_syn_batch<2, false><<<n, tc::kRows, tc::Shape<2, false>::SMEM_LAUNCH, st>>>(a, items); break;
+      case 4: tc_syn_batch<4, false><<<n, tc::kRows, tc::Shape<4, false>::SMEM_LAUNCH, st>>>(a, items); break;
+      case 8: tc_syn_batch<8, false><<<n, tc::kRows, tc::Shape<8, false>::SMEM_LAUNCH, st>>>(a, items); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (nj) {
+      case 1: tc_syn_batch<1, true><<<n, tc::kRows, tc::Shape<1, true>::SMEM_LAUNCH, st>>>(a, items); break;
+      case 2: tc_syn_batch<2, true><<<n, tc::kRows, tc::Shape<2, true>::SMEM_LAUNCH, st>>>(a, items); break;
+      case 4: tc_syn_batch<4, true><<<n, tc::kRows, tc::Shape<4, true>::SMEM_LAUNCH, st>>>(a, items); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_leg_tc_syn(const sht_plan_s *P, const void *mixargs, int n, cudaStream_t st) {

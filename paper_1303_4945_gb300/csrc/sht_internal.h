@@ -254,6 +254,10 @@ cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int po
 // record (MixArgs) with its synthesis work list set; n work items
 cudaError_t launch_leg_tc_syn(const sht_plan_s *P, const void *mixargs, int n, cudaStream_t st);
 cudaError_t tc_prepare_device();
+// batches: one TcArgs record per plan of a tensor-core group
+size_t tc_args_size();
+void leg_tc_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
+cudaError_t launch_leg_tc_batch(int spin, int nj, const void *targs, const int4 *items, int n, cudaStream_t st);
 bool tc_supported(int spin, int njobs_pad);
 float tc_lambda_bound(int lmax);
 // ring FFTs

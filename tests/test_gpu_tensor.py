@@ -179,7 +179,11 @@ def test_tensor_setting_errors(sht):
     with pytest.raises(sht.ShtError) as e:
         wide.tensor_cores = True
     assert e.value.code == sht.SHT_ERR_UNSUPPORTED
+    # the default: the tensor cores for every supported shape but a single spin-0 map
     ok = sht.sht_plan_create(geom, lay, 2, 1, sht.SHT_MIXED)
-    assert not ok.tensor_cores
-    ok.tensor_cores = True
-    assert ok.tensor_cores and ok.device_status() == 0
+    assert ok.tensor_cores
+    assert not sht.sht_plan_create(geom, lay, 0, 1, sht.SHT_MIXED).tensor_cores
+    assert sht.sht_plan_create(geom, lay, 0, 2, sht.SHT_MIXED).tensor_cores
+    assert not sht.sht_plan_create(geom, lay, 0, 16, sht.SHT_MIXED).tensor_cores
+    ok.tensor_cores = False
+    assert not ok.tensor_cores and ok.device_status() == 0
