@@ -154,9 +154,9 @@ int build(sht_batch_s *B) {
         const sht_plan_s *P = B->plans[k];
         if (mixed)
           leg_mixed_fill_args(P, polar, B->ptr_off[k], args.data() + i * rec);
-        if (g.tc) leg_tc_fill_args(P, polar, B->ptr_off[k], targs.data() + i * tc_args_size());
         else
           leg_fp64_fill_args(P, polar, B->ptr_off[k], args.data() + i * rec, lo);
+        if (g.tc) leg_tc_fill_args(P, polar, B->ptr_off[k], targs.data() + i * tc_args_size());
         for (auto &it : (lo ? P->syn_list_lo : P->syn_list)[polar])
           syn.push_back({it.first, make_int4(it.second.x, it.second.y, 0, (int)i)});
         for (auto &it : (lo ? P->ana_list_lo : P->ana_list)[polar])
