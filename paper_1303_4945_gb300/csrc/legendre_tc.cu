@@ -497,8 +497,8 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
     tc::mma_commit(&mbar);
   };
 
-  // after a window: the six levels of this thread's lane, added to the double-float
-  // column sums (the remainder sums are folded in after every K-step)
+  // after a window: the six levels of this thread's lane plus the remainder sums,
+  // added to the double-float column sums
   auto readout = [&]() {
     const uint32_t lane = tbase + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
@@ -512,6 +512,8 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
         f2 t = {dv[0][c], 0.f};
 #pragma unroll
         for (int k = 1; k < tc::kLevels; ++k) t = f2_add_lazy(t, f2{dv[k][c], 0.f});
+        t = f2_add_lazy(t, f2{racc[c0 + c], 0.f});
+        racc[c0 + c] = 0.f;
         acc[c0 + c] = f2_add(acc[c0 + c], t);
       }
     }
@@ -550,13 +552,6 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
     }
     if (!fail) tc::build_b<NJ, SPIN>(rows, umax + ((ks / tc::kWin) & 1) * S::NV, Bt);
     if (ks + 1 < nks) stage_store(ks + 1);  // its buffer's last readers finished before the previous barrier
-    // the K-step's FP32 remainder sums (16 terms each) into the double-float column
-    // sums: summed in FP32 over a whole window their rounding reached ~1e-11
-#pragma unroll
-    for (int c = 0; c < NCOL; ++c) {
-      acc[c] = f2_add_lazy(acc[c], f2{racc[c], 0.f});
-      racc[c] = 0.f;
-    }
     tc::fence_async_smem();
     if (__syncthreads_or(fail)) {
       ok = false;
