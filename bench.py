@@ -761,6 +761,53 @@ def run_maps8_workload(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_decomposed(args, world, rank, local):
+    """The headline pair as ONE transform distributed over the N ranks (Sect. 4.2):
+    round-robin m and ring pairs per rank, the Legendre stage and ring FFTs through
+    sht_execute_legendre / sht_execute_rings, one all-to-all of the phase array per
+    direction (NCCL between GPUs; nothing to exchange at N = 1).  value = ms per
+    synthesis + analysis of the whole problem (strong scaling)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1303_4945_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1303_4945_gb300 import distributed as D
+    from paper_1303_4945_gb300 import inputs, sht
+
+    stream = torch.cuda.current_stream()
+    geom = sht.sht_geom_gauss(NLAT, NLON)
+    r = geom.rings()
+    part = D.Partition.round_robin(LMAX, r["theta"], world)
+    stages = D.LibraryStages(sht, geom, LMAX, LMAX, SPIN, 1, sht.SHT_MIXED, part, rank, stream)
+    alm = inputs.spin2_eb(SEED, LMAX)
+    alm_loc = [torch.from_numpy(D.alm_pack(a, LMAX, LMAX, part.m[rank])).cuda() for a in alm]
+
+    def exchange(send, send_splits, recv_splits):
+        return D.torch_exchange(send, send_splits, recv_splits) if world > 1 else send
+
+    def step():
+        maps = D.synthesis(part, rank, stages, exchange, alm_loc)
+        return D.analysis(part, rank, stages, exchange, maps)
+
+    ms = _events_ms(torch, stream, step, args.steps, args.warmup, world)
+    back = step()
+    torch.cuda.synchronize()
+    err = max(float(np.linalg.norm(b.cpu().numpy() - D.alm_pack(a, LMAX, LMAX, part.m[rank]))
+                    / np.linalg.norm(D.alm_pack(a, LMAX, LMAX, part.m[rank]))) for a, b in zip(alm, back))
+    err = max_over_ranks(err, world)
+    config = dict(CONFIG, parallelism=f"m/ring decomposition over {world} GPU(s), one all-to-all per direction")
+    line = _line(METRIC + " [distributed decomposition]", ms, args, world, config, "f32x2",
+                 {"form": "mixed", "scaling": "strong", "round_trip_rel_l2": err,
+                  "phase_array_bytes_exchanged_per_pair": 2 * 16 * 2 * (LMAX + 1) * NLAT * (world - 1) / max(world, 1),
+                  "gpu_launches": None})
+    line["value"] = ms  # the whole problem's time: strong scaling
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_variants_workload(args, world, rank, local):
     """The transforms beyond the headline pair, each in both forms: derivative
     synthesis at lmax 4095 (GL 4096 x 8191, Sect. 4.3), a spin-2 pair on the
@@ -850,6 +897,9 @@ def main():
     ap.add_argument("--lmax", type=int, default=4095, help="smaller sizes for profiling captures")
     ap.add_argument("--nlat", type=int, default=None,
                     help="fewer rings of the same length for profiling captures (default lmax + 1)")
+    ap.add_argument("--decomposed", action="store_true",
+                    help="spin2 workload as one transform distributed over the ranks (Sect. 4.2 m / ring "
+                         "decomposition, NCCL all-to-all) instead of independent replicas")
     ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad", "healpix", "variants", "maps8"],
                     help="spin2: the headline (spin-2 lmax 4095 pair); batch: 64 uneven scalar problems + "
                          "8 maps at lmax 2047 in one batch; grad: loss + gradient at lmax 8191; healpix: "
@@ -861,6 +911,9 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.decomposed:
+        run_decomposed(args, world, rank, local)
         return
     if args.workload != "spin2":
         runners = {"batch": run_batch_workload, "grad": run_grad_workload, "healpix": run_healpix_workload,

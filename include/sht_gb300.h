@@ -365,6 +365,41 @@ SHT_API int sht_fft_plan_info(int n, int *kind, int *len, int *nrad, int *radice
 SHT_API int sht_geom_polar_cut(sht_geom_t geom, int lmax, int spin, int nm, const int *mval, int *first_pair,
                                double *pair_theta, int64_t *triples);
 
+/* ---- the two stages of a transform (distributed decomposition, Sect. 4.2) --------
+ * Sect. 4.2 (Figs. 3 and 4) distributes a transform over tasks: each task runs
+ * the Legendre stage for its own m values over all rings, the phase array is
+ * rearranged among the tasks so that each holds every m for its own rings, and
+ * each task runs the ring FFTs of its rings; an analysis runs the steps
+ * backwards.  These two calls are the stages of a plan's transform, with the
+ * phase array in caller-owned DEVICE memory in a per-ring layout:
+ *   phase[(c * nm + i) * nrings + y]  (complex, interleaved re, im doubles)
+ * for map c < nmaps (the maps of sht_execute: ncomp, or 2 ncomp for spin),
+ * m = the plan's i-th listed m (sht_alm_create's mval, default 0..mmax), ring y
+ * of the plan's geometry.  For a synthesis F holds the ring's Fourier
+ * coefficients of Eq. syn2, map_c(y, x) = sum over m = -mmax..mmax of
+ * F_{c,m,y} e^{i m (phi0_y + 2 pi x / Nphi_y)} with F_{c,-m} = conj(F_{c,m}) (real
+ * maps); for an analysis G_{c,m,y} of Eq. ana2 (ring weights applied for
+ * SHT_ANALYSIS, not for SHT_ADJOINT_SYNTHESIS).  A distributed transform uses
+ * one plan per task for its m values (a listed-m a_lm layout, the whole
+ * geometry) and one for its rings (sht_geom_subset, every m).
+ *
+ * sht_execute_legendre: SHT_SYNTHESIS / SHT_ADJOINT_ANALYSIS read alm[] and
+ * write phase (entries the polar optimisation of Sect. 3.3 skips are written as
+ * zero; flags SHT_NO_POLAR_OPT, SHT_REAL_HARMONICS); SHT_ANALYSIS /
+ * SHT_ADJOINT_SYNTHESIS read phase and write alm[] (flags SHT_ADD_OUTPUT,
+ * SHT_NO_POLAR_OPT, SHT_REAL_HARMONICS).  sht_execute_rings: SHT_SYNTHESIS /
+ * SHT_ADJOINT_ANALYSIS read phase (every entry, no polar cut) and write map[]
+ * (SHT_ADJOINT_ANALYSIS applies the ring weights; flag SHT_ADD_OUTPUT);
+ * SHT_ANALYSIS / SHT_ADJOINT_SYNTHESIS read map[] and write phase.  Both use the
+ * plan's workspace like sht_execute (calls sharing a plan must not overlap),
+ * allocate nothing and are asynchronous on cuda_stream.  Errors:
+ * SHT_ERR_INVALID_ARG (NULL, bad type or flags), SHT_ERR_CUDA.
+ */
+SHT_API int sht_execute_legendre(sht_plan_t plan, int type, double *const *alm, double *phase, int flags,
+                                 void *cuda_stream);
+SHT_API int sht_execute_rings(sht_plan_t plan, int type, double *phase, double *const *map, int flags,
+                              void *cuda_stream);
+
 /* ---- transforms without allocation -------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that must
  * not allocate device memory while they run transforms -- code recorded under

@@ -65,6 +65,8 @@ _sig = {
     "sht_plan_triples": [_vp, ctypes.c_int, _i64p],
     "sht_plan_destroy": [_vp],
     "sht_execute_noalloc": [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp],
+    "sht_execute_legendre": [_vp, ctypes.c_int, ctypes.POINTER(_vp), _vp, ctypes.c_int, _vp],
+    "sht_execute_rings": [_vp, ctypes.c_int, _vp, ctypes.POINTER(_vp), ctypes.c_int, _vp],
     "sht_plan_profile": [_vp, ctypes.c_int],
     "sht_plan_get_tiling": [_vp, _ip, _ip, _ip],
     "sht_plan_set_tiling": [_vp, ctypes.c_int],
@@ -346,6 +348,28 @@ def sht_execute(plan: Plan, type_, alm, maps, flags=0, stream=None):
     mp = (_vp * n)(*[_devptr(m) for m in maps])
     st = None if stream is None else _vp(_devptr_stream(stream))
     _check(_lib.sht_execute(plan.handle, type_, ap, mp, flags, st), "sht_execute")
+
+
+def sht_execute_legendre(plan: Plan, type_, alm, phase, flags=0, stream=None):
+    """The Legendre stage alone (see include/sht_gb300.h): alm is a sequence of
+    device buffers, phase one complex128 device buffer of nmaps x nm x nrings."""
+    n = plan.narrays
+    if len(alm) != n:
+        raise ValueError(f"expected {n} a_lm buffers")
+    ap = (_vp * n)(*[_devptr(a) for a in alm])
+    st = None if stream is None else _vp(_devptr_stream(stream))
+    _check(_lib.sht_execute_legendre(plan.handle, type_, ap, _devptr(phase), flags, st), "sht_execute_legendre")
+
+
+def sht_execute_rings(plan: Plan, type_, phase, maps, flags=0, stream=None):
+    """The ring-FFT stage alone (see include/sht_gb300.h): phase one complex128
+    device buffer of nmaps x nm x nrings, maps a sequence of device buffers."""
+    n = plan.narrays
+    if len(maps) != n:
+        raise ValueError(f"expected {n} map buffers")
+    mp = (_vp * n)(*[_devptr(m) for m in maps])
+    st = None if stream is None else _vp(_devptr_stream(stream))
+    _check(_lib.sht_execute_rings(plan.handle, type_, _devptr(phase), mp, flags, st), "sht_execute_rings")
 
 
 def sht_execute_noalloc(plan: Plan, type_, alm, maps, flags=0, stream=None):
