@@ -808,6 +808,35 @@ def run_decomposed(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_pair_workload(args, world, rank, local):
+    """Profiling captures: the headline transform pair with the default mixed plan at
+    --lmax (GL (lmax+1) x (2 lmax+1), spin 2, the bench's a_lm seed), one untimed
+    pair and then --steps pairs, nothing else; prints the CUDA-event time per pair."""
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1303_4945_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1303_4945_gb300 import inputs, sht
+
+    stream = torch.cuda.current_stream()
+    geom = sht.sht_geom_gauss(NLAT, NLON)
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(LMAX, LMAX), SPIN, 1, sht.SHT_MIXED)
+    a = [torch.from_numpy(x).cuda() for x in inputs.spin2_eb(SEED, LMAX)]
+    m = [torch.empty(geom.npix, dtype=torch.float64, device="cuda") for _ in range(2)]
+    b = [torch.empty_like(x) for x in a]
+
+    def step():
+        sht.sht_execute(plan, sht.SHT_SYNTHESIS, a, m, 0, stream)
+        sht.sht_execute(plan, sht.SHT_ANALYSIS, b, m, 0, stream)
+
+    ms = _events_ms(torch, stream, step, args.steps, 1, world)
+    if rank == 0:
+        print(json.dumps({"workload": "pair", "lmax": LMAX, "tensor_cores": plan.tensor_cores, "ms_per_pair": ms,
+                          "device_status": plan.device_status()}), flush=True)
+
+
 def run_variants_workload(args, world, rank, local):
     """The transforms beyond the headline pair, each in both forms: derivative
     synthesis at lmax 4095 (GL 4096 x 8191, Sect. 4.3), a spin-2 pair on the
@@ -900,12 +929,13 @@ def main():
     ap.add_argument("--decomposed", action="store_true",
                     help="spin2 workload as one transform distributed over the ranks (Sect. 4.2 m / ring "
                          "decomposition, NCCL all-to-all) instead of independent replicas")
-    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad", "healpix", "variants", "maps8"],
+    ap.add_argument("--workload", default="spin2", choices=["spin2", "batch", "grad", "healpix", "variants", "maps8", "pair"],
                     help="spin2: the headline (spin-2 lmax 4095 pair); batch: 64 uneven scalar problems + "
                          "8 maps at lmax 2047 in one batch; grad: loss + gradient at lmax 8191; healpix: "
                          "Jacobi-refined analysis on HEALPix Nside 512, lmax 1535; variants: derivative "
                          "synthesis, grid variants, real harmonics, spin 37; maps8: 8 scalar maps at lmax 4095 "
-                         "with the tensor-core synthesis")
+                         "with the tensor-core synthesis; pair: one untimed pair, then --steps pairs of the "
+                         "default mixed plan at --lmax, for profiling captures")
     args = ap.parse_args()
     set_workload(args.lmax, args.nlat)
     world, rank, local = dist_setup()
@@ -917,7 +947,7 @@ def main():
         return
     if args.workload != "spin2":
         runners = {"batch": run_batch_workload, "grad": run_grad_workload, "healpix": run_healpix_workload,
-                   "variants": run_variants_workload, "maps8": run_maps8_workload}
+                   "variants": run_variants_workload, "maps8": run_maps8_workload, "pair": run_pair_workload}
         runners[args.workload](args, world, rank, local)
         return
     import numpy as np
