@@ -367,7 +367,9 @@ MEASURED_TRAFFIC = {
 }
 
 
-KERNEL_HEADERS = {"legendre_fp64.cu": ("sht_device.cuh",), "legendre_mixed.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh")}
+KERNEL_HEADERS = {"legendre_fp64.cu": ("sht_device.cuh",),
+                  "legendre_mixed.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh"),
+                  "legendre_tc.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh")}
 
 
 def _kernel_digest(kernel_file):
@@ -437,7 +439,8 @@ def roofline_for(stages, plan, spin, precision, peaks, steps, ncomp=1):
                                "FP64 pipe derived: 152 SMs x 2 DFMA lanes/clk x 2 flops x sm_max clock"),
                "peak_derived": derived}
     else:
-        kfile = "legendre_mixed.cu"
+        tc = name == "legendre_synthesis" and bool(getattr(plan, "tensor_cores", False))
+        kfile = "legendre_tc.cu" if tc else "legendre_mixed.cu"
         derived = SMS * 128 * 2 * clock / 1e12  # 128 FFMA lanes per SM per clock, 2 flops each
         peak = 2 * measured["fp32_fma_tops"] if measured else derived
         ops = triples * f32_ops_per_triple(spin, ncomp)
@@ -810,8 +813,9 @@ def run_decomposed(args, world, rank, local):
 
 def run_pair_workload(args, world, rank, local):
     """Profiling captures: the headline transform pair with the default mixed plan at
-    --lmax (GL (lmax+1) x (2 lmax+1), spin 2, the bench's a_lm seed), one untimed
-    pair and then --steps pairs, nothing else; prints the CUDA-event time per pair."""
+    --lmax (GL (lmax+1) x (2 lmax+1), spin 2, the bench's a_lm seed, analysis tiling
+    autotuned as the bench does: 9 untimed analysis launches), one untimed pair and
+    then --steps pairs, nothing else; prints the CUDA-event time per pair."""
     import torch
 
     torch.cuda.set_device(local)
@@ -823,6 +827,7 @@ def run_pair_workload(args, world, rank, local):
     stream = torch.cuda.current_stream()
     geom = sht.sht_geom_gauss(NLAT, NLON)
     plan = sht.sht_plan_create(geom, sht.sht_alm_create(LMAX, LMAX), SPIN, 1, sht.SHT_MIXED)
+    plan.autotune(stream)  # the analysis tiling the bench's headline form would run
     a = [torch.from_numpy(x).cuda() for x in inputs.spin2_eb(SEED, LMAX)]
     m = [torch.empty(geom.npix, dtype=torch.float64, device="cuda") for _ in range(2)]
     b = [torch.empty_like(x) for x in a]
@@ -834,6 +839,7 @@ def run_pair_workload(args, world, rank, local):
     ms = _events_ms(torch, stream, step, args.steps, 1, world)
     if rank == 0:
         print(json.dumps({"workload": "pair", "lmax": LMAX, "tensor_cores": plan.tensor_cores, "ms_per_pair": ms,
+                          "analysis_pairs_per_thread": plan.tiling()[0],
                           "device_status": plan.device_status()}), flush=True)
 
 
