@@ -358,12 +358,11 @@ def f32_ops_per_triple(spin, ncomp):
 # SHA-256 of the kernel's source file and device headers when they were taken:
 # a changed source makes the figure stale and the bench reports null.
 MEASURED_TRAFFIC = {
-    # profiles/dram_traffic_spin2_lmax4095.md (spin 2, GL 4096 x 8191, lmax 4095, one launch each);
+    # one launch at the headline size (spin 2, GL 4096 x 8191, lmax 4095), single-pass
+    # dram__bytes_read.sum + dram__bytes_write.sum (the pair's traffic capture under profiles/);
     # sha256 over the kernel file and its device headers (_kernel_digest)
-    "fp64:legendre_analysis": {"bytes": 708601344 + 941840384, "sha256": "cd3970788aed5e416475654291e228e1996a18a954c89025fa9634f97ca50d43"},
-    "fp64:legendre_synthesis": {"bytes": 552622848 + 323180544, "sha256": "cd3970788aed5e416475654291e228e1996a18a954c89025fa9634f97ca50d43"},
-    "mixed:legendre_analysis": {"bytes": 656024320 + 3468856832, "sha256": "ea9f20645ae07514fcb5f42e7deb811cee55d6eed60c1317f38d6e7e20ba634f"},
-    "mixed:legendre_synthesis": {"bytes": 549227008 + 321439232, "sha256": "ea9f20645ae07514fcb5f42e7deb811cee55d6eed60c1317f38d6e7e20ba634f"},
+    "mixed:legendre_analysis": {"bytes": 662757632 + 3469790720,
+                                "sha256": "53d00b60195a345d0816673dac167f03e28d031c0fb00e7b7ce779cc0d6855b7"},
 }
 
 

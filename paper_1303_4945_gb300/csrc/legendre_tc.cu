@@ -25,11 +25,17 @@
 //    double-float, together with the CUDA-core remainder sums.
 //
 // MMA shape: M = 128 ring pairs (one TMEM lane per pair: thread t reads lane t),
-// N = 16 or 32 columns, K = 16 degrees per instruction; A (the Lambda digits)
-// and B (the a_lm digits) are K-major in shared memory without swizzle, 8x16-byte
-// core matrices 128 bytes apart along K and 256 bytes apart along M / N.  A is
-// double-buffered (the recursion writes K-step s + 1 while the MMAs of s run),
-// B is rebuilt per K-step once the previous K-step's MMAs have completed.
+// K = 16 degrees per instruction, N = 2 NCW: one instruction reads two
+// consecutive a_lm digit tiles (NCW >= 8 columns each) and so adds L_i B_j and
+// L_i B_(j+1) into two consecutive levels of NCW TMEM columns (level k at column
+// k NCW), which keeps the narrow shapes' MMAs free of padding columns: 8 MMAs per
+// Lambda set and K-step instead of 14.
+// A (the Lambda digits) and B (the a_lm digit stack) are K-major in shared memory
+// without swizzle, 8x16-byte core matrices 128 bytes apart along K and 256 bytes
+// apart along M / N.  One thread issues a K-step's MMAs in program order (the
+// first ones of a window overwrite every level read later); the recursion's
+// digits of K-step s + 1 are written once the MMAs of s have completed, and B is
+// rebuilt then too.
 #include "mixed_common.cuh"
 
 namespace sht {
@@ -40,8 +46,9 @@ constexpr int kK = 16;              // degrees per MMA (bf16 K)
 constexpr int kWin = 16;            // K-steps per TMEM window (256 degrees)
 constexpr int kLamDigits = 3;       // bf16 digits of Lambda (plus an FP32 remainder)
 constexpr int kAlmDigits = 5;       // bf16 digits of the a_lm columns
-constexpr int kLevels = 6;          // TMEM accumulators: digit products with i + j <= 5
+constexpr int kLevels = 6;          // TMEM levels read: digit products with i + j <= 5
 constexpr int kATile = kRows * kK * 2;  // bytes of one 128 x 16 bf16 tile
+constexpr int kPack = 4;            // degrees of digits held in registers before a shared-memory store
 constexpr unsigned long long kWaitNs = 100000000ull;  // bounded mbarrier waits: 100 ms of global time
 
 // ---- PTX wrappers -------------------------------------------------------------
@@ -71,9 +78,8 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-constexpr int kIssuers = 3;  // threads issuing a K-step's MMAs (lane 0 of warps 0-2), one commit each
-__device__ __forceinline__ void bar_init(uint64_t *bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(kIssuers));
+__device__ __forceinline__ void bar_init(uint64_t *bar) {  // one arrival per phase: the issuer's commit
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -104,16 +110,16 @@ __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-// 8 consecutive 32-bit TMEM columns of this thread's lane (warp w reads lanes 32w..32w+31)
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
+// 8 consecutive 32-bit TMEM columns of this thread's lane (warp w reads lanes
+// 32w..32w+31); the registers are valid after tmem_wait_ld
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+               : "r"(taddr)
+               : "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 
 // ---- exact digits ---------------------------------------------------------------
 // round x to a multiple of the quantum q whose magic constant is s = 1.5 * 2^23 * q
@@ -132,18 +138,26 @@ __device__ __forceinline__ float pow2_above(float x) {
 }
 
 // Shapes: NCOL output columns per pair (spin: N1, S4, N2, S3 as re/im per job;
-// spin 0: even-l and odd-l sums as re/im per job), MMA width N >= 16, NV a_lm
-// values per degree (spin: P = E + iB and M = E - iB, re and im; spin 0: re, im).
+// spin 0: even-l and odd-l sums as re/im per job), NCW = max(NCOL, 8) TMEM columns
+// per level and rows per a_lm digit tile, MMA width N = 2 NCW (two digit tiles, two
+// levels), NV a_lm values per degree (spin: P = E + iB and M = E - iB, re and im;
+// spin 0: re, im).  A set's digit stack holds the tiles of digits -1 .. 5, those
+// of digits -1 and 5 zero: Lambda digit i meets the windows of digits
+// (j0, j0 + 1) with j0 = -(i mod 2), j0 + 2, ..., which start on even levels i + j0,
+// so every MMA writes the 2 NCW columns of a level pair at a multiple of N.
 template <int NJ, bool SPIN>
 struct Shape {
   static constexpr int NL = SPIN ? 2 : 1;
   static constexpr int NCOL = SPIN ? 8 * NJ : 4 * NJ;
-  static constexpr int N = NCOL < 16 ? 16 : NCOL;
+  static constexpr int NCW = NCOL < 8 ? 8 : NCOL;
+  static constexpr int N = 2 * NCW;
+  static constexpr int NDT = kAlmDigits + 2;  // digit tiles per Lambda set: -1 .. 5
+  static constexpr int COLS = kLevels * NCW;  // TMEM: levels 0 .. 5
+  static constexpr int TCOLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : 256));
   static constexpr int NV = SPIN ? 4 * NJ : 2 * NJ;
-  static constexpr int TCOLS = kLevels * N <= 128 ? 128 : 256;  // TMEM allocation (a power of two)
-  static constexpr int BTILE = N * kK * 2;                      // bytes of one B digit tile
-  static constexpr int A_BYTES = 2 * NL * kLamDigits * kATile;  // two buffers
-  static constexpr int B_BYTES = NL * kAlmDigits * BTILE;
+  static constexpr int DTILE = NCW * kK * 2;  // bytes of one a_lm digit tile
+  static constexpr int A_BYTES = NL * kLamDigits * kATile;
+  static constexpr int B_BYTES = NL * NDT * DTILE;
   // per degree of a K-step, staged in shared memory one K-step ahead: the two
   // float4 of its recursion coefficients and one float4 per a_lm table row read
   static constexpr int NARR = SPIN ? 2 * NJ : NJ;
@@ -151,11 +165,17 @@ struct Shape {
   static constexpr int STG = kK * ROW;                 // float4 per K-step
   static constexpr int PF = (STG + kRows - 1) / kRows;  // of them per thread
   static constexpr int ST_BYTES = 2 * STG * 16;        // two buffers
-  static constexpr int SMEM = A_BYTES + ST_BYTES + B_BYTES + 2 * NV * 4;
-  // dynamic shared memory requested: enough that at most 512 / TCOLS CTAs fit on an
-  // SM, so their TMEM allocations never wait for one another
-  static constexpr int SMEM_LAUNCH = TCOLS == 128 ? (SMEM > 46 * 1024 ? SMEM : 46 * 1024)
-                                                  : (SMEM > 77 * 1024 ? SMEM : 77 * 1024);
+  static constexpr int ACC_BYTES = NCOL * kRows * 8;  // the double-float column sums [col][pair]
+  static constexpr int SMEM = A_BYTES + ST_BYTES + B_BYTES + ACC_BYTES + 2 * NV * 4;
+  // CTAs per SM the kernel is compiled for, and the dynamic shared memory
+  // requested: at least enough that no more than 512 / TCOLS CTAs fit on an SM,
+  // so their TMEM allocations never wait for one another
+  static constexpr int MINB = TCOLS <= 64 ? 5 : (TCOLS == 128 ? 4 : 2);
+  static constexpr int SMEM_FLOOR = (228 * 1024) / (512 / TCOLS + 1) - 1024 + 1;
+  static constexpr int SMEM_LAUNCH = SMEM > SMEM_FLOOR ? SMEM : SMEM_FLOOR;
+  static_assert(N % 16 == 0 && N <= 256 && NCW % 8 == 0, "MMA width; digit tiles of whole core-matrix rows");
+  static_assert(kLevels % 2 == 0 && kLamDigits <= 3, "level pairs");
+  static_assert(COLS <= TCOLS, "TMEM allocation");
   static_assert(NCOL <= 32, "tensor-core synthesis: at most 32 output columns");
   static_assert(128 % NV == 0, "a_lm values per degree must divide the CTA");
 };
@@ -204,14 +224,18 @@ __device__ __forceinline__ void window_bounds(const MixArgs &a, int64_t co, int 
   if ((threadIdx.x & 31) < S::NV) atomicMax(reinterpret_cast<int *>(umax) + v, __float_as_int(mx));
 }
 
-// The B digit tiles of a K-step from its staged rows (zero past lmax): value v of degree
-// lb + k split into kAlmDigits digits on its window's grid and written, with the
-// parity sign s = (-1)^(l - l0) where the column needs it, into the rows of the
-// columns that read it (see the column layout in tc_syn_body).  Rows no value
-// writes stay zero from the kernel's start.
+// The a_lm digit stacks of a K-step from its staged rows (zero past lmax): value v
+// of degree lb + k split into kAlmDigits digits on its window's grid and written,
+// with the parity sign s = (-1)^(l - l0) where the column needs it, into the rows
+// of the columns that read it (see the column layout in tc_syn_body).  Set t's
+// stack holds NDT digit tiles of NCW rows, digit j at rows (j + 1) NCW ..; rows no
+// value writes (the other set's columns, padding columns, the tiles of digits -1
+// and 5) stay zero from the kernel's start.
 template <int NJ, bool SPIN>
 __device__ __forceinline__ void build_b(const float4 *stg, const float *umax, unsigned char *Bt) {
   using S = Shape<NJ, SPIN>;
+  // byte offset of (row r of the stack, degree k) in the K-major core-matrix layout
+  auto at = [](int r, int k) { return (r / 8) * 256 + (r % 8) * 16 + (k / 8) * 128 + (k % 8) * 2; };
   for (int t = threadIdx.x; t < kK * S::NV; t += kRows) {
     const int k = t % kK, v = t / kK;
     const f2 x = staged_value<NJ, SPIN>(stg + k * S::ROW, v);  // zero past lmax
@@ -228,36 +252,29 @@ __device__ __forceinline__ void build_b(const float4 *stg, const float *umax, un
     r = __fsub_rn(r, d[3]);
     d[4] = round_to(r, s0 * 0x1p-32f);
     const bool odd = k & 1;
-    // (tile, row) pairs of this value; spin: P.re -> (+, 8j) and (-, 8j+6) signed,
+    // (set, column) pairs of this value; spin: P.re -> (+, 8j) and (-, 8j+6) signed,
     // P.im -> (+, 8j+1) and (-, 8j+7) signed, M.re -> (+, 8j+2) signed and (-, 8j+4),
-    // M.im -> (+, 8j+3) signed and (-, 8j+5); spin 0: the even- or odd-l row of its job
-    int lam0, row0, lam1 = -1, row1 = 0, neg0 = 0, neg1 = 0;
-    int zrow = -1;
+    // M.im -> (+, 8j+3) signed and (-, 8j+5); spin 0: the even- or odd-l column of its job
+    int col0, col1 = 0, neg0 = 0, neg1 = 0, zcol = 0;
     if (SPIN) {
       const int j = v / 4, c = v % 4;
-      lam0 = 0;
-      lam1 = 1;
-      row0 = 8 * j + c;
-      row1 = 8 * j + (c < 2 ? 6 + c : 2 + c);
+      col0 = 8 * j + c;
+      col1 = 8 * j + (c < 2 ? 6 + c : 2 + c);
       neg0 = (c >= 2) && odd;
       neg1 = (c < 2) && odd;
     } else {
       const int j = v / 2, c = v % 2;
-      lam0 = 0;
-      row0 = 4 * j + (odd ? 2 : 0) + c;
-      zrow = 4 * j + (odd ? 0 : 2) + c;
+      col0 = 4 * j + (odd ? 2 : 0) + c;
+      zcol = 4 * j + (odd ? 0 : 2) + c;
     }
-    const int off = (k / 8) * 128 + (k % 8) * 2;
 #pragma unroll
     for (int dj = 0; dj < kAlmDigits; ++dj) {
-      unsigned char *tile0 = Bt + (lam0 * kAlmDigits + dj) * S::BTILE + off;
-      *reinterpret_cast<uint16_t *>(tile0 + (row0 / 8) * 256 + (row0 % 8) * 16) = bf16_of(neg0 ? -d[dj] : d[dj]);
-      if (SPIN) {
-        unsigned char *tile1 = Bt + (lam1 * kAlmDigits + dj) * S::BTILE + off;
-        *reinterpret_cast<uint16_t *>(tile1 + (row1 / 8) * 256 + (row1 % 8) * 16) = bf16_of(neg1 ? -d[dj] : d[dj]);
-      } else {
-        *reinterpret_cast<uint16_t *>(tile0 + (zrow / 8) * 256 + (zrow % 8) * 16) = 0;
-      }
+      const int r = (dj + 1) * S::NCW;
+      *reinterpret_cast<uint16_t *>(Bt + at(r + col0, k)) = bf16_of(neg0 ? -d[dj] : d[dj]);
+      if (SPIN)
+        *reinterpret_cast<uint16_t *>(Bt + S::NDT * S::DTILE + at(r + col1, k)) = bf16_of(neg1 ? -d[dj] : d[dj]);
+      else
+        *reinterpret_cast<uint16_t *>(Bt + at(r + zcol, k)) = 0;
     }
   }
 }
@@ -276,7 +293,7 @@ __device__ __forceinline__ void build_b(const float4 *stg, const float *umax, un
 template <int NJ, bool SPIN>
 __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, unsigned char *smem) {
   using S = tc::Shape<NJ, SPIN>;
-  constexpr int NL = S::NL, NCOL = S::NCOL, N = S::N;
+  constexpr int NL = S::NL, NCOL = S::NCOL;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
   const MixArgs &a = ta.m;
@@ -293,7 +310,8 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   unsigned char *const Abuf = smem;
   float4 *const stage = reinterpret_cast<float4 *>(smem + S::A_BYTES);
   unsigned char *const Bt = smem + S::A_BYTES + S::ST_BYTES;
-  float *const umax = reinterpret_cast<float *>(Bt + S::B_BYTES);
+  f2 *const accs = reinterpret_cast<f2 *>(Bt + S::B_BYTES);  // column c of this pair at accs[c * 128 + tid]
+  float *const umax = reinterpret_cast<float *>(Bt + S::B_BYTES + S::ACC_BYTES);
 
   // the staged rows of K-step ks: thread t loads entries t, t + 128, ... (zero past lmax)
   float4 pf[S::PF];
@@ -327,6 +345,9 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = tslot;
+  const uint32_t lane = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c) accs[c * tc::kRows + tid] = f2{0.f, 0.f};
 
   // recursion state (as in the double-float synthesis): +s values lpc/lpp, -s lmc/lmp
   const PairDev pd = a.pairs[valid ? p : 0];
@@ -345,13 +366,9 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   }
   // digit grid of Lambda: magic constants of the quanta u 2^-7, u 2^-15, u 2^-23
   const float ls0 = ta.lam_bound * 98304.0f, ls1 = ls0 * 0x1p-8f, ls2 = ls0 * 0x1p-16f;
-  f2 acc[NCOL];
   float racc[NCOL];
 #pragma unroll
-  for (int c = 0; c < NCOL; ++c) {
-    acc[c] = f2{0.f, 0.f};
-    racc[c] = 0.f;
-  }
+  for (int c = 0; c < NCOL; ++c) racc[c] = 0.f;
 
   // accumulation weight of the +s / -s values (see weight() in mixed_common.cuh): 1 at
   // scale 0, 2^-104 at scale -1, 0 below; scales change only at the rescale checks
@@ -359,16 +376,16 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   float wfp = wfac(scp), wfm = wfac(scm);
   bool settled = false;  // every lane of the warp at scale 0 (warp-uniform; scales only rise)
 
-  // eight degrees lb..lb+7 (lb - l0 even): digits packed per pair of degrees into
+  // kPack degrees from rows (lb - l0 even): digits packed per pair of degrees into
   // pk[set][digit][q / 2], remainders contracted into racc, recursion advanced.
   // Every second degree the warp votes: if every lane's values are negligible for
   // the next two steps (as in the double-float kernels) the digits are zero and
   // only the recursion runs.
-  auto half = [&](const float4 *rows, uint32_t (&pk)[NL][tc::kLamDigits][4]) {
+  auto part = [&](const float4 *rows, uint32_t (&pk)[NL][tc::kLamDigits][tc::kPack / 2]) {
     float dlo[NL][tc::kLamDigits];
     bool dead = false;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < tc::kPack; ++q) {
       // past lmax the staged rows are zero: the recursion runs on zero coefficients
       // (its values become zero one degree later) and meets zero a_lm, so those
       // degrees add nothing and need no test
@@ -450,71 +467,83 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
         }
       }
     }
-    if (!settled) {  // enhanced exponent: rescale every eight degrees (see mixed_common.cuh)
-      if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
-        lpc = {lpc.h * kScaleFactor32, lpc.l * kScaleFactor32};
-        lpp = {lpp.h * kScaleFactor32, lpp.l * kScaleFactor32};
-        ++scp;
-      }
-      if (SPIN && scm < 0 && fabsf(lmc.h) > kScaleUp32) {
-        lmc = {lmc.h * kScaleFactor32, lmc.l * kScaleFactor32};
-        lmp = {lmp.h * kScaleFactor32, lmp.l * kScaleFactor32};
-        ++scm;
-      }
-      wfp = wfac(scp);
-      wfm = wfac(scm);
-      settled = __all_sync(0xffffffffu, scp == 0 && scm == 0);
+  };
+  // enhanced exponent: rescale every eight degrees (see mixed_common.cuh)
+  auto rescale = [&]() {
+    if (settled) return;
+    if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
+      lpc = {lpc.h * kScaleFactor32, lpc.l * kScaleFactor32};
+      lpp = {lpp.h * kScaleFactor32, lpp.l * kScaleFactor32};
+      ++scp;
     }
+    if (SPIN && scm < 0 && fabsf(lmc.h) > kScaleUp32) {
+      lmc = {lmc.h * kScaleFactor32, lmc.l * kScaleFactor32};
+      lmp = {lmp.h * kScaleFactor32, lmp.l * kScaleFactor32};
+      ++scm;
+    }
+    wfp = wfac(scp);
+    wfm = wfac(scm);
+    settled = __all_sync(0xffffffffu, scp == 0 && scm == 0);
+  };
+  // this thread's digits of degrees q0 .. q0 + kPack - 1 of the K-step into the A tiles
+  auto store_a = [&](int q0, const uint32_t (&pk)[NL][tc::kLamDigits][tc::kPack / 2]) {
+#pragma unroll
+    for (int t = 0; t < NL; ++t)
+#pragma unroll
+      for (int i = 0; i < tc::kLamDigits; ++i) {
+        unsigned char *dst = Abuf + (t * tc::kLamDigits + i) * tc::kATile + (tid / 8) * 256 + (q0 / 8) * 128 +
+                             (tid % 8) * 16 + (q0 % 8) * 2;
+        if (tc::kPack == 8)
+          *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(pk[t][i]);
+        else
+          *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(pk[t][i]);
+      }
   };
 
-  // the MMAs of one K-step, issued by lane 0 of warps 0-2: issuer w takes the levels
-  // k = w, w + 3 (every digit product Li Bj with i + j = k; the first product of a
-  // level in a window overwrites it) and commits them to the barrier
-  // descriptors of the first A and B tiles; a tile's descriptor adds its byte offset / 16
+  // the MMAs of one K-step, issued in order by one thread: for each Lambda set t and
+  // digit i, the a_lm digit windows (j0, j0 + 1), j0 = -(i mod 2), j0 + 2, ... up to
+  // the last digit with i + j <= 5, into levels (i + j0, i + j0 + 1); in a window's
+  // first K-step the set-0, digit-0 products come first and overwrite levels 0 .. 5
+  // (every level written), the rest accumulate.  The zero tiles of digits -1 and 5
+  // fill the odd and the last windows; the i = 2 windows end at digit 3.
   const uint64_t adesc0 = tc::mat_desc(tc::smem_u32(Abuf), 128, 256);
   const uint64_t bdesc0 = tc::mat_desc(tc::smem_u32(Bt), 128, 256);
-  auto issue = [&](int ks, int w) {
+  auto issue = [&](int ks) {
     tc::fence_after();
-    constexpr uint32_t idesc = tc::instr_desc(tc::kRows, N);
-    const uint64_t abuf = adesc0 + (uint64_t)(((ks & 1) * (NL * tc::kLamDigits * tc::kATile)) >> 4);
+    constexpr uint32_t idesc = tc::instr_desc(tc::kRows, S::N);
     const bool first = (ks % tc::kWin) == 0;
 #pragma unroll
-    for (int k = 0; k < tc::kLevels; ++k) {
-      if (k % tc::kIssuers != w) continue;
-      bool init = first;
+    for (int t = 0; t < NL; ++t)
 #pragma unroll
-      for (int t = 0; t < NL; ++t)
+      for (int i = 0; i < tc::kLamDigits; ++i)
 #pragma unroll
-        for (int i = 0; i < tc::kLamDigits; ++i) {
-          const int j = k - i;
-          if (j < 0 || j >= tc::kAlmDigits) continue;
-          const uint64_t ad = abuf + (uint64_t)(((t * tc::kLamDigits + i) * tc::kATile) >> 4);
-          const uint64_t bd = bdesc0 + (uint64_t)(((t * tc::kAlmDigits + j) * S::BTILE) >> 4);
-          tc::mma_bf16(tbase + k * N, ad, bd, idesc, init ? 0u : 1u);
-          init = false;
+        for (int j0 = -(i & 1); j0 <= tc::kAlmDigits - 1 && i + j0 < tc::kLevels; j0 += 2) {
+          const uint64_t ad = adesc0 + (uint64_t)(((t * tc::kLamDigits + i) * tc::kATile) >> 4);
+          const uint64_t bd = bdesc0 + (uint64_t)((t * S::NDT * S::DTILE + (j0 + 1) * S::DTILE) >> 4);
+          tc::mma_bf16(tbase + (i + j0) * S::NCW, ad, bd, idesc, (first && t == 0 && i == 0) ? 0u : 1u);
         }
-    }
     tc::mma_commit(&mbar);
   };
 
   // after a window: the six levels of this thread's lane plus the remainder sums,
   // added to the double-float column sums
   auto readout = [&]() {
-    const uint32_t lane = tbase + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
     for (int c0 = 0; c0 < NCOL; c0 += 8) {
-      float dv[tc::kLevels][8];
+      uint32_t dv[tc::kLevels][8];
 #pragma unroll
-      for (int k = 0; k < tc::kLevels; ++k) tc::tmem_ld8(lane + k * N + c0, dv[k]);
+      for (int k = 0; k < tc::kLevels; ++k) tc::tmem_ld8(lane + k * S::NCW + c0, dv[k]);
+      tc::tmem_wait_ld();
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         if (c0 + c >= NCOL) break;
-        f2 t = {dv[0][c], 0.f};
+        f2 t = {__uint_as_float(dv[0][c]), 0.f};
 #pragma unroll
-        for (int k = 1; k < tc::kLevels; ++k) t = f2_add_lazy(t, f2{dv[k][c], 0.f});
+        for (int k = 1; k < tc::kLevels; ++k) t = f2_add_lazy(t, f2{__uint_as_float(dv[k][c]), 0.f});
         t = f2_add_lazy(t, f2{racc[c0 + c], 0.f});
         racc[c0 + c] = 0.f;
-        acc[c0 + c] = f2_add(acc[c0 + c], t);
+        f2 &acc = accs[(c0 + c) * tc::kRows + tid];
+        acc = f2_add(acc, t);
       }
     }
   };
@@ -530,25 +559,21 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
       tc::window_bounds<NJ, SPIN>(a, co, lb, lw1 < lmax ? lw1 : lmax, um);
       __syncthreads();
     }
-    unsigned char *Aw = Abuf + (ks & 1) * (NL * tc::kLamDigits * tc::kATile);
     const float4 *rows = stage + (ks & 1) * S::STG;
     if (ks + 1 < nks) prefetch(ks + 1);  // its latency hides behind this K-step's work
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      uint32_t pk[NL][tc::kLamDigits][4];
-      half(rows + 8 * h * S::ROW, pk);
-#pragma unroll
-      for (int t = 0; t < NL; ++t)
-#pragma unroll
-        for (int i = 0; i < tc::kLamDigits; ++i)
-          *reinterpret_cast<uint4 *>(Aw + (t * tc::kLamDigits + i) * tc::kATile + (tid / 8) * 256 + h * 128 +
-                                     (tid % 8) * 16) = make_uint4(pk[t][i][0], pk[t][i][1], pk[t][i][2], pk[t][i][3]);
-    }
-    // the previous K-step's MMAs read the B tiles: wait for them before rebuilding
     bool fail = false;
-    if (ncommit > nwaited) {
-      fail = !tc::bar_wait(&mbar, (uint32_t)(ncommit - 1) & 1u);
-      nwaited = ncommit;
+#pragma unroll 1
+    for (int q0 = 0; q0 < tc::kK; q0 += tc::kPack) {
+      uint32_t pk[NL][tc::kLamDigits][tc::kPack / 2];
+      part(rows + q0 * S::ROW, pk);
+      if (q0 % 8 == tc::kPack % 8) rescale();  // after every eight degrees
+      // the previous K-step's MMAs read the A and B tiles: wait for them before
+      // the first write (they have long finished by now)
+      if (q0 == 0 && ncommit > nwaited) {
+        fail = !tc::bar_wait(&mbar, (uint32_t)(ncommit - 1) & 1u);
+        nwaited = ncommit;
+      }
+      if (!fail) store_a(q0, pk);
     }
     if (!fail) tc::build_b<NJ, SPIN>(rows, umax + ((ks / tc::kWin) & 1) * S::NV, Bt);
     if (ks + 1 < nks) stage_store(ks + 1);  // its buffer's last readers finished before the previous barrier
@@ -557,7 +582,7 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
       ok = false;
       break;
     }
-    if ((tid & 31) == 0 && warp < tc::kIssuers) issue(ks, warp);
+    if (tid == 0) issue(ks);
     ++ncommit;
     if (ks % tc::kWin == tc::kWin - 1 || ks == nks - 1) {
       fail = !tc::bar_wait(&mbar, (uint32_t)(ncommit - 1) & 1u);
@@ -580,16 +605,17 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   tc::fence_after();
   if (warp == 0) tc::tmem_dealloc(tbase, S::TCOLS);
   if (!ok || !valid) return;
+  auto colsum = [&](int c) { return f2_val(accs[c * tc::kRows + tid]); };
 
   if (SPIN) {
     const double sig = (as & 1) ? -1.0 : 1.0;
     const double h0 = ((l0 + m) & 1) ? -0.5 : 0.5;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
-      const double n1r = f2_val(acc[8 * j + 0]), n1i = f2_val(acc[8 * j + 1]);
-      const double s4r = f2_val(acc[8 * j + 2]), s4i = f2_val(acc[8 * j + 3]);
-      const double n2r = f2_val(acc[8 * j + 4]), n2i = f2_val(acc[8 * j + 5]);
-      const double s3r = f2_val(acc[8 * j + 6]), s3i = f2_val(acc[8 * j + 7]);
+      const double n1r = colsum(8 * j + 0), n1i = colsum(8 * j + 1);
+      const double s4r = colsum(8 * j + 2), s4i = colsum(8 * j + 3);
+      const double n2r = colsum(8 * j + 4), n2i = colsum(8 * j + 5);
+      const double s3r = colsum(8 * j + 6), s3i = colsum(8 * j + 7);
       const double ar = n1r + sig * n2r, ai = n1i + sig * n2i;
       const double br = sig * n2r - n1r, bi = sig * n2i - n1i;
       const double cr = s3r + sig * s4r, ci = s3i + sig * s4i;
@@ -609,8 +635,8 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   } else {
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
-      const double e0 = f2_val(acc[4 * j + 0]), e1 = f2_val(acc[4 * j + 1]);
-      const double o0 = f2_val(acc[4 * j + 2]), o1 = f2_val(acc[4 * j + 3]);
+      const double e0 = colsum(4 * j + 0), e1 = colsum(4 * j + 1);
+      const double o0 = colsum(4 * j + 2), o1 = colsum(4 * j + 3);
       double2 fn = make_double2(e0 + o0, e1 + o1), fs = make_double2(e0 - o0, e1 - o1);
       if (m == 0) fn.y = fs.y = 0.0;
       double2 *o = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
@@ -625,15 +651,14 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
 namespace sht {
 
 template <int NJ, bool SPIN>
-__global__ void __launch_bounds__(tc::kRows, (tc::Shape<NJ, SPIN>::TCOLS == 128 ? 4 : 2))
-    tc_syn(TcArgs ta) {
+__global__ void __launch_bounds__(tc::kRows, tc::Shape<NJ, SPIN>::MINB) tc_syn(TcArgs ta) {
   extern __shared__ __align__(128) unsigned char tc_smem[];
   tc_syn_body<NJ, SPIN>(ta, ta.m.syn_items[blockIdx.x], tc_smem);
 }
 
 // batches: item (mi, first pair, -, record); the record holds the plan's arguments
 template <int NJ, bool SPIN>
-__global__ void __launch_bounds__(tc::kRows, (tc::Shape<NJ, SPIN>::TCOLS == 128 ? 4 : 2))
+__global__ void __launch_bounds__(tc::kRows, tc::Shape<NJ, SPIN>::MINB)
     tc_syn_batch(const TcArgs *__restrict__ args, const int4 *__restrict__ items) {
   extern __shared__ __align__(128) unsigned char tc_smem[];
   const int4 it = items[blockIdx.x];
@@ -642,14 +667,22 @@ __global__ void __launch_bounds__(tc::kRows, (tc::Shape<NJ, SPIN>::TCOLS == 128 
 
 template <int NJ, bool SPIN>
 static cudaError_t tc_set_smem() {
+  // the request, and a shared-memory carveout that lets the compiled number of CTAs fit
   cudaError_t e = cudaFuncSetAttribute(tc_syn_batch<NJ, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        tc::Shape<NJ, SPIN>::SMEM_LAUNCH);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_syn<NJ, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tc::Shape<NJ, SPIN>::SMEM_LAUNCH);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_syn<NJ, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::Shape<NJ, SPIN>::SMEM_LAUNCH);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_syn_batch<NJ, SPIN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_syn<NJ, SPIN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
-// dynamic shared memory above 48 KB for every instance (once per device, at plan time)
+// shared-memory attributes of every instance (once per device, at plan time)
 cudaError_t tc_prepare_device() {
   cudaError_t e = tc_set_smem<1, false>();
   if (e == cudaSuccess) e = tc_set_smem<2, false>();
