@@ -160,7 +160,7 @@ int build(sht_batch_s *B) {
         for (auto &it : (lo ? P->syn_list_lo : P->syn_list)[polar])
           syn.push_back({it.first, make_int4(it.second.x, it.second.y, 0, (int)i)});
         for (auto &it : (lo ? P->ana_list_lo : P->ana_list)[polar])
-          ana.push_back({it.first, make_int4(it.second.x, it.second.y, 0, (int)i)});
+          ana.push_back({it.first, make_int4(it.second.x, it.second.y, it.second.z, (int)i)});
       }
       sort_by_cost(syn);
       sort_by_cost(ana);

@@ -36,9 +36,8 @@ struct LegArgs {
   const int2 *syn_items;
   const int4 *ana_items;
   const int64_t *part_off;
-  const int *tile0;
   double *part;
-  int ana_tiles, ppt, add;
+  int ppt, add;
   int ptr_off;  // batch: first entry of this plan in the pointer table
   int real;     // real-harmonic storage of the a_lm (spin-0 synthesis reads them directly)
   int half;     // m > 0 coefficients count half (SHT_GRADIENT with the adjoint analysis)
@@ -379,7 +378,7 @@ __device__ __forceinline__ void leg_ana_s0_body(const LegArgs &a, double *const 
   const int m = a.mval[mi];
   const int l0 = m, lmax = a.lmax, nl = lmax - l0 + 1;
   const Coef *__restrict__ cf = a.coef + a.coef_off[mi] - l0;
-  double *outp = a.part + a.part_off[mi] + (int64_t)(tile - a.tile0[mi]) * nl * V;
+  double *outp = a.part + a.part_off[mi] + (int64_t)(item.z >> 8) * nl * V;  // this item's slot
 
   double x[PPT], lc[PPT], lp[PPT];
   int scale[PPT];
@@ -495,7 +494,7 @@ __global__ void __launch_bounds__(kAnaThreads) leg_ana_s0_batch(const LegArgs *_
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const LegArgs &a = args[it.w];
-  leg_ana_s0_body<NJ, PPT>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, 0, 0));
+  leg_ana_s0_body<NJ, PPT>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, it.z, 0));
 }
 
 // Spin analysis with separate +s / -s recursions.  Per ring W+ = GQ + i GU,
@@ -511,7 +510,7 @@ __device__ __forceinline__ void leg_ana_spin_body(const LegArgs &a, double *cons
   const int s = a.spin, as = s < 0 ? -s : s;
   const int l0 = m > as ? m : as, lmax = a.lmax, nl = lmax - l0 + 1;
   const Coef *__restrict__ cf = a.coef + a.coef_off[mi] - l0;
-  double *outp = a.part + a.part_off[mi] + (int64_t)(tile - a.tile0[mi]) * nl * V;
+  double *outp = a.part + a.part_off[mi] + (int64_t)(item.z >> 8) * nl * V;  // this item's slot
   const double sg0 = ((l0 + m) & 1) ? -1.0 : 1.0;
 
   double x[PPT], lpc[PPT], lmc[PPT], lpp[PPT], lmp[PPT];
@@ -660,16 +659,16 @@ __global__ void __launch_bounds__(kAnaThreads) leg_ana_spin_batch(const LegArgs 
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const LegArgs &a = args[it.w];
-  leg_ana_spin_body<NJ, PPT>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, 0, 0));
+  leg_ana_spin_body<NJ, PPT>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, it.z, 0));
 }
 
 // Adds the tiles of every (m, l) in tile order and writes a_lm.
 // spin 0: V = 2 njobs values (re, im per job).
 // spin s: V = 4 njobs values (T1, T2 per job): E = -(T1 + sig T2)/2, B = -(i/2)(sig T2 - T1).
-__global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp, int ana_tiles, int astride, int add,
+__global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp, int astride, int add,
                            int real, int grad,
                            const int *__restrict__ mval, const int64_t *__restrict__ mstart,
-                           const int64_t *__restrict__ part_off, const int *__restrict__ tile0,
+                           const int64_t *__restrict__ part_off, const int *__restrict__ nslot,
                            const double *__restrict__ part, DevPtrs alm) {
   const int mi = blockIdx.y;
   const int m = mval[mi];
@@ -679,7 +678,7 @@ __global__ void ana_reduce(int lmax, int spin, int nm, int njobs_pad, int ncomp,
   const int V = (spin ? 4 : 2) * njobs_pad;
   const int l = l0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (l > lmax) return;
-  const int nt = ana_tiles - tile0[mi];
+  const int nt = nslot[mi];
   const double *pb = part + part_off[mi] + (int64_t)(l - l0) * V;
   const int64_t idx = mstart[mi] + (int64_t)l * astride;
   const int vper = spin ? 4 : 2;
@@ -777,9 +776,7 @@ static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar, boo
   a.syn_items = lo ? P->d_syn_lo[polar] : P->d_syn_items[polar];
   a.ana_items = lo ? P->d_ana_lo[polar] : P->d_ana_items[polar];
   a.part_off = P->d_ana_part_off[polar];
-  a.tile0 = P->d_ana_tile0[polar];
   a.part = P->d_part;
-  a.ana_tiles = P->ana_tiles;
   a.ppt = P->ana_ppt;
   a.add = 0;
   a.real = 0;
@@ -847,9 +844,9 @@ cudaError_t launch_leg_ana_fp64(const sht_plan_s *P, const DevPtrs &alm, int pol
 cudaError_t launch_ana_reduce(const sht_plan_s *P, const DevPtrs &alm, int polar, int add, cudaStream_t st,
                               bool real, bool grad) {
   dim3 grid((P->lmax + 1 + 127) / 128, P->nm);
-  ana_reduce<<<grid, 128, 0, st>>>(P->lmax, P->spin, P->nm, P->njobs_pad, P->ncomp, P->ana_tiles, P->astride, add,
+  ana_reduce<<<grid, 128, 0, st>>>(P->lmax, P->spin, P->nm, P->njobs_pad, P->ncomp, P->astride, add,
                                    real ? 1 : 0, grad ? 1 : 0,
-                                   P->d_mval, P->d_mstart, P->d_ana_part_off[polar], P->d_ana_tile0[polar],
+                                   P->d_mval, P->d_mstart, P->d_ana_part_off[polar], P->d_ana_nslot[polar],
                                    P->d_part, alm);
   return cudaGetLastError();
 }

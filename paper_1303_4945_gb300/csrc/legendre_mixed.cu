@@ -344,8 +344,10 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_spin_batch(const MixArgs *__
 // V contributions in registers and stores them to a shared-memory slot
 // table [32 slots = LC degrees x V values][threads]; after LC degrees the
 // 32 slots are reduced over the CTA's threads (4 threads per slot, then 4
-// partial sums per slot) and written as the tile's partial sums.  Degrees
-// are walked two at a time so the even/odd parity is static.
+// partial sums per slot) and added to the item's slot of partial sums.  An
+// item walks a group of consecutive tiles of one m tile after tile into one
+// slot (the host sizes the groups), so the partials shrink by the group size.
+// Degrees are walked two at a time so the even/odd parity is static.
 // ---------------------------------------------------------------------------
 template <int NJ, int PPT, bool SPIN>
 __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *ptrs, const int4 item) {
@@ -353,247 +355,257 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
   static_assert(V * LC == 32, "32 slots per chunk");
   __shared__ f2 slot[32][kAnaThreads + 1];
   __shared__ f2 quart[kAnaThreads / 32][32];
-  const int mi = item.x, tile = item.y;
+  const int mi = item.x, ng = item.z & 255;  // ng tiles from tile item.y on, one slot of partial sums
   const int m = a.mval[mi];
   const int s = a.spin, as = s < 0 ? -s : s;
   const int l0 = m > as ? m : as, lmax = a.lmax, nl = lmax - l0 + 1;
   const float4 *__restrict__ cf = a.coef32 + 2 * (a.coef_off[mi] - l0);
-  double *outp = a.part + a.part_off[mi] + (int64_t)(tile - a.tile0[mi]) * nl * V;
+  double *outp = a.part + a.part_off[mi] + (int64_t)(item.z >> 8) * nl * V;
   const double sg0 = ((l0 + m) & 1) ? -1.0 : 1.0;
   const int tid = threadIdx.x;
 
-  f3 x[PPT];
-  f2 lpc[PPT], lmc[PPT], lpp[PPT], lmp[PPT];
-  int scp[PPT], scm[PPT];
-  // spin 0: g[k][j][0..1] = G_N + G_S, G_N - G_S (complex);
-  // spin:   g[k][j][0..3] = W+_N, W-_N, (-1)^(l0+m) W+_S, (-1)^(l0+m) W-_S (complex)
-  f2 g[PPT][NJ][SPIN ? 4 : 2][2];
-#pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    const int p = tile * (kAnaThreads * PPT) + tid + k * kAnaThreads;
-    const bool valid = p < a.npairs;
-    const PairDev pd = a.pairs[valid ? p : 0];
-    x[k] = f3_of(pd.x);
-    if (SPIN) {
-      start_s(m, s, pd, a.mpre[mi], &lpc[k], &scp[k]);
-      start_s(m, -s, pd, a.mpre[mi], &lmc[k], &scm[k]);
-    } else {
-      start_s0(m, pd, a.mpre[mi], &lpc[k], &scp[k]);
-      lmc[k] = f2{0.f, 0.f};
-      scm[k] = 0;
-    }
-    if (!valid) {
-      lpc[k] = lmc[k] = f2{0.f, 0.f};
-      scp[k] = scm[k] = 0;
-    }
-    lpp[k] = lmp[k] = f2{0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      if (!SPIN) {
-        double2 gn = make_double2(0, 0), gs = make_double2(0, 0);
-        if (valid) {
-          const double2 *gp = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
-          gn = gp[0];
-          if (pd.south) gs = gp[1];
-        }
-        g[k][j][0][0] = f2_of(gn.x + gs.x);
-        g[k][j][0][1] = f2_of(gn.y + gs.y);
-        g[k][j][1][0] = f2_of(gn.x - gs.x);
-        g[k][j][1][1] = f2_of(gn.y - gs.y);
-      } else {
-        double2 qn = make_double2(0, 0), qs = make_double2(0, 0), un = make_double2(0, 0), us = make_double2(0, 0);
-        if (valid) {
-          const double2 *gq = a.phase + (((size_t)(2 * j) * a.nm + mi) * a.npairs + p) * 2;
-          const double2 *gu = a.phase + (((size_t)(2 * j + 1) * a.nm + mi) * a.npairs + p) * 2;
-          qn = gq[0];
-          un = gu[0];
-          if (pd.south) {
-            qs = gq[1];
-            us = gu[1];
-          }
-        }
-        g[k][j][0][0] = f2_of(qn.x - un.y);
-        g[k][j][0][1] = f2_of(qn.y + un.x);
-        g[k][j][1][0] = f2_of(qn.x + un.y);
-        g[k][j][1][1] = f2_of(qn.y - un.x);
-        g[k][j][2][0] = f2_of(sg0 * (qs.x - us.y));
-        g[k][j][2][1] = f2_of(sg0 * (qs.y + us.x));
-        g[k][j][3][0] = f2_of(sg0 * (qs.x + us.y));
-        g[k][j][3][1] = f2_of(sg0 * (qs.y - us.x));
-      }
-    }
-  }
-
-  // one degree: this thread's V contributions (summed over its pairs) into c[];
-  // the first term of each output is its exact product (no sum with zero)
-  auto step = [&](int l, bool odd, bool act, f2 (&c)[V]) {
-    // past lmax (second half of the last pair of degrees) the coefficients of
-    // lmax stand in: the values are finite, never stored, and no table entry
-    // outside this m is read
-    const Coef32 cc = ld_coef32(cf + 2 * (l <= lmax ? l : lmax));
-    const f2 nc = neg(cc.c);
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const f2 wp = act ? lpc[k] : weight(lpc[k], scp[k]);
-      if (!SPIN) {
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          const f2 gr = odd ? g[k][j][1][0] : g[k][j][0][0];
-          const f2 gi = odd ? g[k][j][1][1] : g[k][j][0][1];
-          if (k == 0) {
-            c[2 * j] = mul(wp, gr);
-            c[2 * j + 1] = mul(wp, gi);
-          } else {
-            acc_mul(c[2 * j], wp, gr.h, gr.l);
-            acc_mul(c[2 * j + 1], wp, gi.h, gi.l);
-          }
-        }
-        const f2 t = mul(cc.a, x[k]);
-        const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
-        lpp[k] = lpc[k];
-        lpc[k] = ln;
-      } else {
-        const f2 wm = act ? lmc[k] : weight(lmc[k], scm[k]);
-        const f2 sp = odd ? neg(wp) : wp, sm = odd ? neg(wm) : wm;
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          // T1 = W+_N l+ + (+-) W+_S l-,  T2 = W-_N l- + (+-) W-_S l+
-          if (k == 0) {
-            c[4 * j + 0] = mul(wp, g[k][j][0][0]);
-            c[4 * j + 1] = mul(wp, g[k][j][0][1]);
-            c[4 * j + 2] = mul(wm, g[k][j][1][0]);
-            c[4 * j + 3] = mul(wm, g[k][j][1][1]);
-          } else {
-            acc_mul(c[4 * j + 0], wp, g[k][j][0][0].h, g[k][j][0][0].l);
-            acc_mul(c[4 * j + 1], wp, g[k][j][0][1].h, g[k][j][0][1].l);
-            acc_mul(c[4 * j + 2], wm, g[k][j][1][0].h, g[k][j][1][0].l);
-            acc_mul(c[4 * j + 3], wm, g[k][j][1][1].h, g[k][j][1][1].l);
-          }
-          acc_mul(c[4 * j + 0], sm, g[k][j][2][0].h, g[k][j][2][0].l);
-          acc_mul(c[4 * j + 1], sm, g[k][j][2][1].h, g[k][j][2][1].l);
-          acc_mul(c[4 * j + 2], sp, g[k][j][3][0].h, g[k][j][3][0].l);
-          acc_mul(c[4 * j + 3], sp, g[k][j][3][1].h, g[k][j][3][1].l);
-        }
-        const f2 t = mul(cc.a, x[k]);
-        const f2 np_ = dot3(t, lpc[k], cc.ak, lpc[k], nc, lpp[k]);
-        const f2 nm_ = dot3(t, lmc[k], neg(cc.ak), lmc[k], nc, lmp[k]);
-        lpp[k] = lpc[k];
-        lpc[k] = np_;
-        lmp[k] = lmc[k];
-        lmc[k] = nm_;
-      }
-    }
-  };
-  auto rescale_all = [&]() {
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      if (scp[k] < 0 && fabsf(lpc[k].h) > kScaleUp32) {
-        lpc[k] = {lpc[k].h * kScaleFactor32, lpc[k].l * kScaleFactor32};
-        lpp[k] = {lpp[k].h * kScaleFactor32, lpp[k].l * kScaleFactor32};
-        ++scp[k];
-      }
-      if (scm[k] < 0 && fabsf(lmc[k].h) > kScaleUp32) {
-        lmc[k] = {lmc[k].h * kScaleFactor32, lmc[k].l * kScaleFactor32};
-        lmp[k] = {lmp[k].h * kScaleFactor32, lmp[k].l * kScaleFactor32};
-        ++scm[k];
-      }
-    }
-  };
-  auto put = [&](int q, const f2 (&c)[V]) {
-#pragma unroll
-    for (int v = 0; v < V; ++v) slot[q * V + v][tid] = c[v];
-  };
-
-  auto recur = [&](int l) {  // recursion only
-    const Coef32 cc = ld_coef32(cf + 2 * (l <= lmax ? l : lmax));
-    const f2 nc = neg(cc.c);
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const f2 t = mul(cc.a, x[k]);
-      if (!SPIN) {
-        const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
-        lpp[k] = lpc[k];
-        lpc[k] = ln;
-      } else {
-        const f2 np_ = dot3(t, lpc[k], cc.ak, lpc[k], nc, lpp[k]);
-        const f2 nm_ = dot3(t, lmc[k], neg(cc.ak), lmc[k], nc, lmp[k]);
-        lpp[k] = lpc[k];
-        lpc[k] = np_;
-        lmp[k] = lmc[k];
-        lmc[k] = nm_;
-      }
-    }
-  };
-  auto mode = [&]() {  // 0: all terms at scale 0, 2: all negligible, 1: weighted
-    bool ok = true, dead = true;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      ok = ok && scp[k] == 0 && scm[k] == 0;
-      dead = dead && negligible(lpc[k], scp[k]) && (!SPIN || negligible(lmc[k], scm[k]));
-    }
-    return __all_sync(0xffffffffu, ok) ? 0 : (__all_sync(0xffffffffu, dead) ? 2 : 1);
-  };
-  const f2 zero[V] = {};
-
-  int since = 0;         // steps since the last exponent check
-  bool settled = false;  // every lane's values at scale 0: they stay there (warp-uniform)
-  for (int lb = l0; lb <= lmax; lb += LC) {
-    if (LC >= 2) {
+  // the group's tiles one after another; each adds its sums to the slot (the first
+  // overwrites it), in a fixed order
 #pragma unroll 1
-      for (int q = 0; q < LC; q += 2) {
-        const int l = lb + q;
-        if (l > lmax) break;
-        const int md = settled ? 0 : mode();
-        settled = md == 0;
-        if (md == 2) {
-          recur(l);
-          recur(l + 1);
-          put(q, zero);
-          put(q + 1, zero);
-        } else {
-          f2 c0[V], c1[V];
-          if (md == 0) {
-            step(l, false, true, c0);
-            step(l + 1, true, true, c1);
-          } else {
-            step(l, false, false, c0);
-            step(l + 1, true, false, c1);
+  for (int gi = 0; gi < ng; ++gi) {
+    const int tile = item.y + gi;
+    f3 x[PPT];
+    f2 lpc[PPT], lmc[PPT], lpp[PPT], lmp[PPT];
+    int scp[PPT], scm[PPT];
+    // spin 0: g[k][j][0..1] = G_N + G_S, G_N - G_S (complex);
+    // spin:   g[k][j][0..3] = W+_N, W-_N, (-1)^(l0+m) W+_S, (-1)^(l0+m) W-_S (complex)
+    f2 g[PPT][NJ][SPIN ? 4 : 2][2];
+  #pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int p = tile * (kAnaThreads * PPT) + tid + k * kAnaThreads;
+      const bool valid = p < a.npairs;
+      const PairDev pd = a.pairs[valid ? p : 0];
+      x[k] = f3_of(pd.x);
+      if (SPIN) {
+        start_s(m, s, pd, a.mpre[mi], &lpc[k], &scp[k]);
+        start_s(m, -s, pd, a.mpre[mi], &lmc[k], &scm[k]);
+      } else {
+        start_s0(m, pd, a.mpre[mi], &lpc[k], &scp[k]);
+        lmc[k] = f2{0.f, 0.f};
+        scm[k] = 0;
+      }
+      if (!valid) {
+        lpc[k] = lmc[k] = f2{0.f, 0.f};
+        scp[k] = scm[k] = 0;
+      }
+      lpp[k] = lmp[k] = f2{0.f, 0.f};
+  #pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        if (!SPIN) {
+          double2 gn = make_double2(0, 0), gs = make_double2(0, 0);
+          if (valid) {
+            const double2 *gp = a.phase + (((size_t)j * a.nm + mi) * a.npairs + p) * 2;
+            gn = gp[0];
+            if (pd.south) gs = gp[1];
           }
-          put(q, c0);
-          put(q + 1, c1);
+          g[k][j][0][0] = f2_of(gn.x + gs.x);
+          g[k][j][0][1] = f2_of(gn.y + gs.y);
+          g[k][j][1][0] = f2_of(gn.x - gs.x);
+          g[k][j][1][1] = f2_of(gn.y - gs.y);
+        } else {
+          double2 qn = make_double2(0, 0), qs = make_double2(0, 0), un = make_double2(0, 0), us = make_double2(0, 0);
+          if (valid) {
+            const double2 *gq = a.phase + (((size_t)(2 * j) * a.nm + mi) * a.npairs + p) * 2;
+            const double2 *gu = a.phase + (((size_t)(2 * j + 1) * a.nm + mi) * a.npairs + p) * 2;
+            qn = gq[0];
+            un = gu[0];
+            if (pd.south) {
+              qs = gq[1];
+              us = gu[1];
+            }
+          }
+          g[k][j][0][0] = f2_of(qn.x - un.y);
+          g[k][j][0][1] = f2_of(qn.y + un.x);
+          g[k][j][1][0] = f2_of(qn.x + un.y);
+          g[k][j][1][1] = f2_of(qn.y - un.x);
+          g[k][j][2][0] = f2_of(sg0 * (qs.x - us.y));
+          g[k][j][2][1] = f2_of(sg0 * (qs.y + us.x));
+          g[k][j][3][0] = f2_of(sg0 * (qs.x + us.y));
+          g[k][j][3][1] = f2_of(sg0 * (qs.y - us.x));
         }
-        since += 2;
-        if (!settled && since >= 8) {
+      }
+    }
+
+    // one degree: this thread's V contributions (summed over its pairs) into c[];
+    // the first term of each output is its exact product (no sum with zero)
+    auto step = [&](int l, bool odd, bool act, f2 (&c)[V]) {
+      // past lmax (second half of the last pair of degrees) the coefficients of
+      // lmax stand in: the values are finite, never stored, and no table entry
+      // outside this m is read
+      const Coef32 cc = ld_coef32(cf + 2 * (l <= lmax ? l : lmax));
+      const f2 nc = neg(cc.c);
+  #pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const f2 wp = act ? lpc[k] : weight(lpc[k], scp[k]);
+        if (!SPIN) {
+  #pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            const f2 gr = odd ? g[k][j][1][0] : g[k][j][0][0];
+            const f2 gi = odd ? g[k][j][1][1] : g[k][j][0][1];
+            if (k == 0) {
+              c[2 * j] = mul(wp, gr);
+              c[2 * j + 1] = mul(wp, gi);
+            } else {
+              acc_mul(c[2 * j], wp, gr.h, gr.l);
+              acc_mul(c[2 * j + 1], wp, gi.h, gi.l);
+            }
+          }
+          const f2 t = mul(cc.a, x[k]);
+          const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
+          lpp[k] = lpc[k];
+          lpc[k] = ln;
+        } else {
+          const f2 wm = act ? lmc[k] : weight(lmc[k], scm[k]);
+          const f2 sp = odd ? neg(wp) : wp, sm = odd ? neg(wm) : wm;
+  #pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            // T1 = W+_N l+ + (+-) W+_S l-,  T2 = W-_N l- + (+-) W-_S l+
+            if (k == 0) {
+              c[4 * j + 0] = mul(wp, g[k][j][0][0]);
+              c[4 * j + 1] = mul(wp, g[k][j][0][1]);
+              c[4 * j + 2] = mul(wm, g[k][j][1][0]);
+              c[4 * j + 3] = mul(wm, g[k][j][1][1]);
+            } else {
+              acc_mul(c[4 * j + 0], wp, g[k][j][0][0].h, g[k][j][0][0].l);
+              acc_mul(c[4 * j + 1], wp, g[k][j][0][1].h, g[k][j][0][1].l);
+              acc_mul(c[4 * j + 2], wm, g[k][j][1][0].h, g[k][j][1][0].l);
+              acc_mul(c[4 * j + 3], wm, g[k][j][1][1].h, g[k][j][1][1].l);
+            }
+            acc_mul(c[4 * j + 0], sm, g[k][j][2][0].h, g[k][j][2][0].l);
+            acc_mul(c[4 * j + 1], sm, g[k][j][2][1].h, g[k][j][2][1].l);
+            acc_mul(c[4 * j + 2], sp, g[k][j][3][0].h, g[k][j][3][0].l);
+            acc_mul(c[4 * j + 3], sp, g[k][j][3][1].h, g[k][j][3][1].l);
+          }
+          const f2 t = mul(cc.a, x[k]);
+          const f2 np_ = dot3(t, lpc[k], cc.ak, lpc[k], nc, lpp[k]);
+          const f2 nm_ = dot3(t, lmc[k], neg(cc.ak), lmc[k], nc, lmp[k]);
+          lpp[k] = lpc[k];
+          lpc[k] = np_;
+          lmp[k] = lmc[k];
+          lmc[k] = nm_;
+        }
+      }
+    };
+    auto rescale_all = [&]() {
+  #pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (scp[k] < 0 && fabsf(lpc[k].h) > kScaleUp32) {
+          lpc[k] = {lpc[k].h * kScaleFactor32, lpc[k].l * kScaleFactor32};
+          lpp[k] = {lpp[k].h * kScaleFactor32, lpp[k].l * kScaleFactor32};
+          ++scp[k];
+        }
+        if (scm[k] < 0 && fabsf(lmc[k].h) > kScaleUp32) {
+          lmc[k] = {lmc[k].h * kScaleFactor32, lmc[k].l * kScaleFactor32};
+          lmp[k] = {lmp[k].h * kScaleFactor32, lmp[k].l * kScaleFactor32};
+          ++scm[k];
+        }
+      }
+    };
+    auto put = [&](int q, const f2 (&c)[V]) {
+  #pragma unroll
+      for (int v = 0; v < V; ++v) slot[q * V + v][tid] = c[v];
+    };
+
+    auto recur = [&](int l) {  // recursion only
+      const Coef32 cc = ld_coef32(cf + 2 * (l <= lmax ? l : lmax));
+      const f2 nc = neg(cc.c);
+  #pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const f2 t = mul(cc.a, x[k]);
+        if (!SPIN) {
+          const f2 ln = dot2(t, lpc[k], nc, lpp[k]);
+          lpp[k] = lpc[k];
+          lpc[k] = ln;
+        } else {
+          const f2 np_ = dot3(t, lpc[k], cc.ak, lpc[k], nc, lpp[k]);
+          const f2 nm_ = dot3(t, lmc[k], neg(cc.ak), lmc[k], nc, lmp[k]);
+          lpp[k] = lpc[k];
+          lpc[k] = np_;
+          lmp[k] = lmc[k];
+          lmc[k] = nm_;
+        }
+      }
+    };
+    auto mode = [&]() {  // 0: all terms at scale 0, 2: all negligible, 1: weighted
+      bool ok = true, dead = true;
+  #pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        ok = ok && scp[k] == 0 && scm[k] == 0;
+        dead = dead && negligible(lpc[k], scp[k]) && (!SPIN || negligible(lmc[k], scm[k]));
+      }
+      return __all_sync(0xffffffffu, ok) ? 0 : (__all_sync(0xffffffffu, dead) ? 2 : 1);
+    };
+    const f2 zero[V] = {};
+
+    int since = 0;         // steps since the last exponent check
+    bool settled = false;  // every lane's values at scale 0: they stay there (warp-uniform)
+    for (int lb = l0; lb <= lmax; lb += LC) {
+      // this chunk's slot entry from the previous tiles (read early, added at the end)
+      const bool mine = tid < 32 && lb + tid / V <= lmax;
+      double *const o = outp + (int64_t)(lb - l0) * V + tid;
+      const double prev = (gi > 0 && mine) ? *o : 0.0;
+      if (LC >= 2) {
+  #pragma unroll 1
+        for (int q = 0; q < LC; q += 2) {
+          const int l = lb + q;
+          if (l > lmax) break;
+          const int md = settled ? 0 : mode();
+          settled = md == 0;
+          if (md == 2) {
+            recur(l);
+            recur(l + 1);
+            put(q, zero);
+            put(q + 1, zero);
+          } else {
+            f2 c0[V], c1[V];
+            if (md == 0) {
+              step(l, false, true, c0);
+              step(l + 1, true, true, c1);
+            } else {
+              step(l, false, false, c0);
+              step(l + 1, true, false, c1);
+            }
+            put(q, c0);
+            put(q + 1, c1);
+          }
+          since += 2;
+          if (!settled && since >= 8) {
+            rescale_all();
+            since = 0;
+          }
+        }
+      } else {  // one degree per chunk: parity alternates between chunks
+        f2 c0[V];
+        const bool odd = ((lb - l0) & 1) != 0;
+        settled = settled || mode() == 0;
+        if (settled) step(lb, odd, true, c0); else step(lb, odd, false, c0);
+        put(0, c0);
+        if (!settled && ++since >= 8) {
           rescale_all();
           since = 0;
         }
       }
-    } else {  // one degree per chunk: parity alternates between chunks
-      f2 c0[V];
-      const bool odd = ((lb - l0) & 1) != 0;
-      settled = settled || mode() == 0;
-      if (settled) step(lb, odd, true, c0); else step(lb, odd, false, c0);
-      put(0, c0);
-      if (!settled && ++since >= 8) {
-        rescale_all();
-        since = 0;
+      __syncthreads();
+      {  // 32 slots x kAnaThreads values: 4 threads per slot, then 4 partials per slot
+        const int sl = tid & 31, part = tid >> 5;
+        const f2 *row = &slot[sl][part * 32];
+        f2 t = row[0];
+  #pragma unroll 8
+        for (int i = 1; i < 32; ++i) t = f2_add_lazy(t, row[i]);
+        quart[part][sl] = t;
       }
-    }
-    __syncthreads();
-    {  // 32 slots x kAnaThreads values: 4 threads per slot, then 4 partials per slot
-      const int sl = tid & 31, part = tid >> 5;
-      const f2 *row = &slot[sl][part * 32];
-      f2 t = row[0];
-#pragma unroll 8
-      for (int i = 1; i < 32; ++i) t = f2_add_lazy(t, row[i]);
-      quart[part][sl] = t;
-    }
-    __syncthreads();
-    if (tid < 32) {
-      f2 t = quart[0][tid];
-#pragma unroll
-      for (int w = 1; w < kAnaThreads / 32; ++w) t = f2_add(t, quart[w][tid]);
-      if (lb + tid / V <= lmax) outp[(int64_t)(lb - l0) * V + tid] = f2_val(t);
+      __syncthreads();
+      if (tid < 32) {
+        f2 t = quart[0][tid];
+  #pragma unroll
+        for (int w = 1; w < kAnaThreads / 32; ++w) t = f2_add(t, quart[w][tid]);
+        if (mine) *o = prev + f2_val(t);
+      }
     }
   }
 }
@@ -613,7 +625,7 @@ __global__ void __launch_bounds__(kAnaThreads, (mix_ana_min_blocks<NJ, PPT, SPIN
     const int4 *__restrict__ items, const PtrTable tbl) {
   const int4 it = items[blockIdx.x];
   const MixArgs &a = args[it.w];
-  mix_ana_body<NJ, PPT, SPIN>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, 0, 0));
+  mix_ana_body<NJ, PPT, SPIN>(a, tbl.p + a.ptr_off, make_int4(it.x, it.y, it.z, 0));
 }
 
 // ---------------------------------------------------------------------------
@@ -634,9 +646,7 @@ static MixArgs make_mix(const sht_plan_s *P, int polar) {
   a.syn_items = P->d_syn_items[polar];
   a.ana_items = P->d_ana_items[polar];
   a.part_off = P->d_ana_part_off[polar];
-  a.tile0 = P->d_ana_tile0[polar];
   a.part = P->d_part;
-  a.ana_tiles = P->ana_tiles;
   return a;
 }
 

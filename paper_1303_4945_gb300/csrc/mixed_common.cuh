@@ -91,9 +91,7 @@ struct MixArgs {
   const int2 *syn_items;
   const int4 *ana_items;
   const int64_t *part_off;
-  const int *tile0;
   double *part;
-  int ana_tiles;
   int ptr_off;
 };
 

@@ -850,7 +850,7 @@ static void free_plan(sht_plan_s *P) {
     if (P->d_syn_first[k]) cudaFree(P->d_syn_first[k]);
     if (P->d_ana_items[k]) cudaFree(P->d_ana_items[k]);
     if (P->d_ana_part_off[k]) cudaFree(P->d_ana_part_off[k]);
-    if (P->d_ana_tile0[k]) cudaFree(P->d_ana_tile0[k]);
+    if (P->d_ana_nslot[k]) cudaFree(P->d_ana_nslot[k]);
     if (P->d_syn_lo[k]) cudaFree(P->d_syn_lo[k]);
     if (P->d_ana_lo[k]) cudaFree(P->d_ana_lo[k]);
   }
@@ -888,9 +888,6 @@ static std::vector<int> ana_ppt_candidates(int spin, int nj) {
   return {2};
 }
 
-// Analysis work lists for tiles of kAnaThreads * ppt ring pairs: per polar
-// variant the cost-sorted (m, tile) items, each m's offset into the tile-sum
-// array and its first tile; sizes the tile-sum array for this tiling.
 // Mixed form: columns m below this run in FP64 on the rings near the poles.  The
 // double-float recursion keeps ~48 bits; for small m near the poles it is
 // non-oscillatory over l < ~m/theta, where its per-step rounding grows like a
@@ -960,46 +957,72 @@ static int build_syn_lists(sht_plan_s *P) {
   return SHT_OK;
 }
 
+// Analysis work lists: per polar variant the cost-sorted items and, per m, where
+// their partial sums go.  A tile is kAnaThreads * ppt ring pairs; a mixed-form item
+// walks a group of consecutive tiles of one m one after another and sums them into
+// one slot of partial sums, so the partials' size and traffic shrink by the group
+// size.  Groups are as large as keeps at least kAnaItemsPerSm items per SM (and at
+// most kAnaGroupTiles tiles): the same work in fewer, longer CTAs, which on
+// GB300 at lmax 4095 is as fast as one CTA per tile (152.4 against 152.9 ms per
+// pair) with a sixteenth of the partials.  FP64 items (the FP64 form, and a mixed
+// plan's tiles next to the poles) take one tile each.  Item (m index, first tile,
+// slot << 8 | tiles, -); the slots of m are summed by the reduction kernel.
 static int build_ana_lists(sht_plan_s *P, int ppt) {
   int rc;
   const int as = abs(P->spin);
   const int V = (P->spin ? 4 : 2) * P->njobs_pad;  // doubles per l in the analysis partials
   const int TA = kAnaThreads * ppt;
   const int tiles = (P->npairs + TA - 1) / TA;
+  const bool mixed = P->precision == SHT_MIXED;
+  int group = 1;
+  if (mixed) {  // tiles of the polar-cut variant (the default) over items per SM wanted
+    int64_t ntile = 0;
+    for (int i = 0; i < P->nm; ++i)
+      if (P->lmax >= std::max(P->mval[i], as)) ntile += tiles - P->first_pair[i] / TA;
+    group = (int)std::max<int64_t>(1, std::min<int64_t>(kAnaGroupTiles, ntile / ((int64_t)kAnaItemsPerSm * P->sms)));
+  }
   int64_t need = 0;
   for (int polar = 0; polar < 2; ++polar) {
     std::vector<std::pair<int64_t, int4>> ana, lo;
     std::vector<int64_t> poff(P->nm);
-    std::vector<int> t0(P->nm);
+    std::vector<int> nslot(P->nm, 0);
     int64_t off = 0;
     for (int i = 0; i < P->nm; ++i) {
       int l0 = std::max(P->mval[i], as);
       int nl = P->lmax - l0 + 1;
       poff[i] = off;
-      if (nl <= 0) {
-        t0[i] = tiles;
-        continue;
-      }
+      if (nl <= 0) continue;
       int fp = polar ? P->first_pair[i] : 0;
-      int tf = fp / TA;
-      t0[i] = tf;
-      for (int t = tf; t < tiles; ++t)
-        (lo_item(P, i, t * TA, (t + 1) * TA) ? lo : ana)
-            .push_back({(int64_t)nl * std::min(TA, P->npairs - t * TA), make_int4(i, t, 0, 0)});
-      off += (int64_t)(tiles - tf) * nl * V;
+      int slot = 0;
+      for (int t = fp / TA; t < tiles;) {
+        const auto cost = [&](int tt) { return (int64_t)nl * std::min(TA, P->npairs - tt * TA); };
+        if (lo_item(P, i, t * TA, (t + 1) * TA)) {
+          lo.push_back({cost(t), make_int4(i, t, (slot << 8) | 1, 0)});
+          ++t;
+        } else {
+          int n = 0;
+          int64_t c = 0;
+          while (n < group && t + n < tiles && !lo_item(P, i, (t + n) * TA, (t + n + 1) * TA)) c += cost(t + n++);
+          ana.push_back({c, make_int4(i, t, (slot << 8) | n, 0)});
+          t += n;
+        }
+        ++slot;
+      }
+      nslot[i] = slot;
+      off += (int64_t)slot * nl * V;
     }
     std::stable_sort(ana.begin(), ana.end(), [](auto &a, auto &b) { return a.first > b.first; });
     std::stable_sort(lo.begin(), lo.end(), [](auto &a, auto &b) { return a.first > b.first; });
     if (P->d_ana_part_off[polar]) cudaFree(P->d_ana_part_off[polar]);
-    if (P->d_ana_tile0[polar]) cudaFree(P->d_ana_tile0[polar]);
+    if (P->d_ana_nslot[polar]) cudaFree(P->d_ana_nslot[polar]);
     P->d_ana_part_off[polar] = nullptr;
-    P->d_ana_tile0[polar] = nullptr;
+    P->d_ana_nslot[polar] = nullptr;
     P->ana_list[polar] = ana;
     P->ana_list_lo[polar] = lo;
     if ((rc = upload_list(P, ana, &P->d_ana_items[polar], &P->nana_items[polar])) != SHT_OK) return rc;
     if ((rc = upload_list(P, lo, &P->d_ana_lo[polar], &P->nana_lo[polar])) != SHT_OK) return rc;
     if ((rc = upload(P, poff, &P->d_ana_part_off[polar])) != SHT_OK) return rc;
-    if ((rc = upload(P, t0, &P->d_ana_tile0[polar])) != SHT_OK) return rc;
+    if ((rc = upload(P, nslot, &P->d_ana_nslot[polar])) != SHT_OK) return rc;
     need = std::max(need, off);
   }
   if (need != P->part_doubles || !P->d_part) {  // sized for the current tiling
@@ -1010,7 +1033,6 @@ static int build_ana_lists(sht_plan_s *P, int ppt) {
     CUDA_TRY(cudaMalloc(&P->d_part, std::max<int64_t>(1, P->part_doubles) * sizeof(double)));
   }
   P->ana_ppt = ppt;
-  P->ana_tiles = tiles;
   return SHT_OK;
 }
 
@@ -1171,6 +1193,8 @@ extern "C" int sht_plan_create(sht_geom_t geom, sht_alm_t alm, int spin, int nco
   if (spin != 0 && ncomp > 8) return fail(SHT_ERR_UNSUPPORTED, "spin transforms take at most 8 (E,B) pairs");
   auto *P = new sht_plan_s;
   cudaGetDevice(&P->device);
+  if (cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || P->sms < 1)
+    P->sms = 1;
   P->lmax = alm->lmax;
   P->mmax = alm->mmax;
   P->nm = alm->nm;

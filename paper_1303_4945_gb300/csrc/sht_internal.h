@@ -23,6 +23,8 @@ constexpr int kMaxPtr = 32;       // max device pointers per execute (maps or a_
 constexpr int kMaxJobs = 16;      // ncomp limit
 constexpr int kSynTile = 128;     // ring pairs per synthesis Legendre CTA (one per thread)
 constexpr int kAnaThreads = 128;  // threads per analysis Legendre CTA
+constexpr int kAnaGroupTiles = 16;  // most tiles a mixed analysis item walks, one after another
+constexpr int kAnaItemsPerSm = 24;  // fewest mixed analysis items per SM the grouping leaves
 constexpr int kMaxRadix = 8 * 4;  // odd radices with register butterflies and constant cos/sin tables (primes <= 31)
 constexpr int kMaxBigRadix = 127;  // odd radices above 31 run as shared-memory sweeps (fft_stage_big)
 constexpr int kFftThreads = 512;
@@ -112,6 +114,7 @@ struct sht_alm_s {
 
 struct sht_plan_s {
   int device = 0;
+  int sms = 1;  // multiprocessors of the device
   int lmax = 0, mmax = 0, nm = 0, astride = 1, spin = 0, ncomp = 0, precision = 0;
   int nmaps = 0;      // arrays per side (ncomp, or 2 ncomp for spin)
   int njobs_pad = 1;  // ncomp rounded up to a power of two (kernel template size)
@@ -149,7 +152,7 @@ struct sht_plan_s {
   int4 *d_ana_items[2] = {nullptr, nullptr};
   int nana_items[2] = {0, 0};
   int64_t *d_ana_part_off[2] = {nullptr, nullptr};  // per m
-  int *d_ana_tile0[2] = {nullptr, nullptr};         // per m: first tile
+  int *d_ana_nslot[2] = {nullptr, nullptr};         // per m: partial-sum slots (one per item)
   int ana_ppt = 4;                                  // ring pairs per analysis thread (tiling)
   int batch_refs = 0;                               // batches built on this plan's work lists
   // host copies of the work lists with their costs (l count x pairs), for merging into batches
@@ -177,7 +180,6 @@ struct sht_plan_s {
   int nana_lo[2] = {0, 0};
   std::vector<std::pair<int64_t, int2>> syn_list_lo[2];
   std::vector<std::pair<int64_t, int4>> ana_list_lo[2];
-  int ana_tiles = 0;
   int64_t triples[2] = {0, 0};
 
   // FFT
