@@ -361,18 +361,21 @@ MEASURED_TRAFFIC = {
     # one launch at the headline size (spin 2, GL 4096 x 8191, lmax 4095), single-pass
     # dram__bytes_read.sum + dram__bytes_write.sum (the pair's traffic capture under profiles/);
     # sha256 over the kernel file and its device headers (_kernel_digest)
-    "mixed:legendre_analysis": {"bytes": 662757632 + 3469790720,
-                                "sha256": "53d00b60195a345d0816673dac167f03e28d031c0fb00e7b7ce779cc0d6855b7"},
+    "mixed:legendre_analysis": {"bytes": 6031100928 + 3096419072,
+                                "sha256": "6613060a50cb3b90014a5034fab68cf6fae753b7ebf0ad1222f0db2d4717b087"},
+    "mixed:legendre_synthesis": {"bytes": 547940096 + 321448704,
+                                 "sha256": "f4a6478847d57b233bec85d901e63668b5778c5fee9ad5864eb67219c888e706"},
 }
 
 
 KERNEL_HEADERS = {"legendre_fp64.cu": ("sht_device.cuh",),
-                  "legendre_mixed.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh"),
+                  "legendre_mixed.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh", "sht_internal.h"),
                   "legendre_tc.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh")}
 
 
 def _kernel_digest(kernel_file):
-    """SHA-256 over the kernel's source file and the device headers it includes."""
+    """SHA-256 over the kernel's source file and the headers it includes (for the
+    analysis kernel also the one holding its work-list constants)."""
     import hashlib
     h = hashlib.sha256()
     for name in (kernel_file,) + KERNEL_HEADERS.get(kernel_file, ()):

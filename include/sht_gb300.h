@@ -289,15 +289,16 @@ SHT_API int sht_plan_get_fft_precision(sht_plan_t plan, int *precision);
  * plus an FP32 remainder (contracted on the CUDA cores); the a_lm are split into
  * five bf16 digits on a grid per 256 degrees; the digit products are summed in
  * FP32 accumulators where no rounding can occur, and the sums are added in
- * double-float.  Results agree with the double-float contraction to ~1e-13
- * relative (a term's error is below 2^-40 of the bound of its operands).
+ * double-float.  A term's error is below 2^-40 of the bound of its operands;
+ * at spin 2, lmax 4095 the maps agree with the FP64 form to 6.6e-12 relative
+ * (the double-float contraction: 2.1e-12).
  * Shapes: spin 0 with ncomp <= 8, spin s with ncomp <= 4 (SHT_ERR_UNSUPPORTED
  * otherwise).  It serves SHT_SYNTHESIS, SHT_ADJOINT_ANALYSIS and
  * SHT_DERIV_SYNTHESIS through sht_execute and sht_execute_noalloc, and is a
  * mixed plan's default for every supported shape except a single spin-0 map,
  * where the double-float contraction is faster (measured on GB300 at lmax 4095:
- * spin 2 one E/B pair 66.5 ms against 70.7, spin 0 eight maps 73.3 against 112.0,
- * spin 0 one map 32.1 against 25.6).  sht_plan_set_tensor_cores(plan, 1 or 0)
+ * spin 2 one E/B pair 62.0 ms against 70.7, spin 0 eight maps 75.2 against 112.3,
+ * spin 0 one map 29.4 against 25.6).  sht_plan_set_tensor_cores(plan, 1 or 0)
  * selects it or the double-float contraction; sht_plan_get_tensor_cores reads the
  * setting.  A batch runs each plan with the setting it had when the batch was
  * made (the setting cannot change while a batch refers to the plan).  Errors: SHT_ERR_INVALID_ARG (NULL, an

@@ -960,12 +960,15 @@ static int build_syn_lists(sht_plan_s *P) {
 // Analysis work lists: per polar variant the cost-sorted items and, per m, where
 // their partial sums go.  A tile is kAnaThreads * ppt ring pairs; a mixed-form item
 // walks a group of consecutive tiles of one m one after another and sums them into
-// one slot of partial sums, so the partials' size and traffic shrink by the group
-// size.  Groups are as large as keeps at least kAnaItemsPerSm items per SM (and at
-// most kAnaGroupTiles tiles): the same work in fewer, longer CTAs, which on
-// GB300 at lmax 4095 is as fast as one CTA per tile (152.4 against 152.9 ms per
-// pair) with a sixteenth of the partials.  FP64 items (the FP64 form, and a mixed
-// plan's tiles next to the poles) take one tile each.  Item (m index, first tile,
+// one slot of partial sums, so the partials' size shrinks by the group size (their
+// DRAM traffic only while the slots of the resident CTAs fit in L2).  Groups are
+// as large as keeps at least kAnaItemsPerSm items per SM (and at most
+// kAnaGroupTiles tiles): the same work in fewer, longer CTAs, which on
+// GB300 at lmax 4095 is as fast as one CTA per tile (152.5 against 153.0 ms per
+// pair) with a sixteenth of the partials; an 8-map plan's analysis kernel is 4.4
+// ms slower grouped, its slot reduction 6.6 ms faster (lmax 4095: 157.3 + 1.1
+// against 152.9 + 7.7 ms).  FP64 items (the FP64 form, and a mixed plan's tiles
+// next to the poles) take one tile each.  Item (m index, first tile,
 // slot << 8 | tiles, -); the slots of m are summed by the reduction kernel.
 static int build_ana_lists(sht_plan_s *P, int ppt) {
   int rc;
