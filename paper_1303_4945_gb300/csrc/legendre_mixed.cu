@@ -342,9 +342,11 @@ __global__ void __launch_bounds__(kSynTile) mix_syn_spin_batch(const MixArgs *__
 //
 // Each thread walks PPT ring pairs.  For every degree l it sums its pairs'
 // V contributions in registers and stores them to a shared-memory slot
-// table [32 slots = LC degrees x V values][threads]; after LC degrees the
-// 32 slots are reduced over the CTA's threads (4 threads per slot, then 4
-// partial sums per slot) and added to the item's slot of partial sums.  An
+// table [32 slots = LC degrees x V values][threads]; after LC degrees each warp
+// sums its own 32 columns of the table (a warp's columns are written and read by
+// that warp only: warp-level synchronisation), and after one CTA barrier warp 0
+// adds the four warps' partials (double-buffered by chunk parity) to the item's
+// slot of partial sums.  An
 // item walks a group of consecutive tiles of one m tile after tile into one
 // slot (the host sizes the groups), so the partials shrink by the group size.
 // Degrees are walked two at a time so the even/odd parity is static.
@@ -354,7 +356,7 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
   constexpr int V = (SPIN ? 4 : 2) * NJ, LC = 32 / V;
   static_assert(V * LC == 32, "32 slots per chunk");
   __shared__ f2 slot[32][kAnaThreads + 1];
-  __shared__ f2 quart[kAnaThreads / 32][32];
+  __shared__ f2 quart[2][kAnaThreads / 32][32];  // by chunk parity
   const int mi = item.x, ng = item.z & 255;  // ng tiles from tile item.y on, one slot of partial sums
   const int m = a.mval[mi];
   const int s = a.spin, as = s < 0 ? -s : s;
@@ -544,6 +546,7 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
 
     int since = 0;         // steps since the last exponent check
     bool settled = false;  // every lane's values at scale 0: they stay there (warp-uniform)
+    int cb = 0;            // chunk parity: the quart buffer
     for (int lb = l0; lb <= lmax; lb += LC) {
       // this chunk's slot entry from the previous tiles (read early, added at the end)
       const bool mine = tid < 32 && lb + tid / V <= lmax;
@@ -590,22 +593,28 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
           since = 0;
         }
       }
-      __syncthreads();
-      {  // 32 slots x kAnaThreads values: 4 threads per slot, then 4 partials per slot
+      // a warp's slot columns are written and read by that warp only: warp-level sync
+      __syncwarp();
+      {  // 32 slots x kAnaThreads values: each warp sums its own 32 columns, then 4 partials per slot
         const int sl = tid & 31, part = tid >> 5;
         const f2 *row = &slot[sl][part * 32];
         f2 t = row[0];
   #pragma unroll 8
         for (int i = 1; i < 32; ++i) t = f2_add_lazy(t, row[i]);
-        quart[part][sl] = t;
+        quart[cb][part][sl] = t;
       }
+      __syncwarp();
+      // one barrier per chunk: quart is double-buffered, so warp 0 reads this chunk's
+      // partials while the others fill the other buffer, and it has read them before
+      // it reaches the next barrier, after which this buffer is written again
       __syncthreads();
       if (tid < 32) {
-        f2 t = quart[0][tid];
+        f2 t = quart[cb][0][tid];
   #pragma unroll
-        for (int w = 1; w < kAnaThreads / 32; ++w) t = f2_add(t, quart[w][tid]);
+        for (int w = 1; w < kAnaThreads / 32; ++w) t = f2_add(t, quart[cb][w][tid]);
         if (mine) *o = prev + f2_val(t);
       }
+      cb ^= 1;
     }
   }
 }
