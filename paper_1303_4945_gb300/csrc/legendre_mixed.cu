@@ -357,6 +357,7 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
   static_assert(V * LC == 32, "32 slots per chunk");
   __shared__ f2 slot[32][kAnaThreads + 1];
   __shared__ f2 quart[2][kAnaThreads / 32][32];  // by chunk parity
+  __shared__ int tstart[2][kAnaThreads / 32];     // per tile (parity): the warps' earliest join degree
   const int mi = item.x, ng = item.z & 255;  // ng tiles from tile item.y on, one slot of partial sums
   const int m = a.mval[mi];
   const int s = a.spin, as = s < 0 ? -s : s;
@@ -374,28 +375,22 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
     f3 x[PPT];
     f2 lpc[PPT], lmc[PPT], lpp[PPT], lmp[PPT];
     int scp[PPT], scm[PPT];
+    // the degree at which each pair's terms start (join record; zero state until then)
+    int lj[PPT];
     // spin 0: g[k][j][0..1] = G_N + G_S, G_N - G_S (complex);
     // spin:   g[k][j][0..3] = W+_N, W-_N, (-1)^(l0+m) W+_S, (-1)^(l0+m) W-_S (complex)
     f2 g[PPT][NJ][SPIN ? 4 : 2][2];
+    int jmin = lmax + 1;
   #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int p = tile * (kAnaThreads * PPT) + tid + k * kAnaThreads;
       const bool valid = p < a.npairs;
       const PairDev pd = a.pairs[valid ? p : 0];
       x[k] = f3_of(pd.x);
-      if (SPIN) {
-        start_s(m, s, pd, a.mpre[mi], &lpc[k], &scp[k]);
-        start_s(m, -s, pd, a.mpre[mi], &lmc[k], &scm[k]);
-      } else {
-        start_s0(m, pd, a.mpre[mi], &lpc[k], &scp[k]);
-        lmc[k] = f2{0.f, 0.f};
-        scm[k] = 0;
-      }
-      if (!valid) {
-        lpc[k] = lmc[k] = f2{0.f, 0.f};
-        scp[k] = scm[k] = 0;
-      }
-      lpp[k] = lmp[k] = f2{0.f, 0.f};
+      lj[k] = valid ? __float_as_int(__ldg(a.join + ((size_t)mi * a.npairs + p) * 3 + 2).z) : lmax + 1;
+      jmin = min(jmin, lj[k]);
+      lpc[k] = lmc[k] = lpp[k] = lmp[k] = f2{0.f, 0.f};
+      scp[k] = scm[k] = 0;
   #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         if (!SPIN) {
@@ -432,6 +427,19 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
         }
       }
     }
+
+    // the tile starts at its pairs' earliest join block; the first tile of the group
+    // zeroes the slot's degrees before it (the others leave their sums there)
+    {
+      const int wmin = __reduce_min_sync(0xffffffffu, jmin);
+      if ((tid & 31) == 0) tstart[gi & 1][tid >> 5] = wmin;
+    }
+    __syncthreads();
+    int lstart = tstart[gi & 1][0];
+  #pragma unroll
+    for (int w = 1; w < kAnaThreads / 32; ++w) lstart = min(lstart, tstart[gi & 1][w]);
+    if (gi == 0)
+      for (int i = tid; i < (min(lstart, lmax + 1) - l0) * V; i += kAnaThreads) outp[i] = 0.0;
 
     // one degree: this thread's V contributions (summed over its pairs) into c[];
     // the first term of each output is its exact product (no sum with zero)
@@ -547,7 +555,23 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
     int since = 0;         // steps since the last exponent check
     bool settled = false;  // every lane's values at scale 0: they stay there (warp-uniform)
     int cb = 0;            // chunk parity: the quart buffer
-    for (int lb = l0; lb <= lmax; lb += LC) {
+    for (int lb = lstart; lb <= lmax; lb += LC) {
+      // pairs joining at this degree take the recursion state where their terms start
+      bool joins = false;
+  #pragma unroll
+      for (int k = 0; k < PPT; ++k)
+        if (lj[k] == lb) {
+          const int p = tile * (kAnaThreads * PPT) + tid + k * kAnaThreads;
+          const JoinRec r = ld_join(a.join + ((size_t)mi * a.npairs + p) * 3);
+          lpc[k] = r.lpc;
+          lpp[k] = r.lpp;
+          lmc[k] = r.lmc;
+          lmp[k] = r.lmp;
+          scp[k] = r.scp;
+          scm[k] = r.scm;
+          joins = true;
+        }
+      if (__any_sync(0xffffffffu, joins)) settled = false;
       // this chunk's slot entry from the previous tiles (read early, added at the end)
       const bool mine = tid < 32 && lb + tid / V <= lmax;
       double *const o = outp + (int64_t)(lb - l0) * V + tid;
@@ -656,7 +680,90 @@ static MixArgs make_mix(const sht_plan_s *P, int polar) {
   a.ana_items = P->d_ana_items[polar];
   a.part_off = P->d_ana_part_off[polar];
   a.part = P->d_part;
+  a.join = P->d_join;
+  a.ptr_off = 0;
   return a;
+}
+
+// ---------------------------------------------------------------------------
+// Join records (see JoinRec in mixed_common.cuh), once per plan: each thread runs
+// its ring pair's recursion from l0 with the steps and rescale checks of the
+// double-float kernels, records the state at every block of 16 degrees, and stops
+// at the first degree pair whose values are not negligible.  The work is the
+// recursion over the pairs' negligible stretches only.
+// ---------------------------------------------------------------------------
+template <bool SPIN>
+__global__ void __launch_bounds__(128) join_kernel(MixArgs a, float4 *__restrict__ out) {
+  const int mi = blockIdx.y, p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.npairs) return;
+  const int m = a.mval[mi];
+  const int s = a.spin, as = s < 0 ? -s : s;
+  const int l0 = m > as ? m : as, lmax = a.lmax;
+  const float4 *__restrict__ cf = a.coef32 + 2 * (a.coef_off[mi] - l0);
+  const PairDev pd = a.pairs[p];
+  const f3 x = f3_of(pd.x);
+  f2 lpc, lmc = {0.f, 0.f}, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
+  int scp, scm = 0;
+  if (SPIN) {
+    start_s(m, s, pd, a.mpre[mi], &lpc, &scp);
+    start_s(m, -s, pd, a.mpre[mi], &lmc, &scm);
+  } else {
+    start_s0(m, pd, a.mpre[mi], &lpc, &scp);
+  }
+  JoinRec r = {lpc, lpp, lmc, lmp, scp, scm, l0, 0};
+  bool live = false;
+  for (int l = l0; l <= lmax; l += 2) {
+    const int off = l - l0;
+    if (off % kJoinBlock == 0) r = {lpc, lpp, lmc, lmp, scp, scm, l, 0};
+    if (!(negligible(lpc, scp) && (!SPIN || negligible(lmc, scm)))) {
+      live = true;
+      break;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const Coef32 cc = ld_coef32(cf + 2 * (l + q <= lmax ? l + q : lmax));
+      const f2 t = mul(cc.a, x);
+      const f2 nc = neg(cc.c);
+      if (SPIN) {
+        const f2 np_ = dot3(t, lpc, cc.ak, lpc, nc, lpp);
+        const f2 nm_ = dot3(t, lmc, neg(cc.ak), lmc, nc, lmp);
+        lpp = lpc;
+        lpc = np_;
+        lmp = lmc;
+        lmc = nm_;
+      } else {
+        const f2 ln = dot2(t, lpc, nc, lpp);
+        lpp = lpc;
+        lpc = ln;
+      }
+    }
+    if ((off + 2) % 8 == 0) {  // the kernels' exponent check after every eight degrees
+      if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
+        lpc = {lpc.h * kScaleFactor32, lpc.l * kScaleFactor32};
+        lpp = {lpp.h * kScaleFactor32, lpp.l * kScaleFactor32};
+        ++scp;
+      }
+      if (SPIN && scm < 0 && fabsf(lmc.h) > kScaleUp32) {
+        lmc = {lmc.h * kScaleFactor32, lmc.l * kScaleFactor32};
+        lmp = {lmp.h * kScaleFactor32, lmp.l * kScaleFactor32};
+        ++scm;
+      }
+    }
+  }
+  if (!live) r.lj = lmax + 1;
+  float4 *o = out + ((size_t)mi * a.npairs + p) * 3;
+  o[0] = make_float4(r.lpc.h, r.lpc.l, r.lpp.h, r.lpp.l);
+  o[1] = make_float4(r.lmc.h, r.lmc.l, r.lmp.h, r.lmp.l);
+  o[2] = make_float4(__int_as_float(r.scp), __int_as_float(r.scm), __int_as_float(r.lj), 0.f);
+}
+
+cudaError_t launch_join_records(const sht_plan_s *P, cudaStream_t st) {
+  if (P->nm == 0 || P->npairs == 0) return cudaSuccess;
+  const MixArgs a = make_mix(P, 1);
+  const dim3 grid((P->npairs + 127) / 128, P->nm);
+  if (P->spin) join_kernel<true><<<grid, 128, 0, st>>>(a, P->d_join);
+  else join_kernel<false><<<grid, 128, 0, st>>>(a, P->d_join);
+  return cudaGetLastError();
 }
 
 // Legendre stage over an explicit work list (stage 0: synthesis items int2, 1:

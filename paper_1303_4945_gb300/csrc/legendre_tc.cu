@@ -339,10 +339,18 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
       if (e < S::STG) dst[e] = pf[i];
     }
   };
+  __shared__ int kstart[tc::kRows / 32];
+  // the K-step (block of 16 degrees) at which this pair's terms start (join record);
+  // the CTA starts at its pairs' earliest
+  const float4 *jrec = a.join + ((size_t)mi * a.npairs + (valid ? p : 0)) * 3;
+  const int lj = valid ? __float_as_int(__ldg(jrec + 2).z) : lmax + 1;
+  {
+    const int kj = lj <= lmax ? (lj - l0) / tc::kK : nks;
+    const int wmin = __reduce_min_sync(0xffffffffu, kj);
+    if ((tid & 31) == 0) kstart[warp] = wmin;
+  }
   if (warp == 0) tc::tmem_alloc(&tslot, S::TCOLS);
   if (tid == 0) tc::bar_init(&mbar);
-  prefetch(0);
-  stage_store(0);
   for (int i = tid; i < S::B_BYTES / 16; i += tc::kRows) reinterpret_cast<uint4 *>(Bt)[i] = make_uint4(0, 0, 0, 0);
   if (tid < 2 * S::NV) umax[tid] = 0.f;
   tc::fence_before();
@@ -350,24 +358,22 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   tc::fence_after();
   const uint32_t tbase = tslot;
   const uint32_t lane = tbase + ((uint32_t)(warp * 32) << 16);
+  int ks0 = kstart[0];
+#pragma unroll
+  for (int w = 1; w < tc::kRows / 32; ++w) ks0 = min(ks0, kstart[w]);
+  if (ks0 < nks) {  // its rows; the first K-step's window barrier orders them before any read
+    prefetch(ks0);
+    stage_store(ks0);
+  }
 #pragma unroll
   for (int c = 0; c < NCOL; ++c) accs[c * tc::kRows + tid] = f2{0.f, 0.f};
 
-  // recursion state (as in the double-float synthesis): +s values lpc/lpp, -s lmc/lmp
+  // recursion state (as in the double-float synthesis): +s values lpc/lpp, -s lmc/lmp,
+  // zero until the pair joins (no terms, and a recursion of zeros)
   const PairDev pd = a.pairs[valid ? p : 0];
   const f3 x = f3_of(pd.x);
-  f2 lpc, lmc = {0.f, 0.f}, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
-  int scp, scm = 0;
-  if (SPIN) {
-    start_s(m, s, pd, a.mpre[mi], &lpc, &scp);
-    start_s(m, -s, pd, a.mpre[mi], &lmc, &scm);
-  } else {
-    start_s0(m, pd, a.mpre[mi], &lpc, &scp);
-  }
-  if (!valid) {
-    lpc = lmc = f2{0.f, 0.f};
-    scp = scm = 0;
-  }
+  f2 lpc = {0.f, 0.f}, lmc = {0.f, 0.f}, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
+  int scp = 0, scm = 0;
   // digit grid of Lambda: magic constants of the quanta u 2^-7, u 2^-15, u 2^-23
   const float ls0 = ta.lam_bound * 98304.0f, ls1 = ls0 * 0x1p-8f, ls2 = ls0 * 0x1p-16f;
   float racc[NCOL];
@@ -515,7 +521,7 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   auto issue = [&](int ks) {
     tc::fence_after();
     constexpr uint32_t idesc = tc::instr_desc(tc::kRows, S::N);
-    const bool first = (ks % tc::kWin) == 0;
+    const bool first = (ks % tc::kWin) == 0 || ks == ks0;
 #pragma unroll
     for (int t = 0; t < NL; ++t)
 #pragma unroll
@@ -554,15 +560,27 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
 
   int ncommit = 0, nwaited = 0;
   bool ok = true;
-  for (int ks = 0; ks < nks; ++ks) {
+  for (int ks = ks0; ks < nks; ++ks) {
     const int lb = l0 + ks * tc::kK;
-    if (ks % tc::kWin == 0) {  // column bounds of this window's a_lm
+    if (ks % tc::kWin == 0 || ks == ks0) {  // column bounds of this window's a_lm (from lb on)
       float *um = umax + ((ks / tc::kWin) & 1) * S::NV;
       if (tid < S::NV) umax[(((ks / tc::kWin) & 1) ^ 1) * S::NV + tid] = 0.f;  // the other window's, for later
-      const int lw1 = lb + tc::kWin * tc::kK - 1;
+      const int lw1 = l0 + (ks / tc::kWin + 1) * tc::kWin * tc::kK - 1;
       tc::window_bounds<NJ, SPIN>(a, co, lb, lw1 < lmax ? lw1 : lmax, um);
       __syncthreads();
     }
+    if (lj == lb) {  // this pair joins: the recursion state where its terms start
+      const JoinRec r = ld_join(jrec);
+      lpc = r.lpc;
+      lpp = r.lpp;
+      lmc = r.lmc;
+      lmp = r.lmp;
+      scp = r.scp;
+      scm = r.scm;
+      wfp = wfac(scp);
+      wfm = wfac(scm);
+    }
+    if (__any_sync(0xffffffffu, lj == lb)) settled = __all_sync(0xffffffffu, scp == 0 && scm == 0);
     const float4 *rows = stage + (ks & 1) * S::STG;
     if (ks + 1 < nks) prefetch(ks + 1);  // its latency hides behind this K-step's work
     bool fail = false;

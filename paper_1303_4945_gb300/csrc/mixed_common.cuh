@@ -78,6 +78,34 @@ __device__ __forceinline__ f2 to_scaled32(double mant, int E, int *scale) {
   return f2_of(ldexp(mant, E - kScaleStep32 * sc));
 }
 
+// Where a ring pair's terms start for one m: the first block of 16 degrees
+// (counted from l0) that holds a degree pair whose values are not negligible
+// (the test the kernels apply every second degree), and the recursion state at
+// that block's first degree, as the kernels reach it (same steps, same rescale
+// checks every eight degrees).  Kernels that walk the degrees in blocks of 16 let
+// a pair join there with that state (before, it adds only terms below the
+// negligible bound) and start a CTA at its pairs' earliest block.  lj = lmax + 1:
+// the pair never contributes.  48 bytes, read as three float4.
+struct JoinRec {
+  f2 lpc, lpp, lmc, lmp;  // +s current / previous, -s current / previous
+  int scp, scm, lj, pad;
+};
+static_assert(sizeof(JoinRec) == 48, "three float4");
+__device__ __forceinline__ JoinRec ld_join(const float4 *p) {
+  const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  JoinRec r;
+  r.lpc = f2{a.x, a.y};
+  r.lpp = f2{a.z, a.w};
+  r.lmc = f2{b.x, b.y};
+  r.lmp = f2{b.z, b.w};
+  r.scp = __float_as_int(c.x);
+  r.scm = __float_as_int(c.y);
+  r.lj = __float_as_int(c.z);
+  r.pad = 0;
+  return r;
+}
+constexpr int kJoinBlock = 16;  // degrees per join block
+
 struct MixArgs {
   int lmax, spin, npairs, nm;
   const int *mval;
@@ -93,6 +121,7 @@ struct MixArgs {
   const int64_t *part_off;
   double *part;
   int ptr_off;
+  const float4 *join;  // JoinRec per (m index, pair), 3 float4 each
 };
 
 struct Coef32 {

@@ -842,7 +842,7 @@ static void free_plan(sht_plan_s *P) {
   cudaSetDevice(P->device);
   void *ptrs[] = {P->d_pairs, P->d_pair_rings, P->d_rings, P->d_mval, P->d_mstart, P->d_coef_off,
                   P->d_coef, P->d_coef32, P->d_alm32, P->d_pm64, P->d_mpre, P->d_minv, P->d_phase, P->d_part, P->d_fft,
-                  P->d_pair_fft, P->d_fft_scratch, P->d_err};
+                  P->d_pair_fft, P->d_fft_scratch, P->d_err, P->d_join};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 2; ++k) {
@@ -1118,6 +1118,14 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
     P->tc_syn = tc_supported(P->spin, P->njobs_pad) && !(P->spin == 0 && P->njobs_pad == 1);
   }
   CUDA_TRY(launch_coef_tables(P, 0));
+  if (P->precision == SHT_MIXED && P->nm > 0 && P->npairs > 0) {
+    // where each ring pair's terms start, per m (the mixed Legendre kernels skip
+    // the recursion over the negligible stretch before it)
+    const size_t bytes = (size_t)P->nm * P->npairs * 3 * sizeof(float4);
+    CUDA_TRY(cudaMalloc(&P->d_join, bytes));
+    P->workspace += bytes;
+    CUDA_TRY(launch_join_records(P, 0));
+  }
   CUDA_TRY(cudaDeviceSynchronize());
 
   P->first_pair = polar_first_pairs(g, P->pair_n, P->lmax, P->spin, P->mval);

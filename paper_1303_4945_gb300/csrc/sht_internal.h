@@ -168,6 +168,7 @@ struct sht_plan_s {
   int tc_syn = 0;
   float tc_lam_bound = 0.f;  // power of two bounding |Lambda_lm| for lmax
   int *d_err = nullptr;      // device status word written by kernels with bounded waits
+  float4 *d_join = nullptr;  // mixed plans: join record per (m index, pair), 3 float4 each
   int m_identity = 0;   // the m list is 0, 1, ..., nm - 1
   // the FP64 columns run beside the mixed kernels: a side stream forked and joined by events
   cudaStream_t side = nullptr;
@@ -256,6 +257,7 @@ cudaError_t launch_leg_ana_mixed(const sht_plan_s *P, const DevPtrs &alm, int po
 // record (MixArgs) with its synthesis work list set; n work items
 cudaError_t launch_leg_tc_syn(const sht_plan_s *P, const void *mixargs, int n, cudaStream_t st);
 cudaError_t tc_prepare_device();
+cudaError_t launch_join_records(const sht_plan_s *P, cudaStream_t st);
 // batches: one TcArgs record per plan of a tensor-core group
 size_t tc_args_size();
 void leg_tc_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
