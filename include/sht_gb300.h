@@ -210,7 +210,10 @@ SHT_API int sht_plan_create(sht_geom_t geom, sht_alm_t alm, int spin, int ncomp,
 SHT_API int sht_execute(sht_plan_t plan, int type, double *const *alm, double *const *map, int flags,
                 void *cuda_stream);
 
-/* Bytes of device workspace the plan holds (tables + phase arrays). */
+/* Bytes of device workspace the plan holds: coefficient tables, the phase array,
+ * the analysis partial sums and, for a mixed plan, the recursion state where each
+ * (m, ring pair)'s terms start (48 bytes each, built once at plan creation so the
+ * Legendre kernels skip the negligible stretch of the recursion). */
 SHT_API int sht_plan_workspace(sht_plan_t plan, int64_t *bytes);
 
 /*

@@ -88,13 +88,11 @@ __device__ __forceinline__ void mix_syn_s0_body(const MixArgs &a, double *const 
   const float4 *__restrict__ cf = a.coef32 + 2 * co;
   const PairDev pd = a.pairs[valid ? p : 0];
   const f3 x = f3_of(pd.x);
-  f2 lc, lp = {0.f, 0.f};
-  int scale;
-  start_s0(m, pd, a.mpre[mi], &lc, &scale);
-  if (!valid) {
-    lc = {0.f, 0.f};
-    scale = 0;
-  }
+  // zero until the pair joins at its join record's block (no terms, a recursion of zeros)
+  f2 lc = {0.f, 0.f}, lp = {0.f, 0.f};
+  int scale = 0;
+  const float4 *jrec = a.join + ((size_t)mi * a.npairs + (valid ? p : 0)) * 3;
+  const int lj = valid ? __float_as_int(__ldg(jrec + 2).z) : lmax + 1;
   f2 acc[2][NJ][2];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
@@ -132,8 +130,16 @@ __device__ __forceinline__ void mix_syn_s0_body(const MixArgs &a, double *const 
       }
   };
 
-  int l = l0;
-  while (l <= lmax && __any_sync(0xffffffffu, scale < 0)) {
+  // the warp starts at its lanes' earliest join block and walks carefully (scale
+  // checks, negligible terms skipped) while a lane is below scale 0 or yet to join
+  int l = __reduce_min_sync(0xffffffffu, lj);
+  while (l <= lmax && __any_sync(0xffffffffu, scale < 0 || (lj <= lmax && lj >= l))) {
+    if (lj == l) {
+      const JoinRec r = ld_join(jrec);
+      lc = r.lpc;
+      lp = r.lpp;
+      scale = r.scp;
+    }
 #pragma unroll 1
     for (int k = 0; k < 4 && l <= lmax; ++k, l += 2) {
       if (__all_sync(0xffffffffu, negligible(lc, scale))) {
@@ -201,14 +207,11 @@ __device__ __forceinline__ void mix_syn_spin_body(const MixArgs &a, double *cons
   const float4 *__restrict__ cf = a.coef32 + 2 * co;
   const PairDev pd = a.pairs[valid ? p : 0];
   const f3 x = f3_of(pd.x);
-  f2 lpc, lmc, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
-  int scp, scm;
-  start_s(m, s, pd, a.mpre[mi], &lpc, &scp);
-  start_s(m, -s, pd, a.mpre[mi], &lmc, &scm);
-  if (!valid) {
-    lpc = lmc = f2{0.f, 0.f};
-    scp = scm = 0;
-  }
+  // zero until the pair joins at its join record's block (no terms, a recursion of zeros)
+  f2 lpc = {0.f, 0.f}, lmc = {0.f, 0.f}, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
+  int scp = 0, scm = 0;
+  const float4 *jrec = a.join + ((size_t)mi * a.npairs + (valid ? p : 0)) * 3;
+  const int lj = valid ? __float_as_int(__ldg(jrec + 2).z) : lmax + 1;
   // N1 = sum P l+, N2 = sum M l-, S3 = sum (-1)^(l-l0) P l-, S4 = sum (-1)^(l-l0) M l+
   f2 r[NJ][4][2];
 #pragma unroll
@@ -263,8 +266,19 @@ __device__ __forceinline__ void mix_syn_spin_body(const MixArgs &a, double *cons
       }
   };
 
-  int l = l0;
-  while (l <= lmax && __any_sync(0xffffffffu, scp < 0 || scm < 0)) {
+  // the warp starts at its lanes' earliest join block and walks carefully (scale
+  // checks, negligible terms skipped) while a lane is below scale 0 or yet to join
+  int l = __reduce_min_sync(0xffffffffu, lj);
+  while (l <= lmax && __any_sync(0xffffffffu, scp < 0 || scm < 0 || (lj <= lmax && lj >= l))) {
+    if (lj == l) {
+      const JoinRec r = ld_join(jrec);
+      lpc = r.lpc;
+      lpp = r.lpp;
+      lmc = r.lmc;
+      lmp = r.lmp;
+      scp = r.scp;
+      scm = r.scm;
+    }
 #pragma unroll 1
     for (int k = 0; k < 4 && l <= lmax; ++k, l += 2) {
       if (__all_sync(0xffffffffu, negligible(lpc, scp) && negligible(lmc, scm))) {
