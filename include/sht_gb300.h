@@ -223,6 +223,16 @@ SHT_API int sht_plan_workspace(sht_plan_t plan, int64_t *bytes);
  */
 SHT_API int sht_plan_triples(sht_plan_t plan, int flags, int64_t *triples);
 
+/*
+ * The part of that work a mixed plan's Legendre kernels cannot skip: the steps
+ * from each kept pair's join block on (the first block of 16 degrees from l0 with
+ * terms that are not negligible; before it a pair adds nothing), the polar cut
+ * applied.  The kernels walk a CTA (or a warp) from its pairs' earliest join block,
+ * so they run somewhat more steps than this.  An FP64 plan reports its
+ * sht_plan_triples count.  Errors: SHT_ERR_INVALID_ARG.
+ */
+SHT_API int sht_plan_triples_joined(sht_plan_t plan, int64_t *triples);
+
 SHT_API void sht_plan_destroy(sht_plan_t plan);
 
 /* ---- analysis tiling and autotuning -------------------------------------------
@@ -288,20 +298,21 @@ SHT_API int sht_plan_get_fft_precision(sht_plan_t plan, int *precision);
  * The paper's synthesis (Eq. syn2; the inner loop of Sect. 3.2, Fig. 1) is, for
  * one m, a product F = Lambda^T a over the degrees l.  A mixed plan can run that
  * product on the tensor cores: the double-float recursion of Sect. 4.1 still
- * generates Lambda, which is split exactly into three bf16 digits on a fixed grid
- * plus an FP32 remainder (contracted on the CUDA cores); the a_lm are split into
- * five bf16 digits on a grid per 256 degrees; the digit products are summed in
- * FP32 accumulators where no rounding can occur, and the sums are added in
- * double-float.  A term's error is below 2^-40 of the bound of its operands;
- * at spin 2, lmax 4095 the maps agree with the FP64 form to 6.6e-12 relative
- * (the double-float contraction: 2.1e-12).
+ * generates Lambda, which is split exactly into three bf16 digits on a grid set
+ * by the ring pair's own bound (found once at plan creation) plus an FP32
+ * remainder (contracted on the CUDA cores); the a_lm are split into six bf16
+ * digits on a grid per 256 degrees; the digit products are summed in FP32
+ * accumulators where no rounding can occur, and the sums are added in
+ * double-float.  A term's error is below 2^-43 of the bound of its operands; at
+ * spin 2, lmax 4095 the maps agree with the FP64 form to 2.1e-12 relative, as
+ * with the double-float contraction.
  * Shapes: spin 0 with ncomp <= 8, spin s with ncomp <= 4 (SHT_ERR_UNSUPPORTED
  * otherwise).  It serves SHT_SYNTHESIS, SHT_ADJOINT_ANALYSIS and
  * SHT_DERIV_SYNTHESIS through sht_execute and sht_execute_noalloc, and is a
  * mixed plan's default for every supported shape except a single spin-0 map,
  * where the double-float contraction is faster (measured on GB300 at lmax 4095:
- * spin 2 one E/B pair 62.0 ms against 70.7, spin 0 eight maps 75.2 against 112.3,
- * spin 0 one map 29.4 against 25.6).  sht_plan_set_tensor_cores(plan, 1 or 0)
+ * spin 2 one E/B pair 54.3 ms against 62.7, spin 0 eight maps 69.9 against 103.7,
+ * spin 0 one map 26.3 against 22.2).  sht_plan_set_tensor_cores(plan, 1 or 0)
  * selects it or the double-float contraction; sht_plan_get_tensor_cores reads the
  * setting.  A batch runs each plan with the setting it had when the batch was
  * made (the setting cannot change while a batch refers to the plan).  Errors: SHT_ERR_INVALID_ARG (NULL, an

@@ -702,12 +702,12 @@ static MixArgs make_mix(const sht_plan_s *P, int polar) {
 // ---------------------------------------------------------------------------
 // Join records (see JoinRec in mixed_common.cuh), once per plan: each thread runs
 // its ring pair's recursion from l0 with the steps and rescale checks of the
-// double-float kernels, records the state at every block of 16 degrees, and stops
-// at the first degree pair whose values are not negligible.  The work is the
-// recursion over the pairs' negligible stretches only.
+// double-float kernels, records the state at every block of 16 degrees up to the
+// first degree pair whose values are not negligible, then walks on to lmax + 1 for
+// the bound on the values' true size.
 // ---------------------------------------------------------------------------
 template <bool SPIN>
-__global__ void __launch_bounds__(128) join_kernel(MixArgs a, float4 *__restrict__ out) {
+__global__ void __launch_bounds__(128) join_kernel(MixArgs a, float4 *__restrict__ out, int min_exp) {
   const int mi = blockIdx.y, p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.npairs) return;
   const int m = a.mval[mi];
@@ -724,59 +724,94 @@ __global__ void __launch_bounds__(128) join_kernel(MixArgs a, float4 *__restrict
   } else {
     start_s0(m, pd, a.mpre[mi], &lpc, &scp);
   }
+  // one recursion step at degree l (its row's coefficients; lmax's past lmax)
+  auto step = [&](int l) {
+    const Coef32 cc = ld_coef32(cf + 2 * (l <= lmax ? l : lmax));
+    const f2 t = mul(cc.a, x);
+    const f2 nc = neg(cc.c);
+    if (SPIN) {
+      const f2 np_ = dot3(t, lpc, cc.ak, lpc, nc, lpp);
+      const f2 nm_ = dot3(t, lmc, neg(cc.ak), lmc, nc, lmp);
+      lpp = lpc;
+      lpc = np_;
+      lmp = lmc;
+      lmc = nm_;
+    } else {
+      const f2 ln = dot2(t, lpc, nc, lpp);
+      lpp = lpc;
+      lpc = ln;
+    }
+  };
+  // the kernels' exponent check, made after every eight degrees from l0
+  auto rescale = [&]() {
+    if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
+      lpc = {lpc.h * kScaleFactor32, lpc.l * kScaleFactor32};
+      lpp = {lpp.h * kScaleFactor32, lpp.l * kScaleFactor32};
+      ++scp;
+    }
+    if (SPIN && scm < 0 && fabsf(lmc.h) > kScaleUp32) {
+      lmc = {lmc.h * kScaleFactor32, lmc.l * kScaleFactor32};
+      lmp = {lmp.h * kScaleFactor32, lmp.l * kScaleFactor32};
+      ++scm;
+    }
+  };
   JoinRec r = {lpc, lpp, lmc, lmp, scp, scm, l0, 0};
   bool live = false;
-  for (int l = l0; l <= lmax; l += 2) {
+  int l = l0;
+  for (; l <= lmax; l += 2) {
     const int off = l - l0;
     if (off % kJoinBlock == 0) r = {lpc, lpp, lmc, lmp, scp, scm, l, 0};
     if (!(negligible(lpc, scp) && (!SPIN || negligible(lmc, scm)))) {
       live = true;
       break;
     }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const Coef32 cc = ld_coef32(cf + 2 * (l + q <= lmax ? l + q : lmax));
-      const f2 t = mul(cc.a, x);
-      const f2 nc = neg(cc.c);
-      if (SPIN) {
-        const f2 np_ = dot3(t, lpc, cc.ak, lpc, nc, lpp);
-        const f2 nm_ = dot3(t, lmc, neg(cc.ak), lmc, nc, lmp);
-        lpp = lpc;
-        lpc = np_;
-        lmp = lmc;
-        lmc = nm_;
-      } else {
-        const f2 ln = dot2(t, lpc, nc, lpp);
-        lpp = lpc;
-        lpc = ln;
-      }
-    }
-    if ((off + 2) % 8 == 0) {  // the kernels' exponent check after every eight degrees
-      if (scp < 0 && fabsf(lpc.h) > kScaleUp32) {
-        lpc = {lpc.h * kScaleFactor32, lpc.l * kScaleFactor32};
-        lpp = {lpp.h * kScaleFactor32, lpp.l * kScaleFactor32};
-        ++scp;
-      }
-      if (SPIN && scm < 0 && fabsf(lmc.h) > kScaleUp32) {
-        lmc = {lmc.h * kScaleFactor32, lmc.l * kScaleFactor32};
-        lmp = {lmp.h * kScaleFactor32, lmp.l * kScaleFactor32};
-        ++scm;
-      }
-    }
+    step(l);
+    step(l + 1);
+    if ((off + 2) % 8 == 0) rescale();
   }
-  if (!live) r.lj = lmax + 1;
+  // from the first live degree on: the largest true size (the kernels' weights:
+  // scale 0 as is, scale -1 times 2^-104, below that dropped), low word included
+  float vmax = 0.f;
+  if (live) {
+    auto size = [](f2 y, int sc) {
+      const float v = fabsf(y.h) + fabsf(y.l);
+      return sc == 0 ? v : (sc == -1 ? v * kScaleFactor32 : 0.f);
+    };
+    for (; l <= lmax + 1; ++l) {
+      vmax = fmaxf(vmax, size(lpc, scp));
+      if (SPIN) vmax = fmaxf(vmax, size(lmc, scm));
+      if (l > lmax) break;
+      step(l);
+      if ((l + 1 - l0) % 8 == 0) rescale();
+    }
+  } else {
+    r.lj = lmax + 1;
+  }
+  // 2^lexp >= vmax (with a margin of 2^-20 for the rounding of the bound), not
+  // below 2^min_exp (the plan-wide bound / 2^16: finer grids would bring the
+  // digit products near FP32's range end and add nothing)
+  int e = min_exp;
+  if (vmax > 0.f) {
+    int ev;
+    frexpf(vmax * (1.f + 0x1p-20f), &ev);  // vmax' = f 2^ev, f in [0.5, 1)
+    e = max(e, ev);
+  }
+  r.lexp = e;
   float4 *o = out + ((size_t)mi * a.npairs + p) * 3;
   o[0] = make_float4(r.lpc.h, r.lpc.l, r.lpp.h, r.lpp.l);
   o[1] = make_float4(r.lmc.h, r.lmc.l, r.lmp.h, r.lmp.l);
-  o[2] = make_float4(__int_as_float(r.scp), __int_as_float(r.scm), __int_as_float(r.lj), 0.f);
+  o[2] = make_float4(__int_as_float(r.scp), __int_as_float(r.scm), __int_as_float(r.lj), __int_as_float(r.lexp));
 }
 
 cudaError_t launch_join_records(const sht_plan_s *P, cudaStream_t st) {
   if (P->nm == 0 || P->npairs == 0) return cudaSuccess;
   const MixArgs a = make_mix(P, 1);
   const dim3 grid((P->npairs + 127) / 128, P->nm);
-  if (P->spin) join_kernel<true><<<grid, 128, 0, st>>>(a, P->d_join);
-  else join_kernel<false><<<grid, 128, 0, st>>>(a, P->d_join);
+  int ub;
+  frexpf(P->tc_lam_bound, &ub);  // tc_lam_bound = 2^(ub - 1)
+  const int min_exp = ub - 1 - 16;
+  if (P->spin) join_kernel<true><<<grid, 128, 0, st>>>(a, P->d_join, min_exp);
+  else join_kernel<false><<<grid, 128, 0, st>>>(a, P->d_join, min_exp);
   return cudaGetLastError();
 }
 

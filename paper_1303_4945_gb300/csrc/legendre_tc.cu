@@ -11,12 +11,16 @@
 // into digits on a common grid (an Ozaki-style error-free split):
 //
 //  * Lambda = L0 + L1 + L2 + r.  The digits Lj are multiples of qj = u 2^(-7-8j)
-//    with |Lj| <= 128 qj, where u is a power of two bounding |Lambda_lm| for the
-//    whole plan (|sLambda_lm| <= sqrt((2l+1)/(4 pi)) since |d^l| <= 1); each fits
-//    a bf16 exactly.  The FP32 remainder r (|r| <= q2/2) is contracted on the
-//    CUDA cores (one FFMA per output column), so Lambda enters to ~2^-43 u.
-//  * B = B0 + ... + B4 with digits on the grid u_c 2^(-7-8j), u_c a power of two
-//    bounding column c of B over a window of 256 degrees.
+//    with |Lj| <= 128 qj, where u is a power of two bounding the ring pair's own
+//    |Lambda_lm| from its join block to lmax + 1 (its join record: one walk of the
+//    recursion at plan creation; not below 2^-16 of the plan-wide bound
+//    sqrt((2 lmax + 3)/(4 pi)), |d^l| <= 1); each digit fits a bf16 exactly.  One
+//    row of the product is one pair, so rows on different grids never share a sum.
+//    The FP32 remainder r (|r| <= q2/2) is contracted on the CUDA cores (one FFMA
+//    per output column), so Lambda enters to ~2^-43 u.
+//  * B = B0 + ... + B5 with digits on the grid u_c 2^(-7-8j), u_c a power of two
+//    bounding column c of B over a window of 256 degrees: a value enters to
+//    2^-48 u_c (with five digits the truncation at 2^-40 u_c was the larger error).
 //  * The products Li Bj with i + j = k are accumulated in TMEM level k (k <= 5;
 //    the dropped products are below 2^-48 of the bounds).  Every product is a
 //    multiple of the level's quantum and a level's sum over one window stays
@@ -45,7 +49,7 @@ constexpr int kRows = 128;          // ring pairs per CTA = MMA M = TMEM lanes
 constexpr int kK = 16;              // degrees per MMA (bf16 K)
 constexpr int kWin = 16;            // K-steps per TMEM window (256 degrees)
 constexpr int kLamDigits = 3;       // bf16 digits of Lambda (plus an FP32 remainder)
-constexpr int kAlmDigits = 5;       // bf16 digits of the a_lm columns
+constexpr int kAlmDigits = 6;       // bf16 digits of the a_lm columns
 constexpr int kLevels = 6;          // TMEM levels read: digit products with i + j <= 5
 constexpr int kATile = kRows * kK * 2;  // bytes of one 128 x 16 bf16 tile
 constexpr int kPack = 4;            // degrees of digits held in registers before a shared-memory store
@@ -145,8 +149,8 @@ __device__ __forceinline__ float pow2_above(float x) {
 // spin 0: even-l and odd-l sums as re/im per job), NCW = max(NCOL, 8) TMEM columns
 // per level and rows per a_lm digit tile, MMA width N = 2 NCW (two digit tiles, two
 // levels), NV a_lm values per degree (spin: P = E + iB and M = E - iB, re and im;
-// spin 0: re, im).  A set's digit stack holds the tiles of digits -1 .. 5, those
-// of digits -1 and 5 zero: Lambda digit i meets the windows of digits
+// spin 0: re, im).  A set's digit stack holds the tiles of digits -1 .. 5, that of
+// digit -1 zero: Lambda digit i meets the windows of digits
 // (j0, j0 + 1) with j0 = -(i mod 2), j0 + 2, ..., which start on even levels i + j0,
 // so every MMA writes the 2 NCW columns of a level pair at a multiple of N.
 template <int NJ, bool SPIN>
@@ -155,7 +159,7 @@ struct Shape {
   static constexpr int NCOL = SPIN ? 8 * NJ : 4 * NJ;
   static constexpr int NCW = NCOL < 8 ? 8 : NCOL;
   static constexpr int N = 2 * NCW;
-  static constexpr int NDT = kAlmDigits + 2;  // digit tiles per Lambda set: -1 .. 5
+  static constexpr int NDT = kAlmDigits + 1;  // digit tiles per Lambda set: -1 .. 5
   static constexpr int COLS = kLevels * NCW;  // TMEM: levels 0 .. 5
   static constexpr int TCOLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : 256));
   static constexpr int NV = SPIN ? 4 * NJ : 2 * NJ;
@@ -233,8 +237,8 @@ __device__ __forceinline__ void window_bounds(const MixArgs &a, int64_t co, int 
 // with the parity sign s = (-1)^(l - l0) where the column needs it, into the rows
 // of the columns that read it (see the column layout in tc_syn_body).  Set t's
 // stack holds NDT digit tiles of NCW rows, digit j at rows (j + 1) NCW ..; rows no
-// value writes (the other set's columns, padding columns, the tiles of digits -1
-// and 5) stay zero from the kernel's start.
+// value writes (the other set's columns, padding columns, the tile of digit -1)
+// stay zero from the kernel's start.
 template <int NJ, bool SPIN>
 __device__ __forceinline__ void build_b(const float4 *stg, const float *umax, unsigned char *Bt) {
   using S = Shape<NJ, SPIN>;
@@ -255,6 +259,8 @@ __device__ __forceinline__ void build_b(const float4 *stg, const float *umax, un
     d[3] = round_to(r, s0 * 0x1p-24f);
     r = __fsub_rn(r, d[3]);
     d[4] = round_to(r, s0 * 0x1p-32f);
+    r = __fsub_rn(r, d[4]);
+    d[5] = round_to(r, s0 * 0x1p-40f);
     const bool odd = k & 1;
     // (set, column) pairs of this value; spin: P.re -> (+, 8j) and (-, 8j+6) signed,
     // P.im -> (+, 8j+1) and (-, 8j+7) signed, M.re -> (+, 8j+2) signed and (-, 8j+4),
@@ -374,8 +380,9 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   const f3 x = f3_of(pd.x);
   f2 lpc = {0.f, 0.f}, lmc = {0.f, 0.f}, lpp = {0.f, 0.f}, lmp = {0.f, 0.f};
   int scp = 0, scm = 0;
-  // digit grid of Lambda: magic constants of the quanta u 2^-7, u 2^-15, u 2^-23
-  const float ls0 = ta.lam_bound * 98304.0f, ls1 = ls0 * 0x1p-8f, ls2 = ls0 * 0x1p-16f;
+  // digit grid of Lambda: magic constants of the quanta u 2^-7, u 2^-15, u 2^-23,
+  // u the pair's own bound from its join record (the plan-wide bound until it joins)
+  float ls0 = ta.lam_bound * 98304.0f, ls1 = ls0 * 0x1p-8f, ls2 = ls0 * 0x1p-16f;
   float racc[NCOL];
 #pragma unroll
   for (int c = 0; c < NCOL; ++c) racc[c] = 0.f;
@@ -514,8 +521,8 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
   // digit i, the a_lm digit windows (j0, j0 + 1), j0 = -(i mod 2), j0 + 2, ... up to
   // the last digit with i + j <= 5, into levels (i + j0, i + j0 + 1); in a window's
   // first K-step the set-0, digit-0 products come first and overwrite levels 0 .. 5
-  // (every level written), the rest accumulate.  The zero tiles of digits -1 and 5
-  // fill the odd and the last windows; the i = 2 windows end at digit 3.
+  // (every level written), the rest accumulate.  The zero tile of digit -1 fills
+  // the odd windows' first halves; the i = 2 windows end at digit 3.
   const uint64_t adesc0 = tc::mat_desc(tc::smem_u32(Abuf), 128, 256);
   const uint64_t bdesc0 = tc::mat_desc(tc::smem_u32(Bt), 128, 256);
   auto issue = [&](int ks) {
@@ -579,6 +586,9 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
       scm = r.scm;
       wfp = wfac(scp);
       wfm = wfac(scm);
+      ls0 = __int_as_float((127 + r.lexp) << 23) * 98304.0f;
+      ls1 = ls0 * 0x1p-8f;
+      ls2 = ls0 * 0x1p-16f;
     }
     if (__any_sync(0xffffffffu, lj == lb)) settled = __all_sync(0xffffffffu, scp == 0 && scm == 0);
     const float4 *rows = stage + (ks & 1) * S::STG;

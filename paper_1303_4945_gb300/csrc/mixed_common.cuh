@@ -85,10 +85,13 @@ __device__ __forceinline__ f2 to_scaled32(double mant, int E, int *scale) {
 // checks every eight degrees).  Kernels that walk the degrees in blocks of 16 let
 // a pair join there with that state (before, it adds only terms below the
 // negligible bound) and start a CTA at its pairs' earliest block.  lj = lmax + 1:
-// the pair never contributes.  48 bytes, read as three float4.
+// the pair never contributes.  lexp: a power of two 2^lexp bounding the true
+// size of every value the pair's recursion takes from its join block to lmax + 1
+// (the tensor-core synthesis puts the pair's Lambda digits on that grid).  48
+// bytes, read as three float4.
 struct JoinRec {
   f2 lpc, lpp, lmc, lmp;  // +s current / previous, -s current / previous
-  int scp, scm, lj, pad;
+  int scp, scm, lj, lexp;
 };
 static_assert(sizeof(JoinRec) == 48, "three float4");
 __device__ __forceinline__ JoinRec ld_join(const float4 *p) {
@@ -101,7 +104,7 @@ __device__ __forceinline__ JoinRec ld_join(const float4 *p) {
   r.scp = __float_as_int(c.x);
   r.scm = __float_as_int(c.y);
   r.lj = __float_as_int(c.z);
-  r.pad = 0;
+  r.lexp = __float_as_int(c.w);
   return r;
 }
 constexpr int kJoinBlock = 16;  // degrees per join block

@@ -1129,6 +1129,18 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   CUDA_TRY(cudaDeviceSynchronize());
 
   P->first_pair = polar_first_pairs(g, P->pair_n, P->lmax, P->spin, P->mval);
+  if (P->d_join) {  // the steps left after the join records, over the pairs the polar cut keeps
+    std::vector<int> lj((size_t)P->nm * P->npairs);
+    CUDA_TRY(cudaMemcpy2D(lj.data(), sizeof(int), reinterpret_cast<const char *>(P->d_join) + 2 * sizeof(float4) + 8,
+                          3 * sizeof(float4), sizeof(int), lj.size(), cudaMemcpyDeviceToHost));
+    int64_t t = 0;
+    for (int i = 0; i < P->nm; ++i)
+      for (int p = P->first_pair[i]; p < P->npairs; ++p) {
+        const int l = lj[(size_t)i * P->npairs + p];
+        if (l <= P->lmax) t += P->lmax - l + 1;
+      }
+    P->triples_joined = t;
+  }
 
   // ---- work lists ----
   P->fp64_m_below = P->precision == SHT_MIXED ? default_fp64_columns(P->lmax) : 0;
@@ -1396,6 +1408,12 @@ extern "C" int sht_plan_workspace(sht_plan_t P, int64_t *bytes) {
 extern "C" int sht_plan_triples(sht_plan_t P, int flags, int64_t *t) {
   if (!P || !t) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
   *t = P->triples[(flags & SHT_NO_POLAR_OPT) ? 0 : 1];
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_triples_joined(sht_plan_t P, int64_t *t) {
+  if (!P || !t) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  *t = P->precision == SHT_MIXED ? P->triples_joined : P->triples[1];
   return SHT_OK;
 }
 

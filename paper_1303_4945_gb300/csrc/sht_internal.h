@@ -169,6 +169,7 @@ struct sht_plan_s {
   float tc_lam_bound = 0.f;  // power of two bounding |Lambda_lm| for lmax
   int *d_err = nullptr;      // device status word written by kernels with bounded waits
   float4 *d_join = nullptr;  // mixed plans: join record per (m index, pair), 3 float4 each
+  int64_t triples_joined = 0;  // steps from each kept pair's join block on (polar cut applied)
   int m_identity = 0;   // the m list is 0, 1, ..., nm - 1
   // the FP64 columns run beside the mixed kernels: a side stream forked and joined by events
   cudaStream_t side = nullptr;

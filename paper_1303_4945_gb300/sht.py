@@ -63,6 +63,7 @@ _sig = {
     "sht_execute": [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp],
     "sht_plan_workspace": [_vp, _i64p],
     "sht_plan_triples": [_vp, ctypes.c_int, _i64p],
+    "sht_plan_triples_joined": [_vp, _i64p],
     "sht_plan_destroy": [_vp],
     "sht_execute_noalloc": [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp],
     "sht_execute_legendre": [_vp, ctypes.c_int, ctypes.POINTER(_vp), _vp, ctypes.c_int, _vp],
@@ -268,6 +269,11 @@ class Plan(_Handle):
     def triples(self, flags=0):
         n = ctypes.c_int64()
         _check(_lib.sht_plan_triples(self._h, flags, ctypes.byref(n)), "sht_plan_triples")
+        return n.value
+
+    def triples_joined(self):
+        n = ctypes.c_int64()
+        _check(_lib.sht_plan_triples_joined(self._h, ctypes.byref(n)), "sht_plan_triples_joined")
         return n.value
 
 

@@ -57,6 +57,9 @@ class _Plan:
     def triples(self, flags=0):
         return 10 ** 10
 
+    def triples_joined(self):
+        return 9 * 10 ** 9
+
 
 def test_roofline_arithmetic(monkeypatch):
     stages = {"legendre_synthesis": (300.0, 3), "legendre_analysis": (450.0, 3)}
@@ -73,6 +76,9 @@ def test_roofline_arithmetic(monkeypatch):
     assert m["peak"] == pytest.approx(152 * 128 * 2 * 2e9 / 1e12)
     assert m["frac"] == pytest.approx(m["achieved"] / m["peak"])
     assert m["issue_frac"] == pytest.approx(163e10 / 0.150 / 1e12 / (152 * 128 * 2e9 / 1e12))
+    # the same work counted on the steps left after the join records
+    assert m["triples_after_join"] == 9 * 10 ** 9
+    assert m["frac_after_join"] == pytest.approx(0.9 * m["frac"])
     # with the box's measured pipe rates the peak is 2 x the measured FFMA rate
     peaks["pipes_measured"] = {"fp64_fma_tflops": 1.25, "fp32_fma_tops": 38.3, "fp32_add_tops": 38.3}
     m = bench.roofline_for(stages, _Plan(), 2, "mixed", peaks, 3)

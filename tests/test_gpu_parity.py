@@ -495,3 +495,28 @@ def test_high_spin(sht, precision):
     torch.cuda.synchronize()
     for a, b in zip(alm, back):
         assert float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) <= 10 * l2
+
+
+def test_join_records_skip_only_negligible_steps(sht):
+    # a mixed plan's kernels skip each pair's steps before its join block; the
+    # count of steps left is below the polar-cut count, the FP64 plan reports the
+    # polar-cut count, and the mixed synthesis with the skip matches the oracle on
+    # the pole-most rings, where the skipped stretches are longest
+    lmax = 600
+    geom = sht.sht_geom_gauss(lmax + 1, 2 * lmax + 1)
+    lay = sht.sht_alm_create(lmax, lmax)
+    rings = rings_of(geom)
+    sel = [0, 1, 3, 20, 150, 300]
+    for spin in (0, 2):
+        mixed = sht.sht_plan_create(geom, lay, spin, 1, sht.SHT_MIXED)
+        fp64 = sht.sht_plan_create(geom, lay, spin, 1, sht.SHT_FP64)
+        assert fp64.triples_joined() == fp64.triples(0)
+        assert 0 < mixed.triples_joined() < mixed.triples(0)
+        rng = np.random.default_rng(60 + spin)
+        alm = [inputs.gaussian_alm(rng, lmax, lmax, lmin=abs(spin)) for _ in range(2 if spin else 1)]
+        got = gpu_synthesis(sht, mixed, alm, geom.npix)
+        ref = oracle.synthesis(spin, lmax, lmax, alm, rings, rings_sel=sel)
+        for c, r in zip(got, ref):
+            for y in sel:
+                o, n = rings.ofs[y], rings.nphi[y]
+                assert rel_l2(c[o:o + n], r[o:o + n]) < 1e-10, (spin, y)
