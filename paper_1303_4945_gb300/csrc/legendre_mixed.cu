@@ -586,11 +586,15 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
           joins = true;
         }
       if (__any_sync(0xffffffffu, joins)) settled = false;
+      // a warp none of whose lanes has joined holds zeros: it skips this chunk's
+      // steps and adds zeros to the reduction
+      const bool wlive = __any_sync(0xffffffffu, jmin <= lb);
       // this chunk's slot entry from the previous tiles (read early, added at the end)
       const bool mine = tid < 32 && lb + tid / V <= lmax;
       double *const o = outp + (int64_t)(lb - l0) * V + tid;
       const double prev = (gi > 0 && mine) ? *o : 0.0;
-      if (LC >= 2) {
+      if (!wlive) {
+      } else if (LC >= 2) {
   #pragma unroll 1
         for (int q = 0; q < LC; q += 2) {
           const int l = lb + q;
@@ -635,10 +639,13 @@ __device__ __forceinline__ void mix_ana_body(const MixArgs &a, double *const *pt
       __syncwarp();
       {  // 32 slots x kAnaThreads values: each warp sums its own 32 columns, then 4 partials per slot
         const int sl = tid & 31, part = tid >> 5;
-        const f2 *row = &slot[sl][part * 32];
-        f2 t = row[0];
+        f2 t = {0.f, 0.f};
+        if (wlive) {
+          const f2 *row = &slot[sl][part * 32];
+          t = row[0];
   #pragma unroll 8
-        for (int i = 1; i < 32; ++i) t = f2_add_lazy(t, row[i]);
+          for (int i = 1; i < 32; ++i) t = f2_add_lazy(t, row[i]);
+        }
         quart[cb][part][sl] = t;
       }
       __syncwarp();

@@ -591,13 +591,24 @@ __device__ __forceinline__ void tc_syn_body(const TcArgs &ta, const int2 item, u
       ls2 = ls0 * 0x1p-16f;
     }
     if (__any_sync(0xffffffffu, lj == lb)) settled = __all_sync(0xffffffffu, scp == 0 && scm == 0);
+    // a warp none of whose lanes has joined holds zeros: it skips the recursion
+    const bool wlive = __any_sync(0xffffffffu, lj <= lb);
     const float4 *rows = stage + (ks & 1) * S::STG;
     if (ks + 1 < nks) prefetch(ks + 1);  // its latency hides behind this K-step's work
     bool fail = false;
 #pragma unroll 1
     for (int q0 = 0; q0 < tc::kK; q0 += tc::kPack) {
       uint32_t pk[NL][tc::kLamDigits][tc::kPack / 2];
-      part(rows + q0 * S::ROW, pk);
+      if (wlive) {
+        part(rows + q0 * S::ROW, pk);
+      } else {  // no lane of the warp has joined: zero digits, and nothing to advance
+#pragma unroll
+        for (int t = 0; t < NL; ++t)
+#pragma unroll
+          for (int i = 0; i < tc::kLamDigits; ++i)
+#pragma unroll
+            for (int q = 0; q < tc::kPack / 2; ++q) pk[t][i][q] = 0u;
+      }
       if (q0 % 8 == tc::kPack % 8) rescale();  // after every eight degrees
       // the previous K-step's MMAs read the A and B tiles: wait for them before
       // the first write (they have long finished by now)
