@@ -370,7 +370,8 @@ MEASURED_TRAFFIC = {
 
 KERNEL_HEADERS = {"legendre_fp64.cu": ("sht_device.cuh",),
                   "legendre_mixed.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh", "sht_internal.h"),
-                  "legendre_tc.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh")}
+                  "legendre_tc.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh", "tcgen05.cuh"),
+                  "legendre_tc_ana.cu": ("df.cuh", "sht_device.cuh", "mixed_common.cuh", "tcgen05.cuh", "sht_internal.h")}
 
 
 def _kernel_digest(kernel_file):
@@ -441,8 +442,10 @@ def roofline_for(stages, plan, spin, precision, peaks, steps, ncomp=1):
                                "FP64 pipe derived: 152 SMs x 2 DFMA lanes/clk x 2 flops x sm_max clock"),
                "peak_derived": derived}
     else:
-        tc = name == "legendre_synthesis" and bool(getattr(plan, "tensor_cores", False))
-        kfile = "legendre_tc.cu" if tc else "legendre_mixed.cu"
+        tc_syn = name == "legendre_synthesis" and bool(getattr(plan, "tensor_cores", False))
+        tc_ana = name == "legendre_analysis" and bool(getattr(plan, "tensor_core_analysis", False))
+        tc = tc_syn or tc_ana
+        kfile = "legendre_tc.cu" if tc_syn else ("legendre_tc_ana.cu" if tc_ana else "legendre_mixed.cu")
         derived = SMS * 128 * 2 * clock / 1e12  # 128 FFMA lanes per SM per clock, 2 flops each
         peak = 2 * measured["fp32_fma_tops"] if measured else derived
         ops = triples * f32_ops_per_triple(spin, ncomp)
@@ -453,14 +456,17 @@ def roofline_for(stages, plan, spin, precision, peaks, steps, ncomp=1):
                                "sht_measure_pipe_peaks" if measured else
                                "FP32 pipe derived: 152 SMs x 128 FFMA lanes/clk x 2 flops x sm_max clock"),
                "peak_derived": derived,
-               "issue_frac": ops / sec / 1e12 / issue_peak,
-               "issue_frac_note": "double-float FP32-pipe operations issued per second over the FP32 issue rate "
-                                  "(emulation work included; not the method's work)",
-               "fp32_ops_per_triple": f32_ops_per_triple(spin, ncomp),
+               "issue_frac": None if tc else ops / sec / 1e12 / issue_peak,
+               "issue_frac_note": ("the contraction runs on the tensor cores: the double-float operation count "
+                                   "does not apply" if tc else
+                                   "double-float FP32-pipe operations issued per second over the FP32 issue rate "
+                                   "(emulation work included; not the method's work)"),
+               "tensor_cores": tc,
+               "fp32_ops_per_triple": None if tc else f32_ops_per_triple(spin, ncomp),
                "fp64_equivalent_tflops": achieved, "fp64_pipe_tflops": fp64_pipe}
     out["frac"] = achieved / peak
     out["flops_per_triple"] = flops_per_triple(spin, ncomp)
-    key = ("fp64:" if precision == "fp64" else "mixed:") + name
+    key = ("fp64:" if precision == "fp64" else "mixed:") + name + (":tc" if precision != "fp64" and tc_ana else "")
     out["traffic"] = _traffic(kfile, key)
     out.update({"ms_per_launch": per_launch_ms, "triples_per_launch": triples,
                 "algorithmic_flops_per_launch": flops})

@@ -246,10 +246,14 @@ SHT_API void sht_plan_destroy(sht_plan_t plan);
  * sht_plan_get_tiling writes the current pairs per thread and, when the
  * pointers are not NULL, the number of candidates and the candidates (at most
  * 4).  sht_plan_set_tiling selects a candidate (SHT_ERR_UNSUPPORTED for any
- * other value).  sht_plan_autotune runs the plan's analysis Legendre kernel
- * once untimed and twice timed per candidate on cuda_stream, keeps the
- * fastest and, if ms_per_candidate is not NULL, writes each candidate's time
- * per run.  It overwrites the plan's phase workspace, synchronises the stream
+ * other value, and for any value but 1 while the tensor-core analysis is on).
+ * sht_plan_autotune runs the plan's analysis Legendre kernel once untimed and
+ * twice timed per candidate on cuda_stream -- the tilings with the double-float
+ * analysis and, for a mixed plan of a shape the tensor-core analysis supports,
+ * that analysis (one pair per thread) -- keeps the fastest (setting
+ * sht_plan_set_tensor_core_analysis accordingly) and, if ms_per_candidate is not
+ * NULL (room for ncandidates + 1 floats), writes each candidate's time per run,
+ * the tensor-core analysis' last (0 where it is no candidate).  It overwrites the plan's phase workspace, synchronises the stream
  * and must not be captured.  Results do not depend on the tiling beyond
  * rounding.  Neither call may change a plan that a batch refers to
  * (SHT_ERR_INVALID_ARG).  Errors: SHT_ERR_INVALID_ARG, SHT_ERR_UNSUPPORTED,
@@ -327,6 +331,29 @@ SHT_API int sht_plan_get_fft_precision(sht_plan_t plan, int *precision);
 SHT_API int sht_plan_set_tensor_cores(sht_plan_t plan, int on);
 SHT_API int sht_plan_get_tensor_cores(sht_plan_t plan, int *on);
 SHT_API int sht_plan_device_status(sht_plan_t plan, int *status);
+
+/* ---- the analysis contraction on the tensor cores ----------------------------
+ * The paper's analysis (Eq. ana1; the loop over rings inside the loop over l,
+ * Sect. 3.2, Fig. 2) is, for one m and the ring pairs of a tile, a product
+ * a = G Lambda over the ring pairs.  A mixed plan can run it transposed on the
+ * tensor cores: the double-float recursion of Sect. 4.1 still generates Lambda,
+ * one thread per ring pair, which is split exactly into six bf16 digits of
+ * Lambda / u_p (u_p the ring pair's own bound, found once at plan creation);
+ * the ring pair's phase values times u_p are split into six bf16 digits on a
+ * grid per tile and column; the digit products are summed over the tile's pairs
+ * in FP32 accumulators where no rounding can occur, and the levels are added in
+ * double-float.  Shapes: ncomp <= 2 (SHT_ERR_UNSUPPORTED otherwise); tiles of
+ * one pair per thread (the call sets that tiling).  It serves SHT_ANALYSIS and
+ * SHT_ADJOINT_SYNTHESIS through sht_execute, sht_execute_noalloc and the stage
+ * call; batches run the double-float analysis.  sht_plan_autotune selects it
+ * where it is measured faster; sht_plan_set_tensor_core_analysis(plan, 1 or 0)
+ * sets it, sht_plan_get_tensor_core_analysis reads it.  Its waits are bounded
+ * like the synthesis kernel's (status word bit 0).  Errors: SHT_ERR_INVALID_ARG
+ * (NULL, an FP64 plan, a plan in a batch), SHT_ERR_UNSUPPORTED, and those of
+ * sht_plan_set_tiling.
+ */
+SHT_API int sht_plan_set_tensor_core_analysis(sht_plan_t plan, int on);
+SHT_API int sht_plan_get_tensor_core_analysis(sht_plan_t plan, int *on);
 
 /* ---- measurement ----------------------------------------------------------
  * Sect. 5.2 times whole transforms by wall clock; these two calls report the

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsht_gb300.so")
-UNITS = ["sht_host.cu", "tables.cu", "legendre_fp64.cu", "legendre_mixed.cu", "legendre_tc.cu", "fft.cu", "noalloc.cu", "stages.cu", "batch.cu", "peaks.cu"]
-HEADERS = ["sht_internal.h", "sht_device.cuh", "df.cuh", "mixed_common.cuh"]
+UNITS = ["sht_host.cu", "tables.cu", "legendre_fp64.cu", "legendre_mixed.cu", "legendre_tc.cu", "legendre_tc_ana.cu", "fft.cu", "noalloc.cu", "stages.cu", "batch.cu", "peaks.cu"]
+HEADERS = ["sht_internal.h", "sht_device.cuh", "df.cuh", "mixed_common.cuh", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

@@ -850,6 +850,7 @@ cudaError_t launch_leg_mixed_items(const sht_plan_s *P, int stage, int polar, co
     }
   } else {
     a.ana_items = static_cast<const int4 *>(items);
+    if (P->tc_ana) return launch_leg_tc_ana(P, &a, n, st);
     if (P->spin == 0)
       ana_shape_s0(nj, P->ana_ppt, [&](auto sh) {
         mix_ana<decltype(sh)::nj, decltype(sh)::ppt, false><<<n, kAnaThreads, 0, st>>>(a);

@@ -112,9 +112,14 @@ inline void ana_shape_s0(int nj, int ppt, F &&f) {
     case 1:
       if (ppt == 8) f(AnaShape<1, 8>{});
       else if (ppt == 2) f(AnaShape<1, 2>{});
+      else if (ppt == 1) f(AnaShape<1, 1>{});  // the tensor-core analysis' tiling (its FP64 items)
       else f(AnaShape<1, 4>{});
       break;
-    case 2: if (ppt == 2) f(AnaShape<2, 2>{}); else f(AnaShape<2, 4>{}); break;
+    case 2:
+      if (ppt == 2) f(AnaShape<2, 2>{});
+      else if (ppt == 1) f(AnaShape<2, 1>{});
+      else f(AnaShape<2, 4>{});
+      break;
     case 4: f(AnaShape<4, 2>{}); break;
     case 8: f(AnaShape<8, 2>{}); break;
     default: f(AnaShape<16, 2>{}); break;

@@ -1113,6 +1113,7 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   if (P->precision == SHT_MIXED) {
     P->tc_lam_bound = tc_lambda_bound(P->lmax);
     CUDA_TRY(tc_prepare_device());
+    CUDA_TRY(tc_ana_prepare_device());
     // the tensor-core synthesis by default wherever it was measured faster: every
     // supported shape except a single spin-0 map (lmax 4095: 32.1 ms against 25.6)
     P->tc_syn = tc_supported(P->spin, P->njobs_pad) && !(P->spin == 0 && P->njobs_pad == 1);
@@ -1262,6 +1263,8 @@ extern "C" int sht_plan_set_tiling(sht_plan_t P, int pairs_per_thread) {
     return fail(SHT_ERR_UNSUPPORTED, "no analysis kernel with %d ring pairs per thread for this plan",
                 pairs_per_thread);
   if (pairs_per_thread == P->ana_ppt) return SHT_OK;
+  if (P->tc_ana)
+    return fail(SHT_ERR_UNSUPPORTED, "the tensor-core analysis takes one ring pair per thread");
   return retile(P, pairs_per_thread);
 }
 
@@ -1333,6 +1336,27 @@ extern "C" int sht_plan_set_tensor_cores(sht_plan_t P, int on) {
   return SHT_OK;
 }
 
+extern "C" int sht_plan_set_tensor_core_analysis(sht_plan_t P, int on) {
+  if (!P) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  if (on && P->precision != SHT_MIXED) return fail(SHT_ERR_INVALID_ARG, "FP64 plans have no tensor-core form");
+  if (on && !tc_ana_supported(P->spin, P->njobs_pad))
+    return fail(SHT_ERR_UNSUPPORTED, "tensor-core analysis holds at most two jobs (ncomp <= 2)");
+  if (P->batch_refs)
+    return fail(SHT_ERR_INVALID_ARG, "the plan belongs to %d batch(es); destroy them first", P->batch_refs);
+  if (on && P->ana_ppt != 1) {  // its tiles: one ring pair per thread
+    const int rc = retile(P, 1);
+    if (rc != SHT_OK) return rc;
+  }
+  P->tc_ana = on ? 1 : 0;
+  return SHT_OK;
+}
+
+extern "C" int sht_plan_get_tensor_core_analysis(sht_plan_t P, int *on) {
+  if (!P || !on) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
+  *on = P->tc_ana;
+  return SHT_OK;
+}
+
 extern "C" int sht_plan_get_tensor_cores(sht_plan_t P, int *on) {
   if (!P || !on) return fail(SHT_ERR_INVALID_ARG, "NULL argument");
   *on = P->tc_syn;
@@ -1371,8 +1395,18 @@ extern "C" int sht_plan_autotune(sht_plan_t P, void *stream, float *ms_per_candi
   if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
   DevPtrs none;
   memset(&none, 0, sizeof(none));
-  for (size_t i = 0; i < cands.size() && e == cudaSuccess && rc == SHT_OK; ++i) {
-    if ((rc = build_ana_lists(P, cands[i])) != SHT_OK) break;
+  // the tiling candidates with the double-float analysis, then (mixed plans of
+  // supported shapes) the tensor-core analysis on tiles of one pair per thread
+  const bool tc_cand = P->precision == SHT_MIXED && tc_ana_supported(P->spin, P->njobs_pad);
+  const size_t ncand = cands.size() + (tc_cand ? 1 : 0);
+  int best_tc = P->tc_ana;
+  if (ms_per_candidate)
+    for (size_t i = 0; i <= cands.size(); ++i) ms_per_candidate[i] = 0.f;
+  for (size_t i = 0; i < ncand && e == cudaSuccess && rc == SHT_OK; ++i) {
+    const bool tc = i == cands.size();
+    const int ppt = tc ? 1 : cands[i];
+    P->tc_ana = tc ? 1 : 0;
+    if ((rc = build_ana_lists(P, ppt)) != SHT_OK) break;
     // one untimed and two timed runs of the analysis Legendre stage (polar cut on)
     for (int it = 0; it < 3 && e == cudaSuccess; ++it) {
       if (it == 1) e = cudaEventRecord(ev[0], st);
@@ -1387,9 +1421,11 @@ extern "C" int sht_plan_autotune(sht_plan_t P, void *stream, float *ms_per_candi
     if (ms_per_candidate) ms_per_candidate[i] = ms / 2;
     if (e == cudaSuccess && (i == 0 || ms < best_ms)) {
       best_ms = ms;
-      best = cands[i];
+      best = ppt;
+      best_tc = tc ? 1 : 0;
     }
   }
+  P->tc_ana = best_tc;
   if (rc == SHT_OK && e == cudaSuccess && P->ana_ppt != best) rc = build_ana_lists(P, best);
   for (auto x : ev)
     if (x) cudaEventDestroy(x);

@@ -166,6 +166,9 @@ struct sht_plan_s {
   bool fft_df = false;  // ring FFTs in double-float (mixed plans, by default)
   // mixed plans: the synthesis contraction on the tensor cores (legendre_tc.cu)
   int tc_syn = 0;
+  // mixed plans: the analysis contraction on the tensor cores (legendre_tc_ana.cu;
+  // tiles of kAnaThreads ring pairs, one per thread)
+  int tc_ana = 0;
   float tc_lam_bound = 0.f;  // power of two bounding |Lambda_lm| for lmax
   int *d_err = nullptr;      // device status word written by kernels with bounded waits
   float4 *d_join = nullptr;  // mixed plans: join record per (m index, pair), 3 float4 each
@@ -265,6 +268,10 @@ void leg_tc_fill_args(const sht_plan_s *P, int polar, int ptr_off, void *out);
 cudaError_t launch_leg_tc_batch(int spin, int nj, const void *targs, const int4 *items, int n, cudaStream_t st);
 bool tc_supported(int spin, int njobs_pad);
 float tc_lambda_bound(int lmax);
+// tensor-core analysis (legendre_tc_ana.cu): mixargs with its analysis work list set
+cudaError_t launch_leg_tc_ana(const sht_plan_s *P, const void *mixargs, int n, cudaStream_t st);
+cudaError_t tc_ana_prepare_device();
+bool tc_ana_supported(int spin, int njobs_pad);
 // ring FFTs
 // ring pairs [p0, p1) (p1 < 0: to the last pair)
 cudaError_t launch_fft_syn(const sht_plan_s *P, const DevPtrs &map, int polar, int weighted, int add,

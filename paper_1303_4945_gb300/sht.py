@@ -81,6 +81,8 @@ _sig = {
     "sht_plan_get_fft_precision": [_vp, _ip],
     "sht_plan_set_tensor_cores": [_vp, ctypes.c_int],
     "sht_plan_get_tensor_cores": [_vp, _ip],
+    "sht_plan_set_tensor_core_analysis": [_vp, ctypes.c_int],
+    "sht_plan_get_tensor_core_analysis": [_vp, _ip],
     "sht_plan_device_status": [_vp, _ip],
     "sht_batch_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "sht_batch_execute": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(ctypes.POINTER(_vp)),
@@ -220,12 +222,17 @@ class Plan(_Handle):
         _check(_lib.sht_plan_set_tiling(self._h, pairs_per_thread), "sht_plan_set_tiling")
 
     def autotune(self, stream=None):
-        """Times every candidate tiling, keeps the fastest; returns {candidate: ms per run}."""
+        """Times every candidate tiling (and, for mixed plans of up to two jobs, the
+        tensor-core analysis), keeps the fastest; returns {candidate: ms per run},
+        the tensor-core analysis under "tensor_cores"."""
         _, cands = self.tiling()
-        ms = (ctypes.c_float * 4)()
+        ms = (ctypes.c_float * 5)()
         st = None if stream is None else _vp(_devptr_stream(stream))
         _check(_lib.sht_plan_autotune(self._h, st, ms), "sht_plan_autotune")
-        return {c: float(ms[i]) for i, c in enumerate(cands)}
+        out = {c: float(ms[i]) for i, c in enumerate(cands)}
+        if ms[len(cands)] > 0:
+            out["tensor_cores"] = float(ms[len(cands)])
+        return out
 
     @property
     def fp64_columns(self):
@@ -259,6 +266,17 @@ class Plan(_Handle):
     @tensor_cores.setter
     def tensor_cores(self, on):
         _check(_lib.sht_plan_set_tensor_cores(self._h, 1 if on else 0), "sht_plan_set_tensor_cores")
+
+    @property
+    def tensor_core_analysis(self):
+        """Mixed plans: True when the analysis contraction runs on the tensor cores."""
+        n = ctypes.c_int()
+        _check(_lib.sht_plan_get_tensor_core_analysis(self._h, ctypes.byref(n)), "sht_plan_get_tensor_core_analysis")
+        return bool(n.value)
+
+    @tensor_core_analysis.setter
+    def tensor_core_analysis(self, on):
+        _check(_lib.sht_plan_set_tensor_core_analysis(self._h, 1 if on else 0), "sht_plan_set_tensor_core_analysis")
 
     def device_status(self):
         """Synchronises; raises ShtError (SHT_ERR_TIMEOUT) if a bounded device-side wait gave up."""

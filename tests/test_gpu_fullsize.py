@@ -80,3 +80,22 @@ def test_headline_workload_against_oracle(setup, precision):
         err = rel_l2(got.cpu().numpy()[sel], ref[sel])
         print("precision", precision, "sampled m rel L2", f"{err:.2e}")
         assert err <= TOL[precision]
+
+
+def test_headline_analysis_tensor_cores(setup):
+    # the mixed analysis with its contraction on the tensor cores, whichever the
+    # autotuner would pick: the sampled m against the oracle
+    sht, rings, alm, maps_in, ref_syn, ref_ana = setup
+    geom = sht.sht_geom_gauss(NLAT, NLON)
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(LMAX, LMAX), SPIN, 1, 1)
+    plan.tensor_core_analysis = True
+    out = [torch.empty(len(a), dtype=torch.complex128, device="cuda") for a in alm]
+    sht.sht_execute(plan, sht.SHT_ANALYSIS, out, [torch.from_numpy(m).cuda() for m in maps_in], 0)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    _, m = inputs.lm_arrays(LMAX, LMAX)
+    sel = np.isin(m, MS)
+    for got, ref in zip(out, ref_ana):
+        err = rel_l2(got.cpu().numpy()[sel], ref[sel])
+        print("tensor-core analysis, sampled m rel L2", f"{err:.2e}")
+        assert err <= TOL[1]
