@@ -830,8 +830,9 @@ def run_decomposed(args, world, rank, local):
 
 def run_pair_workload(args, world, rank, local):
     """Profiling captures: the headline transform pair with the default mixed plan at
-    --lmax (GL (lmax+1) x (2 lmax+1), spin 2, the bench's a_lm seed, analysis tiling
-    autotuned as the bench does: 9 untimed analysis launches), one untimed pair and
+    --lmax (GL (lmax+1) x (2 lmax+1), spin 2, the bench's a_lm seed, analysis
+    autotuned as the bench does: 3 untimed launches per candidate, the three
+    double-float tilings and then the tensor-core analysis), one untimed pair and
     then --steps pairs, nothing else; prints the CUDA-event time per pair."""
     import torch
 
@@ -855,7 +856,8 @@ def run_pair_workload(args, world, rank, local):
 
     ms = _events_ms(torch, stream, step, args.steps, 1, world)
     if rank == 0:
-        print(json.dumps({"workload": "pair", "lmax": LMAX, "tensor_cores": plan.tensor_cores, "ms_per_pair": ms,
+        print(json.dumps({"workload": "pair", "lmax": LMAX, "tensor_cores": plan.tensor_cores,
+                          "tensor_core_analysis": plan.tensor_core_analysis, "ms_per_pair": ms,
                           "analysis_pairs_per_thread": plan.tiling()[0],
                           "device_status": plan.device_status()}), flush=True)
 
