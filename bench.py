@@ -361,10 +361,10 @@ MEASURED_TRAFFIC = {
     # one launch at the headline size (spin 2, GL 4096 x 8191, lmax 4095), single-pass
     # dram__bytes_read.sum + dram__bytes_write.sum (the pair's traffic capture under profiles/);
     # sha256 over the kernel file and its headers (_kernel_digest)
-    "mixed:legendre_analysis": {"bytes": 5595713280 + 2818798592,
-                                "sha256": "ec6e8d30b68eb738436d03ddd7f7e27ff74a785a80803814482bf2dbf745326c"},
-    "mixed:legendre_synthesis": {"bytes": 823961856 + 333659136,
-                                 "sha256": "5cdd776c9779879a6d41e0c87c65a2f4e02360cf195ec26fe32d3963129ee8e6"},
+    "mixed:legendre_analysis:tc": {"bytes": 3972392448 + 2118539264,
+                                   "sha256": "359746cccda4b482b3a8270fbf9897eae624481eff82c9df78f8e598a2b032ae"},
+    "mixed:legendre_synthesis": {"bytes": 821292800 + 333250304,
+                                 "sha256": "496732199f70bc1042da624d1beee0f0a165b65442e88dd40586423658ea2a5f"},
 }
 
 
@@ -1031,7 +1031,11 @@ def main():
                          "setup": {"plan_create_ms": 1e3 * (t1 - t0), "autotune_ms": 1e3 * (t2 - t1),
                                    "workspace_over_data": plan.workspace() / data_bytes},
                          "fp64_columns": plan.fp64_columns if prec == sht.SHT_MIXED else 0,
+                         "analysis_contraction": ("tensor cores (tcgen05, exact bf16 digit split)"
+                                                  if prec == sht.SHT_MIXED and plan.tensor_core_analysis
+                                                  else ("FP64" if prec == sht.SHT_FP64 else "double-float FP32")),
                          "tiling": {"analysis_pairs_per_thread": plan.tiling()[0],
+                                    "tensor_core_analysis": prec == sht.SHT_MIXED and plan.tensor_core_analysis,
                                     "autotune_ms_per_candidate": {str(k): v for k, v in tune.items()}}}
         outputs[name] = {"maps": [m.cpu().numpy() for m in maps_d], "alm": [a.cpu().numpy() for a in out_d]}
         if world == 1:
@@ -1063,7 +1067,10 @@ def main():
     plan = sht.sht_plan_create(geom, lay, SPIN, 1, forms[head][0])
     if forms[head][0] == sht.SHT_MIXED:
         plan.tensor_cores = forms[head][1]
-    plan.set_tiling(results[head]["tiling"]["analysis_pairs_per_thread"])
+    if results[head]["tiling"]["tensor_core_analysis"]:  # the analysis the autotuner chose for the headline
+        plan.tensor_core_analysis = True
+    else:
+        plan.set_tiling(results[head]["tiling"]["analysis_pairs_per_thread"])
     host_in = [torch.from_numpy(a).pin_memory() for a in alm_h]
     host_out = [[torch.empty(a.shape, dtype=torch.complex128).pin_memory() for a in alm_h] for _ in range(2)]
     in_d = [alm_d, [torch.empty_like(a) for a in alm_d]]
