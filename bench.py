@@ -362,7 +362,7 @@ MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum (the pair's traffic capture under profiles/);
     # sha256 over the kernel file and its headers (_kernel_digest)
     "mixed:legendre_analysis:tc": {"bytes": 3972392448 + 2118539264,
-                                   "sha256": "359746cccda4b482b3a8270fbf9897eae624481eff82c9df78f8e598a2b032ae"},
+                                   "sha256": "a93ae606e1efcaf14b4e91f8a39fb804c9d3b8c4040d86f34506a0f11a899d50"},
     "mixed:legendre_synthesis": {"bytes": 821292800 + 333250304,
                                  "sha256": "496732199f70bc1042da624d1beee0f0a165b65442e88dd40586423658ea2a5f"},
 }

@@ -144,8 +144,9 @@ __global__ void __launch_bounds__(tca::kPairs, (tca::AnaShape<NJ, SPIN>::MINB)) 
   const double sg0 = ((l0 + m) & 1) ? -1.0 : 1.0;
   unsigned char *const Abuf = tca_smem;
   unsigned char *const Bbuf = tca_smem + S::A_BYTES;
-  // a reading warp's staged D rows (kN columns each)
-  float *const Ebuf = reinterpret_cast<float *>(tca_smem + S::A_BYTES + S::B_BYTES) + (warp % S::NREAD) * S::EROWS * tca::kEStride;
+  // a reading warp's staged D rows (kN columns each; the other warps never use theirs)
+  float *const Ebuf =
+      reinterpret_cast<float *>(tca_smem + S::A_BYTES + S::B_BYTES) + (warp % S::NREAD) * S::EROWS * tca::kEStride;
 
   if (warp == 0) tc::tmem_alloc(&tslot, 2 * tca::kDCols);
   if (tid == 0) {
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(tca::kPairs, (tca::AnaShape<NJ, SPIN>::MINB)) 
     for (int w = 0; w < tca::kWarps; ++w) tc::bar_init(&mine[w], 1);
     stop = 0;
   }
-  // A starts at zero: the zero rows before each column's digits stay so
+  // A starts at zero: rows 6 and 7 of each column (below its six digits) stay so
   for (int i = tid; i < S::A_BYTES / 16; i += tca::kPairs) reinterpret_cast<uint4 *>(Abuf)[i] = make_uint4(0, 0, 0, 0);
   tc::fence_before();
   __syncthreads();
