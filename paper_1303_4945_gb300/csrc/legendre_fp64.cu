@@ -28,7 +28,7 @@ struct LegArgs {
   const int64_t *coef_off;
   const Coef *coef;
   const double2 *pm;  // spin: P = E + iB, M = E - iB per (array, m, l), indexed like coef
-  int64_t ncoef;
+  int64_t ncoef;      // pm's entries per array
   const double2 *mpre;
   const PairDev *pairs;
   DevPtrs alm;
@@ -725,6 +725,7 @@ __global__ void alm_to_pm(int lmax, int spin, int nm, int astride, const int *__
                           const int64_t *__restrict__ mstart, const int64_t *__restrict__ coef_off, int64_t ncoef,
                           DevPtrs alm, double2 *__restrict__ out, int mode) {
   const int mi = blockIdx.x, j = blockIdx.y;
+  if (coef_off[mi] >= ncoef) return;  // beyond the table (a mixed plan's m above its FP64 columns)
   const int deriv = mode & kAlmDeriv, real = (mode & kAlmReal) && mval[mi] > 0;
   const int m = mval[mi];
   const double hf = ((mode & kAlmHalf) && m > 0) ? 0.5 : 1.0;
@@ -768,7 +769,7 @@ static LegArgs make_args(const sht_plan_s *P, const DevPtrs &alm, int polar, boo
   a.coef_off = P->d_coef_off;
   a.coef = P->d_coef;
   a.pm = P->d_pm64;
-  a.ncoef = P->ncoef;
+  a.ncoef = P->ncoef64;  // the P/M table's stride between arrays
   a.mpre = P->d_mpre;
   a.pairs = P->d_pairs;
   a.alm = alm;
@@ -872,7 +873,7 @@ cudaError_t launch_alm_prepare_fp64(const sht_plan_s *P, const DevPtrs &alm, cud
   if (P->spin == 0 || P->nm == 0) return cudaSuccess;
   dim3 g(P->nm, P->njobs_pad);
   alm_to_pm<<<g, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->astride, P->d_mval, P->d_mstart, P->d_coef_off,
-                               P->ncoef, alm, P->d_pm64, mode);
+                               P->ncoef64, alm, P->d_pm64, mode);
   return cudaGetLastError();
 }
 

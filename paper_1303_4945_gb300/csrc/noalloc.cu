@@ -79,7 +79,7 @@ extern "C" int sht_execute_noalloc(sht_plan_t P, int type, double *const *alm, d
   const int64_t b_alm32 = (synth && mixed) ? align256(P->ncoef * P->nmaps_pad * (int64_t)sizeof(float4)) : 0;
   const bool lo = mixed && (P->nsyn_lo[0] || P->nsyn_lo[1]);  // mixed plan with FP64 columns
   const int64_t b_pm64 =
-      (synth && P->spin && (!mixed || lo)) ? align256(P->ncoef * P->nmaps_pad * (int64_t)sizeof(double2)) : 0;
+      (synth && P->spin && (!mixed || lo)) ? align256(P->ncoef64 * P->nmaps_pad * (int64_t)sizeof(double2)) : 0;
   const int64_t need = b_phase + b_part + b_alm32 + b_pm64;
   if (need > kNoallocBytes)
     return set_error(SHT_ERR_UNSUPPORTED, "this transform needs %lld bytes of working memory; the static area holds %lld",

@@ -900,6 +900,18 @@ static std::vector<int> ana_ppt_candidates(int spin, int nj) {
 // are below 3e-11 without them, and the items would no longer be hidden.
 static int default_fp64_columns(int lmax) { return lmax < 2000 ? 0 : lmax / 170; }
 
+// Entries of the coefficient table that the columns m < m_below occupy, as a
+// prefix (their last entry + 1): what a mixed plan's FP64 tables must hold.
+static int64_t fp64_prefix(const sht_plan_s *P, int m_below) {
+  int64_t n = 0;
+  for (int i = 0; i < P->nm; ++i)
+    if (P->mval[i] < m_below) {
+      const int l0 = std::max(P->mval[i], std::abs(P->spin));
+      n = std::max<int64_t>(n, P->coef_off[i] + std::max(0, P->lmax - l0 + 1));
+    }
+  return n;
+}
+
 // an item of column mi over ring pairs [p0, p1) runs in FP64 (mixed plans only)
 static bool lo_item(const sht_plan_s *P, int mi, int p0, int p1) {
   if (P->precision != SHT_MIXED || P->mval[mi] >= P->fp64_m_below) return false;
@@ -1095,8 +1107,11 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
   if ((rc = upload(P, P->mstart, &P->d_mstart)) != SHT_OK) return rc;
   if ((rc = upload(P, coff, &P->d_coef_off)) != SHT_OK) return rc;
   if ((rc = upload(P, minv, &P->d_minv)) != SHT_OK) return rc;
-  CUDA_TRY(cudaMalloc(&P->d_coef, std::max<int64_t>(1, nco) * sizeof(Coef)));
-  P->workspace += nco * sizeof(Coef);
+  // the FP64 tables: every entry for an FP64 plan; for a mixed plan the prefix its
+  // default FP64 columns read (grown by sht_plan_set_fp64_columns when needed)
+  P->ncoef64 = P->precision == SHT_MIXED ? fp64_prefix(P, default_fp64_columns(P->lmax)) : nco;
+  CUDA_TRY(cudaMalloc(&P->d_coef, std::max<int64_t>(1, P->ncoef64) * sizeof(Coef)));
+  P->workspace += P->ncoef64 * sizeof(Coef);
   if (P->precision == SHT_MIXED) {
     CUDA_TRY(cudaMalloc(&P->d_coef32, std::max<int64_t>(1, nco) * 2 * sizeof(float4)));
     P->workspace += nco * 2 * sizeof(float4);
@@ -1104,8 +1119,8 @@ static int plan_build(sht_plan_s *P, const sht_geom_s *g) {
     P->workspace += nco * P->nmaps_pad * sizeof(float4);
   }
   if (P->spin != 0 && (P->precision == SHT_FP64 || default_fp64_columns(P->lmax) > 0)) {
-    CUDA_TRY(cudaMalloc(&P->d_pm64, std::max<int64_t>(1, nco) * P->nmaps_pad * sizeof(double2)));
-    P->workspace += nco * P->nmaps_pad * sizeof(double2);
+    CUDA_TRY(cudaMalloc(&P->d_pm64, std::max<int64_t>(1, P->ncoef64) * P->nmaps_pad * sizeof(double2)));
+    P->workspace += P->ncoef64 * P->nmaps_pad * sizeof(double2);
   }
   CUDA_TRY(cudaMalloc(&P->d_mpre, P->nm * sizeof(double2)));
   CUDA_TRY(cudaMalloc(&P->d_err, sizeof(int)));
@@ -1288,10 +1303,36 @@ extern "C" int sht_plan_set_fp64_columns(sht_plan_t P, int m_below) {
   cudaGetDevice(&cur);
   if (cur != P->device) CUDA_TRY(cudaSetDevice(P->device));
   int rc = SHT_OK;
-  if (P->spin != 0 && !P->d_pm64 && m_below > 0) {  // the FP64 spin kernels read P = E+iB, M = E-iB
-    const size_t bytes = std::max<int64_t>(1, P->ncoef) * P->nmaps_pad * sizeof(double2);
-    if (cudaMalloc(&P->d_pm64, bytes) != cudaSuccess) rc = fail(SHT_ERR_OOM, "P/M table");
-    else P->workspace += bytes;
+  // the FP64 tables (coefficients; at spin s the P = E+iB, M = E-iB table the FP64
+  // spin kernels read) must reach the new columns: regrow them to the new prefix
+  const int64_t need = fp64_prefix(P, m_below);
+  if (need > P->ncoef64 || (P->spin != 0 && !P->d_pm64 && m_below > 0)) {
+    const int64_t n = std::max(need, P->ncoef64);
+    Coef *coef = nullptr;
+    double2 *pm = nullptr;
+    if (cudaMalloc(&coef, std::max<int64_t>(1, n) * sizeof(Coef)) != cudaSuccess) {
+      rc = fail(SHT_ERR_OOM, "FP64 coefficient table");
+    } else if (P->spin != 0 &&
+               cudaMalloc(&pm, std::max<int64_t>(1, n) * P->nmaps_pad * sizeof(double2)) != cudaSuccess) {
+      cudaFree(coef);
+      rc = fail(SHT_ERR_OOM, "P/M table");
+    } else {
+      cudaFree(P->d_coef);
+      P->workspace += (n - P->ncoef64) * (int64_t)sizeof(Coef);
+      P->d_coef = coef;
+      if (P->spin != 0) {
+        if (P->d_pm64) {
+          cudaFree(P->d_pm64);
+          P->workspace -= P->ncoef64 * P->nmaps_pad * (int64_t)sizeof(double2);
+        }
+        P->d_pm64 = pm;
+        P->workspace += n * P->nmaps_pad * (int64_t)sizeof(double2);
+      }
+      P->ncoef64 = n;
+      cudaError_t e = launch_coef_tables(P, 0);  // the FP64 coefficients of the new prefix
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) rc = fail(SHT_ERR_CUDA, "coefficient tables: %s", cudaGetErrorString(e));
+    }
   }
   if (rc == SHT_OK) {
     P->fp64_m_below = m_below;

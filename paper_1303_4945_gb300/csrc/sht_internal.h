@@ -2,7 +2,7 @@
 //
 // Layout of the device data a plan holds (all in HBM, built once at plan time):
 //   pairs      PairDev[npairs]      ring pairs sorted pole -> equator (Sect. 3.3 order)
-//   coef       Coef[ncoef]          recursion coefficients {A, AK, C, 0} per (m, l), Sect. 4.1
+//   coef       Coef[ncoef64]        recursion coefficients {A, AK, C, 0} per (m, l), Sect. 4.1
 //   coef32     float4[2*ncoef]      the same split into FP32 pairs (mixed form)
 //   mpre       double2[nm]          start-value prefactor (mantissa, exponent) per m
 //   F / G      double2[nmaps][nm][npairs][2]   phase arrays of Eqs. syn2 / ana2 (north, south)
@@ -127,6 +127,9 @@ struct sht_plan_s {
   std::vector<int> first_pair;             // per m: first pair not removed by the polar cut
   std::vector<int64_t> coef_off;           // per m: table index of l = l0
   int64_t ncoef = 0;
+  // entries of the FP64 tables (coef, and d_pm64 per array): all of them for an FP64
+  // plan; for a mixed plan the prefix its FP64 columns read (m < the FP64 column bound)
+  int64_t ncoef64 = 0;
 
   // device arrays
   sht::PairDev *d_pairs = nullptr;
@@ -138,7 +141,7 @@ struct sht_plan_s {
   sht::Coef *d_coef = nullptr;
   float4 *d_coef32 = nullptr;
   float4 *d_alm32 = nullptr;               // mixed form: a_lm as double-float pairs [array][ncoef]
-  double2 *d_pm64 = nullptr;               // FP64 spin form: P = E + iB, M = E - iB [array][ncoef]
+  double2 *d_pm64 = nullptr;               // FP64 spin form: P = E + iB, M = E - iB [array][ncoef64]
   double2 *d_mpre = nullptr;
   int *d_minv = nullptr;                   // m -> index in mval, or -1
   double2 *d_phase = nullptr;              // F / G workspace

@@ -18,8 +18,10 @@
 
 namespace sht {
 
+// coef: the FP64 table's first ncoef64 entries (a mixed plan keeps only the prefix
+// its FP64 columns read); coef32 (mixed plans): every entry
 __global__ void coef_kernel(int lmax, int spin, int nm, const int *__restrict__ mval,
-                            const int64_t *__restrict__ coef_off, Coef *__restrict__ coef,
+                            const int64_t *__restrict__ coef_off, Coef *__restrict__ coef, int64_t ncoef64,
                             float4 *__restrict__ coef32) {
   const int mi = blockIdx.x;
   if (mi >= nm) return;
@@ -38,7 +40,7 @@ __global__ void coef_kernel(int lmax, int spin, int nm, const int *__restrict__ 
       C = sqrt((2.0 * L + 3.0) / (2.0 * L - 1.0)) * (L1 / L) * sqrt(pa / qa) * sqrt(pb / qb);
     }
     const int64_t i = coef_off[mi] + (l - l0);
-    coef[i] = Coef{A, AK, C, 0.0};
+    if (i < ncoef64) coef[i] = Coef{A, AK, C, 0.0};
     if (coef32) {
       const float ah = (float)A, kh = (float)AK, ch = (float)C;
       coef32[2 * i] = make_float4(ah, (float)(A - (double)ah), kh, (float)(AK - (double)kh));
@@ -90,7 +92,7 @@ __global__ void prefactor_kernel(int spin, int nm, const int *__restrict__ mval,
 
 cudaError_t launch_coef_tables(const sht_plan_s *P, cudaStream_t st) {
   if (P->nm > 0) {
-    coef_kernel<<<P->nm, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->d_mval, P->d_coef_off, P->d_coef,
+    coef_kernel<<<P->nm, 256, 0, st>>>(P->lmax, P->spin, P->nm, P->d_mval, P->d_coef_off, P->d_coef, P->ncoef64,
                                        P->d_coef32);
     prefactor_kernel<<<(P->nm + 127) / 128, 128, 0, st>>>(P->spin, P->nm, P->d_mval, P->d_mpre);
   }
