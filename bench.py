@@ -362,7 +362,7 @@ MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum (the pair's traffic capture under profiles/);
     # sha256 over the kernel file and its headers (_kernel_digest)
     "mixed:legendre_analysis:tc": {"bytes": 3972392448 + 2118539264,
-                                   "sha256": "a93ae606e1efcaf14b4e91f8a39fb804c9d3b8c4040d86f34506a0f11a899d50"},
+                                   "sha256": "a4ba9ae45c7cbca6de42ac84185752e21aa480a9b4ca012788c4285d2ef23ab0"},
     "mixed:legendre_synthesis": {"bytes": 821292800 + 333250304,
                                  "sha256": "496732199f70bc1042da624d1beee0f0a165b65442e88dd40586423658ea2a5f"},
 }
