@@ -67,6 +67,7 @@ struct F64 {
   using C = double2;
   using S = double;
   static constexpr int kRegRadix = kMaxRadix;  // largest odd radix with a register-resident butterfly
+  static constexpr int kRollFrom = kMaxRadix + 2;  // odd radices whose outputs run one k at a time: none
   static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
   static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
   static __device__ __forceinline__ C sub(C a, C b) { return csub(a, b); }
@@ -103,6 +104,9 @@ struct DF {
   using C = cf2;
   using S = f2;
   static constexpr int kRegRadix = 13;  // above, the butterfly's pairs spill: sweeps instead
+  // radices 11 and 13: the outputs one k at a time (the unrolled k loop spilled 76
+  // bytes per thread at radix 13 under the 512-thread CTA's 128 registers)
+  static constexpr int kRollFrom = 11;
   static __device__ __forceinline__ C mk(f2 r, f2 i) { return {make_float4(r.h, r.l, i.h, i.l)}; }
   static __device__ __forceinline__ S re(C a) { return {a.v.x, a.v.y}; }
   static __device__ __forceinline__ S im(C a) { return {a.v.z, a.v.w}; }
@@ -192,7 +196,9 @@ __device__ __forceinline__ void dft_small(typename N::C (&x)[R], Out &&out) {
     }
     N::fin(y0);
     out(0, y0);
-#pragma unroll
+    // (N::kRollFrom: from that radix on the outputs run one k at a time, so that not
+    // every k's constants and accumulators are live at once)
+#pragma unroll(R >= N::kRollFrom ? 1 : h)
     for (int k = 1; k <= h; ++k) {
       C A = x0, B = N::zero();
 #pragma unroll
