@@ -802,6 +802,7 @@ def run_decomposed(args, world, rank, local):
     r = geom.rings()
     part = D.Partition.round_robin(LMAX, r["theta"], world)
     stages = D.LibraryStages(sht, geom, LMAX, LMAX, SPIN, 1, sht.SHT_MIXED, part, rank, stream)
+    stages.plan_m.autotune(stream)  # the task's analysis kernel and tiling, as the headline's
     alm = inputs.spin2_eb(SEED, LMAX)
     alm_loc = [torch.from_numpy(D.alm_pack(a, LMAX, LMAX, part.m[rank])).cuda() for a in alm]
 
