@@ -9,7 +9,8 @@ partial tile; Gauss-Legendre, HEALPix (aliased rings, phi0 != 0) and
 Clenshaw-Curtis grids, with and without the polar cut; the analysis and the
 adjoint synthesis; m subsets; forced FP64 columns; the no-alloc entry point;
 inputs scaled far from 1; work items that walk several tiles into one slot of
-partial sums; and the device status word after every run.
+partial sums; the Sect. 4.2 stage calls, CUDA-graph capture and a batch of such a
+plan; and the device status word after every run.
 """
 import numpy as np
 import pytest
@@ -214,3 +215,56 @@ def test_tensor_analysis_settings(sht):
     assert "tensor_cores" not in wide.autotune(torch.cuda.current_stream())
     ok.tensor_core_analysis = False
     assert not ok.tensor_core_analysis and ok.device_status() == 0
+
+
+def test_tensor_analysis_stage_calls_graph_and_batch(sht):
+    from paper_1303_4945_gb300 import distributed as D
+
+    lmax = 200
+    geom = sht.sht_geom_gauss(lmax + 2, 2 * lmax + 1)
+    rings = rings_of(geom)
+    r = geom.rings()
+    rng = np.random.default_rng(1904)
+    maps = [inputs.gaussian_map(rng, geom.npix) for _ in range(2)]
+    nalm = oracle.nalm(lmax, lmax)
+    # the stage calls of the Sect. 4.2 decomposition (two tasks emulated on this GPU),
+    # each task's Legendre plan on the tensor-core analysis
+    part = D.Partition.round_robin(lmax, r["theta"], 2)
+    stages = [D.LibraryStages(sht, geom, lmax, lmax, 2, 1, sht.SHT_MIXED, part, k) for k in range(2)]
+    for st in stages:
+        st.plan_m.tensor_core_analysis = True
+    maps_loc = [[torch.from_numpy(p[D.ring_pixels(r["ofs"], r["nphi"], part.rings[k])]).cuda() for p in maps]
+                for k in range(2)]
+    back = D.analysis_emulated(part, stages, maps_loc)
+    torch.cuda.synchronize()
+    got = [np.zeros(nalm, dtype=np.complex128) for _ in range(2)]
+    for k in range(2):
+        assert stages[k].plan_m.device_status() == 0
+        for c in range(2):
+            D.alm_unpack(back[k][c].cpu().numpy(), lmax, lmax, part.m[k], got[c])
+    check(got, oracle.analysis(2, lmax, lmax, maps, rings))
+    # captured in a CUDA graph after one call outside the capture, replayed with new maps
+    plan = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), 2, 1, sht.SHT_MIXED)
+    plan.tensor_core_analysis = True
+    m_d = [torch.from_numpy(x).cuda() for x in maps]
+    a_d = [torch.zeros(nalm, dtype=torch.complex128, device="cuda") for _ in range(2)]
+    sht.sht_execute(plan, sht.SHT_ANALYSIS, a_d, m_d)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        sht.sht_execute(plan, sht.SHT_ANALYSIS, a_d, m_d, 0, torch.cuda.current_stream())
+    maps2 = [inputs.gaussian_map(rng, geom.npix) for _ in range(2)]
+    for x, y in zip(m_d, maps2):
+        x.copy_(torch.from_numpy(y))
+    g.replay()
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    check([a.cpu().numpy() for a in a_d], oracle.analysis(2, lmax, lmax, maps2, rings))
+    # a batch of that plan runs the double-float analysis: the same a_lm to 1e-11
+    batch = sht.sht_batch_create([plan])
+    b_d = [torch.zeros_like(a) for a in a_d]
+    sht.sht_batch_execute(batch, sht.SHT_ANALYSIS, [b_d], [m_d])
+    torch.cuda.synchronize()
+    for x, y in zip(b_d, a_d):
+        assert rel_l2(x.cpu().numpy(), y.cpu().numpy()) <= 1e-11
+    del batch
