@@ -345,7 +345,7 @@ SHT_API int sht_plan_device_status(sht_plan_t plan, int *status);
  * double-float.  Shapes: ncomp <= 2 (SHT_ERR_UNSUPPORTED otherwise); tiles of
  * one pair per thread (the call sets that tiling).  It serves SHT_ANALYSIS and
  * SHT_ADJOINT_SYNTHESIS through sht_execute, sht_execute_noalloc and the stage
- * call; batches run the double-float analysis.  sht_plan_autotune selects it
+ * call, and in a batch made while the plan has it set.  sht_plan_autotune selects it
  * where it is measured faster (GB300, lmax 4095: spin 2 one E/B pair 73.8 ms
  * against 76.5 for the double-float analysis, two pairs 100.7 against 134.1;
  * spin 0 one map 45.7 against 25.2); sht_plan_set_tensor_core_analysis(plan, 1

@@ -7,8 +7,8 @@
 // whole batch is one grid: the block scheduler hands CTAs out in index order
 // as SMs free up, i.e. greedy longest-processing-time list scheduling over the
 // uneven problems.  Plans whose Legendre kernels differ (precision, spin
-// class, padded job count, analysis tiling, synthesis on the tensor cores or
-// not) form separate groups, one launch each; every item
+// class, padded job count, analysis tiling, synthesis or analysis on the tensor
+// cores or not) form separate groups, one launch each; every item
 // carries the index of its plan's argument record, which lives on the device
 // from creation on.  Per call only the caller's array pointers change; they
 // travel in the kernel parameters (PtrTable), so an execute neither
@@ -31,7 +31,8 @@ namespace {
 struct Group {
   int precision = 0, spin = 0, nj = 1, ppt = 2;
   bool tc = false;                   // mixed plans whose synthesis runs on the tensor cores
-  void *d_targs[2] = {nullptr, nullptr};  // per polar: their TcArgs records (synthesis)
+  bool tca = false;                  // mixed plans whose analysis runs on the tensor cores
+  void *d_targs[2] = {nullptr, nullptr};  // per polar: their TcArgs records (tensor-core kernels)
   std::vector<int> plans;            // batch indices; item.w is the position in this list
   std::vector<char> lo;              // per entry: the mixed plan's FP64 columns (FP64 group)
   void *d_args[2] = {nullptr, nullptr};  // per polar: one argument record per plan
@@ -117,10 +118,11 @@ int build(sht_batch_s *B) {
     const sht_plan_s *P = B->plans[k];
     const int spin_class = P->spin ? 1 : 0;
     const bool tc = precision == SHT_MIXED && P->tc_syn;
+    const bool tca = precision == SHT_MIXED && P->tc_ana;
     Group *g = nullptr;
     for (auto &c : B->groups)
       if (c.precision == precision && c.spin == spin_class && c.nj == P->njobs_pad && c.ppt == P->ana_ppt &&
-          c.tc == tc)
+          c.tc == tc && c.tca == tca)
         g = &c;
     if (!g) {
       B->groups.emplace_back();
@@ -130,6 +132,7 @@ int build(sht_batch_s *B) {
       g->nj = P->njobs_pad;
       g->ppt = P->ana_ppt;
       g->tc = tc;
+      g->tca = tca;
     }
     g->plans.push_back(k);
     g->lo.push_back(lo ? 1 : 0);
@@ -146,7 +149,8 @@ int build(sht_batch_s *B) {
     const size_t rec = mixed ? leg_mixed_args_size() : leg_fp64_args_size();
     for (int polar = 0; polar < 2; ++polar) {
       std::vector<unsigned char> args(rec * g.plans.size());
-      std::vector<unsigned char> targs(g.tc ? tc_args_size() * g.plans.size() : 0);
+      const bool tcrec = g.tc || g.tca;
+      std::vector<unsigned char> targs(tcrec ? tc_args_size() * g.plans.size() : 0);
       std::vector<std::pair<int64_t, int4>> syn, ana;
       for (size_t i = 0; i < g.plans.size(); ++i) {
         const int k = g.plans[i];
@@ -156,7 +160,7 @@ int build(sht_batch_s *B) {
           leg_mixed_fill_args(P, polar, B->ptr_off[k], args.data() + i * rec);
         else
           leg_fp64_fill_args(P, polar, B->ptr_off[k], args.data() + i * rec, lo);
-        if (g.tc) leg_tc_fill_args(P, polar, B->ptr_off[k], targs.data() + i * tc_args_size());
+        if (tcrec) leg_tc_fill_args(P, polar, B->ptr_off[k], targs.data() + i * tc_args_size());
         for (auto &it : (lo ? P->syn_list_lo : P->syn_list)[polar])
           syn.push_back({it.first, make_int4(it.second.x, it.second.y, 0, (int)i)});
         for (auto &it : (lo ? P->ana_list_lo : P->ana_list)[polar])
@@ -168,7 +172,7 @@ int build(sht_batch_s *B) {
       g.nsyn[polar] = (int)si.size();
       g.nana[polar] = (int)ai.size();
       if (e == cudaSuccess) e = upload_bytes(B, args, &g.d_args[polar]);
-      if (e == cudaSuccess && g.tc) e = upload_bytes(B, targs, &g.d_targs[polar]);
+      if (e == cudaSuccess && tcrec) e = upload_bytes(B, targs, &g.d_targs[polar]);
       if (e == cudaSuccess) e = upload(B, si.data(), si.size(), &g.d_syn[polar]);
       if (e == cudaSuccess) e = upload(B, ai.data(), ai.size(), &g.d_ana[polar]);
     }
@@ -311,6 +315,8 @@ extern "C" int sht_batch_execute(sht_batch_t B, int type, double *const *const *
         const int ni = stage ? g.nana[polar] : g.nsyn[polar];
         if (stage == 0 && g.tc)
           r = launch_leg_tc_batch(g.spin, g.nj, g.d_targs[polar], items, ni, s);
+        else if (stage == 1 && g.tca)
+          r = launch_leg_tc_ana_batch(g.spin, g.nj, g.d_targs[polar], items, ni, s);
         else
           r = mixed_groups ? launch_leg_mixed_batch(stage, g.spin, g.nj, g.ppt, g.d_args[polar], items, ni, TA, s)
                            : launch_leg_fp64_batch(stage, g.spin, g.nj, g.ppt, g.d_args[polar], items, ni, TA, s);

@@ -123,17 +123,15 @@ __device__ __forceinline__ void split6(f2 x, float s0, float (&d)[kDig]) {
 // sum over G_N - G_S.
 // ---------------------------------------------------------------------------
 template <int NJ, bool SPIN>
-__global__ void __launch_bounds__(tca::kPairs, (tca::AnaShape<NJ, SPIN>::MINB)) tc_ana(TcArgs ta) {
+__device__ __forceinline__ void tc_ana_body(const TcArgs &ta, const int4 item, unsigned char *tca_smem) {
   using S = tca::AnaShape<NJ, SPIN>;
   constexpr int NSET = S::NSET, NC = S::NC, V = S::V, kDig = tca::kDig;
-  extern __shared__ __align__(128) unsigned char tca_smem[];
   __shared__ __align__(8) uint64_t full[2], freeb[2], mine[tca::kWarps];
   __shared__ uint32_t tslot;
   __shared__ unsigned vmax[NC];
   __shared__ int tstart[tca::kWarps];
   __shared__ volatile int stop;
   const MixArgs &a = ta.m;
-  const int4 item = a.ana_items[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mi = item.x, ng = item.z & 255;
   const int m = a.mval[mi];
@@ -541,12 +539,29 @@ __global__ void __launch_bounds__(tca::kPairs, (tca::AnaShape<NJ, SPIN>::MINB)) 
 }
 
 template <int NJ, bool SPIN>
+__global__ void __launch_bounds__(tca::kPairs, (tca::AnaShape<NJ, SPIN>::MINB)) tc_ana(TcArgs ta) {
+  extern __shared__ __align__(128) unsigned char tca_smem[];
+  tc_ana_body<NJ, SPIN>(ta, ta.m.ana_items[blockIdx.x], tca_smem);
+}
+
+// batches: item (mi, first tile, slot << 8 | tiles, record); the record holds the plan's arguments
+template <int NJ, bool SPIN>
+__global__ void __launch_bounds__(tca::kPairs, (tca::AnaShape<NJ, SPIN>::MINB))
+    tc_ana_batch(const TcArgs *__restrict__ args, const int4 *__restrict__ items) {
+  extern __shared__ __align__(128) unsigned char tca_smem[];
+  const int4 it = items[blockIdx.x];
+  tc_ana_body<NJ, SPIN>(args[it.w], make_int4(it.x, it.y, it.z, 0), tca_smem);
+}
+
+template <int NJ, bool SPIN>
 static cudaError_t tca_set_smem() {
-  cudaError_t e = cudaFuncSetAttribute(tc_ana<NJ, SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tca::AnaShape<NJ, SPIN>::SMEM_LAUNCH);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc_ana<NJ, SPIN>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+  cudaError_t e = cudaSuccess;
+  for (const void *k : {(const void *)tc_ana<NJ, SPIN>, (const void *)tc_ana_batch<NJ, SPIN>}) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tca::AnaShape<NJ, SPIN>::SMEM_LAUNCH);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  }
   return e;
 }
 
@@ -561,6 +576,25 @@ cudaError_t tc_ana_prepare_device() {
 bool tc_ana_supported(int spin, int njobs_pad) {
   (void)spin;
   return njobs_pad <= 2;
+}
+
+cudaError_t launch_leg_tc_ana_batch(int spin, int nj, const void *targs, const int4 *items, int n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const TcArgs *a = static_cast<const TcArgs *>(targs);
+  if (spin == 0) {
+    switch (nj) {
+      case 1: tc_ana_batch<1, false><<<n, tca::kPairs, tca::AnaShape<1, false>::SMEM_LAUNCH, st>>>(a, items); break;
+      case 2: tc_ana_batch<2, false><<<n, tca::kPairs, tca::AnaShape<2, false>::SMEM_LAUNCH, st>>>(a, items); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (nj) {
+      case 1: tc_ana_batch<1, true><<<n, tca::kPairs, tca::AnaShape<1, true>::SMEM_LAUNCH, st>>>(a, items); break;
+      case 2: tc_ana_batch<2, true><<<n, tca::kPairs, tca::AnaShape<2, true>::SMEM_LAUNCH, st>>>(a, items); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_leg_tc_ana(const sht_plan_s *P, const void *mixargs, int n, cudaStream_t st) {

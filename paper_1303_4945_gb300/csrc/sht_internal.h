@@ -273,6 +273,8 @@ bool tc_supported(int spin, int njobs_pad);
 float tc_lambda_bound(int lmax);
 // tensor-core analysis (legendre_tc_ana.cu): mixargs with its analysis work list set
 cudaError_t launch_leg_tc_ana(const sht_plan_s *P, const void *mixargs, int n, cudaStream_t st);
+// batches: one TcArgs record per plan of a tensor-core analysis group
+cudaError_t launch_leg_tc_ana_batch(int spin, int nj, const void *targs, const int4 *items, int n, cudaStream_t st);
 cudaError_t tc_ana_prepare_device();
 bool tc_ana_supported(int spin, int njobs_pad);
 // ring FFTs

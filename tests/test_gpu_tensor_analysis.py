@@ -9,8 +9,8 @@ partial tile; Gauss-Legendre, HEALPix (aliased rings, phi0 != 0) and
 Clenshaw-Curtis grids, with and without the polar cut; the analysis and the
 adjoint synthesis; m subsets; forced FP64 columns; the no-alloc entry point;
 inputs scaled far from 1; work items that walk several tiles into one slot of
-partial sums; the Sect. 4.2 stage calls, CUDA-graph capture and a batch of such a
-plan; and the device status word after every run.
+partial sums; the Sect. 4.2 stage calls, CUDA-graph capture and a batch (bit for
+bit against the plan's own call); and the device status word after every run.
 """
 import numpy as np
 import pytest
@@ -260,11 +260,16 @@ def test_tensor_analysis_stage_calls_graph_and_batch(sht):
     torch.cuda.synchronize()
     assert plan.device_status() == 0
     check([a.cpu().numpy() for a in a_d], oracle.analysis(2, lmax, lmax, maps2, rings))
-    # a batch of that plan runs the double-float analysis: the same a_lm to 1e-11
-    batch = sht.sht_batch_create([plan])
+    # a batch of that plan (with a double-float one beside it) runs the tensor-core
+    # analysis too: the same items and arithmetic, the same bits
+    other = sht.sht_plan_create(geom, sht.sht_alm_create(lmax, lmax), 2, 1, sht.SHT_MIXED)
+    batch = sht.sht_batch_create([plan, other])
     b_d = [torch.zeros_like(a) for a in a_d]
-    sht.sht_batch_execute(batch, sht.SHT_ANALYSIS, [b_d], [m_d])
+    o_d = [torch.zeros_like(a) for a in a_d]
+    sht.sht_batch_execute(batch, sht.SHT_ANALYSIS, [b_d, o_d], [m_d, m_d])
     torch.cuda.synchronize()
+    assert plan.device_status() == 0
     for x, y in zip(b_d, a_d):
-        assert rel_l2(x.cpu().numpy(), y.cpu().numpy()) <= 1e-11
+        assert torch.equal(x, y)
+    check([x.cpu().numpy() for x in o_d], oracle.analysis(2, lmax, lmax, maps2, rings))
     del batch
