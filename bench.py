@@ -361,9 +361,9 @@ MEASURED_TRAFFIC = {
     # one launch at the headline size (spin 2, GL 4096 x 8191, lmax 4095), single-pass
     # dram__bytes_read.sum + dram__bytes_write.sum (the pair's traffic capture under profiles/);
     # sha256 over the kernel file and its headers (_kernel_digest)
-    "mixed:legendre_analysis:tc": {"bytes": 3972392448 + 2118539264,
-                                   "sha256": "a4ba9ae45c7cbca6de42ac84185752e21aa480a9b4ca012788c4285d2ef23ab0"},
-    "mixed:legendre_synthesis": {"bytes": 821292800 + 333250304,
+    "mixed:legendre_analysis:tc": {"bytes": 4001973504 + 2131988992,
+                                   "sha256": "2e50caf248f96cd559969ddffe65fc269699d1a208db803f398fb4924f05aa56"},
+    "mixed:legendre_synthesis": {"bytes": 822240512 + 333381376,
                                  "sha256": "496732199f70bc1042da624d1beee0f0a165b65442e88dd40586423658ea2a5f"},
 }
 
