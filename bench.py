@@ -362,9 +362,9 @@ MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum (the pair's traffic capture under profiles/);
     # sha256 over the kernel file and its headers (_kernel_digest)
     "mixed:legendre_analysis:tc": {"bytes": 4001973504 + 2131988992,
-                                   "sha256": "2e50caf248f96cd559969ddffe65fc269699d1a208db803f398fb4924f05aa56"},
+                                   "sha256": "8992b7456376424874dc34ab13698b6e8fdf662921ba8387a1bf6a9a3598a047"},
     "mixed:legendre_synthesis": {"bytes": 822240512 + 333381376,
-                                 "sha256": "496732199f70bc1042da624d1beee0f0a165b65442e88dd40586423658ea2a5f"},
+                                 "sha256": "27f6f176d8deecc2e9d79217b9e50f084adec901dcffa36f46880253b4aae717"},
 }
 
 

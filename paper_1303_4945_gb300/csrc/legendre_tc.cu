@@ -20,9 +20,10 @@
 //    per output column), so Lambda enters to ~2^-43 u.
 //  * B = B0 + ... + B5 with digits on the grid u_c 2^(-7-8j), u_c a power of two
 //    bounding column c of B over a window of 256 degrees: a value enters to
-//    2^-48 u_c (with five digits the truncation at 2^-40 u_c was the larger error).
+//    2^-47 u_c (the last digit's rounding and that of the low word's entry; with
+//    five digits the truncation at 2^-40 u_c was the larger error).
 //  * The products Li Bj with i + j = k are accumulated in TMEM level k (k <= 5;
-//    the dropped products are below 2^-48 of the bounds).  Every product is a
+//    the dropped products sum to below 2^-47 of the bounds).  Every product is a
 //    multiple of the level's quantum and a level's sum over one window stays
 //    below 2^24 quanta, so the FP32 accumulation is exact whatever its rounding.
 //  * After each window the six levels are read from TMEM and added in

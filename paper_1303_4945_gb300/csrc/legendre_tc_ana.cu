@@ -17,9 +17,10 @@
 //    |Lambda / u_p| < 1; the pair's factor u_p moves into its G values.
 //  * G'[c][p] = G[c][p] u_p = G0 + ... + G5 on the grid v_c 2^(-7-8j), v_c the
 //    power of two above column c's largest |G'| over the tile.
-//  * Every product Gj Li is a multiple of v_c 2^(-14-8(i+j)) below 2^14 of them;
-//    a sum over the tile's K = 128 or 256 pair entries stays below 2^24 quanta,
-//    so the FP32 accumulation is exact whatever its order.
+//  * Every product Gj Li is a multiple of v_c 2^(-14-8(i+j)); a digit is at most
+//    128 of its quanta (192 for digit 3, which takes the low word), so a sum over
+//    the tile's K = 128 or 256 pair entries stays below 256 * 192^2 < 2^24 quanta
+//    and the FP32 accumulation is exact whatever its order.
 //
 // One MMA per 16 pair entries: M = 64 rows (column c's six G digits and two zero
 // rows at rows 8c .. 8c + 7), N = 48 (the six Lambda digits of 8 degrees), so D
@@ -96,7 +97,8 @@ struct AnaShape {
 
 // six digits of x on the grid whose first quantum has the magic constant s0
 // (1.5 * 2^23 * quantum; |x| < 2^22 quanta): each a multiple of its quantum with at
-// most 8 significant bits, the low word entering after the third
+// most 8 significant bits (at most 128 quanta; 192 for d[3], after the low word
+// enters)
 __device__ __forceinline__ void split6(f2 x, float s0, float (&d)[kDig]) {
   float r = x.h;
   d[0] = tc::round_to(r, s0);
