@@ -275,9 +275,12 @@ SHT_API int sht_plan_autotune(sht_plan_t plan, void *cuda_stream, float *ms_per_
  * (12 at lmax 2047, 24 at 4095, 48 at 8191), 0 below: every ring's own error
  * stays near or below 5e-11 (spin-2 synthesis against the FP64 form, ring by
  * ring; the rings nearest the poles need the most columns), and the FP64 items
- * stay hidden beside the mixed kernels.  sht_plan_set_fp64_columns
- * changes it (any m_below >= 0; it rebuilds the work lists and may allocate a
- * P/M table of ncoef x arrays x 16 bytes); sht_plan_get_fp64_columns reads it.
+ * stay hidden beside the mixed kernels.  The plan keeps FP64 coefficients (32
+ * bytes per (m, l)) and, at spin s, a P = E+iB, M = E-iB table (16 bytes per (m,
+ * l) and array) only for the columns below the bound.  sht_plan_set_fp64_columns
+ * changes it (any m_below >= 0; it rebuilds the work lists and, for a higher
+ * bound, reallocates those tables, which synchronises the device);
+ * sht_plan_get_fp64_columns reads it.
  * Errors: SHT_ERR_INVALID_ARG (NULL, an FP64 plan, a plan in a batch,
  * m_below < 0), SHT_ERR_OOM, SHT_ERR_CUDA.
  */
